@@ -1,0 +1,215 @@
+"""The two solvers that drive the encoding operator, in FP64.
+
+Test infrastructure (see the package header).
+
+MPI-BL (sensitivity estimation): IRGN on the Maxwell-parameterised model.  At
+each outer step the penalised Gauss-Newton sub-problem of Eq. 6 is solved by CG
+on its normal equations (Theory, "Regularized Nonlinear Inversion").
+
+MPI-L (density reconstruction): the constrained problem of Eq. 8 solved by
+scaled ADMM with the splitting A = [I; F_s S_1; ...; F_s S_C], B = -I
+(Eqs. 9-11): TV prox for z_0, l2-ball projections for z_k, a CG solve for p,
+the dual update, and a residual-balancing rho (He et al. 2000; Boyd et al. 2011).
+
+Readings of what the paper leaves open (all fixed numbers are choices, not
+the paper's):
+* Eq. 6's objective is (1/2)||r - J dx||^2 + a_n||p + dp||^2 + b_n sum||alpha_k + dalpha_k||^2;
+  setting its gradient to zero gives (J^H J + 2 L_n) dx = J^H r - 2 L_n x,
+  L_n = diag(a_n I_N, b_n I_{Cq}).
+* Start p = 1, alpha = 0 (the convention of the NLINV method the section
+  builds on); a_n = a_0 d^n, b_n = b_0 d^n with a floor; step gamma = 1 (no
+  line search); the data are scaled to ||y|| = 100 and the scale is put back
+  on p at the end.
+* CG: fixed iteration count from zero; a zero curvature or residual makes the
+  step 0 instead of dividing by zero.
+* The z_0 update of Eq. 11 is printed as prox(z_0^n - (p^n + u_0^n)); with
+  A p + B z = 0 and B = -I the scaled-form update is prox(p^n + u_0^n), which is
+  what is computed.
+* R = isotropic TV with forward differences and a zero difference at the last
+  sample (Neumann), on complex images: TV(x) = sum sqrt(sum_d |D_d x|^2).  Its prox
+  is computed by n_tv iterations of FGP (Beck and Teboulle 2009) from P = 0.
+* rho: primal residual ||A p - z||; the z-block is updated first and p second,
+  so the dual residual is rho ||A (p - p_prev)|| (Boyd et al. 2011, Sec. 3.3,
+  with the roles of the two blocks exchanged);
+  if primal > mu dual then rho *= tau, u /= tau; if dual > mu primal then
+  rho /= tau, u *= tau (mu = 10, tau = 2).  ADMM starts from p = z = u = 0.
+"""
+
+import numpy as np
+
+from . import operator as op
+
+
+def _dot(a, b):
+    return np.vdot(np.ravel(a), np.ravel(b))
+
+
+def cg(apply_A, b, x0, n_iter):
+    """Plain CG for a Hermitian positive definite operator (Shewchuk 1994).
+
+    ``b`` and ``x0`` are tuples of arrays (the blocks of one vector).
+    """
+    x = [np.array(v, dtype=np.complex128, copy=True) for v in x0]
+    Ax = apply_A(x)
+    r = [bi - ai for bi, ai in zip(b, Ax)]
+    d = [ri.copy() for ri in r]
+    rr = sum(_dot(ri, ri).real for ri in r)
+    for _ in range(n_iter):
+        Ad = apply_A(d)
+        dAd = sum(_dot(di, adi).real for di, adi in zip(d, Ad))
+        a = rr / dAd if dAd > 0 else 0.0
+        x = [xi + a * di for xi, di in zip(x, d)]
+        r = [ri - a * adi for ri, adi in zip(r, Ad)]
+        rr_new = sum(_dot(ri, ri).real for ri in r)
+        beta = rr_new / rr if rr > 0 else 0.0
+        d = [ri + beta * di for ri, di in zip(r, d)]
+        rr = rr_new
+    return x
+
+
+def irgn(Fs, U, y, C, q, n_outer=20, n_cg=10, a0=1.0, b0=1.0, decay=0.5,
+         floor=1e-6, gamma=1.0, scale_target=100.0):
+    """MPI-BL: returns (p, alpha, history of ||y - G(x^n)|| in the scaled units)."""
+    y = np.asarray(y, dtype=np.complex128)
+    N = Fs.N
+    ny = np.linalg.norm(y)
+    scale = scale_target / ny if ny > 0 else 1.0
+    ys = y * scale
+    p = np.ones(N, dtype=np.complex128)
+    alpha = np.zeros((C, q), dtype=np.complex128)
+    hist = []
+    for n in range(n_outer):
+        an = max(a0 * decay ** n, floor)
+        bn = max(b0 * decay ** n, floor)
+        r = ys - op.forward(Fs, U, alpha, p)
+        hist.append(np.linalg.norm(r))
+        gp, ga = op.jacobian_adjoint(Fs, U, alpha, p, r)
+        rhs = (gp - 2.0 * an * p, ga - 2.0 * bn * alpha)
+
+        def normal(d, p=p, alpha=alpha, an=an, bn=bn):
+            jd = op.jacobian(Fs, U, alpha, p, d[0], d[1])
+            hp, ha = op.jacobian_adjoint(Fs, U, alpha, p, jd)
+            return [hp + 2.0 * an * d[0], ha + 2.0 * bn * d[1]]
+
+        dp, da = cg(normal, rhs, (np.zeros(N), np.zeros((C, q))), n_cg)
+        p = p + gamma * dp
+        alpha = alpha + gamma * da
+    hist.append(np.linalg.norm(ys - op.forward(Fs, U, alpha, p)))
+    return p / scale, alpha, np.array(hist)
+
+
+# --- TV prox (FGP) -----------------------------------------------------------
+
+def grad_fd(x):
+    """Forward differences along every axis, zero at the last sample."""
+    out = np.zeros((x.ndim,) + x.shape, dtype=np.complex128)
+    for ax in range(x.ndim):
+        sl_hi = [slice(None)] * x.ndim
+        sl_lo = [slice(None)] * x.ndim
+        sl_hi[ax] = slice(1, None)
+        sl_lo[ax] = slice(0, -1)
+        out[(ax,) + tuple(sl_lo)] = x[tuple(sl_hi)] - x[tuple(sl_lo)]
+    return out
+
+
+def grad_fd_adj(P):
+    """Adjoint of ``grad_fd`` (minus the discrete divergence)."""
+    nd = P.shape[0]
+    x = np.zeros(P.shape[1:], dtype=np.complex128)
+    for ax in range(nd):
+        sl_hi = [slice(None)] * nd
+        sl_lo = [slice(None)] * nd
+        sl_hi[ax] = slice(1, None)
+        sl_lo[ax] = slice(0, -1)
+        d = P[ax][tuple(sl_lo)]
+        x[tuple(sl_hi)] += d
+        x[tuple(sl_lo)] -= d
+    return x
+
+
+def tv(x):
+    g = grad_fd(x)
+    return float(np.sum(np.sqrt(np.sum(np.abs(g) ** 2, axis=0))))
+
+
+def tv_prox(v, lam, shape, n_iter):
+    """argmin_x (1/2)||x - v||^2 + lam TV(x) by n_iter FGP iterations."""
+    b = np.asarray(v, dtype=np.complex128).reshape(shape)
+    if lam <= 0:
+        return b.ravel().copy()
+    nd = len(shape)
+    L = 4.0 * nd  # ||grad_fd||^2 <= 4 * ndim
+    P = np.zeros((nd,) + tuple(shape), dtype=np.complex128)
+    R = P.copy()
+    t = 1.0
+    for _ in range(n_iter):
+        x = b - lam * grad_fd_adj(R)
+        Pn = R + grad_fd(x) / (L * lam)
+        mag = np.sqrt(np.sum(np.abs(Pn) ** 2, axis=0))
+        Pn = Pn / np.maximum(1.0, mag)[None]
+        tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        R = Pn + ((t - 1.0) / tn) * (Pn - P)
+        P, t = Pn, tn
+    return (b - lam * grad_fd_adj(P)).ravel()
+
+
+def project_ball(z, y, eps):
+    """Pi_{C(y, eps)}(z) = y + eps (z - y) / max(||z - y||, eps), per coil row."""
+    d = z - y
+    nrm = np.linalg.norm(d, axis=-1)
+    return y + (eps / np.maximum(nrm, eps))[:, None] * d
+
+
+def admm_tv(Fs, s, y, eps, shape, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0, tau=2.0):
+    """MPI-L: returns (p, history of (primal, dual, rho))."""
+    s = np.asarray(s, dtype=np.complex128)
+    y = np.asarray(y, dtype=np.complex128)
+    eps = np.asarray(eps, dtype=np.float64)
+    N = Fs.N
+    C = s.shape[0]
+    M = y.shape[1]
+    p = np.zeros(N, dtype=np.complex128)
+    u0 = np.zeros(N, dtype=np.complex128)
+    uk = np.zeros((C, M), dtype=np.complex128)
+    rho = rho0
+
+    def AH(w0, wk):
+        return w0 + np.sum(s.conj() * Fs.adj(wk), axis=0)
+
+    def normal(v):
+        return [v[0] + np.sum(s.conj() * Fs.adj(Fs.fwd(s * v[0][None, :])), axis=0)]
+
+    hist = []
+    Apk = np.zeros((C, M), dtype=np.complex128)
+    for _ in range(n_outer):
+        z0n = tv_prox(p + u0, 1.0 / rho, shape, n_tv)
+        zkn = project_ball(Apk + uk, y, eps)
+        rhs = AH(z0n - u0, zkn - uk)
+        p_prev, Apk_prev = p, Apk
+        (p,) = cg(normal, (rhs,), (p,), n_cg)
+        Apk = Fs.fwd(s * p[None, :])
+        u0 = u0 + p - z0n
+        uk = uk + Apk - zkn
+        r_norm = np.sqrt(np.linalg.norm(p - z0n) ** 2 + np.linalg.norm(Apk - zkn) ** 2)
+        s_norm = rho * np.sqrt(np.linalg.norm(p - p_prev) ** 2 + np.linalg.norm(Apk - Apk_prev) ** 2)
+        hist.append((r_norm, s_norm, rho))
+        if r_norm > mu * s_norm:
+            rho *= tau
+            u0 = u0 / tau
+            uk = uk / tau
+        elif s_norm > mu * r_norm:
+            rho /= tau
+            u0 = u0 * tau
+            uk = uk * tau
+    return p, np.array(hist)
+
+
+def project_onto_basis(U, S):
+    """alpha_k = (U^H U)^{-1} U^H s_k via a Cholesky factor of the Gram matrix
+    (the projection in the Fig. 2 caption).  S is (C, N); returns (C, q)."""
+    U = np.asarray(U, dtype=np.complex128)
+    G = U.conj().T @ U
+    L = np.linalg.cholesky(G)
+    rhs = U.conj().T @ np.asarray(S, dtype=np.complex128).T  # (q, C)
+    w = np.linalg.solve(L, rhs)
+    return np.linalg.solve(L.conj().T, w).T

@@ -1,0 +1,204 @@
+/*
+ * mpi_gb300.h -- C ABI of the GB300 (sm_103a) Maxwell Parallel Imaging encoding operator.
+ *
+ * Operator (Theory, "Regularized Nonlinear Inversion", Eq. 5):
+ *   G(p, alpha_1..alpha_C) = [ F_s( (U alpha_k) (.) p ) ]_{k=1..C}
+ * with p in C^N the image, U in C^{N x q} the Maxwell basis, alpha_k in C^q the
+ * coefficients of coil k, (.) the element-wise product and F_s in C^{M x N} the
+ * undersampled Fourier operator of one coil (Eq. 1: F = I_C (x) F_s).
+ *
+ * Conventions shared by every call
+ *   - complex numbers are interleaved float pairs (mpi_c32, 8 bytes);
+ *   - arrays are C order: p [N] raster (x fastest, then y, then z), alpha [C][q],
+ *     maps [C][N], k-space data y [C][M];
+ *   - F_s is the centred unitary DFT (forward sign e^{-i}, index origin at n/2 on
+ *     every axis, scale N^{-1/2}) followed by selection of the sampled points;
+ *     for radial sampling it is the Kaiser-Bessel gridding NUFFT of the same
+ *     non-uniform DFT;
+ *   - pointers named in "device" are caller-owned device memory; the library never
+ *     frees them, never keeps them after the call returns, overwrites outputs
+ *     (never accumulates) and enqueues all work on the context's stream without
+ *     synchronising (results are ready when that stream is);
+ *   - every call checks its arguments before launching anything and returns
+ *     MPI_ERR_ARG / MPI_ERR_SHAPE without side effects on a bad argument;
+ *     CUDA failures return MPI_ERR_CUDA; mpi_last_error() gives the text;
+ *   - a context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef MPI_GB300_H
+#define MPI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float x, y; } mpi_c32;
+
+typedef enum {
+  MPI_OK = 0,
+  MPI_ERR_ARG = 1,
+  MPI_ERR_SHAPE = 2,
+  MPI_ERR_CUDA = 3,
+  MPI_ERR_OOM = 4,
+  MPI_ERR_NOT_CONVERGED = 5,
+  MPI_ERR_TIMEOUT = 6,
+  MPI_ERR_UNSUPPORTED = 7
+} mpi_status;
+
+typedef enum { MPI_TRAJ_CARTESIAN = 0, MPI_TRAJ_RADIAL = 1 } mpi_traj_kind;
+
+/* Arithmetic of the basis expansion U alpha (the only dense contraction).
+ * FP32: CUDA-core FFMA, FP32 in and out.  BF16: tensor cores, BF16 basis and
+ * coefficients, FP32 accumulation.  FFT, gridding and reductions are FP32 in
+ * both. */
+typedef enum { MPI_PREC_FP32 = 0, MPI_PREC_BF16 = 1 } mpi_precision;
+
+typedef struct mpi_ctx mpi_ctx;
+typedef struct mpi_plan mpi_plan;
+typedef struct mpi_basis mpi_basis;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  The context owns a growable
+ * device workspace (scratch between kernel passes); it grows on a call that
+ * needs more, which synchronises the stream once -- call mpi_ctx_reserve first
+ * to size it up front. */
+mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_stream);
+mpi_status mpi_ctx_destroy(mpi_ctx* ctx);
+mpi_status mpi_ctx_set_stream(mpi_ctx* ctx, void* cuda_stream);
+mpi_status mpi_ctx_synchronize(mpi_ctx* ctx);
+/* Size the workspace for operator calls with `C` coils on this plan and basis. */
+mpi_status mpi_ctx_reserve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C);
+/* Text of the last error on this context (static storage inside ctx; never NULL). */
+const char* mpi_last_error(const mpi_ctx* ctx);
+/* Number of kernels this context has launched since creation (for accounting). */
+int64_t mpi_ctx_launch_count(const mpi_ctx* ctx);
+
+/* ------------------------------------------------------------------- plan */
+
+/* Geometry and sampling of F_s (Eq. 1).  Host pointers; the plan copies them.
+ *   ndim        2 or 3
+ *   dims        (nz, ny, nx); nz = 1 when ndim = 2.  Cartesian FFT axes must have
+ *               lengths in {16, 32, 48, 64, 96, 128, 192, 256, 320, 512}
+ *   kind        MPI_TRAJ_CARTESIAN or MPI_TRAJ_RADIAL (2D square only)
+ *   M           samples per coil (M >= 0; M = 0 gives empty k-space)
+ *   sample_idx  Cartesian: M strictly increasing flat indices into the centred
+ *               k-space grid (raster order, same layout as the image);
+ *               checked: sorted, unique, in [0, N) -- else MPI_ERR_ARG
+ *   traj        radial: M x 2 floats (kx, ky) in radians per pixel, [-pi, pi)
+ *   kb_width    radial: Kaiser-Bessel width W (2..8)
+ *   oversamp    radial: grid oversampling sigma (grid = sigma * n, must be a
+ *               supported FFT length) */
+typedef struct {
+  int ndim;
+  int dims[3];
+  int kind;
+  int M;
+  const int32_t* sample_idx;
+  const float* traj;
+  int kb_width;
+  float oversamp;
+} mpi_plan_desc;
+
+mpi_status mpi_plan_create(mpi_ctx* ctx, const mpi_plan_desc* desc, mpi_plan** out);
+mpi_status mpi_plan_destroy(mpi_plan* plan);
+/* Radial plans: the first grid tap of every sample and axis, int32 [M][2]
+ * (x, y), array index in [0, G): floor(k G / 2 pi) - W/2 + 1 + G/2 taken in FP64,
+ * wrapped mod G (device pointer out). */
+mpi_status mpi_plan_grid_index(mpi_ctx* ctx, const mpi_plan* plan, int32_t* out_dev);
+
+/* ------------------------------------------------------------------ basis */
+
+/* Dense basis U in C^{N x q} (Maxwell Regularization section: s_k ~ U alpha_k),
+ * given column-major as [q][N] (basis vector j contiguous).  `U` is a host
+ * pointer when on_device = 0, else a device pointer.  The basis keeps its own
+ * copies (FP32, and a BF16 copy for MPI_PREC_BF16). */
+mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N, int q, int on_device,
+                                mpi_basis** out);
+mpi_status mpi_basis_destroy(mpi_basis* basis);
+
+/* ------------------------------------------------------- operator (device) */
+
+/* maps[k] = U alpha_k for k < C (Eq. 5 inside F_s(.)).  alpha [C][q], maps [C][N]. */
+mpi_status mpi_basis_expand(mpi_ctx* ctx, const mpi_basis* basis, const mpi_c32* alpha, int C,
+                            mpi_c32* maps, mpi_precision prec);
+
+/* y = G(p, alpha) (Eq. 5).  alpha [C][q], p [N], y [C][M]. */
+mpi_status mpi_forward(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                       const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y,
+                       mpi_precision prec);
+
+/* p_out = S^H F^H y = sum_k conj(U alpha_k) (.) F_s^H y_k (adjoint of Eq. 1 in p).
+ * y [C][M], p_out [N]. */
+mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                       const mpi_c32* alpha, int C, const mpi_c32* y, mpi_c32* p_out,
+                       mpi_precision prec);
+
+/* dy = J(p, alpha)[dp; dalpha] = [F_s(U alpha_k (.) dp + p (.) U dalpha_k)]_k (Eq. 7). */
+mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                        const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* dp,
+                        const mpi_c32* dalpha, mpi_c32* dy, mpi_precision prec);
+
+/* [dp; dalpha] = J^H(p, alpha) r (the display after Eq. 7; ^H on a vector inside
+ * (.) is the element-wise conjugate):
+ *   dp        = sum_k conj(U alpha_k) (.) F_s^H r_k            [N]
+ *   dalpha_k  = U^H (conj(p) (.) F_s^H r_k)                     [C][q]
+ * Coil maps are recomputed from alpha, never stored. */
+mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* r,
+                                mpi_c32* dp, mpi_c32* dalpha, mpi_precision prec);
+
+/* alpha_k = (U^H U)^{-1} U^H maps_k: projection of given maps onto the basis
+ * (Fig. 2 caption).  Gram matrix, Cholesky factor and triangular solves in FP64.
+ * maps [C][N] -> alpha [C][q]. */
+mpi_status mpi_basis_project(mpi_ctx* ctx, const mpi_basis* basis, const mpi_c32* maps, int C,
+                             mpi_c32* alpha);
+
+/* ----------------------------------------------------------------- solvers */
+
+/* MPI-BL: IRGN for (p, alpha) (Eq. 6) with CG on the normal equations
+ *   (J^H J + 2 diag(a_n I, b_n I)) dx = J^H r - 2 diag(a_n I, b_n I) x,
+ * r = y_s - G(x), y_s = y * (scale_target / ||y||), a_n = max(a0 d^n, floor),
+ * b_n = max(b0 d^n, floor), x <- x + gamma dx, start p = 1, alpha = 0.
+ * Outputs: alpha_out [C][q]; p_out [N] divided by the data scale;
+ * resid_out (host, may be NULL) [n_outer + 1] residual norms in scaled units. */
+typedef struct {
+  int n_outer, n_cg;
+  double a0, b0, decay, floor_, gamma, scale_target;
+} mpi_irgn_params;
+
+mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                           const mpi_c32* y, int C, const mpi_irgn_params* prm,
+                           mpi_c32* alpha_out, mpi_c32* p_out, double* resid_out,
+                           mpi_precision prec);
+
+/* MPI-L: constrained TV reconstruction (Eq. 8) by scaled ADMM (Eq. 11):
+ *   z0 = prox_{TV/rho}(p + u0)        (n_tv FGP iterations from zero)
+ *   zk = Pi_{C(y_k, eps_k)}(F_s S_k p + u_k)
+ *   p  = (I + sum S_k^H F_s^H F_s S_k)^{-1}(z0 - u0 + sum S_k^H F_s^H (zk - u_k))
+ *        (n_cg CG iterations from the previous p)
+ *   u  = u + A p - z ; residual-balancing rho (mu, tau).
+ * Start p = z = u = 0.  eps: host [C] (FP64).  hist_out (host, may be NULL)
+ * [n_outer][3] (primal, dual, rho). */
+typedef struct {
+  int n_outer, n_cg, n_tv;
+  double rho0, mu, tau;
+} mpi_admm_params;
+
+mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                           const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
+                           const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out,
+                           mpi_precision prec);
+
+/* TV prox alone: x = argmin (1/2)||x - v||^2 + lam TV(x) by n_iter FGP
+ * iterations (the z0 update of Eq. 11).  v, x device [N] on the plan's grid. */
+mpi_status mpi_tv_prox(mpi_ctx* ctx, const mpi_plan* plan, const mpi_c32* v, double lam,
+                       int n_iter, mpi_c32* x);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPI_GB300_H */

@@ -1,0 +1,22 @@
+"""GB300-native (sm_103a) Maxwell Parallel Imaging encoding operator.
+
+The operator G(p, alpha) = [F_s(U alpha_k (.) p)]_k, its adjoint, Jacobian and
+Jacobian-adjoint, and the two solvers built on them, all run in the CUDA
+kernels of ``libmpi_gb300.so`` behind the C ABI declared in
+``include/mpi_gb300.h``.  This package only marshals arguments.
+"""
+
+from ._lib import MpiError, load  # noqa: F401
+from .api import (  # noqa: F401
+    Basis,
+    Context,
+    MPIOperator,
+    Plan,
+    adjoint,
+    basis_expand,
+    basis_project,
+    forward,
+    jacobian,
+    jacobian_adjoint,
+    mpi_operator,
+)

@@ -1,0 +1,234 @@
+"""Python face of the C ABI: contexts, plans, bases and the operator calls.
+
+Tensors are torch complex64 CUDA tensors (contiguous); the calls pass their
+device pointers and the current torch stream to the library, which does all
+the work in its own kernels.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PREC, check, load
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _need(t, shape, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous complex64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+class Context:
+    """A library context bound to a CUDA device and stream."""
+
+    def __init__(self, device=0, stream=None):
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self.lib.mpi_ctx_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        check(None, st)
+        self.h = h
+
+    def set_stream(self, stream):
+        self.stream = stream
+        check(self.h, self.lib.mpi_ctx_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def synchronize(self):
+        check(self.h, self.lib.mpi_ctx_synchronize(self.h))
+
+    def launches(self):
+        return int(self.lib.mpi_ctx_launch_count(self.h))
+
+    def reserve(self, plan, basis, C):
+        check(self.h, self.lib.mpi_ctx_reserve(self.h, plan.h, basis.h, C))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpi_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Geometry and sampling of F_s."""
+
+    def __init__(self, ctx, dims, sample_idx=None, traj=None, kb_width=6, oversamp=2.0):
+        self.ctx = ctx
+        dims = tuple(int(d) for d in dims)
+        if len(dims) == 2:
+            self.ndim, full = 2, (1,) + dims
+        elif len(dims) == 3:
+            self.ndim, full = 3, dims
+        else:
+            raise ValueError("dims must have 2 or 3 entries")
+        self.dims = dims
+        self.N = int(np.prod(dims))
+        d = _lib.PlanDesc()
+        d.ndim = self.ndim
+        d.dims[0], d.dims[1], d.dims[2] = full
+        keep = []
+        if traj is None:
+            idx = np.ascontiguousarray(np.asarray(sample_idx, dtype=np.int32))
+            keep.append(idx)
+            d.kind = _lib.TRAJ_CARTESIAN
+            d.M = int(idx.size)
+            d.sample_idx = idx.ctypes.data if idx.size else None
+            self.kind = "cartesian"
+        else:
+            k = np.ascontiguousarray(np.asarray(traj, dtype=np.float32).reshape(-1, 2))
+            keep.append(k)
+            d.kind = _lib.TRAJ_RADIAL
+            d.M = int(k.shape[0])
+            d.traj = k.ctypes.data if k.size else None
+            d.kb_width = int(kb_width)
+            d.oversamp = float(oversamp)
+            self.kind = "radial"
+        self.M = int(d.M)
+        h = ctypes.c_void_p()
+        check(ctx.h, ctx.lib.mpi_plan_create(ctx.h, ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+
+    def grid_index(self):
+        out = torch.empty((self.M, 2), dtype=torch.int32, device=f"cuda:{self.ctx.device}")
+        check(self.ctx.h, self.ctx.lib.mpi_plan_grid_index(self.ctx.h, self.h, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.mpi_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Basis:
+    """Dense basis U (N x q) held by the library as [q][N] complex64."""
+
+    def __init__(self, ctx, U_qN):
+        self.ctx = ctx
+        if isinstance(U_qN, torch.Tensor):
+            t = U_qN.to(device=f"cuda:{ctx.device}", dtype=torch.complex64).contiguous()
+        else:
+            t = torch.from_numpy(np.ascontiguousarray(np.asarray(U_qN, dtype=np.complex64))).to(
+                f"cuda:{ctx.device}")
+        q, N = t.shape
+        self.q, self.N = int(q), int(N)
+        h = ctypes.c_void_p()
+        check(ctx.h, ctx.lib.mpi_basis_load_dense(ctx.h, _ptr(t), self.N, self.q, 1, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.mpi_basis_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def basis_expand(ctx, basis, alpha, prec="fp32", out=None):
+    C = alpha.shape[0]
+    _need(alpha, (C, basis.q), "alpha")
+    out = out if out is not None else torch.empty((C, basis.N), dtype=torch.complex64, device=alpha.device)
+    check(ctx.h, ctx.lib.mpi_basis_expand(ctx.h, basis.h, _ptr(alpha), C, _ptr(out), PREC[prec]))
+    return out
+
+
+def forward(ctx, plan, basis, alpha, p, prec="fp32", out=None):
+    C = alpha.shape[0]
+    _need(alpha, (C, basis.q), "alpha")
+    _need(p, (plan.N,), "p")
+    out = out if out is not None else torch.empty((C, plan.M), dtype=torch.complex64, device=p.device)
+    check(ctx.h, ctx.lib.mpi_forward(ctx.h, plan.h, basis.h, _ptr(alpha), C, _ptr(p), _ptr(out), PREC[prec]))
+    return out
+
+
+def adjoint(ctx, plan, basis, alpha, y, prec="fp32", out=None):
+    C = alpha.shape[0]
+    _need(alpha, (C, basis.q), "alpha")
+    _need(y, (C, plan.M), "y")
+    out = out if out is not None else torch.empty((plan.N,), dtype=torch.complex64, device=y.device)
+    check(ctx.h, ctx.lib.mpi_adjoint(ctx.h, plan.h, basis.h, _ptr(alpha), C, _ptr(y), _ptr(out), PREC[prec]))
+    return out
+
+
+def jacobian(ctx, plan, basis, alpha, p, dp, dalpha, prec="fp32", out=None):
+    C = alpha.shape[0]
+    for t, s, n in ((alpha, (C, basis.q), "alpha"), (dalpha, (C, basis.q), "dalpha"),
+                    (p, (plan.N,), "p"), (dp, (plan.N,), "dp")):
+        _need(t, s, n)
+    out = out if out is not None else torch.empty((C, plan.M), dtype=torch.complex64, device=p.device)
+    check(ctx.h, ctx.lib.mpi_jacobian(ctx.h, plan.h, basis.h, _ptr(alpha), C, _ptr(p), _ptr(dp), _ptr(dalpha),
+                                      _ptr(out), PREC[prec]))
+    return out
+
+
+def jacobian_adjoint(ctx, plan, basis, alpha, p, r, prec="fp32", out_p=None, out_alpha=None):
+    C = alpha.shape[0]
+    _need(alpha, (C, basis.q), "alpha")
+    _need(p, (plan.N,), "p")
+    _need(r, (C, plan.M), "r")
+    out_p = out_p if out_p is not None else torch.empty((plan.N,), dtype=torch.complex64, device=p.device)
+    out_alpha = out_alpha if out_alpha is not None else torch.empty((C, basis.q), dtype=torch.complex64,
+                                                                    device=p.device)
+    check(ctx.h, ctx.lib.mpi_jacobian_adjoint(ctx.h, plan.h, basis.h, _ptr(alpha), C, _ptr(p), _ptr(r),
+                                              _ptr(out_p), _ptr(out_alpha), PREC[prec]))
+    return out_p, out_alpha
+
+
+def basis_project(ctx, basis, maps):
+    C = maps.shape[0]
+    _need(maps, (C, basis.N), "maps")
+    out = torch.empty((C, basis.q), dtype=torch.complex64, device=maps.device)
+    check(ctx.h, ctx.lib.mpi_basis_project(ctx.h, basis.h, _ptr(maps), C, _ptr(out)))
+    return out
+
+
+class MPIOperator(torch.autograd.Function):
+    """y = G(p, alpha) with a backward that calls the library's J^H kernel.
+
+    G is complex-bilinear (no conjugates), so the vector-Jacobian product torch
+    asks for is J^H applied to the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(fctx, p, alpha, ctx, plan, basis, prec):
+        fctx.save_for_backward(p, alpha)
+        fctx.lib_ctx, fctx.plan, fctx.basis, fctx.prec = ctx, plan, basis, prec
+        return forward(ctx, plan, basis, alpha.contiguous(), p.contiguous(), prec)
+
+    @staticmethod
+    def backward(fctx, gy):
+        p, alpha = fctx.saved_tensors
+        gp, ga = jacobian_adjoint(fctx.lib_ctx, fctx.plan, fctx.basis, alpha.contiguous(), p.contiguous(),
+                                  gy.contiguous(), fctx.prec)
+        return gp, ga, None, None, None, None
+
+
+def mpi_operator(p, alpha, ctx, plan, basis, prec="fp32"):
+    return MPIOperator.apply(p, alpha, ctx, plan, basis, prec)

@@ -1,0 +1,476 @@
+// C ABI entry points: argument checks, workspace, and the order of kernel
+// passes for each operator (Theory section, Eqs. 1, 5, 7 and the
+// Jacobian-adjoint display after Eq. 7).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mpi_internal.h"
+
+// ------------------------------------------------------------------ helpers
+
+mpi_status set_err(mpi_ctx* ctx, mpi_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+mpi_status cuda_check(mpi_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MPI_OK;
+  return set_err(ctx, MPI_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool fft_length_supported(int n) {
+  for (int i = 0; i < kNumFftLengths; ++i)
+    if (kFftLengths[i] == n) return true;
+  return false;
+}
+
+const float2* twiddle_table(const mpi_ctx* ctx, int n) {
+  for (int i = 0; i < kNumFftLengths; ++i)
+    if (kFftLengths[i] == n) return ctx->twiddles + ctx->tw_offset[i];
+  return nullptr;
+}
+
+mpi_status ensure_work(mpi_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->work_bytes) return MPI_OK;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "workspace sync");
+  if (ctx->work) cudaFree(ctx->work);
+  ctx->work = nullptr;
+  ctx->work_bytes = 0;
+  const size_t want = std::max(bytes, (size_t)1 << 20);
+  e = cudaMalloc(&ctx->work, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, MPI_ERR_OOM, "workspace allocation failed");
+  }
+  ctx->work_bytes = want;
+  return MPI_OK;
+}
+
+namespace {
+
+struct DeviceGuard {
+  explicit DeviceGuard(int dev) { cudaSetDevice(dev); }
+};
+
+bool bad_ptr(const void* p) { return p == nullptr; }
+
+size_t op_work_bytes(const mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C) {
+  const size_t cn = (size_t)C * plan->N;
+  size_t grid = 0;
+  if (plan->kind == MPI_TRAJ_RADIAL) grid = (size_t)C * plan->G * plan->G;
+  size_t partial = basis ? uh_v_partial_elems(ctx, basis->N, basis->q, C) : 0;
+  return (2 * cn + grid + partial) * sizeof(float2) + 4096;
+}
+
+mpi_status check_op(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C,
+                    mpi_precision prec) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!plan || !basis) return set_err(ctx, MPI_ERR_ARG, "null plan or basis");
+  if (plan->ctx != ctx || basis->ctx != ctx) return set_err(ctx, MPI_ERR_ARG, "plan/basis from another context");
+  if (C < 1) return set_err(ctx, MPI_ERR_ARG, "C must be >= 1");
+  if (basis->N != plan->N) return set_err(ctx, MPI_ERR_SHAPE, "basis N differs from plan N");
+  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return set_err(ctx, MPI_ERR_ARG, "bad precision");
+  if (prec == MPI_PREC_BF16) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion not built");
+  return MPI_OK;
+}
+
+ExpandArgs base_args(const mpi_plan* plan, const mpi_basis* basis, int C) {
+  ExpandArgs a;
+  a.U = basis->U;
+  a.N = basis->N;
+  a.q = basis->q;
+  a.nx = plan->nx;
+  a.ny = plan->ny;
+  a.C = C;
+  if (plan->kind == MPI_TRAJ_CARTESIAN) {
+    a.centre = 1;
+    a.scale = 1.0f / sqrtf((float)plan->N);
+  } else {
+    a.centre = 0;  // the NUFFT passes handle centring and scale themselves
+    a.scale = 1.0f;
+  }
+  return a;
+}
+
+// k-space -> image-side grid (inverse FFT passes) into `w` [C][N].
+mpi_status kspace_to_image(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C, float2* w,
+                           float2* grid) {
+  if (plan->kind == MPI_TRAJ_RADIAL) return nufft_adjoint(ctx, plan, y, C, w, grid);
+  mpi_status st = launch_rows_scatter_inv(ctx, plan, y, C, w);
+  if (st) return st;
+  st = launch_fft_cols(ctx, w, C, plan->nz, plan->ny, plan->nx, true);
+  if (st) return st;
+  if (plan->ndim == 3) st = launch_fft_z(ctx, w, C, plan->nz, plan->ny, plan->nx, true);
+  return st;
+}
+
+// image-side grid `v` [C][N] (already multiplied by sign and scale) -> k-space y.
+mpi_status image_to_kspace(mpi_ctx* ctx, const mpi_plan* plan, float2* v, int C, float2* y,
+                           float2* grid) {
+  if (plan->kind == MPI_TRAJ_RADIAL) return nufft_forward(ctx, plan, v, C, y, grid);
+  mpi_status st = MPI_OK;
+  if (plan->ndim == 3) st = launch_fft_z(ctx, v, C, plan->nz, plan->ny, plan->nx, false);
+  if (st) return st;
+  st = launch_fft_cols(ctx, v, C, plan->nz, plan->ny, plan->nx, false);
+  if (st) return st;
+  return launch_rows_fwd_gather(ctx, plan, v, C, y);
+}
+
+struct Work {
+  float2* A;
+  float2* B;
+  float2* grid;
+  float2* partials;
+  size_t partial_cap;
+};
+
+mpi_status carve_work(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C, Work* w) {
+  mpi_status st = ensure_work(ctx, op_work_bytes(ctx, plan, basis, C));
+  if (st) return st;
+  const size_t cn = (size_t)C * plan->N;
+  float2* base = (float2*)ctx->work;
+  w->A = base;
+  w->B = base + cn;
+  size_t grid = plan->kind == MPI_TRAJ_RADIAL ? (size_t)C * plan->G * plan->G : 0;
+  w->grid = base + 2 * cn;
+  w->partials = base + 2 * cn + grid;
+  w->partial_cap = uh_v_partial_elems(ctx, basis->N, basis->q, C);
+  return MPI_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+
+extern "C" mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_stream) {
+  if (!out) return MPI_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MPI_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return MPI_ERR_CUDA;
+  mpi_ctx* ctx = new mpi_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  // twiddle tables exp(-2 pi i m / n) for every supported length, from FP64
+  std::vector<float2> host;
+  for (int i = 0; i < kNumFftLengths; ++i) {
+    const int n = kFftLengths[i];
+    ctx->tw_offset[i] = (int)host.size();
+    for (int m = 0; m < n; ++m) {
+      const double ang = -2.0 * M_PI * (double)m / (double)n;
+      host.push_back(make_float2((float)cos(ang), (float)sin(ang)));
+    }
+  }
+  cudaError_t e = cudaMalloc(&ctx->twiddles, host.size() * sizeof(float2));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->twiddles, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->twiddles) cudaFree(ctx->twiddles);
+    delete ctx;
+    return MPI_ERR_CUDA;
+  }
+  *out = ctx;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_ctx_destroy(mpi_ctx* ctx) {
+  if (!ctx) return MPI_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->work) cudaFree(ctx->work);
+  if (ctx->twiddles) cudaFree(ctx->twiddles);
+  delete ctx;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_ctx_set_stream(mpi_ctx* ctx, void* stream) {
+  if (!ctx) return MPI_ERR_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_ctx_synchronize(mpi_ctx* ctx) {
+  if (!ctx) return MPI_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize");
+}
+
+extern "C" mpi_status mpi_ctx_reserve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!plan || !basis || C < 1) return set_err(ctx, MPI_ERR_ARG, "reserve: bad arguments");
+  DeviceGuard g(ctx->device);
+  // operators plus the solver state (IRGN/ADMM vectors)
+  size_t extra = ((size_t)12 * plan->N + (size_t)8 * C * std::max(plan->M, 1) +
+                  (size_t)8 * C * basis->q + 1024) * sizeof(float2);
+  return ensure_work(ctx, op_work_bytes(ctx, plan, basis, C) + extra);
+}
+
+extern "C" const char* mpi_last_error(const mpi_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+extern "C" int64_t mpi_ctx_launch_count(const mpi_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+// ------------------------------------------------------------------- plan
+
+extern "C" mpi_status mpi_plan_create(mpi_ctx* ctx, const mpi_plan_desc* d, mpi_plan** out) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!d || !out) return set_err(ctx, MPI_ERR_ARG, "null plan descriptor or output");
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  if (d->ndim != 2 && d->ndim != 3) return set_err(ctx, MPI_ERR_SHAPE, "ndim must be 2 or 3");
+  const int nz = d->ndim == 3 ? d->dims[0] : 1, ny = d->dims[1], nx = d->dims[2];
+  if (nz < 1 || ny < 1 || nx < 1) return set_err(ctx, MPI_ERR_SHAPE, "non-positive dimension");
+  const long long Nll = (long long)nz * ny * nx;
+  if (Nll > (1LL << 31) - 1) return set_err(ctx, MPI_ERR_SHAPE, "grid too large");
+  if (d->M < 0) return set_err(ctx, MPI_ERR_ARG, "M < 0");
+  mpi_plan* plan = new mpi_plan();
+  plan->ctx = ctx;
+  plan->ndim = d->ndim;
+  plan->nz = nz;
+  plan->ny = ny;
+  plan->nx = nx;
+  plan->N = (int)Nll;
+  plan->kind = d->kind;
+  plan->M = d->M;
+  mpi_status st = MPI_OK;
+  if (d->kind == MPI_TRAJ_CARTESIAN) {
+    if (!fft_length_supported(nx) || !fft_length_supported(ny) || (d->ndim == 3 && !fft_length_supported(nz))) {
+      delete plan;
+      return set_err(ctx, MPI_ERR_SHAPE, "unsupported Cartesian FFT length");
+    }
+    if (d->M > 0 && !d->sample_idx) {
+      delete plan;
+      return set_err(ctx, MPI_ERR_ARG, "null sample_idx");
+    }
+    for (int m = 0; m < d->M; ++m) {
+      const int32_t v = d->sample_idx[m];
+      if (v < 0 || v >= plan->N || (m > 0 && v <= d->sample_idx[m - 1])) {
+        delete plan;
+        return set_err(ctx, MPI_ERR_ARG, "sample_idx must be strictly increasing and in [0, N)");
+      }
+    }
+    plan->n_rows = nz * ny;
+    std::vector<int32_t> row_ptr(plan->n_rows + 1, 0);
+    int m = 0;
+    for (int r = 0; r < plan->n_rows; ++r) {
+      row_ptr[r] = m;
+      const long long end = (long long)(r + 1) * nx;
+      while (m < d->M && d->sample_idx[m] < end) ++m;
+    }
+    row_ptr[plan->n_rows] = m;
+    cudaError_t e = cudaMalloc(&plan->row_ptr, row_ptr.size() * sizeof(int32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(plan->row_ptr, row_ptr.data(), row_ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && d->M > 0) {
+      e = cudaMalloc(&plan->idx, (size_t)d->M * sizeof(int32_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(plan->idx, d->sample_idx, (size_t)d->M * sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) st = cuda_check(ctx, e, "plan upload");
+  } else if (d->kind == MPI_TRAJ_RADIAL) {
+    if (d->ndim != 2 || nx != ny) {
+      delete plan;
+      return set_err(ctx, MPI_ERR_SHAPE, "radial plans are 2D square");
+    }
+    if (d->M > 0 && !d->traj) {
+      delete plan;
+      return set_err(ctx, MPI_ERR_ARG, "null trajectory");
+    }
+    if (d->kb_width < 2 || d->kb_width > 8) {
+      delete plan;
+      return set_err(ctx, MPI_ERR_ARG, "kb_width must be in [2, 8]");
+    }
+    plan->W = d->kb_width;
+    plan->G = (int)lround((double)d->oversamp * nx);
+    if (!fft_length_supported(plan->G) || plan->G < nx || (plan->G - nx) % 2) {
+      delete plan;
+      return set_err(ctx, MPI_ERR_SHAPE, "unsupported oversampled grid size");
+    }
+    for (int m = 0; m < 2 * d->M; ++m) {
+      const float v = d->traj[m];
+      if (!(v >= -3.14159274f && v <= 3.14159274f)) {
+        delete plan;
+        return set_err(ctx, MPI_ERR_ARG, "trajectory outside [-pi, pi]");
+      }
+    }
+    st = nufft_plan_init(ctx, plan, d->traj);
+  } else {
+    delete plan;
+    return set_err(ctx, MPI_ERR_ARG, "unknown trajectory kind");
+  }
+  if (st != MPI_OK) {
+    mpi_plan_destroy(plan);
+    return st;
+  }
+  *out = plan;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
+  if (!plan) return MPI_ERR_ARG;
+  DeviceGuard g(plan->ctx->device);
+  cudaStreamSynchronize(plan->ctx->stream);
+  void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw,
+                  plan->deap, plan->bin_ptr, plan->bin_perm};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete plan;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_plan_grid_index(mpi_ctx* ctx, const mpi_plan* plan, int32_t* out_dev) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!plan || bad_ptr(out_dev)) return set_err(ctx, MPI_ERR_ARG, "null argument");
+  if (plan->kind != MPI_TRAJ_RADIAL) return set_err(ctx, MPI_ERR_ARG, "not a radial plan");
+  DeviceGuard g(ctx->device);
+  if (plan->M == 0) return MPI_OK;
+  return cuda_check(ctx,
+                    cudaMemcpyAsync(out_dev, plan->gstart, (size_t)plan->M * 2 * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, ctx->stream),
+                    "grid index copy");
+}
+
+// ------------------------------------------------------------------ basis
+
+extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N, int q, int on_device,
+                                           mpi_basis** out) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!U || !out) return set_err(ctx, MPI_ERR_ARG, "null basis pointer");
+  if (N < 2 || (N & 1) || q < 1 || q > 256) return set_err(ctx, MPI_ERR_SHAPE, "need even N >= 2 and 1 <= q <= 256");
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  mpi_basis* b = new mpi_basis();
+  b->ctx = ctx;
+  b->N = N;
+  b->q = q;
+  const size_t bytes = (size_t)N * q * sizeof(float2);
+  cudaError_t e = cudaMalloc(&b->U, bytes);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->U, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    mpi_status st = cuda_check(ctx, e, "basis upload");
+    if (b->U) cudaFree(b->U);
+    delete b;
+    return st == MPI_OK ? MPI_ERR_CUDA : st;
+  }
+  *out = b;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
+  if (!b) return MPI_ERR_ARG;
+  DeviceGuard g(b->ctx->device);
+  cudaStreamSynchronize(b->ctx->stream);
+  if (b->U) cudaFree(b->U);
+  if (b->Ubf) cudaFree(b->Ubf);
+  delete b;
+  return MPI_OK;
+}
+
+// --------------------------------------------------------------- operators
+
+extern "C" mpi_status mpi_basis_expand(mpi_ctx* ctx, const mpi_basis* basis, const mpi_c32* alpha, int C,
+                                       mpi_c32* maps, mpi_precision prec) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!basis || bad_ptr(alpha) || bad_ptr(maps) || C < 1) return set_err(ctx, MPI_ERR_ARG, "bad argument");
+  if (prec == MPI_PREC_BF16) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion not built");
+  if (prec != MPI_PREC_FP32) return set_err(ctx, MPI_ERR_ARG, "bad precision");
+  DeviceGuard g(ctx->device);
+  ExpandArgs a;
+  a.U = basis->U;
+  a.N = basis->N;
+  a.q = basis->q;
+  a.C = C;
+  a.alpha = (const float2*)alpha;
+  a.out = (float2*)maps;
+  return launch_expand(ctx, EX_MAPS, a);
+}
+
+extern "C" mpi_status mpi_forward(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                  const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y,
+                                  mpi_precision prec) {
+  mpi_status st = check_op(ctx, plan, basis, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p) || (plan->M > 0 && bad_ptr(y))) return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  ExpandArgs a = base_args(plan, basis, C);
+  a.alpha = (const float2*)alpha;
+  a.p = (const float2*)p;
+  a.out = w.A;
+  if ((st = launch_expand(ctx, EX_FWD, a))) return st;
+  return image_to_kspace(ctx, plan, w.A, C, (float2*)y, w.grid);
+}
+
+extern "C" mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                  const mpi_c32* alpha, int C, const mpi_c32* y, mpi_c32* p_out,
+                                  mpi_precision prec) {
+  mpi_status st = check_op(ctx, plan, basis, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p_out) || (plan->M > 0 && bad_ptr(y))) return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  if ((st = kspace_to_image(ctx, plan, (const float2*)y, C, w.A, w.grid))) return st;
+  ExpandArgs a = base_args(plan, basis, C);
+  a.alpha = (const float2*)alpha;
+  a.w = w.A;
+  a.out = (float2*)p_out;
+  return launch_expand(ctx, EX_ADJ, a);
+}
+
+extern "C" mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                   const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* dp,
+                                   const mpi_c32* dalpha, mpi_c32* dy, mpi_precision prec) {
+  mpi_status st = check_op(ctx, plan, basis, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p) || bad_ptr(dp) || bad_ptr(dalpha) || (plan->M > 0 && bad_ptr(dy)))
+    return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  ExpandArgs a = base_args(plan, basis, C);
+  a.alpha = (const float2*)alpha;
+  a.dalpha = (const float2*)dalpha;
+  a.p = (const float2*)p;
+  a.dp = (const float2*)dp;
+  a.out = w.A;
+  if ((st = launch_expand(ctx, EX_JFWD, a))) return st;
+  return image_to_kspace(ctx, plan, w.A, C, (float2*)dy, w.grid);
+}
+
+extern "C" mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                           const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* r,
+                                           mpi_c32* dp, mpi_c32* dalpha, mpi_precision prec) {
+  mpi_status st = check_op(ctx, plan, basis, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p) || bad_ptr(dp) || bad_ptr(dalpha) || (plan->M > 0 && bad_ptr(r)))
+    return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  if ((st = kspace_to_image(ctx, plan, (const float2*)r, C, w.A, w.grid))) return st;
+  ExpandArgs a = base_args(plan, basis, C);
+  a.alpha = (const float2*)alpha;
+  a.p = (const float2*)p;
+  a.w = w.A;
+  a.out = (float2*)dp;
+  a.vout = w.B;
+  if ((st = launch_expand(ctx, EX_JADJ, a))) return st;
+  return launch_uh_v(ctx, basis->U, basis->N, basis->q, w.B, C, (float2*)dalpha, w.partials, w.partial_cap);
+}

@@ -1,0 +1,277 @@
+// Basis expansion s_k = U alpha_k (Eq. 5) fused with the point-wise products of
+// the operator (Eq. 5 forward, Eq. 7 Jacobian, the Jacobian-adjoint display after
+// Eq. 7) and the U^H contraction of the coefficient block.
+//
+// FP32 CUDA-core path.  U is [q][N] (basis vector contiguous), so one thread per
+// pixel reads U[j][n] fully coalesced for every j, while the coefficients of a
+// block of coils sit in shared memory and are read as warp-wide broadcasts.
+#include <algorithm>
+
+#include "mpi_internal.h"
+
+namespace {
+
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfma_conj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// (-1)^(x + y + z) for raster index n of an (nz, ny, nx) grid.
+__device__ __forceinline__ float centre_sign(int n, int nx, int ny) {
+  int x = n % nx;
+  int t = n / nx;
+  int y = t % ny;
+  int z = t / ny;
+  return ((x + y + z) & 1) ? -1.f : 1.f;
+}
+
+constexpr int kExpandThreads = 128;
+
+// One thread per pixel.  MODE selects the epilogue; CB coils per pass.
+// Forward-type modes (MAPS, FWD, JFWD) split coil blocks over blockIdx.y;
+// adjoint-type modes (ADJ, JADJ) loop over all coil blocks to sum over coils.
+template <int MODE, int CB>
+__global__ void __launch_bounds__(kExpandThreads) k_expand(ExpandArgs a) {
+  extern __shared__ float4 smem4[];
+  float2* sA = reinterpret_cast<float2*>(smem4);  // [q][CB]
+  float2* sD = sA + a.q * CB;                      // [q][CB], Jacobian only
+  const int tid = threadIdx.x;
+  const int n = blockIdx.x * kExpandThreads + tid;
+  const bool active = n < a.N;
+  const float sg = active ? (a.centre ? centre_sign(n, a.nx, a.ny) : 1.f) * a.scale : 0.f;
+  constexpr bool kAdjLike = (MODE == EX_ADJ || MODE == EX_JADJ);
+  const int cb_begin = kAdjLike ? 0 : blockIdx.y * CB;
+  const int cb_end = kAdjLike ? a.C : min(a.C, cb_begin + CB);
+  float2 pimg = make_float2(0.f, 0.f);
+  float2 pacc = make_float2(0.f, 0.f);
+  if (active && MODE != EX_MAPS) pimg = a.p[n];
+
+  for (int c0 = cb_begin; c0 < cb_end; c0 += CB) {
+    __syncthreads();
+    for (int e = tid; e < a.q * CB; e += kExpandThreads) {
+      const int j = e / CB, c = e % CB;
+      const bool ok = (c0 + c) < a.C;
+      sA[e] = ok ? a.alpha[(size_t)(c0 + c) * a.q + j] : make_float2(0.f, 0.f);
+      if (MODE == EX_JFWD) sD[e] = ok ? a.dalpha[(size_t)(c0 + c) * a.q + j] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (!active) continue;
+
+    float2 acc[CB];
+    float2 dacc[MODE == EX_JFWD ? CB : 1];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < (MODE == EX_JFWD ? CB : 1); ++c) dacc[c] = make_float2(0.f, 0.f);
+
+    const float2* Up = a.U + n;
+#pragma unroll 4
+    for (int j = 0; j < a.q; ++j) {
+      const float2 u = __ldg(Up + (size_t)j * a.N);
+      const float4* ap = reinterpret_cast<const float4*>(sA + j * CB);
+#pragma unroll
+      for (int c2 = 0; c2 < CB / 2; ++c2) {
+        const float4 av = ap[c2];
+        cfma(acc[2 * c2], u, make_float2(av.x, av.y));
+        cfma(acc[2 * c2 + 1], u, make_float2(av.z, av.w));
+      }
+      if (MODE == EX_JFWD) {
+        const float4* dpp = reinterpret_cast<const float4*>(sD + j * CB);
+#pragma unroll
+        for (int c2 = 0; c2 < CB / 2; ++c2) {
+          const float4 dv = dpp[c2];
+          cfma(dacc[2 * c2], u, make_float2(dv.x, dv.y));
+          cfma(dacc[2 * c2 + 1], u, make_float2(dv.z, dv.w));
+        }
+      }
+    }
+
+    if (MODE == EX_MAPS) {
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (c0 + c < a.C) a.out[(size_t)(c0 + c) * a.N + n] = acc[c];
+    } else if (MODE == EX_FWD) {
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (c0 + c < a.C) a.out[(size_t)(c0 + c) * a.N + n] = cscale(cmul(acc[c], pimg), sg);
+    } else if (MODE == EX_JFWD) {
+      const float2 dpi = a.dp[n];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        if (c0 + c < a.C) {
+          float2 v = cmul(acc[c], dpi);
+          const float2 t = cmul(dacc[c], pimg);
+          v.x += t.x;
+          v.y += t.y;
+          a.out[(size_t)(c0 + c) * a.N + n] = cscale(v, sg);
+        }
+      }
+    } else {  // ADJ / JADJ
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        if (c0 + c < a.C) {
+          const float2 wv = a.w[(size_t)(c0 + c) * a.N + n];
+          cfma_conj(pacc, acc[c], wv);
+          if (MODE == EX_JADJ)
+            a.vout[(size_t)(c0 + c) * a.N + n] = cscale(cmul_conj(pimg, wv), sg);
+        }
+      }
+    }
+  }
+  if (kAdjLike && active) a.out[n] = cscale(pacc, sg);
+}
+
+template <int MODE, int CB>
+mpi_status launch_mode(mpi_ctx* ctx, const ExpandArgs& a) {
+  const size_t smem = (size_t)a.q * CB * sizeof(float2) * (MODE == EX_JFWD ? 2 : 1);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_expand<MODE, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "expand smem attribute");
+  }
+  const int gx = (a.N + kExpandThreads - 1) / kExpandThreads;
+  const bool adj_like = (MODE == EX_ADJ || MODE == EX_JADJ);
+  const int gy = adj_like ? 1 : (a.C + CB - 1) / CB;
+  k_expand<MODE, CB><<<dim3(gx, gy), kExpandThreads, smem, ctx->stream>>>(a);
+  MPI_LAUNCH_CHECK(ctx, "k_expand");
+  return MPI_OK;
+}
+
+// ---------------------------------------------------------------- U^H V
+
+constexpr int kUhvThreads = 256;
+constexpr int kUhvP = 64;  // pixels per staged chunk
+
+// Split-K over pixels: every CTA walks chunks blockIdx.x, blockIdx.x + gridDim.x,
+// ... and keeps its share of the (C x q) outputs in registers.  Thread t owns
+// basis index j = t % q and coils [cs*CT, cs*CT + CT) with cs = t / q + cgroup
+// offset.  sU rows are padded to P + 1 so that lanes with consecutive j hit
+// distinct banks.
+template <int CT>
+__global__ void __launch_bounds__(kUhvThreads) k_uh_v(const float2* __restrict__ U, int N, int q,
+                                                      const float2* __restrict__ V, int C, int c_begin,
+                                                      int c_count, float2* __restrict__ partials) {
+  extern __shared__ float4 smem4[];
+  float2* sU = reinterpret_cast<float2*>(smem4);  // [q][P + 1]
+  float2* sV = sU + q * (kUhvP + 1);               // [P][c_count_pad]
+  const int cpad = ((c_count + CT - 1) / CT) * CT;
+  const int tid = threadIdx.x;
+  const int groups = kUhvThreads / q;  // >= 1 (q <= 256)
+  const int j = tid % q;
+  const int cs = tid / q;
+  const bool owner = (tid < groups * q);
+  float2 acc[CT];
+#pragma unroll
+  for (int k = 0; k < CT; ++k) acc[k] = make_float2(0.f, 0.f);
+  const int n_chunks = (N + kUhvP - 1) / kUhvP;
+
+  for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const int n0 = ch * kUhvP;
+    const int cnt = min(kUhvP, N - n0);
+    __syncthreads();
+    for (int e = tid; e < q * kUhvP; e += kUhvThreads) {
+      const int jj = e / kUhvP, i = e % kUhvP;
+      sU[jj * (kUhvP + 1) + i] = (i < cnt) ? __ldg(U + (size_t)jj * N + n0 + i) : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < cpad * kUhvP; e += kUhvThreads) {
+      const int c = e / kUhvP, i = e % kUhvP;
+      sV[i * cpad + c] = (i < cnt && c < c_count) ? __ldg(V + (size_t)(c_begin + c) * N + n0 + i)
+                                                  : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (owner) {
+      // this thread's coil slots: cs, cs + groups, ... (CT of them)
+      for (int i = 0; i < kUhvP; ++i) {
+        const float2 u = sU[j * (kUhvP + 1) + i];
+#pragma unroll
+        for (int k = 0; k < CT; ++k) {
+          const int c = cs + k * groups;
+          if (c < cpad) cfma_conj(acc[k], u, sV[i * cpad + c]);
+        }
+      }
+    }
+  }
+  if (owner) {
+#pragma unroll
+    for (int k = 0; k < CT; ++k) {
+      const int c = cs + k * groups;
+      if (c < c_count) partials[((size_t)blockIdx.x * C + c_begin + c) * q + j] = acc[k];
+    }
+  }
+}
+
+__global__ void k_reduce_partials(const float2* __restrict__ partials, int nblk, int CQ,
+                                  float2* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= CQ) return;
+  float2 s = make_float2(0.f, 0.f);
+  for (int b = 0; b < nblk; ++b) {
+    const float2 v = partials[(size_t)b * CQ + e];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[e] = s;
+}
+
+int uhv_blocks(const mpi_ctx* ctx, int N) {
+  const int n_chunks = (N + kUhvP - 1) / kUhvP;
+  return std::max(1, std::min(n_chunks, 2 * std::max(ctx->num_sms, 1)));
+}
+
+}  // namespace
+
+mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a) {
+  if (a.N <= 0 || a.C <= 0) return MPI_OK;
+  switch (mode) {
+    case EX_MAPS: return launch_mode<EX_MAPS, 16>(ctx, a);
+    case EX_FWD: return launch_mode<EX_FWD, 16>(ctx, a);
+    case EX_JFWD: return launch_mode<EX_JFWD, 8>(ctx, a);
+    case EX_ADJ: return launch_mode<EX_ADJ, 16>(ctx, a);
+    case EX_JADJ: return launch_mode<EX_JADJ, 16>(ctx, a);
+    default: return set_err(ctx, MPI_ERR_ARG, "unknown expansion mode");
+  }
+}
+
+size_t uh_v_partial_elems(const mpi_ctx* ctx, int N, int q, int C) {
+  return (size_t)uhv_blocks(ctx, N) * (size_t)C * (size_t)q;
+}
+
+mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
+                       float2* dalpha, float2* partials, size_t partial_cap_elems) {
+  if (C <= 0) return MPI_OK;
+  if (q > kUhvThreads) return set_err(ctx, MPI_ERR_UNSUPPORTED, "dense basis with q > 256");
+  const int nblk = uhv_blocks(ctx, N);
+  if ((size_t)nblk * C * q > partial_cap_elems) return set_err(ctx, MPI_ERR_OOM, "U^H V partials");
+  const int groups = kUhvThreads / q;
+  constexpr int CT = 8;
+  const int per_launch = CT * groups;  // coils one launch covers
+  for (int c_begin = 0; c_begin < C; c_begin += per_launch) {
+    const int c_count = std::min(per_launch, C - c_begin);
+    const int cpad = ((c_count + CT - 1) / CT) * CT;
+    const size_t smem = ((size_t)q * (kUhvP + 1) + (size_t)kUhvP * cpad) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_uh_v<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "uh_v smem attribute");
+    k_uh_v<CT><<<nblk, kUhvThreads, smem, ctx->stream>>>(U, N, q, V, C, c_begin, c_count, partials);
+    MPI_LAUNCH_CHECK(ctx, "k_uh_v");
+  }
+  const int CQ = C * q;
+  k_reduce_partials<<<(CQ + 255) / 256, 256, 0, ctx->stream>>>(partials, nblk, CQ, dalpha);
+  MPI_LAUNCH_CHECK(ctx, "k_reduce_partials");
+  return MPI_OK;
+}

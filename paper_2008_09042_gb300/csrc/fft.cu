@@ -1,0 +1,477 @@
+// Cartesian F_s (Eq. 1): centred unitary DFT per coil followed by selection of
+// the sampled points, as shared-memory FFT passes.
+//
+// The centred DFT along an axis of even length n is
+//   F_c = (-1)^(n/2) D F D / sqrt(n),  D = diag((-1)^j),
+// with F the plain DFT.  The image-side sign D and the 1/sqrt(N) scale are
+// applied by the expansion kernels; these passes do the plain FFTs, the
+// k-side sign and the gather / zero-fill of the sampled points.
+//
+// Every line (one row, or one column of a tile) is transformed by one warp in
+// shared memory with a mixed-radix (2, 3, 4, 5, 8) Stockham auto-sort FFT: for
+// a stage of radix R after Ns points have been combined, butterfly j reads
+// x[j + r N/R], r < R, multiplies input r by w^(r (j mod Ns)) with w =
+// exp(-+2 pi i / (Ns R)), takes an R-point DFT and writes output r to
+// (j div Ns) Ns R + (j mod Ns) + r Ns.  Each lane keeps its butterflies in
+// registers across a __syncwarp, so the stage runs in place.
+#include <algorithm>
+
+#include "mpi_internal.h"
+
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// R-point DFT in registers, y[a] = sum_r x[r] exp(-+2 pi i a r / R).
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+  static __device__ __forceinline__ void go(float2* v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+  static __device__ __forceinline__ void go(float2* v) {
+    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const float2 s13 = cadd(v[1], v[3]), d13 = rot90<INV>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+  static __device__ __forceinline__ void go(float2* v) {
+    // two 4-point DFTs on the even and odd inputs, then the radix-2 combine
+    // with twiddles exp(-+2 pi i m / 8), m = 0..3.
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, INV>::go(e);
+    Dft<4, INV>::go(o);
+    const float h = 0.70710678118654752f;  // 1/sqrt(2)
+    // o[1] *= exp(-+i pi/4), o[2] *= -+i, o[3] *= exp(-+3 i pi/4)
+    const float2 o1 = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                          : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+    const float2 o2 = rot90<INV>(o[2]);
+    const float2 o3 = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                          : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+};
+
+template <bool INV>
+struct Dft<3, INV> {
+  static __device__ __forceinline__ void go(float2* v) {
+    // c = cos(2 pi / 3) = -1/2, s = sin(2 pi / 3) = sqrt(3)/2
+    const float s = INV ? -0.86602540378443865f : 0.86602540378443865f;
+    const float2 t = cadd(v[1], v[2]);
+    const float2 d = csub(v[1], v[2]);
+    const float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    // -+ i s d
+    const float2 isd = make_float2(s * d.y, -s * d.x);
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, isd);
+    v[2] = csub(m, isd);
+  }
+};
+
+template <bool INV>
+struct Dft<5, INV> {
+  static __device__ __forceinline__ void go(float2* v) {
+    // c1 = cos(2 pi/5) = (sqrt 5 - 1)/4, c2 = cos(4 pi/5) = -(sqrt 5 + 1)/4,
+    // s1 = sin(2 pi/5), s2 = sin(4 pi/5)
+    const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;
+    const float s1 = INV ? -0.95105651629515357f : 0.95105651629515357f;
+    const float s2 = INV ? -0.58778525229247313f : 0.58778525229247313f;
+    const float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    const float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    const float2 x0 = v[0];
+    const float2 r1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+    const float2 r2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+    // forward: y1 = r1 - i (s1 b1 + s2 b2), y2 = r2 - i (s2 b1 - s1 b2)
+    const float2 i1 = make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);
+    const float2 i2 = make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);
+    v[0] = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+    v[1] = make_float2(r1.x + i1.y, r1.y - i1.x);
+    v[4] = make_float2(r1.x - i1.y, r1.y + i1.x);
+    v[2] = make_float2(r2.x + i2.y, r2.y - i2.x);
+    v[3] = make_float2(r2.x - i2.y, r2.y + i2.x);
+  }
+};
+
+template <int N, int R, int NS, bool INV>
+__device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lane) {
+  constexpr int NB = N / R;
+  constexpr int PER = (NB + 31) / 32;
+  float2 v[PER][R];
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = lane + 32 * b;
+    if (j < NB) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = buf[j + r * NB];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = lane + 32 * b;
+    if (j < NB) {
+      const int k = j % NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[(r * k * (N / (NS * R))) % N];
+          if (INV) w.y = -w.y;
+          v[b][r] = cmul(v[b][r], w);
+        }
+      }
+      Dft<R, INV>::go(v[b]);
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[base + r * NS] = v[b][r];
+    }
+  }
+  __syncwarp();
+}
+
+template <int N, bool INV, int NS, int R, int... Rest>
+struct Run {
+  static __device__ __forceinline__ void go(float2* b, const float2* tw, int lane) {
+    fft_stage<N, R, NS, INV>(b, tw, lane);
+    Run<N, INV, NS * R, Rest...>::go(b, tw, lane);
+  }
+};
+template <int N, bool INV, int NS, int R>
+struct Run<N, INV, NS, R> {
+  static __device__ __forceinline__ void go(float2* b, const float2* tw, int lane) {
+    fft_stage<N, R, NS, INV>(b, tw, lane);
+  }
+};
+
+template <int N, bool INV>
+struct Fft;
+#define MPI_FFT_PLAN(n, ...)                                                    \
+  template <bool INV>                                                           \
+  struct Fft<n, INV> {                                                          \
+    static __device__ __forceinline__ void go(float2* b, const float2* tw, int lane) { \
+      Run<n, INV, 1, __VA_ARGS__>::go(b, tw, lane);                             \
+    }                                                                           \
+  };
+MPI_FFT_PLAN(16, 4, 4)
+MPI_FFT_PLAN(32, 8, 4)
+MPI_FFT_PLAN(48, 4, 4, 3)
+MPI_FFT_PLAN(64, 8, 8)
+MPI_FFT_PLAN(96, 8, 4, 3)
+MPI_FFT_PLAN(128, 8, 4, 4)
+MPI_FFT_PLAN(192, 8, 8, 3)
+MPI_FFT_PLAN(256, 8, 8, 4)
+MPI_FFT_PLAN(320, 8, 8, 5)
+MPI_FFT_PLAN(512, 8, 8, 8)
+#undef MPI_FFT_PLAN
+
+constexpr int kRowWarps = 4;
+
+// One warp per (coil, k-space row).  Forward: FFT along x, k-side centring sign,
+// gather the row's samples (contiguous in the sorted list).  Rows without
+// samples are skipped.
+template <int NX>
+__global__ void __launch_bounds__(kRowWarps * 32) k_rows_fwd_gather(
+    const float2* __restrict__ data, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
+    const int32_t* __restrict__ row_ptr, float2* __restrict__ y, int M, float ksign,
+    const float2* __restrict__ tw_g) {
+  __shared__ float2 tw[NX];
+  __shared__ float2 buf[kRowWarps][NX];
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long gr = (long)blockIdx.x * kRowWarps + warp;
+  if (gr >= (long)C * n_rows) return;
+  const int c = (int)(gr / n_rows), row = (int)(gr % n_rows);
+  const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
+  if (m0 == m1) return;
+  float2* b = buf[warp];
+  const float2* src = data + ((size_t)c * n_rows + row) * NX;
+  for (int i = lane; i < NX; i += 32) b[i] = src[i];
+  __syncwarp();
+  Fft<NX, false>::go(b, tw, lane);
+  const int rpar = (row / ny + row % ny) & 1;  // (kz + ky) parity
+  const size_t rbase = (size_t)row * NX;
+  for (int m = m0 + lane; m < m1; m += 32) {
+    const int kx = (int)(idx[m] - rbase);
+    const float s = ((kx + rpar) & 1) ? -ksign : ksign;
+    const float2 v = b[kx];
+    y[(size_t)c * M + m] = make_float2(v.x * s, v.y * s);
+  }
+}
+
+// Adjoint: zero-fill the row from its samples (with the k-side sign), inverse FFT.
+template <int NX>
+__global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
+    const float2* __restrict__ y, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
+    const int32_t* __restrict__ row_ptr, float2* __restrict__ data, int M, float ksign,
+    const float2* __restrict__ tw_g) {
+  __shared__ float2 tw[NX];
+  __shared__ float2 buf[kRowWarps][NX];
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long gr = (long)blockIdx.x * kRowWarps + warp;
+  if (gr >= (long)C * n_rows) return;
+  const int c = (int)(gr / n_rows), row = (int)(gr % n_rows);
+  const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
+  float2* dst = data + ((size_t)c * n_rows + row) * NX;
+  if (m0 == m1) {
+    for (int i = lane; i < NX; i += 32) dst[i] = make_float2(0.f, 0.f);
+    return;
+  }
+  float2* b = buf[warp];
+  for (int i = lane; i < NX; i += 32) b[i] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const int rpar = (row / ny + row % ny) & 1;
+  const size_t rbase = (size_t)row * NX;
+  for (int m = m0 + lane; m < m1; m += 32) {
+    const int kx = (int)(idx[m] - rbase);
+    const float s = ((kx + rpar) & 1) ? -ksign : ksign;
+    const float2 v = y[(size_t)c * M + m];
+    b[kx] = make_float2(v.x * s, v.y * s);
+  }
+  __syncwarp();
+  Fft<NX, true>::go(b, tw, lane);
+  for (int i = lane; i < NX; i += 32) dst[i] = b[i];
+}
+
+constexpr int kColTile = 8;  // adjacent lines per CTA (one warp each)
+constexpr int kColPad = 4;
+
+// In-place FFT of lines of length L with element stride `stride`.  A CTA takes
+// kColTile lines that are adjacent in memory (consecutive x), loads them with
+// 64-byte row segments, transposes into shared memory (one contiguous padded
+// line per warp), transforms and writes back.  Tiles are enumerated as
+// (slab, x-tile) with slab base offset = (slab / inner) * outer_stride +
+// (slab % inner) * inner_stride.
+template <int L, bool INV>
+__global__ void __launch_bounds__(kColTile * 32) k_fft_lines(float2* __restrict__ data, int nx,
+                                                            long stride, int n_slabs, int inner,
+                                                            long outer_stride, long inner_stride,
+                                                            const float2* __restrict__ tw_g) {
+  __shared__ float2 tw[L];
+  __shared__ float2 buf[kColTile][L + kColPad];
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tw_g[i];
+  const int x_tiles = (nx + kColTile - 1) / kColTile;
+  const long tile = blockIdx.x;
+  const int slab = (int)(tile / x_tiles);
+  const int x0 = (int)(tile % x_tiles) * kColTile;
+  if (slab >= n_slabs) return;
+  const size_t base = (size_t)(slab / inner) * outer_stride + (size_t)(slab % inner) * inner_stride + x0;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < L * kColTile; e += blockDim.x) {
+    const int r = e / kColTile, cx = e % kColTile;
+    if (x0 + cx < nx) buf[cx][r] = data[base + (size_t)r * stride + cx];
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  if (x0 + warp < nx) Fft<L, INV>::go(buf[warp], tw, lane);
+  __syncthreads();
+  for (int e = tid; e < L * kColTile; e += blockDim.x) {
+    const int r = e / kColTile, cx = e % kColTile;
+    if (x0 + cx < nx) data[base + (size_t)r * stride + cx] = buf[cx][r];
+  }
+}
+
+template <bool INV>
+mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride, int n_slabs, int inner,
+                          long outer_stride, long inner_stride) {
+  const int x_tiles = (nx + kColTile - 1) / kColTile;
+  const long blocks = (long)n_slabs * x_tiles;
+  if (blocks == 0) return MPI_OK;
+  if (blocks > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many FFT tiles");
+  const float2* tw = twiddle_table(ctx, L);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+#define MPI_LINES_CASE(n)                                                                          \
+  case n:                                                                                          \
+    k_fft_lines<n, INV><<<(unsigned)blocks, kColTile * 32, 0, ctx->stream>>>(                     \
+        data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw);                         \
+    break;
+  switch (L) {
+    MPI_LINES_CASE(16)
+    MPI_LINES_CASE(32)
+    MPI_LINES_CASE(48)
+    MPI_LINES_CASE(64)
+    MPI_LINES_CASE(96)
+    MPI_LINES_CASE(128)
+    MPI_LINES_CASE(192)
+    MPI_LINES_CASE(256)
+    MPI_LINES_CASE(320)
+    MPI_LINES_CASE(512)
+    default:
+      return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  }
+#undef MPI_LINES_CASE
+  MPI_LAUNCH_CHECK(ctx, "k_fft_lines");
+  return MPI_OK;
+}
+
+float axis_sign(int n) { return ((n / 2) & 1) ? -1.f : 1.f; }
+
+}  // namespace
+
+mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse) {
+  // lines along y: stride nx; slabs = (c, z); base = slab * ny * nx
+  const long plane = (long)ny * nx;
+  if (inverse) return lines_dispatch<true>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0);
+  return lines_dispatch<false>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0);
+}
+
+mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse) {
+  // lines along z: stride ny * nx; slabs = (c, y); base = c * vol + y * nx
+  const long plane = (long)ny * nx;
+  const long vol = plane * nz;
+  if (inverse) return lines_dispatch<true>(ctx, data, nz, nx, plane, C * ny, ny, vol, nx);
+  return lines_dispatch<false>(ctx, data, nz, nx, plane, C * ny, ny, vol, nx);
+}
+
+mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const float2* data, int C,
+                                  float2* y) {
+  if (plan->M == 0 || C == 0) return MPI_OK;
+  const int n_rows = plan->n_rows;
+  const long blocks = ((long)C * n_rows + kRowWarps - 1) / kRowWarps;
+  const float ks = axis_sign(plan->nx) * axis_sign(plan->ny) * (plan->ndim == 3 ? axis_sign(plan->nz) : 1.f);
+  const float2* tw = twiddle_table(ctx, plan->nx);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+#define MPI_ROWS_CASE(n)                                                                          \
+  case n:                                                                                         \
+    k_rows_fwd_gather<n><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(                  \
+        data, C, n_rows, plan->ny, plan->idx, plan->row_ptr, y, plan->M, ks, tw);                 \
+    break;
+  switch (plan->nx) {
+    MPI_ROWS_CASE(16)
+    MPI_ROWS_CASE(32)
+    MPI_ROWS_CASE(48)
+    MPI_ROWS_CASE(64)
+    MPI_ROWS_CASE(96)
+    MPI_ROWS_CASE(128)
+    MPI_ROWS_CASE(192)
+    MPI_ROWS_CASE(256)
+    MPI_ROWS_CASE(320)
+    MPI_ROWS_CASE(512)
+    default:
+      return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  }
+#undef MPI_ROWS_CASE
+  MPI_LAUNCH_CHECK(ctx, "k_rows_fwd_gather");
+  return MPI_OK;
+}
+
+mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C,
+                                   float2* data) {
+  if (C == 0) return MPI_OK;
+  const int n_rows = plan->n_rows;
+  const long blocks = ((long)C * n_rows + kRowWarps - 1) / kRowWarps;
+  const float ks = axis_sign(plan->nx) * axis_sign(plan->ny) * (plan->ndim == 3 ? axis_sign(plan->nz) : 1.f);
+  const float2* tw = twiddle_table(ctx, plan->nx);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+#define MPI_ROWS_CASE(n)                                                                          \
+  case n:                                                                                         \
+    k_rows_scatter_inv<n><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(                 \
+        y, C, n_rows, plan->ny, plan->idx, plan->row_ptr, data, plan->M, ks, tw);                 \
+    break;
+  switch (plan->nx) {
+    MPI_ROWS_CASE(16)
+    MPI_ROWS_CASE(32)
+    MPI_ROWS_CASE(48)
+    MPI_ROWS_CASE(64)
+    MPI_ROWS_CASE(96)
+    MPI_ROWS_CASE(128)
+    MPI_ROWS_CASE(192)
+    MPI_ROWS_CASE(256)
+    MPI_ROWS_CASE(320)
+    MPI_ROWS_CASE(512)
+    default:
+      return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  }
+#undef MPI_ROWS_CASE
+  MPI_LAUNCH_CHECK(ctx, "k_rows_scatter_inv");
+  return MPI_OK;
+}
+
+namespace {
+
+// In-place FFT of contiguous lines of length L, one warp per line.
+template <int L, bool INV>
+__global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __restrict__ data, long n_rows,
+                                                                    const float2* __restrict__ tw_g) {
+  __shared__ float2 tw[L];
+  __shared__ float2 buf[kRowWarps][L];
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long row = (long)blockIdx.x * kRowWarps + warp;
+  if (row >= n_rows) return;
+  float2* src = data + (size_t)row * L;
+  float2* b = buf[warp];
+  for (int i = lane; i < L; i += 32) b[i] = src[i];
+  __syncwarp();
+  Fft<L, INV>::go(b, tw, lane);
+  for (int i = lane; i < L; i += 32) src[i] = b[i];
+}
+
+template <bool INV>
+mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L) {
+  const long blocks = (n_rows + kRowWarps - 1) / kRowWarps;
+  if (blocks == 0) return MPI_OK;
+  const float2* tw = twiddle_table(ctx, L);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+#define MPI_RI_CASE(n)                                                                           \
+  case n:                                                                                        \
+    k_fft_rows_inplace<n, INV><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(data, n_rows, tw); \
+    break;
+  switch (L) {
+    MPI_RI_CASE(16)
+    MPI_RI_CASE(32)
+    MPI_RI_CASE(48)
+    MPI_RI_CASE(64)
+    MPI_RI_CASE(96)
+    MPI_RI_CASE(128)
+    MPI_RI_CASE(192)
+    MPI_RI_CASE(256)
+    MPI_RI_CASE(320)
+    MPI_RI_CASE(512)
+    default:
+      return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  }
+#undef MPI_RI_CASE
+  MPI_LAUNCH_CHECK(ctx, "k_fft_rows_inplace");
+  return MPI_OK;
+}
+
+}  // namespace
+
+mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse) {
+  if (inverse) return rows_inplace_dispatch<true>(ctx, data, n_rows, L);
+  return rows_inplace_dispatch<false>(ctx, data, n_rows, L);
+}

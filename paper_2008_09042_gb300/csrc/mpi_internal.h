@@ -1,0 +1,122 @@
+// Internal declarations shared by the CUDA translation units of libmpi_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mpi_gb300.h"
+
+// Supported FFT lengths (per axis) and the offset of each one's twiddle table
+// exp(-2 pi i m / n), m < n, inside the context's table buffer.
+static const int kFftLengths[] = {16, 32, 48, 64, 96, 128, 192, 256, 320, 512};
+static const int kNumFftLengths = sizeof(kFftLengths) / sizeof(int);
+
+struct mpi_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* work = nullptr;  // scratch between kernel passes
+  size_t work_bytes = 0;
+  float2* twiddles = nullptr;  // all tables back to back
+  int tw_offset[kNumFftLengths] = {0};
+  int num_sms = 0;
+  int64_t launches = 0;
+  std::string err;
+};
+
+struct mpi_plan {
+  mpi_ctx* ctx = nullptr;
+  int ndim = 2;
+  int nz = 1, ny = 0, nx = 0;
+  int N = 0;
+  int kind = MPI_TRAJ_CARTESIAN;
+  int M = 0;
+  // Cartesian: sorted sample list and, per k-space row (nz * ny rows of nx), the
+  // first sample of that row (rows + 1 entries).
+  int32_t* idx = nullptr;
+  int32_t* row_ptr = nullptr;
+  int n_rows = 0;
+  // Radial (Kaiser-Bessel gridding)
+  int W = 0, G = 0;
+  float* traj = nullptr;      // [M][2]
+  int32_t* gstart = nullptr;  // [M][2] first tap, array index in [0, G)
+  float* gw = nullptr;        // [M][2][W] separable kernel weights
+  float* deap = nullptr;      // [n] 1 / Phi(t), t = j - n/2
+  int32_t* bin_ptr = nullptr;  // spreading: samples sorted by grid tile
+  int32_t* bin_perm = nullptr;
+  int n_bins_x = 0, n_bins_y = 0;
+};
+
+struct mpi_basis {
+  mpi_ctx* ctx = nullptr;
+  int N = 0, q = 0;
+  float2* U = nullptr;  // [q][N] FP32 complex
+  __nv_bfloat16* Ubf = nullptr;  // BF16 operand copy (layout owned by the tensor-core path)
+  size_t Ubf_bytes = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+
+mpi_status set_err(mpi_ctx* ctx, mpi_status st, const std::string& msg);
+mpi_status cuda_check(mpi_ctx* ctx, cudaError_t e, const char* what);
+// Make sure ctx->work holds at least `bytes`; grows (after a stream sync) if needed.
+mpi_status ensure_work(mpi_ctx* ctx, size_t bytes);
+const float2* twiddle_table(const mpi_ctx* ctx, int n);
+bool fft_length_supported(int n);
+
+#define MPI_LAUNCH_CHECK(ctx, what)                                   \
+  do {                                                                \
+    (ctx)->launches++;                                                \
+    cudaError_t e__ = cudaGetLastError();                             \
+    if (e__ != cudaSuccess) return cuda_check((ctx), e__, (what));    \
+  } while (0)
+
+// ------------------------------------------------------- expansion kernels
+
+enum ExpandMode { EX_MAPS = 0, EX_FWD = 1, EX_JFWD = 2, EX_ADJ = 3, EX_JADJ = 4 };
+
+struct ExpandArgs {
+  const float2* U = nullptr;  // [q][N]
+  int N = 0, q = 0;
+  int nx = 1, ny = 1;          // grid, for the (-1)^(x+y+z) centring sign
+  int centre = 0;              // apply the centring sign
+  float scale = 1.f;           // N^{-1/2} (and the n/2-odd sign) for F_s
+  const float2* alpha = nullptr;   // [C][q]
+  const float2* dalpha = nullptr;  // [C][q] (Jacobian)
+  int C = 0;
+  const float2* p = nullptr;   // [N]
+  const float2* dp = nullptr;  // [N]
+  const float2* w = nullptr;   // [C][N] adjoint input (after inverse FFT passes)
+  float2* out = nullptr;       // maps / v [C][N], or image [N]
+  float2* vout = nullptr;      // Jacobian adjoint: conj(p) w [C][N]
+};
+
+mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
+// dalpha[c][j] = sum_n conj(U[j][n]) V[c][n]; partials in `work_partials`.
+mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
+                       float2* dalpha, float2* work_partials, size_t partial_cap_elems);
+size_t uh_v_partial_elems(const mpi_ctx* ctx, int N, int q, int C);
+
+// ------------------------------------------------------------ FFT passes
+
+// In-place FFT along the y axis of `data` [C][nz][ny][nx] (unnormalised).
+mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);
+// In-place FFT along z of [C][nz][ny][nx].
+mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);
+// Forward: FFT along x of every row, centring sign on k, gather of the sampled points.
+mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const float2* data, int C,
+                                  float2* y);
+// Adjoint: zero-fill every row from the samples, centring sign, inverse FFT along x.
+mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C,
+                                   float2* data);
+
+// ------------------------------------------------------------- NUFFT (radial)
+
+mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host);
+mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* img_deap_src, int C,
+                         float2* y, float2* grid);
+mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C,
+                         float2* img_out, float2* grid);

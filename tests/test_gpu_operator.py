@@ -1,0 +1,246 @@
+"""GPU parity of the encoding operator against the FP64 oracle.
+
+Every case runs the CUDA path through the C ABI and compares element by
+element with the oracle on the same seeded inputs.  Tolerance for the FP32 path:
+relative L2 error <= 1e-5 on every output.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from oracle import basis as obasis, fourier, nufft, operator as op, solvers
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def c64(x, dev="cuda"):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x, dtype=np.complex64))).to(dev)
+
+
+def f64(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import paper_2008_09042_gb300 as mp
+
+    return mp
+
+
+@pytest.fixture(scope="module")
+def ctx(mp):
+    return mp.Context(0)
+
+
+def _case(ctx, mp, shape, C, q, mask, U=None, seed=0):
+    rng = np.random.default_rng(seed)
+    N = int(np.prod(shape))
+    if U is None:
+        U = w.smooth_orthonormal_basis(shape[-2], shape[-1], q, seed=seed) if len(shape) == 2 else \
+            np.linalg.qr(rng.normal(size=(N, q)) + 1j * rng.normal(size=(N, q)))[0]
+    # the problem is defined by the FP32 values the GPU receives
+    U = U.astype(np.complex64).astype(np.complex128)
+    idx = w.mask_to_indices(mask)
+    Fs = fourier.CartesianSampling(shape, idx)
+    a = w.random_coefficients(C, q, seed=seed + 1).astype(np.complex64).astype(np.complex128)
+    p = w.random_image(N, seed=seed + 2).astype(np.complex64).astype(np.complex128)
+    plan = mp.Plan(ctx, shape, sample_idx=idx)
+    B = mp.Basis(ctx, U.T)
+    return dict(U=U, Fs=Fs, a=a, p=p, plan=plan, B=B, C=C, q=q, N=N, M=idx.size, rng=rng)
+
+
+def _check_all(ctx, mp, cs):
+    U, Fs, a, p, plan, B = cs["U"], cs["Fs"], cs["a"], cs["p"], cs["plan"], cs["B"]
+    rng = cs["rng"]
+    C, q, N, M = cs["C"], cs["q"], cs["N"], cs["M"]
+    ag, pg = c64(a), c64(p)
+    # forward (Eq. 5)
+    y = mp.forward(ctx, plan, B, ag, pg)
+    assert rel(f64(y), op.forward(Fs, U, a, p)) < TOL
+    # adjoint
+    r = (rng.normal(size=(C, M)) + 1j * rng.normal(size=(C, M))).astype(np.complex64).astype(np.complex128)
+    rg = c64(r)
+    x = mp.adjoint(ctx, plan, B, ag, rg)
+    assert rel(f64(x), op.adjoint(Fs, U, a, r)) < TOL
+    # Jacobian (Eq. 7)
+    dp = w.random_image(N, seed=7).astype(np.complex64).astype(np.complex128)
+    da = w.random_coefficients(C, q, seed=8).astype(np.complex64).astype(np.complex128)
+    dy = mp.jacobian(ctx, plan, B, ag, pg, c64(dp), c64(da))
+    assert rel(f64(dy), op.jacobian(Fs, U, a, p, dp, da)) < TOL
+    # Jacobian adjoint
+    gp, ga = mp.jacobian_adjoint(ctx, plan, B, ag, pg, rg)
+    rp, ra = op.jacobian_adjoint(Fs, U, a, p, r)
+    assert rel(f64(gp), rp) < TOL
+    assert rel(f64(ga), ra) < TOL
+    # maps
+    s = mp.basis_expand(ctx, B, ag)
+    assert rel(f64(s), op.expand(U, a)) < TOL
+
+
+def test_cartesian_64_vd_lines_maxwell_basis(ctx, mp):
+    b = obasis.build_maxwell_basis_2d(64, 64, 32, n_sites=32, n_exc=200, seed=0)
+    mask = w.vd_lines_mask(64, 64, 3, 16, seed=1)
+    cs = _case(ctx, mp, (64, 64), 4, 32, mask, U=b.U)
+    _check_all(ctx, mp, cs)
+
+
+@pytest.mark.parametrize("shape,C,q", [((48, 96), 5, 20), ((32, 16), 17, 3), ((192, 64), 3, 40),
+                                       ((128, 320), 2, 9)])
+def test_cartesian_ragged_shapes(ctx, mp, shape, C, q):
+    # coil counts that leave a partial coil block, non-square grids, radix-3/5 lengths
+    mask = w.poisson_disc_mask(shape[0], shape[1], 3, calib=(8, 8), seed=3)
+    cs = _case(ctx, mp, shape, C, q, mask, seed=4)
+    _check_all(ctx, mp, cs)
+
+
+def test_cartesian_full_size_256_c16_q128(ctx, mp):
+    mask = w.poisson_disc_mask(256, 256, 6, calib=(24, 24), seed=5)
+    cs = _case(ctx, mp, (256, 256), 16, 128, mask, seed=6)
+    _check_all(ctx, mp, cs)
+
+
+def test_fully_sampled_and_empty(ctx, mp):
+    full = np.ones((32, 32), dtype=bool)
+    cs = _case(ctx, mp, (32, 32), 3, 8, full, seed=9)
+    _check_all(ctx, mp, cs)
+    # fully sampled, unitary F: adjoint(forward(p)) = sum_k |s_k|^2 p
+    ag, pg = c64(cs["a"]), c64(cs["p"])
+    back = f64(mp.adjoint(ctx, cs["plan"], cs["B"], ag, mp.forward(ctx, cs["plan"], cs["B"], ag, pg)))
+    s = op.expand(cs["U"], cs["a"])
+    assert rel(back, np.sum(np.abs(s) ** 2, axis=0) * cs["p"]) < TOL
+    # no samples at all: y is empty and the adjoint is exactly zero
+    empty = np.zeros((32, 32), dtype=bool)
+    ce = _case(ctx, mp, (32, 32), 2, 4, empty, seed=10)
+    ag = c64(ce["a"])
+    y = mp.forward(ctx, ce["plan"], ce["B"], ag, c64(ce["p"]))
+    assert y.shape == (2, 0)
+    x = mp.adjoint(ctx, ce["plan"], ce["B"], ag, torch.zeros((2, 0), dtype=torch.complex64, device="cuda"))
+    assert torch.count_nonzero(x).item() == 0
+
+
+def test_adjoint_dot_products_at_full_size(ctx, mp):
+    # <G p, r> = <p, G^H r> and <J d, r> = <d, J^H r> hold at any size; checked
+    # in FP64 from the FP32 outputs.
+    mask = w.poisson_disc_mask(256, 256, 6, calib=(24, 24), seed=5)
+    cs = _case(ctx, mp, (256, 256), 16, 128, mask, seed=11)
+    ag, pg = c64(cs["a"]), c64(cs["p"])
+    r = w.random_coefficients(16, cs["M"], seed=12, decay=False)
+    rg = c64(r)
+    r = r.astype(np.complex64).astype(np.complex128)
+    lhs = np.vdot(f64(mp.forward(ctx, cs["plan"], cs["B"], ag, pg)), r)
+    rhs = np.vdot(cs["p"], f64(mp.adjoint(ctx, cs["plan"], cs["B"], ag, rg)))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+    dp = c64(w.random_image(cs["N"], seed=13))
+    da = c64(w.random_coefficients(16, 128, seed=14))
+    gp, ga = mp.jacobian_adjoint(ctx, cs["plan"], cs["B"], ag, pg, rg)
+    lhs = np.vdot(f64(mp.jacobian(ctx, cs["plan"], cs["B"], ag, pg, dp, da)), r)
+    rhs = np.vdot(f64(dp), f64(gp)) + np.vdot(f64(da), f64(ga))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_jacobian_central_difference_32_directions(ctx, mp):
+    # G is bilinear: (G(x + h d) - G(x - h d)) / 2h = J d exactly; h = 1e-3,
+    # 32 random directions, evaluated with the GPU forward.
+    mask = w.poisson_disc_mask(64, 64, 4, calib=(12, 12), seed=15)
+    cs = _case(ctx, mp, (64, 64), 4, 16, mask, seed=16)
+    a, p = cs["a"], cs["p"]
+    h = 1e-3
+    for k in range(32):
+        dp = w.random_image(cs["N"], seed=100 + k)
+        da = w.random_coefficients(4, 16, seed=200 + k)
+        yp = f64(mp.forward(ctx, cs["plan"], cs["B"], c64(a + h * da), c64(p + h * dp)))
+        ym = f64(mp.forward(ctx, cs["plan"], cs["B"], c64(a - h * da), c64(p - h * dp)))
+        J = f64(mp.jacobian(ctx, cs["plan"], cs["B"], c64(a), c64(p), c64(dp), c64(da)))
+        # FP32 inputs perturbed by h: difference quotient error ~ eps32 |G| / h
+        assert rel((yp - ym) / (2 * h), J) < 5e-3
+
+
+def test_autograd_backward_is_jacobian_adjoint(ctx, mp):
+    mask = w.poisson_disc_mask(64, 64, 3, calib=(12, 12), seed=17)
+    cs = _case(ctx, mp, (64, 64), 3, 12, mask, seed=18)
+    p = c64(cs["p"]).requires_grad_(True)
+    a = c64(cs["a"]).requires_grad_(True)
+    y = mp.mpi_operator(p, a, ctx, cs["plan"], cs["B"])
+    target = c64(w.random_coefficients(3, cs["M"], seed=19, decay=False))
+    loss = 0.5 * (y - target).abs().pow(2).sum()
+    loss.backward()
+    rp, ra = op.jacobian_adjoint(cs["Fs"], cs["U"], cs["a"], cs["p"],
+                                 op.forward(cs["Fs"], cs["U"], cs["a"], cs["p"]) - f64(target))
+    # torch's gradient of a real loss is the conjugate-Wirtinger one: J^H (G(x) - y)
+    assert rel(f64(p.grad), rp) < 1e-4
+    assert rel(f64(a.grad), ra) < 1e-4
+
+
+def test_bad_arguments_rejected_before_launch(ctx, mp):
+    idx = np.array([3, 2], dtype=np.int32)  # not increasing
+    with pytest.raises(mp.MpiError):
+        mp.Plan(ctx, (32, 32), sample_idx=idx)
+    with pytest.raises(mp.MpiError):
+        mp.Plan(ctx, (32, 32), sample_idx=np.array([0, 1024], dtype=np.int32))  # out of range
+    with pytest.raises(mp.MpiError):
+        mp.Plan(ctx, (30, 32), sample_idx=np.array([0], dtype=np.int32))  # unsupported length
+
+
+def test_launch_count_grows(ctx, mp):
+    before = ctx.launches()
+    mask = w.poisson_disc_mask(32, 32, 3, calib=(8, 8), seed=20)
+    cs = _case(ctx, mp, (32, 32), 2, 4, mask, seed=21)
+    mp.forward(ctx, cs["plan"], cs["B"], c64(cs["a"]), c64(cs["p"]))
+    torch.cuda.synchronize()
+    assert ctx.launches() >= before + 3
+
+
+# ----------------------------------------------------------------- radial
+
+def _radial_case(ctx, mp, n, C, q, spokes, readout, seed=30):
+    k = w.golden_angle_radial(spokes, readout).astype(np.float32)
+    U = w.smooth_orthonormal_basis(n, n, q, seed=seed).astype(np.complex64).astype(np.complex128)
+    a = w.random_coefficients(C, q, seed=seed + 1).astype(np.complex64).astype(np.complex128)
+    p = w.random_image(n * n, seed=seed + 2).astype(np.complex64).astype(np.complex128)
+    plan = mp.Plan(ctx, (n, n), traj=k, kb_width=6, oversamp=2.0)
+    B = mp.Basis(ctx, U.T)
+    kb = nufft.KBGriddingNUFFT((n, n), k.astype(np.float64), W=6, sigma=2.0)
+    return dict(k=k, U=U, a=a, p=p, plan=plan, B=B, kb=kb, C=C, q=q, N=n * n, M=k.shape[0])
+
+
+def test_radial_gridding_indices_bit_exact(ctx, mp):
+    cs = _radial_case(ctx, mp, 64, 2, 8, 16, 128)
+    got = cs["plan"].grid_index().cpu().numpy()
+    ref = nufft.gridding_indices(cs["k"], 128, 6)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("n,C,q,spokes,readout", [(64, 3, 8, 16, 128), (256, 12, 96, 64, 512)])
+def test_radial_operator_matches_fp64_gridding(ctx, mp, n, C, q, spokes, readout):
+    cs = _radial_case(ctx, mp, n, C, q, spokes, readout)
+    kb, U, a, p = cs["kb"], cs["U"], cs["a"], cs["p"]
+    ag, pg = c64(a), c64(p)
+    y = mp.forward(ctx, cs["plan"], cs["B"], ag, pg)
+    assert rel(f64(y), op.forward(kb, U, a, p)) < TOL
+    r = w.random_coefficients(C, cs["M"], seed=40, decay=False).astype(np.complex64).astype(np.complex128)
+    x = mp.adjoint(ctx, cs["plan"], cs["B"], ag, c64(r))
+    assert rel(f64(x), op.adjoint(kb, U, a, r)) < TOL
+    gp, ga = mp.jacobian_adjoint(ctx, cs["plan"], cs["B"], ag, pg, c64(r))
+    rp, ra = op.jacobian_adjoint(kb, U, a, p, r)
+    assert rel(f64(gp), rp) < TOL and rel(f64(ga), ra) < TOL
+
+
+def test_radial_close_to_direct_nudft(ctx, mp):
+    cs = _radial_case(ctx, mp, 64, 2, 8, 24, 128)
+    ex = fourier.DirectNUDFT((64, 64), cs["k"].astype(np.float64))
+    y = f64(mp.forward(ctx, cs["plan"], cs["B"], c64(cs["a"]), c64(cs["p"])))
+    ref_exact = op.forward(ex, cs["U"], cs["a"], cs["p"])
+    ref_kb = op.forward(cs["kb"], cs["U"], cs["a"], cs["p"])
+    kb_err = rel(ref_kb, ref_exact)  # the gridding's own error, FP64
+    assert rel(y, ref_exact) < kb_err + 1e-5

@@ -1,0 +1,390 @@
+"""Benchmark of the Maxwell Parallel Imaging encoding operator on GB300.
+
+Metric: forward + adjoint operator pairs per second (one mpi_forward plus one
+mpi_adjoint of the Maxwell-parameterised bilinear operator, Eq. 5 and its
+adjoint) on the 2D Cartesian 256 x 256, 16-coil, q = 128 workload with a
+variable-density Poisson-disc mask (R = 6, 24 x 24 calibration), complex64 data.
+
+One step = one forward + one adjoint on one slice, inputs resident in HBM.  L2
+(129 MB) is flushed between timed steps by writing a 256 MiB buffer, because
+the 67 MB FP32 basis would otherwise stay L2-resident.  Steps are timed with
+CUDA events on the library's stream; the expansion kernel's own launches are
+timed with per-launch events inside the same region (the library's profiling
+hook) for the roofline entry.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: independent replicas (one slice per rank, no collective on the data
+path); the value is the pairs of all ranks over the slowest rank's time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as w  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cart2d_256_c16_q128")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def make_inputs(name, seed_offset=0):
+    cfg = w.workload(name)
+    if cfg["kind"] != "cartesian":
+        raise SystemExit(f"bench workload {name} is not a 2D Cartesian slice")
+    ny, nx = cfg["dims"]
+    C, q = cfg["C"], cfg["q"]
+    base = w.BASE_SEED + seed_offset
+    U = w.smooth_orthonormal_basis(ny, nx, q, seed=base)
+    if cfg["mask"] == "poisson":
+        mask = w.poisson_disc_mask(ny, nx, cfg["R"], calib=cfg["calib"], seed=base + 1)
+    else:
+        mask = w.vd_lines_mask(ny, nx, cfg["R"], cfg["acs"], seed=base + 1)
+    idx = w.mask_to_indices(mask)
+    alpha = w.random_coefficients(C, q, seed=base + 2)
+    p = w.random_ellipses(ny, nx, seed=base + 3).ravel().astype(np.complex128)
+    return cfg, U, idx, alpha, p
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return float(d.get("hbm_gbs")), float(d.get("bf16_tflops")), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches
+    the kernel's source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2008_09042_gb300", "csrc", d["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["bytes_per_launch"] if sha == d.get("source_sha") else None
+
+
+def cpu_oracle_pairs(cfg, U, idx, alpha, p, budget_s=12.0, max_pairs=200):
+    """Forward+adjoint pairs/s of the FP64 oracle on this host (bounded sample)."""
+    from oracle import fourier, operator as op
+
+    Fs = fourier.CartesianSampling(cfg["dims"], idx)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_pairs:
+        y = op.forward(Fs, U, alpha, p)
+        op.adjoint(Fs, U, alpha, y)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [1])
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    cfg, U, idx, alpha, p = make_inputs(args.workload)
+    from oracle import fourier, operator as op
+
+    Fs = fourier.CartesianSampling(cfg["dims"], idx)
+    for _ in range(args.warmup):
+        op.adjoint(Fs, U, alpha, op.forward(Fs, U, alpha, p))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op.adjoint(Fs, U, alpha, op.forward(Fs, U, alpha, p))
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": "MPI forward+adjoint operator pairs per second",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": int(np.prod(cfg["dims"])), "C": cfg["C"], "q": cfg["q"],
+                   "M": int(idx.size)},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full forward+adjoint pairs of the workload (complex128, "
+                                   f"explicit DFT matrices, numpy BLAS)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    import paper_2008_09042_gb300 as mp
+
+    cfg, U, idx, alpha, p = make_inputs(args.workload, seed_offset=rank)
+    C, q = cfg["C"], cfg["q"]
+    N, M = U.shape[0], int(idx.size)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = mp.Context(local_rank, stream=stream)
+    plan = mp.Plan(ctx, cfg["dims"], sample_idx=idx)
+    basis = mp.Basis(ctx, U.T)
+    ctx.reserve(plan, basis, C)
+    a_d = torch.from_numpy(alpha.astype(np.complex64)).to(dev)
+    p_d = torch.from_numpy(p.astype(np.complex64)).to(dev)
+    y_d = torch.empty((C, M), dtype=torch.complex64, device=dev)
+    x_d = torch.empty((N,), dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        mp.forward(ctx, plan, basis, a_d, p_d, args.prec, out=y_d)
+        mp.adjoint(ctx, plan, basis, a_d, y_d, args.prec, out=x_d)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = ctx.launches()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launches() - launches0
+    clk = clocks.stop()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    total_ms = sum(s.elapsed_time(e) for s, e in evs)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end: pinned host buffers, copies inside the timed region
+    a_h = torch.from_numpy(alpha.astype(np.complex64)).pin_memory()
+    p_h = torch.from_numpy(p.astype(np.complex64)).pin_memory()
+    y_h = torch.empty((C, M), dtype=torch.complex64).pin_memory()
+    x_h = torch.empty((N,), dtype=torch.complex64).pin_memory()
+    a_e = torch.empty_like(a_d)
+    p_e = torch.empty_like(p_d)
+    y_e = torch.empty_like(y_d)
+
+    def e2e_step():
+        a_e.copy_(a_h, non_blocking=True)
+        p_e.copy_(p_h, non_blocking=True)
+        mp.forward(ctx, plan, basis, a_e, p_e, args.prec, out=y_d)
+        y_h.copy_(y_d, non_blocking=True)
+        y_e.copy_(y_h, non_blocking=True)
+        mp.adjoint(ctx, plan, basis, a_e, y_e, args.prec, out=x_d)
+        x_h.copy_(x_d, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        e2e_step()
+        e.record(stream)
+        e.synchronize()
+        e2e_ms += s.elapsed_time(e)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * args.steps / (e2e_ms / 1000.0)
+    h2d = (C * q + N + C * M) * 8
+    d2h = (C * M + N) * 8
+
+    # ---- roofline of the dominant kernel (the basis expansion, forward and adjoint launches)
+    hbm_gbs, bf16_tflops, peak_src = load_peaks()
+    ex_ms, ex_n = prof["expand"]
+    fam_total = sum(v[0] for v in prof.values())
+    ex_avg_s = ex_ms / max(ex_n, 1) / 1000.0
+    # per launch: read U (N q), alpha (C q), the image or per-coil data, write per-coil data or image
+    ex_bytes = (N * q + C * q + C * N + N) * (8 if args.prec == "fp32" else 4)
+    ex_flops = 8.0 * N * q * C
+    if args.prec == "fp32":
+        t_hbm = ex_bytes / (hbm_gbs * 1e9)
+        t_alu = ex_flops / (FP32_ALU_TFLOPS * 1e12)
+        if t_alu >= t_hbm:
+            roof = {"bound": "alu", "achieved": ex_flops / ex_avg_s / 1e12, "peak": FP32_ALU_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+        else:
+            roof = {"bound": "hbm", "achieved": ex_bytes / ex_avg_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "peak_source": f"{peak_src} HBM copy bandwidth"}
+    else:
+        roof = {"bound": "hbm", "achieved": ex_bytes / ex_avg_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                "peak_source": f"{peak_src} HBM copy bandwidth"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = "k_expand (basis expansion fused with the point-wise products)"
+    roof["algorithmic_bytes_per_launch"] = ex_bytes
+    roof["algorithmic_flops_per_launch"] = ex_flops
+    roof["avg_launch_us"] = ex_avg_s * 1e6
+    roof["share_of_kernel_time"] = ex_ms / fam_total if fam_total > 0 else None
+    roof["traffic"] = ncu_traffic("k_expand")
+
+    line = {
+        "metric": "MPI forward+adjoint operator pairs per second",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16+f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "C": C, "q": q, "M": M,
+                   "mask": f"2D variable-density Poisson-disc R={cfg.get('R')} calib {cfg.get('calib')}",
+                   "basis": "smooth orthonormal stand-in of the Maxwell basis shape (complex64 [q][N])",
+                   "expansion_precision": args.prec, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, dt = cpu_oracle_pairs(cfg, U, idx, alpha, p)
+        line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": blas_threads(), "kind": "oracle",
+                                "sample": f"{n} forward+adjoint pairs of the same workload in {dt:.1f} s "
+                                          f"(complex128 numpy oracle)"}
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -75,6 +75,16 @@ mpi_status mpi_ctx_reserve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* 
 const char* mpi_last_error(const mpi_ctx* ctx);
 /* Number of kernels this context has launched since creation (for accounting). */
 int64_t mpi_ctx_launch_count(const mpi_ctx* ctx);
+/* Per-launch device timing: while enabled, every kernel the context launches is
+ * bracketed by two CUDA events on the context's stream (16384 launches at most
+ * between reads; later ones are not timed).  mpi_ctx_profile_read synchronises
+ * the stream and returns, for one kernel family, the summed device time (ms) and
+ * the number of timed launches since the last reset; reset != 0 clears the sums.
+ * Families: 0 basis expansion, 1 U^H V contraction, 2 row FFT passes, 3 strided
+ * FFT passes, 4 NUFFT gridding, 5 solver vector kernels, 6 other. */
+mpi_status mpi_ctx_profile(mpi_ctx* ctx, int enable);
+mpi_status mpi_ctx_profile_read(mpi_ctx* ctx, int family, double* ms_out, int64_t* launches_out,
+                                int reset);
 
 /* ------------------------------------------------------------------- plan */
 

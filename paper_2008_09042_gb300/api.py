@@ -52,6 +52,25 @@ class Context:
     def launches(self):
         return int(self.lib.mpi_ctx_launch_count(self.h))
 
+    FAMILIES = {"expand": 0, "uh_v": 1, "fft_rows": 2, "fft_lines": 3, "nufft": 4, "solver": 5, "other": 6}
+
+    def profile(self, enable=True):
+        check(self.h, self.lib.mpi_ctx_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, reset=False):
+        """{family: (ms, launches)} summed since the last reset."""
+        out = {}
+        for name, fam in self.FAMILIES.items():
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            check(self.h, self.lib.mpi_ctx_profile_read(self.h, fam, ctypes.byref(ms), ctypes.byref(n), 0))
+            out[name] = (ms.value, n.value)
+        if reset:
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            check(self.h, self.lib.mpi_ctx_profile_read(self.h, 0, ctypes.byref(ms), ctypes.byref(n), 1))
+        return out
+
     def reserve(self, plan, basis, C):
         check(self.h, self.lib.mpi_ctx_reserve(self.h, plan.h, basis.h, C))
 

@@ -51,7 +51,23 @@ mpi_status ensure_work(mpi_ctx* ctx, size_t bytes) {
   return MPI_OK;
 }
 
+void prof_begin(mpi_ctx* ctx, int family) {
+  if (!ctx->profiling || ctx->ev_used >= (int)ctx->ev_begin.size()) return;
+  cudaEventRecord(ctx->ev_begin[ctx->ev_used], ctx->stream);
+  ctx->pending_family = family;
+}
+
+void prof_end(mpi_ctx* ctx) {
+  if (!ctx->profiling || ctx->pending_family < 0 || ctx->ev_used >= (int)ctx->ev_begin.size()) return;
+  cudaEventRecord(ctx->ev_end[ctx->ev_used], ctx->stream);
+  ctx->ev_family[ctx->ev_used] = ctx->pending_family;
+  ctx->ev_used++;
+  ctx->pending_family = -1;
+}
+
 namespace {
+
+constexpr int kProfileSlots = 16384;
 
 struct DeviceGuard {
   explicit DeviceGuard(int dev) { cudaSetDevice(dev); }
@@ -187,6 +203,10 @@ extern "C" mpi_status mpi_ctx_destroy(mpi_ctx* ctx) {
   if (!ctx) return MPI_ERR_ARG;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (size_t i = 0; i < ctx->ev_begin.size(); ++i) {
+    cudaEventDestroy(ctx->ev_begin[i]);
+    cudaEventDestroy(ctx->ev_end[i]);
+  }
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->twiddles) cudaFree(ctx->twiddles);
   delete ctx;
@@ -213,6 +233,54 @@ extern "C" mpi_status mpi_ctx_reserve(mpi_ctx* ctx, const mpi_plan* plan, const 
   size_t extra = ((size_t)12 * plan->N + (size_t)8 * C * std::max(plan->M, 1) +
                   (size_t)8 * C * basis->q + 1024) * sizeof(float2);
   return ensure_work(ctx, op_work_bytes(ctx, plan, basis, C) + extra);
+}
+
+extern "C" mpi_status mpi_ctx_profile(mpi_ctx* ctx, int enable) {
+  if (!ctx) return MPI_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  if (enable && ctx->ev_begin.empty()) {
+    ctx->ev_begin.resize(kProfileSlots);
+    ctx->ev_end.resize(kProfileSlots);
+    ctx->ev_family.assign(kProfileSlots, 0);
+    for (int i = 0; i < kProfileSlots; ++i) {
+      if (cudaEventCreate(&ctx->ev_begin[i]) != cudaSuccess || cudaEventCreate(&ctx->ev_end[i]) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ev_begin.resize(i);
+        ctx->ev_end.resize(i);
+        return set_err(ctx, MPI_ERR_CUDA, "event creation failed");
+      }
+    }
+  }
+  ctx->profiling = enable != 0;
+  ctx->pending_family = -1;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_ctx_profile_read(mpi_ctx* ctx, int family, double* ms, int64_t* launches, int reset) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (family < 0 || family >= KF_COUNT || !ms || !launches) return set_err(ctx, MPI_ERR_ARG, "bad profile query");
+  DeviceGuard g(ctx->device);
+  mpi_status st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "profile sync");
+  if (st) return st;
+  for (int i = 0; i < ctx->ev_used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->ev_begin[i], ctx->ev_end[i]) == cudaSuccess) {
+      ctx->prof_ms[ctx->ev_family[i]] += t;
+      ctx->prof_launches[ctx->ev_family[i]] += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  ctx->ev_used = 0;
+  *ms = ctx->prof_ms[family];
+  *launches = ctx->prof_launches[family];
+  if (reset) {
+    for (int k = 0; k < KF_COUNT; ++k) {
+      ctx->prof_ms[k] = 0;
+      ctx->prof_launches[k] = 0;
+    }
+  }
+  return MPI_OK;
 }
 
 extern "C" const char* mpi_last_error(const mpi_ctx* ctx) {

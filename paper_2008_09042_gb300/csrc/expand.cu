@@ -148,6 +148,7 @@ mpi_status launch_mode(mpi_ctx* ctx, const ExpandArgs& a) {
   const int gx = (a.N + kExpandThreads - 1) / kExpandThreads;
   const bool adj_like = (MODE == EX_ADJ || MODE == EX_JADJ);
   const int gy = adj_like ? 1 : (a.C + CB - 1) / CB;
+  MPI_PROF(ctx, KF_EXPAND);
   k_expand<MODE, CB><<<dim3(gx, gy), kExpandThreads, smem, ctx->stream>>>(a);
   MPI_LAUNCH_CHECK(ctx, "k_expand");
   return MPI_OK;
@@ -267,10 +268,12 @@ mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2
     const size_t smem = ((size_t)q * (kUhvP + 1) + (size_t)kUhvP * cpad) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_uh_v<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "uh_v smem attribute");
-    k_uh_v<CT><<<nblk, kUhvThreads, smem, ctx->stream>>>(U, N, q, V, C, c_begin, c_count, partials);
+    MPI_PROF(ctx, KF_UHV);
+  k_uh_v<CT><<<nblk, kUhvThreads, smem, ctx->stream>>>(U, N, q, V, C, c_begin, c_count, partials);
     MPI_LAUNCH_CHECK(ctx, "k_uh_v");
   }
   const int CQ = C * q;
+  MPI_PROF(ctx, KF_UHV);
   k_reduce_partials<<<(CQ + 255) / 256, 256, 0, ctx->stream>>>(partials, nblk, CQ, dalpha);
   MPI_LAUNCH_CHECK(ctx, "k_reduce_partials");
   return MPI_OK;

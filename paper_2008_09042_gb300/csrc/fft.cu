@@ -317,6 +317,7 @@ mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride
     k_fft_lines<n, INV><<<(unsigned)blocks, kColTile * 32, 0, ctx->stream>>>(                     \
         data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw);                         \
     break;
+  MPI_PROF(ctx, KF_FFT_LINES);
   switch (L) {
     MPI_LINES_CASE(16)
     MPI_LINES_CASE(32)
@@ -368,6 +369,7 @@ mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const floa
     k_rows_fwd_gather<n><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(                  \
         data, C, n_rows, plan->ny, plan->idx, plan->row_ptr, y, plan->M, ks, tw);                 \
     break;
+  MPI_PROF(ctx, KF_FFT_ROWS);
   switch (plan->nx) {
     MPI_ROWS_CASE(16)
     MPI_ROWS_CASE(32)
@@ -400,6 +402,7 @@ mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const flo
     k_rows_scatter_inv<n><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(                 \
         y, C, n_rows, plan->ny, plan->idx, plan->row_ptr, data, plan->M, ks, tw);                 \
     break;
+  MPI_PROF(ctx, KF_FFT_ROWS);
   switch (plan->nx) {
     MPI_ROWS_CASE(16)
     MPI_ROWS_CASE(32)
@@ -450,6 +453,7 @@ mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L)
   case n:                                                                                        \
     k_fft_rows_inplace<n, INV><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(data, n_rows, tw); \
     break;
+  MPI_PROF(ctx, KF_FFT_ROWS);
   switch (L) {
     MPI_RI_CASE(16)
     MPI_RI_CASE(32)

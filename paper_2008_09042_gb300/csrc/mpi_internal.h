@@ -15,6 +15,10 @@
 static const int kFftLengths[] = {16, 32, 48, 64, 96, 128, 192, 256, 320, 512};
 static const int kNumFftLengths = sizeof(kFftLengths) / sizeof(int);
 
+// Kernel families for the optional per-launch event timing.
+enum KernelFamily { KF_EXPAND = 0, KF_UHV = 1, KF_FFT_ROWS = 2, KF_FFT_LINES = 3, KF_NUFFT = 4,
+                    KF_SOLVER = 5, KF_OTHER = 6, KF_COUNT = 7 };
+
 struct mpi_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -25,6 +29,14 @@ struct mpi_ctx {
   int num_sms = 0;
   int64_t launches = 0;
   std::string err;
+  // profiling: event pairs around launches while enabled
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_begin, ev_end;
+  std::vector<int> ev_family;
+  int ev_used = 0;
+  int pending_family = -1;
+  double prof_ms[KF_COUNT] = {0};
+  int64_t prof_launches[KF_COUNT] = {0};
 };
 
 struct mpi_plan {
@@ -67,9 +79,17 @@ mpi_status ensure_work(mpi_ctx* ctx, size_t bytes);
 const float2* twiddle_table(const mpi_ctx* ctx, int n);
 bool fft_length_supported(int n);
 
+// Record the start event of the next launch (when profiling is on).
+void prof_begin(mpi_ctx* ctx, int family);
+// Record the end event of the launch just issued.
+void prof_end(mpi_ctx* ctx);
+
+#define MPI_PROF(ctx, fam) prof_begin((ctx), (fam))
+
 #define MPI_LAUNCH_CHECK(ctx, what)                                   \
   do {                                                                \
     (ctx)->launches++;                                                \
+    prof_end(ctx);                                                    \
     cudaError_t e__ = cudaGetLastError();                             \
     if (e__ != cudaSuccess) return cuda_check((ctx), e__, (what));    \
   } while (0)

@@ -200,10 +200,12 @@ mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host)
       e = cudaMemcpy(plan->traj, traj_host, (size_t)M * 2 * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_check(ctx, e, "nufft plan alloc");
     const double kscale = (double)G / (2.0 * M_PI);
+    MPI_PROF(ctx, KF_NUFFT);
     k_nufft_setup<<<blocks_for((size_t)2 * M, 256), 256, 0, ctx->stream>>>(plan->traj, M, G, W, beta, kscale,
                                                                           plan->gstart, plan->gw);
     MPI_LAUNCH_CHECK(ctx, "k_nufft_setup");
   }
+  MPI_PROF(ctx, KF_NUFFT);
   k_nufft_deap<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(n, G, W, beta, plan->deap);
   MPI_LAUNCH_CHECK(ctx, "k_nufft_deap");
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "nufft plan setup");
@@ -212,6 +214,7 @@ mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host)
 mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, int C, float2* y, float2* grid) {
   const int n = plan->nx, G = plan->G, M = plan->M;
   const size_t total = (size_t)C * G * G;
+  MPI_PROF(ctx, KF_NUFFT);
   k_nufft_pad<<<blocks_for(total, 256), 256, 0, ctx->stream>>>(v, C, n, G, plan->deap, grid);
   MPI_LAUNCH_CHECK(ctx, "k_nufft_pad");
   mpi_status st = launch_fft_cols(ctx, grid, C, 1, G, G, false);
@@ -221,6 +224,7 @@ mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, in
   if (M == 0) return MPI_OK;
   const float ks = axis_sign(G) * axis_sign(G);
   const size_t cm = (size_t)C * M;
+  MPI_PROF(ctx, KF_NUFFT);
   switch (plan->W) {
 #define MPI_W_CASE(w)                                                                                \
   case w:                                                                                            \
@@ -244,7 +248,8 @@ mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, in
   if (M > 0) {
     const float ks = axis_sign(G) * axis_sign(G);
     const size_t cm = (size_t)C * M;
-    switch (plan->W) {
+    MPI_PROF(ctx, KF_NUFFT);
+  switch (plan->W) {
 #define MPI_W_CASE(w)                                                                                \
   case w:                                                                                            \
     k_nufft_spread<w><<<blocks_for(cm, 256), 256, 0, ctx->stream>>>(y, C, G, M, plan->gstart,       \
@@ -261,6 +266,7 @@ mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, in
   if (st) return st;
   st = launch_fft_cols(ctx, grid, C, 1, G, G, true);
   if (st) return st;
+  MPI_PROF(ctx, KF_NUFFT);
   k_nufft_crop<<<blocks_for((size_t)C * n * n, 256), 256, 0, ctx->stream>>>(grid, C, n, G, plan->deap, out);
   MPI_LAUNCH_CHECK(ctx, "k_nufft_crop");
   return MPI_OK;

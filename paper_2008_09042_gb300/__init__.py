@@ -18,5 +18,8 @@ from .api import (  # noqa: F401
     forward,
     jacobian,
     jacobian_adjoint,
+    image_solve,
     mpi_operator,
+    sm_estimate,
+    tv_prox,
 )

@@ -251,3 +251,40 @@ class MPIOperator(torch.autograd.Function):
 
 def mpi_operator(p, alpha, ctx, plan, basis, prec="fp32"):
     return MPIOperator.apply(p, alpha, ctx, plan, basis, prec)
+
+
+def sm_estimate(ctx, plan, basis, y, C, n_outer=20, n_cg=10, a0=1.0, b0=1.0, decay=0.5, floor=1e-6, gamma=1.0,
+                scale_target=100.0, prec="fp32"):
+    """MPI-BL (IRGN, Eq. 6).  Returns (alpha [C][q], p [N], residual history (n_outer + 1,))."""
+    _need(y, (C, plan.M), "y")
+    prm = _lib.IrgnParams(n_outer, n_cg, a0, b0, decay, floor, gamma, scale_target)
+    alpha = torch.empty((C, basis.q), dtype=torch.complex64, device=y.device)
+    p = torch.empty((plan.N,), dtype=torch.complex64, device=y.device)
+    hist = np.zeros(n_outer + 1, dtype=np.float64)
+    check(ctx.h, ctx.lib.mpi_sm_estimate(ctx.h, plan.h, basis.h, _ptr(y), C, ctypes.byref(prm), _ptr(alpha), _ptr(p),
+                                         hist.ctypes.data_as(ctypes.c_void_p), PREC[prec]))
+    return alpha, p, hist
+
+
+def image_solve(ctx, plan, basis, alpha, y, eps, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0, tau=2.0,
+                prec="fp32"):
+    """MPI-L (ADMM-TV, Eqs. 8-11).  Returns (p [N], history (n_outer, 3) of primal, dual, rho)."""
+    C = alpha.shape[0]
+    _need(alpha, (C, basis.q), "alpha")
+    _need(y, (C, plan.M), "y")
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(C))
+    prm = _lib.AdmmParams(n_outer, n_cg, n_tv, rho0, mu, tau)
+    p = torch.empty((plan.N,), dtype=torch.complex64, device=y.device)
+    hist = np.zeros((max(n_outer, 1), 3), dtype=np.float64)
+    check(ctx.h, ctx.lib.mpi_image_solve(ctx.h, plan.h, basis.h, _ptr(alpha), C, _ptr(y),
+                                         eps.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _ptr(p),
+                                         hist.ctypes.data_as(ctypes.c_void_p), PREC[prec]))
+    return p, hist[:n_outer]
+
+
+def tv_prox(ctx, plan, v, lam, n_iter):
+    """argmin (1/2)||x - v||^2 + lam TV(x) by n_iter FGP iterations."""
+    _need(v, (plan.N,), "v")
+    x = torch.empty_like(v)
+    check(ctx.h, ctx.lib.mpi_tv_prox(ctx.h, plan.h, _ptr(v), float(lam), int(n_iter), _ptr(x)))
+    return x

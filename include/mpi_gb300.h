@@ -151,6 +151,25 @@ mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* bas
                         const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* dp,
                         const mpi_c32* dalpha, mpi_c32* dy, mpi_precision prec);
 
+/* Allocation-free variant of mpi_forward (Cartesian plans, FP32 expansion).
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc once running -- a service whose device memory is carved up at
+ * start-up by its own pool allocator, or a real-time loop that must not block in
+ * the driver's allocator (cudaMalloc may synchronise the device and can fail at
+ * an unpredictable point).  mpi_forward may grow the context workspace; this
+ * call never allocates: its [C][N] intermediate lives in a 16 MiB static device
+ * array inside the library, held by every GPU that loads the library until the
+ * process exits.  Limit: C * N <= 2,097,152, else MPI_ERR_SHAPE (nothing is
+ * launched).  Radial plans return MPI_ERR_UNSUPPORTED.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call,
+ * from any context, shares the one array: calls whose work overlaps on the GPU
+ * (different streams, or concurrent host threads) race and corrupt each other's
+ * results; serialise them.  The caller still passes every input and output
+ * (device pointers), as for mpi_forward. */
+mpi_status mpi_forward_noalloc(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                               const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y);
+
 /* [dp; dalpha] = J^H(p, alpha) r (the display after Eq. 7; ^H on a vector inside
  * (.) is the element-wise conjugate):
  *   dp        = sum_k conj(U alpha_k) (.) F_s^H r_k            [N]

@@ -24,7 +24,7 @@ EXPORTS = [
     "mpi_last_error", "mpi_ctx_launch_count", "mpi_ctx_profile", "mpi_ctx_profile_read", "mpi_plan_create", "mpi_plan_destroy", "mpi_plan_grid_index",
     "mpi_basis_load_dense", "mpi_basis_destroy", "mpi_basis_expand", "mpi_forward", "mpi_adjoint",
     "mpi_jacobian", "mpi_jacobian_adjoint", "mpi_basis_project", "mpi_sm_estimate", "mpi_image_solve",
-    "mpi_tv_prox",
+    "mpi_tv_prox", "mpi_forward_noalloc",
 ]
 
 
@@ -97,6 +97,7 @@ def load(path=LIB_PATH):
         "mpi_sm_estimate": [vp, vp, vp, vp, i, ctypes.POINTER(IrgnParams), vp, vp, vp, i],
         "mpi_image_solve": [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(AdmmParams), vp, vp, i],
         "mpi_tv_prox": [vp, vp, vp, d, i, vp],
+        "mpi_forward_noalloc": [vp, vp, vp, vp, i, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

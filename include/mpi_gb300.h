@@ -68,6 +68,9 @@ typedef struct mpi_basis mpi_basis;
 mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_stream);
 mpi_status mpi_ctx_destroy(mpi_ctx* ctx);
 mpi_status mpi_ctx_set_stream(mpi_ctx* ctx, void* cuda_stream);
+/* Wait for the context's stream, then read the context's device error word:
+ * a kernel whose bounded barrier wait ran out sets it (and exits early), in
+ * which case this returns MPI_ERR_TIMEOUT and clears the word. */
 mpi_status mpi_ctx_synchronize(mpi_ctx* ctx);
 /* Size the workspace for operator calls with `C` coils on this plan and basis. */
 mpi_status mpi_ctx_reserve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C);

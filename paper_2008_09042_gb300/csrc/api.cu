@@ -91,8 +91,14 @@ mpi_status check_op(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, 
   if (C < 1) return set_err(ctx, MPI_ERR_ARG, "C must be >= 1");
   if (basis->N != plan->N) return set_err(ctx, MPI_ERR_SHAPE, "basis N differs from plan N");
   if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return set_err(ctx, MPI_ERR_ARG, "bad precision");
-  if (prec == MPI_PREC_BF16) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion not built");
+  if (prec == MPI_PREC_BF16 && !basis->Ubf)
+    return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + basis->bf16_err);
   return MPI_OK;
+}
+
+mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec) {
+  if (prec == MPI_PREC_BF16) return launch_expand_tc(ctx, basis, mode, a);
+  return launch_expand(ctx, mode, a);
 }
 
 ExpandArgs base_args(const mpi_plan* plan, const mpi_basis* basis, int C) {
@@ -186,9 +192,13 @@ extern "C" mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_strea
       host.push_back(make_float2((float)cos(ang), (float)sin(ang)));
     }
   }
-  cudaError_t e = cudaMalloc(&ctx->twiddles, host.size() * sizeof(float2));
+  cudaError_t e = cudaMalloc(&ctx->twiddles, host.size() * sizeof(float2) + 256);
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->twiddles, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    ctx->dev_err = (int*)((char*)ctx->twiddles + ((host.size() * sizeof(float2) + 127) & ~(size_t)127));
+    e = cudaMemset(ctx->dev_err, 0, sizeof(int));
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (ctx->twiddles) cudaFree(ctx->twiddles);
@@ -222,7 +232,16 @@ extern "C" mpi_status mpi_ctx_set_stream(mpi_ctx* ctx, void* stream) {
 extern "C" mpi_status mpi_ctx_synchronize(mpi_ctx* ctx) {
   if (!ctx) return MPI_ERR_ARG;
   DeviceGuard g(ctx->device);
-  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  mpi_status st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  if (st) return st;
+  int err = 0;
+  st = cuda_check(ctx, cudaMemcpy(&err, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+  if (st) return st;
+  if (err) {
+    cudaMemset(ctx->dev_err, 0, sizeof(int));
+    return set_err(ctx, MPI_ERR_TIMEOUT, "a kernel gave up on a bounded barrier wait (device error word set)");
+  }
+  return MPI_OK;
 }
 
 extern "C" mpi_status mpi_ctx_reserve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C) {
@@ -416,7 +435,7 @@ extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N
                                            mpi_basis** out) {
   if (!ctx) return MPI_ERR_ARG;
   if (!U || !out) return set_err(ctx, MPI_ERR_ARG, "null basis pointer");
-  if (N < 2 || (N & 1) || q < 1 || q > 256) return set_err(ctx, MPI_ERR_SHAPE, "need even N >= 2 and 1 <= q <= 256");
+  if (N < 4 || (N % 4) || q < 1 || q > 256) return set_err(ctx, MPI_ERR_SHAPE, "need N >= 4 divisible by 4 and 1 <= q <= 256");
   *out = nullptr;
   DeviceGuard g(ctx->device);
   mpi_basis* b = new mpi_basis();
@@ -435,6 +454,19 @@ extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N
     delete b;
     return st == MPI_OK ? MPI_ERR_CUDA : st;
   }
+  // BF16 operand copy for the tensor-core path; without it only FP32 is served
+  if (tc_basis_prepare(ctx, b) != MPI_OK) {
+    b->bf16_err = ctx->err;
+    if (b->Ubf) cudaFree(b->Ubf);
+    b->Ubf = nullptr;
+    tc_basis_release(b);
+  }
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    mpi_status st = cuda_check(ctx, e, "basis conversion");
+    mpi_basis_destroy(b);
+    return st;
+  }
   *out = b;
   return MPI_OK;
 }
@@ -445,6 +477,7 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   cudaStreamSynchronize(b->ctx->stream);
   if (b->U) cudaFree(b->U);
   if (b->Ubf) cudaFree(b->Ubf);
+  tc_basis_release(b);
   delete b;
   return MPI_OK;
 }
@@ -455,8 +488,9 @@ extern "C" mpi_status mpi_basis_expand(mpi_ctx* ctx, const mpi_basis* basis, con
                                        mpi_c32* maps, mpi_precision prec) {
   if (!ctx) return MPI_ERR_ARG;
   if (!basis || bad_ptr(alpha) || bad_ptr(maps) || C < 1) return set_err(ctx, MPI_ERR_ARG, "bad argument");
-  if (prec == MPI_PREC_BF16) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion not built");
-  if (prec != MPI_PREC_FP32) return set_err(ctx, MPI_ERR_ARG, "bad precision");
+  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return set_err(ctx, MPI_ERR_ARG, "bad precision");
+  if (prec == MPI_PREC_BF16 && !basis->Ubf)
+    return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + basis->bf16_err);
   DeviceGuard g(ctx->device);
   ExpandArgs a;
   a.U = basis->U;
@@ -465,6 +499,7 @@ extern "C" mpi_status mpi_basis_expand(mpi_ctx* ctx, const mpi_basis* basis, con
   a.C = C;
   a.alpha = (const float2*)alpha;
   a.out = (float2*)maps;
+  if (prec == MPI_PREC_BF16) return launch_expand_tc(ctx, basis, EX_MAPS, a);
   return launch_expand(ctx, EX_MAPS, a);
 }
 
@@ -481,7 +516,7 @@ extern "C" mpi_status mpi_forward(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   a.alpha = (const float2*)alpha;
   a.p = (const float2*)p;
   a.out = w.A;
-  if ((st = launch_expand(ctx, EX_FWD, a))) return st;
+  if ((st = expand(ctx, basis, EX_FWD, a, prec))) return st;
   return image_to_kspace(ctx, plan, w.A, C, (float2*)y, w.grid);
 }
 
@@ -499,7 +534,7 @@ extern "C" mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   a.alpha = (const float2*)alpha;
   a.w = w.A;
   a.out = (float2*)p_out;
-  return launch_expand(ctx, EX_ADJ, a);
+  return expand(ctx, basis, EX_ADJ, a, prec);
 }
 
 extern "C" mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
@@ -518,7 +553,7 @@ extern "C" mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi
   a.p = (const float2*)p;
   a.dp = (const float2*)dp;
   a.out = w.A;
-  if ((st = launch_expand(ctx, EX_JFWD, a))) return st;
+  if ((st = expand(ctx, basis, EX_JFWD, a, prec))) return st;
   return image_to_kspace(ctx, plan, w.A, C, (float2*)dy, w.grid);
 }
 
@@ -539,6 +574,6 @@ extern "C" mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, c
   a.w = w.A;
   a.out = (float2*)dp;
   a.vout = w.B;
-  if ((st = launch_expand(ctx, EX_JADJ, a))) return st;
+  if ((st = expand(ctx, basis, EX_JADJ, a, prec))) return st;
   return launch_uh_v(ctx, basis->U, basis->N, basis->q, w.B, C, (float2*)dalpha, w.partials, w.partial_cap);
 }

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "mpi_internal.h"
+#include "ptx.cuh"
 
 namespace {
 
@@ -41,115 +42,140 @@ __device__ __forceinline__ float centre_sign(int n, int nx, int ny) {
   return ((x + y + z) & 1) ? -1.f : 1.f;
 }
 
-constexpr int kExpandThreads = 128;
+constexpr int kExpandMaxThreads = 512;
+constexpr int kPrefetch = 8;  // basis rows of U kept in flight per thread
 
-// One thread per pixel.  MODE selects the epilogue; CB coils per pass.
-// Forward-type modes (MAPS, FWD, JFWD) split coil blocks over blockIdx.y;
-// adjoint-type modes (ADJ, JADJ) loop over all coil blocks to sum over coils.
+// One thread per pixel, grid sized so that every SM gets the same number of
+// pixels.  All coils' coefficients sit in shared memory as [q_pad][c_pad]
+// (zero padded), read as warp-wide broadcasts, CB coils per pass.  U[j][n] is
+// prefetched kPrefetch rows ahead into registers so that each thread keeps
+// that many independent loads in flight while it does the FFMAs of the
+// previous rows.  Forward-type modes (MAPS, FWD, JFWD) split coil blocks over
+// blockIdx.y (the CTAs of one pixel range run together, so the second read of
+// U hits L2); adjoint-type modes (ADJ, JADJ) loop over all coil blocks to sum
+// over coils.
 template <int MODE, int CB>
-__global__ void __launch_bounds__(kExpandThreads) k_expand(ExpandArgs a) {
+__global__ void __launch_bounds__(kExpandMaxThreads) k_expand(ExpandArgs a, int q_pad, int c_pad) {
   extern __shared__ float4 smem4[];
-  float2* sA = reinterpret_cast<float2*>(smem4);  // [q][CB]
-  float2* sD = sA + a.q * CB;                      // [q][CB], Jacobian only
+  float2* sA = reinterpret_cast<float2*>(smem4);  // [q_pad][c_pad]
+  float2* sD = sA + (size_t)q_pad * c_pad;         // [q_pad][c_pad], Jacobian only
   const int tid = threadIdx.x;
-  const int n = blockIdx.x * kExpandThreads + tid;
-  const bool active = n < a.N;
-  const float sg = active ? (a.centre ? centre_sign(n, a.nx, a.ny) : 1.f) * a.scale : 0.f;
   constexpr bool kAdjLike = (MODE == EX_ADJ || MODE == EX_JADJ);
+  for (int e = tid; e < q_pad * c_pad; e += blockDim.x) {
+    const int j = e / c_pad, c = e % c_pad;
+    const bool ok = c < a.C && j < a.q;
+    sA[e] = ok ? a.alpha[(size_t)c * a.q + j] : make_float2(0.f, 0.f);
+    if (MODE == EX_JFWD) sD[e] = ok ? a.dalpha[(size_t)c * a.q + j] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
   const int cb_begin = kAdjLike ? 0 : blockIdx.y * CB;
   const int cb_end = kAdjLike ? a.C : min(a.C, cb_begin + CB);
-  float2 pimg = make_float2(0.f, 0.f);
-  float2 pacc = make_float2(0.f, 0.f);
-  if (active && MODE != EX_MAPS) pimg = a.p[n];
 
-  for (int c0 = cb_begin; c0 < cb_end; c0 += CB) {
-    __syncthreads();
-    for (int e = tid; e < a.q * CB; e += kExpandThreads) {
-      const int j = e / CB, c = e % CB;
-      const bool ok = (c0 + c) < a.C;
-      sA[e] = ok ? a.alpha[(size_t)(c0 + c) * a.q + j] : make_float2(0.f, 0.f);
-      if (MODE == EX_JFWD) sD[e] = ok ? a.dalpha[(size_t)(c0 + c) * a.q + j] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    if (!active) continue;
-
-    float2 acc[CB];
-    float2 dacc[MODE == EX_JFWD ? CB : 1];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) acc[c] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int c = 0; c < (MODE == EX_JFWD ? CB : 1); ++c) dacc[c] = make_float2(0.f, 0.f);
-
+  for (int n = blockIdx.x * blockDim.x + tid; n < a.N; n += gridDim.x * blockDim.x) {
+    const float sg = (a.centre ? centre_sign(n, a.nx, a.ny) : 1.f) * a.scale;
+    const float2 pimg = (MODE != EX_MAPS) ? a.p[n] : make_float2(0.f, 0.f);
+    float2 pacc = make_float2(0.f, 0.f);
     const float2* Up = a.U + n;
-#pragma unroll 4
-    for (int j = 0; j < a.q; ++j) {
-      const float2 u = __ldg(Up + (size_t)j * a.N);
-      const float4* ap = reinterpret_cast<const float4*>(sA + j * CB);
+    for (int c0 = cb_begin; c0 < cb_end; c0 += CB) {
+      float2 acc[CB];
+      float2 dacc[MODE == EX_JFWD ? CB : 1];
 #pragma unroll
-      for (int c2 = 0; c2 < CB / 2; ++c2) {
-        const float4 av = ap[c2];
-        cfma(acc[2 * c2], u, make_float2(av.x, av.y));
-        cfma(acc[2 * c2 + 1], u, make_float2(av.z, av.w));
-      }
-      if (MODE == EX_JFWD) {
-        const float4* dpp = reinterpret_cast<const float4*>(sD + j * CB);
+      for (int c = 0; c < CB; ++c) acc[c] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c2 = 0; c2 < CB / 2; ++c2) {
-          const float4 dv = dpp[c2];
-          cfma(dacc[2 * c2], u, make_float2(dv.x, dv.y));
-          cfma(dacc[2 * c2 + 1], u, make_float2(dv.z, dv.w));
-        }
-      }
-    }
+      for (int c = 0; c < (MODE == EX_JFWD ? CB : 1); ++c) dacc[c] = make_float2(0.f, 0.f);
 
-    if (MODE == EX_MAPS) {
+      float2 ubuf[kPrefetch];
 #pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (c0 + c < a.C) a.out[(size_t)(c0 + c) * a.N + n] = acc[c];
-    } else if (MODE == EX_FWD) {
+      for (int t = 0; t < kPrefetch; ++t)
+        ubuf[t] = t < a.q ? __ldg(Up + (size_t)t * a.N) : make_float2(0.f, 0.f);
+      for (int j0 = 0; j0 < q_pad; j0 += kPrefetch) {
+        float2 nbuf[kPrefetch];
 #pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (c0 + c < a.C) a.out[(size_t)(c0 + c) * a.N + n] = cscale(cmul(acc[c], pimg), sg);
-    } else if (MODE == EX_JFWD) {
-      const float2 dpi = a.dp[n];
-#pragma unroll
-      for (int c = 0; c < CB; ++c) {
-        if (c0 + c < a.C) {
-          float2 v = cmul(acc[c], dpi);
-          const float2 t = cmul(dacc[c], pimg);
-          v.x += t.x;
-          v.y += t.y;
-          a.out[(size_t)(c0 + c) * a.N + n] = cscale(v, sg);
+        for (int t = 0; t < kPrefetch; ++t) {
+          const int jn = j0 + kPrefetch + t;
+          nbuf[t] = jn < a.q ? __ldg(Up + (size_t)jn * a.N) : make_float2(0.f, 0.f);
         }
-      }
-    } else {  // ADJ / JADJ
 #pragma unroll
-      for (int c = 0; c < CB; ++c) {
-        if (c0 + c < a.C) {
-          const float2 wv = a.w[(size_t)(c0 + c) * a.N + n];
-          cfma_conj(pacc, acc[c], wv);
-          if (MODE == EX_JADJ)
-            a.vout[(size_t)(c0 + c) * a.N + n] = cscale(cmul_conj(pimg, wv), sg);
+        for (int t = 0; t < kPrefetch; ++t) {
+          const float2 u = ubuf[t];
+          const float4* ap = reinterpret_cast<const float4*>(sA + (size_t)(j0 + t) * c_pad + c0);
+#pragma unroll
+          for (int c2 = 0; c2 < CB / 2; ++c2) {
+            const float4 av = ap[c2];
+            cfma(acc[2 * c2], u, make_float2(av.x, av.y));
+            cfma(acc[2 * c2 + 1], u, make_float2(av.z, av.w));
+          }
+          if (MODE == EX_JFWD) {
+            const float4* dpp = reinterpret_cast<const float4*>(sD + (size_t)(j0 + t) * c_pad + c0);
+#pragma unroll
+            for (int c2 = 0; c2 < CB / 2; ++c2) {
+              const float4 dv = dpp[c2];
+              cfma(dacc[2 * c2], u, make_float2(dv.x, dv.y));
+              cfma(dacc[2 * c2 + 1], u, make_float2(dv.z, dv.w));
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < kPrefetch; ++t) ubuf[t] = nbuf[t];
+      }
+
+      if (MODE == EX_MAPS) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c)
+          if (c0 + c < a.C) a.out[(size_t)(c0 + c) * a.N + n] = acc[c];
+      } else if (MODE == EX_FWD) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c)
+          if (c0 + c < a.C) a.out[(size_t)(c0 + c) * a.N + n] = cscale(cmul(acc[c], pimg), sg);
+      } else if (MODE == EX_JFWD) {
+        const float2 dpi = a.dp[n];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          if (c0 + c < a.C) {
+            float2 v = cmul(acc[c], dpi);
+            const float2 t = cmul(dacc[c], pimg);
+            v.x += t.x;
+            v.y += t.y;
+            a.out[(size_t)(c0 + c) * a.N + n] = cscale(v, sg);
+          }
+        }
+      } else {  // ADJ / JADJ
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          if (c0 + c < a.C) {
+            const float2 wv = a.w[(size_t)(c0 + c) * a.N + n];
+            cfma_conj(pacc, acc[c], wv);
+            if (MODE == EX_JADJ)
+              a.vout[(size_t)(c0 + c) * a.N + n] = cscale(cmul_conj(pimg, wv), sg);
+          }
         }
       }
     }
+    if (kAdjLike) a.out[n] = cscale(pacc, sg);
   }
-  if (kAdjLike && active) a.out[n] = cscale(pacc, sg);
 }
 
 template <int MODE, int CB>
 mpi_status launch_mode(mpi_ctx* ctx, const ExpandArgs& a) {
-  const size_t smem = (size_t)a.q * CB * sizeof(float2) * (MODE == EX_JFWD ? 2 : 1);
+  const int q_pad = ((a.q + kPrefetch - 1) / kPrefetch) * kPrefetch;
+  const int c_pad = ((a.C + CB - 1) / CB) * CB;
+  const size_t smem = (size_t)q_pad * c_pad * sizeof(float2) * (MODE == EX_JFWD ? 2 : 1);
+  if (smem > 200 * 1024) return set_err(ctx, MPI_ERR_UNSUPPORTED, "coefficient block too large for shared memory");
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_expand<MODE, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "expand smem attribute");
   }
-  const int gx = (a.N + kExpandThreads - 1) / kExpandThreads;
+  // every SM gets the same number of pixels: grid = k * SMs CTAs of a warp multiple
+  const long sms = std::max(ctx->num_sms, 1);
+  const long k = std::max(1L, ((long)a.N + sms * kExpandMaxThreads - 1) / (sms * kExpandMaxThreads));
+  const long grid = sms * k;
+  const int block = std::max(32, (int)(32 * (((long)a.N + grid * 32 - 1) / (grid * 32))));
   const bool adj_like = (MODE == EX_ADJ || MODE == EX_JADJ);
   const int gy = adj_like ? 1 : (a.C + CB - 1) / CB;
+  const long gx = std::min(grid, ((long)a.N + block - 1) / block);
   MPI_PROF(ctx, KF_EXPAND);
-  k_expand<MODE, CB><<<dim3(gx, gy), kExpandThreads, smem, ctx->stream>>>(a);
+  k_expand<MODE, CB><<<dim3((unsigned)gx, gy), block, smem, ctx->stream>>>(a, q_pad, c_pad);
   MPI_LAUNCH_CHECK(ctx, "k_expand");
   return MPI_OK;
 }
@@ -240,8 +266,8 @@ int uhv_blocks(const mpi_ctx* ctx, int N) {
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a) {
   if (a.N <= 0 || a.C <= 0) return MPI_OK;
   switch (mode) {
-    case EX_MAPS: return launch_mode<EX_MAPS, 16>(ctx, a);
-    case EX_FWD: return launch_mode<EX_FWD, 16>(ctx, a);
+    case EX_MAPS: return launch_mode<EX_MAPS, 8>(ctx, a);
+    case EX_FWD: return launch_mode<EX_FWD, 8>(ctx, a);
     case EX_JFWD: return launch_mode<EX_JFWD, 8>(ctx, a);
     case EX_ADJ: return launch_mode<EX_ADJ, 16>(ctx, a);
     case EX_JADJ: return launch_mode<EX_JADJ, 16>(ctx, a);

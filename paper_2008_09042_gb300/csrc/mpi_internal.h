@@ -27,6 +27,7 @@ struct mpi_ctx {
   float2* twiddles = nullptr;  // all tables back to back
   int tw_offset[kNumFftLengths] = {0};
   int num_sms = 0;
+  int* dev_err = nullptr;  // device error word written by kernels whose waits time out
   int64_t launches = 0;
   std::string err;
   // profiling: event pairs around launches while enabled
@@ -66,8 +67,11 @@ struct mpi_basis {
   mpi_ctx* ctx = nullptr;
   int N = 0, q = 0;
   float2* U = nullptr;  // [q][N] FP32 complex
-  __nv_bfloat16* Ubf = nullptr;  // BF16 operand copy (layout owned by the tensor-core path)
+  __nv_bfloat16* Ubf = nullptr;  // BF16 operand copy [N][Kp] (tensor-core path)
   size_t Ubf_bytes = 0;
+  int Kp = 0;                    // padded K = round_up(2 q, 64)
+  void* tmap = nullptr;          // CUtensorMap of Ubf (owned)
+  std::string bf16_err;          // why the BF16 copy is missing, if it is
 };
 
 // ------------------------------------------------------------------ helpers
@@ -112,9 +116,14 @@ struct ExpandArgs {
   const float2* w = nullptr;   // [C][N] adjoint input (after inverse FFT passes)
   float2* out = nullptr;       // maps / v [C][N], or image [N]
   float2* vout = nullptr;      // Jacobian adjoint: conj(p) w [C][N]
+  int* err = nullptr;          // device error word (bounded-wait timeouts)
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
+// BF16 tensor-core expansion (tcgen05); same modes and arguments.
+mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a);
+mpi_status tc_basis_prepare(mpi_ctx* ctx, mpi_basis* b);
+void tc_basis_release(mpi_basis* b);
 // dalpha[c][j] = sum_n conj(U[j][n]) V[c][n]; partials in `work_partials`.
 mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
                        float2* dalpha, float2* work_partials, size_t partial_cap_elems);

@@ -130,6 +130,17 @@ mpi_status mpi_plan_grid_index(mpi_ctx* ctx, const mpi_plan* plan, int32_t* out_
  * copies (FP32, and a BF16 copy for MPI_PREC_BF16). */
 mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N, int q, int on_device,
                                 mpi_basis** out);
+/* Tucker-factored basis for a 3D grid (n1, n2, n3) = (nz, ny, nx) ("A Compression
+ * Scheme for Maxwell Basis", Eqs. 19-20): basis column j reshaped onto the grid
+ * is G_j x1 U1 x2 U2 x3 U3, with the core G given as [q][r1][r2][r3] (the core
+ * slice of column j contiguous) and factors U_k as [n_k][r_k] (row-major), all
+ * complex64; host pointers when on_device = 0, else device pointers.  Limits:
+ * 1 <= r_k <= n_k <= 128, r1 r2 r3 and n1 n2 n3 multiples of 4, q <= 256.  The
+ * operators expand maps as (G x4 alpha_c^T) x1 U1 x2 U2 x3 U3 (the core
+ * contraction in FP32 or on BF16 tensor cores, the mode products in FP32). */
+mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, const mpi_c32* U1, const mpi_c32* U2,
+                                 const mpi_c32* U3, const int n[3], const int r[3], int q, int on_device,
+                                 mpi_basis** out);
 mpi_status mpi_basis_destroy(mpi_basis* basis);
 
 /* ------------------------------------------------------- operator (device) */

@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     Context,
     MPIOperator,
     Plan,
+    TuckerBasis,
     adjoint,
     basis_expand,
     basis_project,

@@ -22,7 +22,7 @@ PREC = {"fp32": 0, "bf16": 1}
 EXPORTS = [
     "mpi_ctx_create", "mpi_ctx_destroy", "mpi_ctx_set_stream", "mpi_ctx_synchronize", "mpi_ctx_reserve",
     "mpi_last_error", "mpi_ctx_launch_count", "mpi_ctx_profile", "mpi_ctx_profile_read", "mpi_plan_create", "mpi_plan_destroy", "mpi_plan_grid_index",
-    "mpi_basis_load_dense", "mpi_basis_destroy", "mpi_basis_expand", "mpi_forward", "mpi_adjoint",
+    "mpi_basis_load_dense", "mpi_basis_load_tucker", "mpi_basis_destroy", "mpi_basis_expand", "mpi_forward", "mpi_adjoint",
     "mpi_jacobian", "mpi_jacobian_adjoint", "mpi_basis_project", "mpi_sm_estimate", "mpi_image_solve",
     "mpi_tv_prox", "mpi_forward_noalloc",
 ]
@@ -87,6 +87,8 @@ def load(path=LIB_PATH):
         "mpi_plan_destroy": [vp],
         "mpi_plan_grid_index": [vp, vp, vp],
         "mpi_basis_load_dense": [vp, vp, i, i, i, pp],
+        "mpi_basis_load_tucker": [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  i, i, pp],
         "mpi_basis_destroy": [vp],
         "mpi_basis_expand": [vp, vp, vp, i, vp, i],
         "mpi_forward": [vp, vp, vp, vp, i, vp, vp, i],

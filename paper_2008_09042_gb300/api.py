@@ -170,6 +170,31 @@ class Basis:
             pass
 
 
+class TuckerBasis(Basis):
+    """Tucker-factored basis: core (r1, r2, r3, q) and factors U_k (n_k, r_k).
+
+    The library takes the core as [q][r1][r2][r3]; this constructor transposes.
+    """
+
+    def __init__(self, ctx, core, factors):
+        self.ctx = ctx
+        core = np.asarray(core)
+        r = core.shape[:3]
+        self.q = int(core.shape[3])
+        n = tuple(int(f.shape[0]) for f in factors)
+        self.N = int(np.prod(n))
+        core_q = np.ascontiguousarray(np.moveaxis(core, 3, 0).astype(np.complex64))
+        fac = [np.ascontiguousarray(np.asarray(f, dtype=np.complex64)) for f in factors]
+        keep = [core_q] + fac
+        n_arr = (ctypes.c_int * 3)(*n)
+        r_arr = (ctypes.c_int * 3)(*[int(x) for x in r])
+        h = ctypes.c_void_p()
+        check(ctx.h, ctx.lib.mpi_basis_load_tucker(ctx.h, core_q.ctypes.data, fac[0].ctypes.data, fac[1].ctypes.data,
+                                                   fac[2].ctypes.data, n_arr, r_arr, self.q, 0, ctypes.byref(h)))
+        del keep
+        self.h = h
+
+
 def basis_expand(ctx, basis, alpha, prec="fp32", out=None):
     C = alpha.shape[0]
     _need(alpha, (C, basis.q), "alpha")

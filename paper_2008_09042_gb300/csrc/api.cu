@@ -75,12 +75,19 @@ struct DeviceGuard {
 
 bool bad_ptr(const void* p) { return p == nullptr; }
 
+size_t partial_elems(const mpi_ctx* ctx, const mpi_basis* basis, int C) {
+  if (!basis) return 0;
+  const mpi_basis* b = basis->tucker ? basis->core : basis;
+  return uh_v_partial_elems(ctx, b->N, b->q, C);
+}
+
 size_t op_work_bytes(const mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C) {
   const size_t cn = (size_t)C * plan->N;
   size_t grid = 0;
   if (plan->kind == MPI_TRAJ_RADIAL) grid = (size_t)C * plan->G * plan->G;
-  size_t partial = basis ? uh_v_partial_elems(ctx, basis->N, basis->q, C) : 0;
-  return (2 * cn + grid + partial) * sizeof(float2) + 4096;
+  size_t partial = partial_elems(ctx, basis, C);
+  size_t tucker = (basis && basis->tucker) ? 2 * cn + tucker_work_elems(basis, C) : 0;
+  return (2 * cn + grid + partial + tucker) * sizeof(float2) + 4096;
 }
 
 mpi_status check_op(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C,
@@ -91,8 +98,9 @@ mpi_status check_op(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, 
   if (C < 1) return set_err(ctx, MPI_ERR_ARG, "C must be >= 1");
   if (basis->N != plan->N) return set_err(ctx, MPI_ERR_SHAPE, "basis N differs from plan N");
   if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return set_err(ctx, MPI_ERR_ARG, "bad precision");
-  if (prec == MPI_PREC_BF16 && !basis->Ubf)
-    return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + basis->bf16_err);
+  const mpi_basis* eb = basis->tucker ? basis->core : basis;
+  if (prec == MPI_PREC_BF16 && !eb->Ubf)
+    return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + eb->bf16_err);
   return MPI_OK;
 }
 
@@ -149,6 +157,9 @@ struct Work {
   float2* grid;
   float2* partials;
   size_t partial_cap;
+  float2* S;   // Tucker: per-coil maps [C][N]
+  float2* dS;  // Tucker: per-coil Jacobian maps [C][N]
+  float2* T;   // Tucker: core / mode-product intermediates
 };
 
 mpi_status carve_work(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C, Work* w) {
@@ -161,8 +172,22 @@ mpi_status carve_work(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis
   size_t grid = plan->kind == MPI_TRAJ_RADIAL ? (size_t)C * plan->G * plan->G : 0;
   w->grid = base + 2 * cn;
   w->partials = base + 2 * cn + grid;
-  w->partial_cap = uh_v_partial_elems(ctx, basis->N, basis->q, C);
+  w->partial_cap = partial_elems(ctx, basis, C);
+  w->S = w->partials + w->partial_cap;
+  w->dS = w->S + cn;
+  w->T = w->dS + cn;
   return MPI_OK;
+}
+
+// Expansion fused with the point-wise products for dense bases; for Tucker
+// bases the maps are materialised first and combined point-wise.
+mpi_status run_expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec,
+                      const Work& w) {
+  if (!basis->tucker) return expand(ctx, basis, mode, a, prec);
+  mpi_status st = tucker_maps(ctx, basis, a.alpha, a.C, w.S, w.T, prec);
+  if (st) return st;
+  if (mode == EX_JFWD && (st = tucker_maps(ctx, basis, a.dalpha, a.C, w.dS, w.T, prec))) return st;
+  return launch_pointwise(ctx, mode, a, w.S, w.dS);
 }
 
 }  // namespace
@@ -471,6 +496,49 @@ extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N
   return MPI_OK;
 }
 
+extern "C" mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, const mpi_c32* U1, const mpi_c32* U2,
+                                            const mpi_c32* U3, const int n[3], const int r[3], int q, int on_device,
+                                            mpi_basis** out) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!core || !U1 || !U2 || !U3 || !n || !r || !out) return set_err(ctx, MPI_ERR_ARG, "null Tucker argument");
+  *out = nullptr;
+  for (int k = 0; k < 3; ++k)
+    if (n[k] < 1 || r[k] < 1 || r[k] > n[k] || r[k] > 128 || n[k] > 128 * 4096)
+      return set_err(ctx, MPI_ERR_SHAPE, "Tucker ranks must satisfy 1 <= r_k <= min(n_k, 128)");
+  if (n[1] > 128 || n[2] > 128 || n[0] > 128)
+    return set_err(ctx, MPI_ERR_SHAPE, "Tucker factor lengths above 128 are not supported");
+  const long long R = (long long)r[0] * r[1] * r[2];
+  const long long N = (long long)n[0] * n[1] * n[2];
+  if (R % 4 || N % 4 || N > (1LL << 31) - 1) return set_err(ctx, MPI_ERR_SHAPE, "Tucker sizes (R, N must be multiples of 4)");
+  DeviceGuard g(ctx->device);
+  mpi_basis* cb = nullptr;
+  mpi_status st = mpi_basis_load_dense(ctx, core, (int)R, q, on_device, &cb);
+  if (st) return st;
+  mpi_basis* b = new mpi_basis();
+  b->ctx = ctx;
+  b->N = (int)N;
+  b->q = q;
+  b->tucker = true;
+  b->core = cb;
+  const mpi_c32* src[3] = {U1, U2, U3};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    b->n[k] = n[k];
+    b->r[k] = r[k];
+    const size_t bytes = (size_t)n[k] * r[k] * sizeof(float2);
+    e = cudaMalloc(&b->F[k], bytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->F[k], src[k], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    st = cuda_check(ctx, e, "Tucker factor upload");
+    mpi_basis_destroy(b);
+    return st;
+  }
+  *out = b;
+  return MPI_OK;
+}
+
 extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   if (!b) return MPI_ERR_ARG;
   DeviceGuard g(b->ctx->device);
@@ -478,6 +546,9 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   if (b->U) cudaFree(b->U);
   if (b->Ubf) cudaFree(b->Ubf);
   tc_basis_release(b);
+  for (int k = 0; k < 3; ++k)
+    if (b->F[k]) cudaFree(b->F[k]);
+  if (b->core) mpi_basis_destroy(b->core);
   delete b;
   return MPI_OK;
 }
@@ -489,9 +560,15 @@ extern "C" mpi_status mpi_basis_expand(mpi_ctx* ctx, const mpi_basis* basis, con
   if (!ctx) return MPI_ERR_ARG;
   if (!basis || bad_ptr(alpha) || bad_ptr(maps) || C < 1) return set_err(ctx, MPI_ERR_ARG, "bad argument");
   if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return set_err(ctx, MPI_ERR_ARG, "bad precision");
-  if (prec == MPI_PREC_BF16 && !basis->Ubf)
-    return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + basis->bf16_err);
+  const mpi_basis* eb = basis->tucker ? basis->core : basis;
+  if (prec == MPI_PREC_BF16 && !eb->Ubf)
+    return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + eb->bf16_err);
   DeviceGuard g(ctx->device);
+  if (basis->tucker) {
+    mpi_status st = ensure_work(ctx, tucker_work_elems(basis, C) * sizeof(float2) + 4096);
+    if (st) return st;
+    return tucker_maps(ctx, basis, (const float2*)alpha, C, (float2*)maps, (float2*)ctx->work, prec);
+  }
   ExpandArgs a;
   a.U = basis->U;
   a.N = basis->N;
@@ -516,7 +593,7 @@ extern "C" mpi_status mpi_forward(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   a.alpha = (const float2*)alpha;
   a.p = (const float2*)p;
   a.out = w.A;
-  if ((st = expand(ctx, basis, EX_FWD, a, prec))) return st;
+  if ((st = run_expand(ctx, basis, EX_FWD, a, prec, w))) return st;
   return image_to_kspace(ctx, plan, w.A, C, (float2*)y, w.grid);
 }
 
@@ -534,7 +611,7 @@ extern "C" mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   a.alpha = (const float2*)alpha;
   a.w = w.A;
   a.out = (float2*)p_out;
-  return expand(ctx, basis, EX_ADJ, a, prec);
+  return run_expand(ctx, basis, EX_ADJ, a, prec, w);
 }
 
 extern "C" mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
@@ -553,7 +630,7 @@ extern "C" mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi
   a.p = (const float2*)p;
   a.dp = (const float2*)dp;
   a.out = w.A;
-  if ((st = expand(ctx, basis, EX_JFWD, a, prec))) return st;
+  if ((st = run_expand(ctx, basis, EX_JFWD, a, prec, w))) return st;
   return image_to_kspace(ctx, plan, w.A, C, (float2*)dy, w.grid);
 }
 
@@ -574,6 +651,7 @@ extern "C" mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, c
   a.w = w.A;
   a.out = (float2*)dp;
   a.vout = w.B;
-  if ((st = expand(ctx, basis, EX_JADJ, a, prec))) return st;
+  if ((st = run_expand(ctx, basis, EX_JADJ, a, prec, w))) return st;
+  if (basis->tucker) return tucker_adjoint(ctx, basis, w.B, C, (float2*)dalpha, w.T, w.partials, w.partial_cap);
   return launch_uh_v(ctx, basis->U, basis->N, basis->q, w.B, C, (float2*)dalpha, w.partials, w.partial_cap);
 }

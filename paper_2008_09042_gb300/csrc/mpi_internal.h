@@ -72,6 +72,12 @@ struct mpi_basis {
   int Kp = 0;                    // padded K = round_up(2 q, 64)
   void* tmap = nullptr;          // CUtensorMap of Ubf (owned)
   std::string bf16_err;          // why the BF16 copy is missing, if it is
+  // Tucker-factored basis (3D): N = n1 n2 n3; the core (r1 r2 r3 x q) is held
+  // as an internal dense basis `core`; factors F[k] = U_k [n_k][r_k].
+  bool tucker = false;
+  int n[3] = {0, 0, 0}, r[3] = {0, 0, 0};
+  float2* F[3] = {nullptr, nullptr, nullptr};
+  mpi_basis* core = nullptr;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -128,6 +134,14 @@ void tc_basis_release(mpi_basis* b);
 mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
                        float2* dalpha, float2* work_partials, size_t partial_cap_elems);
 size_t uh_v_partial_elems(const mpi_ctx* ctx, int N, int q, int C);
+
+// Tucker basis: per-coil maps, the adjoint contraction, point-wise epilogues.
+size_t tucker_work_elems(const mpi_basis* b, int C);
+mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
+                       mpi_precision prec);
+mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,
+                          float2* partials, size_t partial_cap);
+mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS);
 
 // ------------------------------------------------------------ FFT passes
 

@@ -55,6 +55,7 @@ extern "C" mpi_status mpi_forward_noalloc(mpi_ctx* ctx, const mpi_plan* plan, co
   if (basis->N != plan->N) return set_err(ctx, MPI_ERR_SHAPE, "basis N differs from plan N");
   if (plan->kind != MPI_TRAJ_CARTESIAN)
     return set_err(ctx, MPI_ERR_UNSUPPORTED, "forward_noalloc: Cartesian plans only");
+  if (basis->tucker) return set_err(ctx, MPI_ERR_UNSUPPORTED, "forward_noalloc: dense bases only");
   if ((size_t)C * (size_t)plan->N > kNoallocScratchElems)
     return set_err(ctx, MPI_ERR_SHAPE,
                    "forward_noalloc: C * N exceeds the 2,097,152-element (16 MiB) static scratch");

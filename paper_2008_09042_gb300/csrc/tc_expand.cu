@@ -31,11 +31,11 @@ namespace {
 constexpr int kTileM = 128;
 constexpr int kKChunk = 64;                  // BF16 elements per 128-byte swizzle row
 constexpr int kStageBytes = kTileM * 128;    // one 128 x 64 BF16 tile
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr int kThreads = 192;
 
 struct TcArgs {
-  int N, q, C, KC, n_gemm, half, tmem_cols;
+  int N, q, C, KC, n_gemm, half, half_cols, tmem_cols;
   int nx, ny, centre;
   float scale;
   const float2* alpha;
@@ -129,7 +129,7 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k, int rows) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_expand_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int Kp = a.KC * kKChunk;
@@ -138,9 +138,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_expand_tc(const __grid_constant
   unsigned char* sA = smem + ((b_bytes + 1023) & ~1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(sA + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* acc_full = empty + kStages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_empty + 1;
+  uint64_t* acc_full = empty + kStages;  // [2]: double-buffered accumulator
+  uint64_t* acc_empty = acc_full + 2;    // [2]
+  uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_failed;
 
@@ -173,8 +173,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_expand_tc(const __grid_constant
       mpi_ptx::mbar_init(&full[s], 1);
       mpi_ptx::mbar_init(&empty[s], 1);
     }
-    mpi_ptx::mbar_init(acc_full, 1);
-    mpi_ptx::mbar_init(acc_empty, 4);
+    for (int b = 0; b < 2; ++b) {
+      mpi_ptx::mbar_init(&acc_full[b], 1);
+      mpi_ptx::mbar_init(&acc_empty[b], 4);
+    }
     mpi_ptx::mbar_init(drain, 1);
     mpi_ptx::fence_mbar_init();
   }
@@ -221,7 +223,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_expand_tc(const __grid_constant
     int tc = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tc) {
-      if (!mpi_ptx::mbar_wait(acc_empty, (uint32_t)((tc & 1) ^ 1), a.err)) {
+      const int buf = tc & 1;
+      const uint32_t tacc = tmem + (uint32_t)(buf * a.half_cols);
+      if (!mpi_ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), a.err)) {
         ok = false;
         break;
       }
@@ -237,11 +241,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_expand_tc(const __grid_constant
         for (int ks = 0; ks < kKChunk / 16; ++ks) {
           const uint64_t ad = sdesc_sw128(a_base + s * kStageBytes + ks * 32);
           const uint64_t bd = sdesc_sw128(b_base + kc * a.n_gemm * 128 + ks * 32);
-          mma_bf16(tmem, ad, bd, idesc, (kc | ks) != 0);
+          mma_bf16(tacc, ad, bd, idesc, (kc | ks) != 0);
         }
         mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
       }
-      if (ok) mma_commit(acc_full);
+      if (ok) mma_commit(&acc_full[buf]);
     }
     // all MMAs issued by this thread have completed once `drain` fires
     mma_commit(drain);
@@ -251,57 +255,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_expand_tc(const __grid_constant
     // ---------------- epilogue: one pixel per thread
     const int quarter = warp & 3;  // TMEM lanes 32 * quarter ..
     const int row = quarter * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16);
     int tc = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tc) {
-      const bool got = mpi_ptx::mbar_wait(acc_full, (uint32_t)(tc & 1), a.err);
+      const int buf = tc & 1;
+      const bool got = mpi_ptx::mbar_wait(&acc_full[buf], (uint32_t)((tc >> 1) & 1), a.err);
       if (!__all_sync(0xffffffffu, got)) {  // warp-uniform decision before the .sync.aligned loads
         s_failed = 1;
         break;
       }
       fence_after();
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * a.half_cols);
       const int n = t * kTileM + row;
       const bool valid = n < a.N;
-      const float sg = valid ? (a.centre ? centre_sign(n, a.nx, a.ny) : 1.f) * a.scale : 0.f;
-      const float2 pimg = (valid && MODE != EX_MAPS) ? a.p[n] : make_float2(0.f, 0.f);
+      const int nn = valid ? n : 0;
+      const float sg = (a.centre ? centre_sign(nn, a.nx, a.ny) : 1.f) * a.scale;
+      const float2 pimg = (MODE != EX_MAPS) ? a.p[nn] : make_float2(0.f, 0.f);
+      const float2 dpi = (MODE == EX_JFWD) ? a.dp[nn] : make_float2(0.f, 0.f);
       float2 pacc = make_float2(0.f, 0.f);
       const int n_chunks = (2 * a.C + 15) / 16;
       for (int ch = 0; ch < n_chunks; ++ch) {
+        // issue this chunk's per-coil loads before the accumulator reads
+        float2 wv[8];
+        if (MODE == EX_ADJ || MODE == EX_JADJ) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int c = min(ch * 8 + i, a.C - 1);
+            wv[i] = a.w[(size_t)c * a.N + nn];
+          }
+        }
         float r[16];
         tmem_ld16(tbase + ch * 16, r);
         float rd[16];
         if (MODE == EX_JFWD) tmem_ld16(tbase + a.half + ch * 16, rd);
-        if (!valid) continue;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int c = ch * 8 + i;
-          if (c >= a.C) break;
+          const bool cv = valid && c < a.C;
           const float2 s = make_float2(r[2 * i], r[2 * i + 1]);
           if (MODE == EX_MAPS) {
-            a.out[(size_t)c * a.N + n] = s;
+            if (cv) a.out[(size_t)c * a.N + n] = s;
           } else if (MODE == EX_FWD) {
             const float2 v = cmul(s, pimg);
-            a.out[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
+            if (cv) a.out[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
           } else if (MODE == EX_JFWD) {
             const float2 ds = make_float2(rd[2 * i], rd[2 * i + 1]);
-            const float2 v1 = cmul(s, a.dp[n]);
+            const float2 v1 = cmul(s, dpi);
             const float2 v2 = cmul(ds, pimg);
-            a.out[(size_t)c * a.N + n] = make_float2((v1.x + v2.x) * sg, (v1.y + v2.y) * sg);
+            if (cv) a.out[(size_t)c * a.N + n] = make_float2((v1.x + v2.x) * sg, (v1.y + v2.y) * sg);
           } else {
-            const float2 wv = a.w[(size_t)c * a.N + n];
-            const float2 t2 = cmul_conj(s, wv);
-            pacc.x += t2.x;
-            pacc.y += t2.y;
-            if (MODE == EX_JADJ) {
-              const float2 v = cmul_conj(pimg, wv);
-              a.vout[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
+            if (cv) {
+              const float2 t2 = cmul_conj(s, wv[i]);
+              pacc.x += t2.x;
+              pacc.y += t2.y;
+              if (MODE == EX_JADJ) {
+                const float2 v = cmul_conj(pimg, wv[i]);
+                a.vout[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
+              }
             }
           }
         }
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mpi_ptx::mbar_arrive(acc_empty);
+      if (lane == 0) mpi_ptx::mbar_arrive(&acc_empty[buf]);
       if ((MODE == EX_ADJ || MODE == EX_JADJ) && valid) a.out[n] = make_float2(pacc.x * sg, pacc.y * sg);
     }
   }
@@ -388,7 +404,8 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   if (a.n_gemm > 256) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion: too many coils for one pass");
   int tcols = 32;
   while (tcols < a.n_gemm) tcols <<= 1;
-  a.tmem_cols = tcols;
+  a.half_cols = tcols;     // accumulator buffer stride in TMEM columns
+  a.tmem_cols = 2 * tcols;  // two accumulator buffers
   a.nx = x.nx;
   a.ny = x.ny;
   a.centre = x.centre;
@@ -402,10 +419,12 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.vout = x.vout;
   a.err = ctx->dev_err;
   const size_t b_bytes = round_up(a.n_gemm * b->Kp * 2, 1024);
-  const size_t smem = 1024 + b_bytes + (size_t)kStages * kStageBytes + (2 * kStages + 3) * 8 + 16;
+  const size_t smem = 1024 + b_bytes + (size_t)kStages * kStageBytes + (2 * kStages + 5) * 8 + 16;
   if (smem > 227 * 1024) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion: shared memory");
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
-  const int grid = std::min(n_tiles, std::max(ctx->num_sms, 1));
+  // two CTAs per SM when shared memory allows, so that one's epilogue overlaps the other's loads
+  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  const int grid = std::min(n_tiles, per_sm * std::max(ctx->num_sms, 1));
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap;
   cudaError_t e = cudaSuccess;
 #define MPI_TC_CASE(m)                                                                                        \

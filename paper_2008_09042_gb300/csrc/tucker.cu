@@ -1,0 +1,246 @@
+// Tucker-factored Maxwell basis for 3D volumes ("A Compression Scheme for
+// Maxwell Basis", Eqs. 19-21): the basis tensor is G x1 U1 x2 U2 x3 U3 with a
+// core G of shape (r1, r2, r3, q) shared by the q columns and factors
+// U_k in C^{n_k x r_k}.  A coil map is
+//   s_c = (G x4 alpha_c^T) x1 U1 x2 U2 x3 U3,
+// computed here as
+//   1. the core contraction g_c = G alpha_c, exactly the dense basis expansion
+//      with the core as an (r1 r2 r3) x q basis (FP32 FFMA or BF16 tcgen05 kernels);
+//   2. three mode products (the contraction printed under Eq. 19), last mode
+//      first (x3 U3, then x2 U2, then x1 U1), which keeps the intermediate
+//      tensors smallest;
+// and the adjoint U^H v runs the conjugate-transposed mode products in the
+// reverse order followed by the core's U^H V contraction.  Mode products are
+// FP32 complex on CUDA cores; the per-coil maps are materialised in the context
+// workspace and combined with the image by a point-wise pass.
+#include <algorithm>
+
+#include "mpi_internal.h"
+
+namespace {
+
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+constexpr int kIB = 16;  // outputs along i per thread
+
+// Y[r][i][b] = sum_p X[r][p][b] M(i, p), with M(i, p) = F[i][p] (forward, F is I x P)
+// or conj(F[p][i]) (adjoint, F is P x I).  Threads run along b (coalesced);
+// each thread keeps kIB outputs along i in registers; M is staged in shared
+// memory as [P][kIB] for the CTA's i-block.
+template <bool ADJ>
+__global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, const float2* __restrict__ F, int R,
+                                                int P, int I, long B, float2* __restrict__ Y) {
+  __shared__ float2 sM[128 * kIB];
+  const int i0 = blockIdx.z * kIB;
+  for (int e = threadIdx.x; e < P * kIB; e += blockDim.x) {
+    const int p = e / kIB, ii = e % kIB;
+    const int i = i0 + ii;
+    float2 m = make_float2(0.f, 0.f);
+    if (i < I) {
+      if (ADJ) {
+        const float2 f = F[(size_t)p * I + i];
+        m = make_float2(f.x, -f.y);
+      } else {
+        m = F[(size_t)i * P + p];
+      }
+    }
+    sM[e] = m;
+  }
+  __syncthreads();
+  const long b = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (b >= B || r >= R) return;
+  float2 acc[kIB];
+#pragma unroll
+  for (int ii = 0; ii < kIB; ++ii) acc[ii] = make_float2(0.f, 0.f);
+  const float2* x = X + (size_t)r * P * B + b;
+  for (int p = 0; p < P; ++p) {
+    const float2 xv = x[(size_t)p * B];
+    const float4* mp = reinterpret_cast<const float4*>(sM + p * kIB);
+#pragma unroll
+    for (int i2 = 0; i2 < kIB / 2; ++i2) {
+      const float4 m = mp[i2];
+      cfma(acc[2 * i2], xv, make_float2(m.x, m.y));
+      cfma(acc[2 * i2 + 1], xv, make_float2(m.z, m.w));
+    }
+  }
+  float2* y = Y + (size_t)r * I * B + b;
+#pragma unroll
+  for (int ii = 0; ii < kIB; ++ii)
+    if (i0 + ii < I) y[(size_t)(i0 + ii) * B] = acc[ii];
+}
+
+// Same contraction with B = 1 (last mode): Y[r][i] = sum_p X[r][p] M(i, p).
+// Threads run along i; the CTA handles 8 rows r, whose X rows sit in shared memory.
+template <bool ADJ>
+__global__ void __launch_bounds__(256) k_mode_last(const float2* __restrict__ X, const float2* __restrict__ F, int R,
+                                                   int P, int I, float2* __restrict__ Y) {
+  constexpr int kRows = 8;
+  __shared__ float2 sX[kRows * 128];
+  const int r0 = blockIdx.x * kRows;
+  for (int e = threadIdx.x; e < kRows * P; e += blockDim.x) {
+    const int rr = e / P, p = e % P;
+    sX[e] = (r0 + rr < R) ? X[(size_t)(r0 + rr) * P + p] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < I; i += blockDim.x) {
+    float2 acc[kRows];
+#pragma unroll
+    for (int rr = 0; rr < kRows; ++rr) acc[rr] = make_float2(0.f, 0.f);
+    for (int p = 0; p < P; ++p) {
+      float2 m;
+      if (ADJ) {
+        const float2 f = F[(size_t)p * I + i];
+        m = make_float2(f.x, -f.y);
+      } else {
+        m = F[(size_t)i * P + p];
+      }
+#pragma unroll
+      for (int rr = 0; rr < kRows; ++rr) cfma(acc[rr], sX[rr * P + p], m);
+    }
+#pragma unroll
+    for (int rr = 0; rr < kRows; ++rr)
+      if (r0 + rr < R) Y[(size_t)(r0 + rr) * I + i] = acc[rr];
+  }
+}
+
+float centre_sign_host(int) { return 1.f; }
+
+__device__ __forceinline__ float centre_sign(long n, int nx, int ny) {
+  const int x = (int)(n % nx);
+  const long t = n / nx;
+  const int y = (int)(t % ny);
+  const int z = (int)(t / ny);
+  return ((x + y + z) & 1) ? -1.f : 1.f;
+}
+
+// Point-wise operator epilogues from materialised maps S (and dS) [C][N].
+template <int MODE>
+__global__ void k_pointwise(ExpandArgs a, const float2* __restrict__ S, const float2* __restrict__ dS) {
+  for (long n = (long)blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += (long)gridDim.x * blockDim.x) {
+    const float sg = (a.centre ? centre_sign(n, a.nx, a.ny) : 1.f) * a.scale;
+    const float2 pv = a.p[n];
+    if (MODE == EX_FWD) {
+      for (int c = 0; c < a.C; ++c) {
+        const float2 v = cmul(S[(size_t)c * a.N + n], pv);
+        a.out[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
+      }
+    } else if (MODE == EX_JFWD) {
+      const float2 dpv = a.dp[n];
+      for (int c = 0; c < a.C; ++c) {
+        const float2 v1 = cmul(S[(size_t)c * a.N + n], dpv);
+        const float2 v2 = cmul(dS[(size_t)c * a.N + n], pv);
+        a.out[(size_t)c * a.N + n] = make_float2((v1.x + v2.x) * sg, (v1.y + v2.y) * sg);
+      }
+    } else {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int c = 0; c < a.C; ++c) {
+        const float2 wv = a.w[(size_t)c * a.N + n];
+        const float2 t = cmul_conj(S[(size_t)c * a.N + n], wv);
+        acc.x += t.x;
+        acc.y += t.y;
+        if (MODE == EX_JADJ) {
+          const float2 v = cmul_conj(pv, wv);
+          a.vout[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
+        }
+      }
+      a.out[n] = make_float2(acc.x * sg, acc.y * sg);
+    }
+  }
+}
+
+mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, long B, float2* Y) {
+  if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
+  const dim3 grid((unsigned)((B + 255) / 256), (unsigned)R, (unsigned)((I + kIB - 1) / kIB));
+  if (R > 65535 || grid.z > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
+  MPI_PROF(ctx, KF_EXPAND);
+  if (adj) k_mode_b<true><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
+  else k_mode_b<false><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
+  MPI_LAUNCH_CHECK(ctx, "k_mode_b");
+  return MPI_OK;
+}
+
+mpi_status mode_last(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, float2* Y) {
+  if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
+  const unsigned grid = (unsigned)((R + 7) / 8);
+  MPI_PROF(ctx, KF_EXPAND);
+  if (adj) k_mode_last<true><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, Y);
+  else k_mode_last<false><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, Y);
+  MPI_LAUNCH_CHECK(ctx, "k_mode_last");
+  return MPI_OK;
+}
+
+}  // namespace
+
+size_t tucker_work_elems(const mpi_basis* b, int C) {
+  if (!b->tucker) return 0;
+  const size_t R = (size_t)b->r[0] * b->r[1] * b->r[2];
+  const size_t t1 = (size_t)b->r[0] * b->r[1] * b->n[2];
+  const size_t t2 = (size_t)b->r[0] * b->n[1] * b->n[2];
+  return (size_t)C * (R + t1 + t2);
+}
+
+// maps[c] = s_c for all coils (C x N), through the core contraction and the
+// three mode products; `tmp` holds C * (R + r1 r2 n3 + r1 n2 n3) elements.
+mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
+                       mpi_precision prec) {
+  const int n1 = b->n[0], n2 = b->n[1], n3 = b->n[2];
+  const int r1 = b->r[0], r2 = b->r[1], r3 = b->r[2];
+  const long R = (long)r1 * r2 * r3;
+  float2* g = tmp;                                  // [C][r1][r2][r3]
+  float2* t1 = g + (size_t)C * R;                   // [C][r1][r2][n3]
+  float2* t2 = t1 + (size_t)C * r1 * r2 * n3;       // [C][r1][n2][n3]
+  ExpandArgs a;
+  a.U = b->core->U;
+  a.N = b->core->N;
+  a.q = b->q;
+  a.C = C;
+  a.alpha = alpha;
+  a.out = g;
+  mpi_status st = prec == MPI_PREC_BF16 ? launch_expand_tc(ctx, b->core, EX_MAPS, a) : launch_expand(ctx, EX_MAPS, a);
+  if (st) return st;
+  if ((st = mode_last(ctx, false, g, b->F[2], C * r1 * r2, r3, n3, t1))) return st;
+  if ((st = mode_b(ctx, false, t1, b->F[1], C * r1, r2, n2, n3, t2))) return st;
+  return mode_b(ctx, false, t2, b->F[0], C, r1, n1, (long)n2 * n3, maps);
+}
+
+// dalpha[c] = U^H v_c (C x q): conjugate-transposed mode products, then the core's U^H V.
+mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,
+                          float2* partials, size_t partial_cap) {
+  const int n1 = b->n[0], n2 = b->n[1], n3 = b->n[2];
+  const int r1 = b->r[0], r2 = b->r[1], r3 = b->r[2];
+  const long R = (long)r1 * r2 * r3;
+  float2* g = tmp;                             // [C][r1][r2][r3]
+  float2* t1 = g + (size_t)C * R;              // [C][r1][r2][n3]
+  float2* t2 = t1 + (size_t)C * r1 * r2 * n3;  // [C][r1][n2][n3]
+  mpi_status st;
+  if ((st = mode_b(ctx, true, V, b->F[0], C, n1, r1, (long)n2 * n3, t2))) return st;
+  if ((st = mode_b(ctx, true, t2, b->F[1], C * r1, n2, r2, n3, t1))) return st;
+  if ((st = mode_last(ctx, true, t1, b->F[2], C * r1 * r2, n3, r3, g))) return st;
+  return launch_uh_v(ctx, b->core->U, b->core->N, b->q, g, C, dalpha, partials, partial_cap);
+}
+
+mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS) {
+  const long blocks = std::min(((long)a.N + 255) / 256, 8L * std::max(ctx->num_sms, 1));
+  MPI_PROF(ctx, KF_EXPAND);
+  switch (mode) {
+    case EX_FWD: k_pointwise<EX_FWD><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
+    case EX_JFWD: k_pointwise<EX_JFWD><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
+    case EX_ADJ: k_pointwise<EX_ADJ><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
+    case EX_JADJ: k_pointwise<EX_JADJ><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
+    default: return set_err(ctx, MPI_ERR_ARG, "pointwise mode");
+  }
+  MPI_LAUNCH_CHECK(ctx, "k_pointwise");
+  return MPI_OK;
+}

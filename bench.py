@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--workload", default="cart2d_256_c16_q128")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the radial/3D/recon lines")
     return ap.parse_args()
 
 
@@ -176,6 +177,159 @@ def blas_threads():
         return max([i.get("num_threads", 1) for i in info] or [1])
     except Exception:
         return os.cpu_count()
+
+
+def time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, steps, warmup, flush, stream):
+    """Mean ms of one forward + adjoint pair (CUDA events, L2 flushed between pairs)."""
+    import torch
+
+    C = a_d.shape[0]
+    y = torch.empty((C, plan.M), dtype=torch.complex64, device=a_d.device)
+    x = torch.empty((plan.N,), dtype=torch.complex64, device=a_d.device)
+    for _ in range(warmup):
+        mp.forward(ctx, plan, basis, a_d, p_d, prec, out=y)
+        mp.adjoint(ctx, plan, basis, a_d, y, prec, out=x)
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        mp.forward(ctx, plan, basis, a_d, p_d, prec, out=y)
+        mp.adjoint(ctx, plan, basis, a_d, y, prec, out=x)
+        e.record(stream)
+        e.synchronize()
+        total += s.elapsed_time(e)
+    ctx.synchronize()
+    return total / steps
+
+
+def secondary_workloads(mp, ctx, dev, flush, stream, steps=10, warmup=3):
+    """Forward+adjoint pairs/s on the other workloads (radial, 3D Tucker, 64^2)."""
+    import torch
+
+    out = {}
+    base = w.BASE_SEED
+    # radial 256^2, 12 coils, q = 96, 64 golden-angle spokes x 512 samples, KB W = 6, sigma = 2
+    cfg = w.workload("radial2d_256_c12_q96")
+    n = cfg["dims"][0]
+    k = w.golden_angle_radial(cfg["spokes"], cfg["readout"]).astype(np.float32)
+    plan = mp.Plan(ctx, (n, n), traj=k, kb_width=cfg["W"], oversamp=cfg["sigma"])
+    B = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, cfg["q"], seed=base).T)
+    a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 1).astype(np.complex64)).to(dev)
+    p = torch.from_numpy(w.random_ellipses(n, n, seed=base + 2).ravel().astype(np.complex64)).to(dev)
+    for prec in ("fp32", "bf16"):
+        ms = time_pairs(mp, ctx, plan, B, a, p, prec, steps, warmup, flush, stream)
+        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms}
+    del plan, B
+    # 3D 96 x 128 x 128, 32 coils, Tucker q = 256, ranks (32, 40, 40), 3D Poisson-disc R = 8
+    cfg = w.workload("cart3d_128x128x96_c32_tucker256")
+    dims = cfg["dims"]
+    core, fac = w.smooth_tucker_basis(dims, cfg["ranks"], cfg["q"], seed=base)
+    mask = w.poisson_disc_mask_3d(*dims, R=cfg["R"], calib=cfg["calib"], seed=base + 1)
+    plan = mp.Plan(ctx, dims, sample_idx=w.mask_to_indices(mask))
+    B = mp.TuckerBasis(ctx, core, fac)
+    N = int(np.prod(dims))
+    a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 2).astype(np.complex64)).to(dev)
+    p = torch.from_numpy(w.random_ellipses(dims[1], dims[2], nz=dims[0], seed=base + 3).ravel()
+                         .astype(np.complex64)).to(dev)
+    ctx.reserve(plan, B, cfg["C"])
+    for prec in ("fp32", "bf16"):
+        ms = time_pairs(mp, ctx, plan, B, a, p, prec, max(3, steps // 2), 2, flush, stream)
+        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms}
+    del plan, B
+    return out
+
+
+def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
+    """The 64-slice mixed exam: grids from {128, 192, 256, 320}^2, coils from
+    {8, 16, 32}, q by grid size, Poisson-disc R in 4..8; all slices' forward +
+    adjoint replayed as one CUDA graph.  Returns slices/s per precision."""
+    import torch
+
+    cfg = w.workload("batched2d_64slices")
+    rng = np.random.default_rng(w.BASE_SEED)
+    sizes = rng.choice(cfg["sizes"], size=cfg["slices"])
+    coils = rng.choice(cfg["coils"], size=cfg["slices"])
+    Rs = rng.integers(cfg["R_range"][0], cfg["R_range"][1] + 1, size=cfg["slices"])
+    bases, masks = {}, {}
+    slices = []
+    for i in range(cfg["slices"]):
+        n, C, R = int(sizes[i]), int(coils[i]), int(Rs[i])
+        q = cfg["q_by_size"][n]
+        if n not in bases:
+            bases[n] = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, q, seed=w.BASE_SEED + n).T)
+        if (n, R) not in masks:  # one mask per (grid, R), shared by the slices that draw it
+            masks[(n, R)] = mp.Plan(ctx, (n, n), sample_idx=w.mask_to_indices(
+                w.poisson_disc_mask(n, n, R, calib=(24, 24), seed=w.BASE_SEED + 10 * n + R)))
+        plan = masks[(n, R)]
+        a = torch.from_numpy(w.random_coefficients(C, q, seed=w.BASE_SEED + 100 + i).astype(np.complex64)).to(dev)
+        p = torch.from_numpy(w.random_ellipses(n, n, seed=w.BASE_SEED + 200 + i).ravel().astype(np.complex64)).to(dev)
+        slices.append(dict(plan=plan, basis=bases[n], alpha=a, p=p,
+                           y=torch.empty((C, plan.M), dtype=torch.complex64, device=dev),
+                           x=torch.empty((n * n,), dtype=torch.complex64, device=dev)))
+    out = {"slices": cfg["slices"], "coils_total": int(coils.sum()),
+           "grid_counts": {int(k): int((sizes == k).sum()) for k in cfg["sizes"]}}
+    for prec in ("fp32", "bf16"):
+        batch = mp.Batch(ctx, slices, kind="pair", prec=prec)
+        for _ in range(warmup):
+            batch.run()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            batch.run()
+            e.record(stream)
+            e.synchronize()
+            total += s.elapsed_time(e)
+        ctx.synchronize()
+        ms = total / steps
+        out[prec] = {"value": cfg["slices"] * 1000.0 / ms, "unit": "slice pairs/s", "ms_per_exam": ms,
+                     "graph_kernels": batch.kernels()}
+        batch.close()
+    return out
+
+
+def recon_per_slice(mp, ctx, dev, prec_list=("fp32", "bf16"), reps=2):
+    """MPI-BL (20 IRGN x 10 CG) + MPI-L (50 ADMM x 5 CG x 10 TV) wall time per slice
+    on the 64 x 64, 4-coil, q = 32 workload; NRMSE of each precision's image
+    against the FP32 result."""
+    import torch
+
+    cfg = w.workload("cart2d_64_c4_q32")
+    ny, nx = cfg["dims"]
+    C, q = cfg["C"], cfg["q"]
+    base = w.BASE_SEED
+    U = w.smooth_orthonormal_basis(ny, nx, q, seed=base)
+    mask = w.vd_lines_mask(ny, nx, cfg["R"], cfg["acs"], seed=base + 1)
+    idx = w.mask_to_indices(mask)
+    plan = mp.Plan(ctx, (ny, nx), sample_idx=idx)
+    B = mp.Basis(ctx, U.T)
+    a_true = torch.from_numpy(w.random_coefficients(C, q, seed=base + 2).astype(np.complex64)).to(dev)
+    p_true = torch.from_numpy(w.random_ellipses(ny, nx, seed=base + 3).ravel().astype(np.complex64)).to(dev)
+    y0 = mp.forward(ctx, plan, B, a_true, p_true).cpu().numpy()
+    sig = w.noise_sigma_for_snr(y0, cfg["snr_db"])
+    y = torch.from_numpy((y0 + w.complex_noise(y0.shape, sig, seed=base + 4)).astype(np.complex64)).to(dev)
+    eps = np.full(C, sig * np.sqrt(idx.size))
+    res = {}
+    images = {}
+    for prec in prec_list:
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a, _, _ = mp.sm_estimate(ctx, plan, B, y, C, n_outer=cfg["n_irgn"], n_cg=10, prec=prec)
+            img, _ = mp.image_solve(ctx, plan, B, a, y, eps, n_outer=cfg["n_admm"], n_cg=5, n_tv=10, prec=prec)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        images[prec] = img.cpu().numpy().astype(np.complex128)
+        res[prec] = {"ms_per_slice": 1000.0 * min(times)}
+    ref = images["fp32"]
+    for prec in prec_list:
+        res[prec]["nrmse_vs_fp32"] = float(np.linalg.norm(images[prec] - ref) / np.linalg.norm(ref))
+    return {"workload": cfg["name"], "iterations": "20 IRGN x 10 CG + 50 ADMM x 5 CG x 10 TV", **res}
 
 
 def run_reference(args):
@@ -365,6 +519,10 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clk,
     }
+    if not args.no_secondary:
+        line["workloads"] = secondary_workloads(mp, ctx, dev, flush, stream)
+        line["workloads"]["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
+        line["recon"] = recon_per_slice(mp, ctx, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, dt = cpu_oracle_pairs(cfg, U, idx, alpha, p)
         line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": blas_threads(), "kind": "oracle",

@@ -199,6 +199,37 @@ mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_ba
 mpi_status mpi_basis_project(mpi_ctx* ctx, const mpi_basis* basis, const mpi_c32* maps, int C,
                              mpi_c32* alpha);
 
+/* ------------------------------------------------------------------ batches */
+
+/* Many slices of uneven grid size and coil count (e.g. a multi-slice exam),
+ * each a set of caller-owned device buffers: y = G_s(p) and/or x = G_s^H(y). */
+typedef struct {
+  const mpi_plan* plan;
+  const mpi_basis* basis;  /* slices of one grid size may share one basis */
+  int C;
+  const mpi_c32* alpha;    /* [C][q] */
+  const mpi_c32* p;        /* [N] forward input */
+  mpi_c32* y;              /* [C][M] forward output and adjoint input */
+  mpi_c32* x;              /* [N] adjoint output */
+} mpi_batch_slice;
+
+typedef enum { MPI_BATCH_FORWARD = 1, MPI_BATCH_ADJOINT = 2, MPI_BATCH_PAIR = 3 } mpi_batch_kind;
+typedef struct mpi_batch mpi_batch;
+
+/* Record every kernel of the n slices' operator calls (forward, adjoint, or the
+ * forward followed by the adjoint of its output) into one CUDA graph.  Slices
+ * are ordered by basis so that a shared basis stays L2-resident; the context
+ * workspace is sized first, so replays allocate nothing.  The slice descriptors
+ * are copied; their buffers must stay valid while the batch exists.  Waits for
+ * the context's stream once. */
+mpi_status mpi_batch_create(mpi_ctx* ctx, const mpi_batch_slice* slices, int n, int kind,
+                            mpi_precision prec, mpi_batch** out);
+/* Launch the recorded graph once on the context's stream (asynchronous). */
+mpi_status mpi_batch_run(mpi_ctx* ctx, mpi_batch* batch);
+/* Kernels one replay launches (-1 for a NULL batch). */
+int64_t mpi_batch_kernel_count(const mpi_batch* batch);
+mpi_status mpi_batch_destroy(mpi_batch* batch);
+
 /* ----------------------------------------------------------------- solvers */
 
 /* MPI-BL: IRGN for (p, alpha) (Eq. 6) with CG on the normal equations

@@ -9,6 +9,7 @@ kernels of ``libmpi_gb300.so`` behind the C ABI declared in
 from ._lib import MpiError, load  # noqa: F401
 from .api import (  # noqa: F401
     Basis,
+    Batch,
     Context,
     MPIOperator,
     Plan,

@@ -24,7 +24,8 @@ EXPORTS = [
     "mpi_last_error", "mpi_ctx_launch_count", "mpi_ctx_profile", "mpi_ctx_profile_read", "mpi_plan_create", "mpi_plan_destroy", "mpi_plan_grid_index",
     "mpi_basis_load_dense", "mpi_basis_load_tucker", "mpi_basis_destroy", "mpi_basis_expand", "mpi_forward", "mpi_adjoint",
     "mpi_jacobian", "mpi_jacobian_adjoint", "mpi_basis_project", "mpi_sm_estimate", "mpi_image_solve",
-    "mpi_tv_prox", "mpi_forward_noalloc",
+    "mpi_tv_prox", "mpi_forward_noalloc", "mpi_batch_create", "mpi_batch_run", "mpi_batch_kernel_count",
+    "mpi_batch_destroy",
 ]
 
 
@@ -44,6 +45,13 @@ class PlanDesc(ctypes.Structure):
         ("traj", ctypes.c_void_p),
         ("kb_width", ctypes.c_int),
         ("oversamp", ctypes.c_float),
+    ]
+
+
+class BatchSlice(ctypes.Structure):
+    _fields_ = [
+        ("plan", ctypes.c_void_p), ("basis", ctypes.c_void_p), ("C", ctypes.c_int),
+        ("alpha", ctypes.c_void_p), ("p", ctypes.c_void_p), ("y", ctypes.c_void_p), ("x", ctypes.c_void_p),
     ]
 
 
@@ -100,6 +108,9 @@ def load(path=LIB_PATH):
         "mpi_image_solve": [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(AdmmParams), vp, vp, i],
         "mpi_tv_prox": [vp, vp, vp, d, i, vp],
         "mpi_forward_noalloc": [vp, vp, vp, vp, i, vp, vp],
+        "mpi_batch_create": [vp, ctypes.POINTER(BatchSlice), i, i, i, pp],
+        "mpi_batch_run": [vp, vp],
+        "mpi_batch_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -109,6 +120,8 @@ def load(path=LIB_PATH):
     lib.mpi_last_error.restype = ctypes.c_char_p
     lib.mpi_ctx_launch_count.argtypes = [vp]
     lib.mpi_ctx_launch_count.restype = i64
+    lib.mpi_batch_kernel_count.argtypes = [vp]
+    lib.mpi_batch_kernel_count.restype = i64
     _lib = lib
     return lib
 

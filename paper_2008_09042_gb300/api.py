@@ -313,3 +313,47 @@ def tv_prox(ctx, plan, v, lam, n_iter):
     x = torch.empty_like(v)
     check(ctx.h, ctx.lib.mpi_tv_prox(ctx.h, plan.h, _ptr(v), float(lam), int(n_iter), _ptr(x)))
     return x
+
+
+class Batch:
+    """Many slices' operator calls recorded into one CUDA graph (mpi_batch_*).
+
+    ``slices`` is a list of dicts with keys plan, basis, alpha, p, y, x (device
+    tensors that must outlive the batch); kind is "forward", "adjoint" or "pair".
+    """
+
+    KINDS = {"forward": 1, "adjoint": 2, "pair": 3}
+
+    def __init__(self, ctx, slices, kind="pair", prec="fp32"):
+        self.ctx = ctx
+        self.slices = slices  # keep the tensors alive
+        arr = (_lib.BatchSlice * len(slices))()
+        for i, s in enumerate(slices):
+            arr[i].plan = s["plan"].h.value
+            arr[i].basis = s["basis"].h.value
+            arr[i].C = int(s["alpha"].shape[0])
+            arr[i].alpha = s["alpha"].data_ptr()
+            arr[i].p = s["p"].data_ptr()
+            arr[i].y = s["y"].data_ptr() if s["y"].numel() else None
+            arr[i].x = s["x"].data_ptr()
+        h = ctypes.c_void_p()
+        check(ctx.h, ctx.lib.mpi_batch_create(ctx.h, arr, len(slices), self.KINDS[kind], PREC[prec],
+                                              ctypes.byref(h)))
+        self.h = h
+
+    def run(self):
+        check(self.ctx.h, self.ctx.lib.mpi_batch_run(self.ctx.h, self.h))
+
+    def kernels(self):
+        return int(self.ctx.lib.mpi_batch_kernel_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.mpi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -224,6 +224,7 @@ extern "C" mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_strea
     ctx->dev_err = (int*)((char*)ctx->twiddles + ((host.size() * sizeof(float2) + 127) & ~(size_t)127));
     e = cudaMemset(ctx->dev_err, 0, sizeof(int));
   }
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->coef_img, kCoefImgBytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (ctx->twiddles) cudaFree(ctx->twiddles);
@@ -244,6 +245,7 @@ extern "C" mpi_status mpi_ctx_destroy(mpi_ctx* ctx) {
   }
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->twiddles) cudaFree(ctx->twiddles);
+  if (ctx->coef_img) cudaFree(ctx->coef_img);
   delete ctx;
   return MPI_OK;
 }

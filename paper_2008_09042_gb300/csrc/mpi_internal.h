@@ -14,6 +14,8 @@
 // exp(-2 pi i m / n), m < n, inside the context's table buffer.
 static const int kFftLengths[] = {16, 32, 48, 64, 96, 128, 192, 256, 320, 512};
 static const int kNumFftLengths = sizeof(kFftLengths) / sizeof(int);
+// Bytes reserved per context for the tensor-core coefficient operand image.
+static const size_t kCoefImgBytes = 256 * 512 * 2;
 
 // Kernel families for the optional per-launch event timing.
 enum KernelFamily { KF_EXPAND = 0, KF_UHV = 1, KF_FFT_ROWS = 2, KF_FFT_LINES = 3, KF_NUFFT = 4,
@@ -28,6 +30,7 @@ struct mpi_ctx {
   int tw_offset[kNumFftLengths] = {0};
   int num_sms = 0;
   int* dev_err = nullptr;  // device error word written by kernels whose waits time out
+  void* coef_img = nullptr;  // BF16 coefficient operand image for the tensor-core expansion
   int64_t launches = 0;
   std::string err;
   // profiling: event pairs around launches while enabled

@@ -40,6 +40,7 @@ struct TcArgs {
   float scale;
   const float2* alpha;
   const float2* dalpha;
+  const __nv_bfloat16* coef_img;
   const float2* p;
   const float2* dp;
   const float2* w;
@@ -128,6 +129,33 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k, int rows) {
   return (uint32_t)(kc * rows * 128 + r * 128 + ((((kk >> 3) ^ (r & 7))) << 4) + (kk & 7) * 2);
 }
 
+// The coefficient operand image, built once per call in global memory in the
+// exact swizzled shared-memory layout: rows [0, 2C) from alpha, rows
+// [half, half + 2C) from dalpha (Jacobian), zero elsewhere.
+__global__ void k_build_coef(TcArgs a, int with_dalpha, __nv_bfloat16* __restrict__ img) {
+  const int Kp = a.KC * kKChunk;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n_gemm * Kp) return;
+  const int r = e / Kp, k = e % Kp;
+  float v = 0.f;
+  const float2* src = nullptr;
+  int rr = r;
+  if (r < 2 * a.C) {
+    src = a.alpha;
+  } else if (with_dalpha && r >= a.half && r < a.half + 2 * a.C) {
+    src = a.dalpha;
+    rr = r - a.half;
+  }
+  if (src && k < 2 * a.q) {
+    const int c = rr >> 1, im_row = rr & 1;
+    const int j = k < a.q ? k : k - a.q;
+    const float2 al = src[(size_t)c * a.q + j];
+    if (!im_row) v = k < a.q ? al.x : -al.y;  // row 2c: [Re a, -Im a]
+    else v = k < a.q ? al.y : al.x;             // row 2c+1: [Im a, Re a]
+  }
+  img[sw128_offset(r, k, a.n_gemm) / 2] = __float2bfloat16_rn(v);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -141,32 +169,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
   uint64_t* acc_full = empty + kStages;  // [2]: double-buffered accumulator
   uint64_t* acc_empty = acc_full + 2;    // [2]
   uint64_t* drain = acc_empty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* bfull = drain + 1;  // coefficient operand landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bfull + 1);
   __shared__ int s_failed;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // coefficient operand: rows [0, 2C) from alpha, rows [half, half + 2C) from dalpha (Jacobian)
-  for (int e = tid; e < a.n_gemm * Kp; e += kThreads) {
-    const int r = e / Kp, k = e % Kp;
-    float v = 0.f;
-    const float2* src = nullptr;
-    int rr = r;
-    if (r < 2 * a.C) {
-      src = a.alpha;
-    } else if (MODE == EX_JFWD && r >= a.half && r < a.half + 2 * a.C) {
-      src = a.dalpha;
-      rr = r - a.half;
-    }
-    if (src && k < 2 * a.q) {
-      const int c = rr >> 1, im_row = rr & 1;
-      const int j = k < a.q ? k : k - a.q;
-      const float2 al = src[(size_t)c * a.q + j];
-      if (!im_row) v = k < a.q ? al.x : -al.y;  // row 2c: [Re a, -Im a]
-      else v = k < a.q ? al.y : al.x;             // row 2c+1: [Im a, Re a]
-    }
-    *reinterpret_cast<__nv_bfloat16*>(sB + sw128_offset(r, k, a.n_gemm)) = __float2bfloat16_rn(v);
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
   if (tid == 0) {
     s_failed = 0;
     for (int s = 0; s < kStages; ++s) {
@@ -178,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
       mpi_ptx::mbar_init(&acc_empty[b], 4);
     }
     mpi_ptx::mbar_init(drain, 1);
+    mpi_ptx::mbar_init(bfull, 1);
     mpi_ptx::fence_mbar_init();
   }
   if (warp == 1) {
@@ -194,7 +202,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
 
   const int n_tiles = (a.N + kTileM - 1) / kTileM;
   if (warp == 0 && lane == 0) {
-    // ---------------- producer: TMA tiles of U
+    // ---------------- producer: the coefficient operand image, then TMA tiles of U
+    mpi_ptx::mbar_arrive_expect_tx(bfull, b_bytes);
+    mpi_ptx::bulk_g2s(sB, a.coef_img, b_bytes, bfull);
     long it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
     const uint32_t a_base = mpi_ptx::smem_addr(sA);
     long it = 0;
     int tc = 0;
-    bool ok = true;
+    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err);
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tc) {
       const int buf = tc & 1;
       const uint32_t tacc = tmem + (uint32_t)(buf * a.half_cols);
@@ -419,7 +429,13 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.vout = x.vout;
   a.err = ctx->dev_err;
   const size_t b_bytes = round_up(a.n_gemm * b->Kp * 2, 1024);
-  const size_t smem = 1024 + b_bytes + (size_t)kStages * kStageBytes + (2 * kStages + 5) * 8 + 16;
+  const size_t smem = 1024 + b_bytes + (size_t)kStages * kStageBytes + (2 * kStages + 6) * 8 + 16;
+  if ((size_t)a.n_gemm * b->Kp * 2 > kCoefImgBytes) return set_err(ctx, MPI_ERR_UNSUPPORTED, "coefficient image");
+  a.coef_img = (const __nv_bfloat16*)ctx->coef_img;
+  MPI_PROF(ctx, KF_OTHER);
+  k_build_coef<<<(a.n_gemm * b->Kp + 255) / 256, 256, 0, ctx->stream>>>(a, mode == EX_JFWD,
+                                                                          (__nv_bfloat16*)ctx->coef_img);
+  MPI_LAUNCH_CHECK(ctx, "k_build_coef");
   if (smem > 227 * 1024) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion: shared memory");
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
   // two CTAs per SM when shared memory allows, so that one's epilogue overlaps the other's loads

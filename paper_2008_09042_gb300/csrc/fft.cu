@@ -8,7 +8,8 @@
 // k-side sign and the gather / zero-fill of the sampled points.
 //
 // Every line (one row, or one column of a tile) is transformed by one warp in
-// shared memory with a mixed-radix (2, 3, 4, 5, 8) Stockham auto-sort FFT: for
+// shared memory (padded by one element per 8, see pad8) with a mixed-radix
+// (2, 3, 4, 5, 8) Stockham auto-sort FFT: for
 // a stage of radix R after Ns points have been combined, butterfly j reads
 // x[j + r N/R], r < R, multiplies input r by w^(r (j mod Ns)) with w =
 // exp(-+2 pi i / (Ns R)), takes an R-point DFT and writes output r to
@@ -123,77 +124,11 @@ struct Dft<5, INV> {
   }
 };
 
-template <bool INV>
-struct Dft<16, INV> {
-  // 16 = 4 x 4: Y[m1][k1] = DFT4 over m2 of x[m1 + 4 m2], times W16^(m1 k1),
-  // then X[k1 + 4 k2] = DFT4 over m1 of Y[m1][k1].
-  static __device__ __forceinline__ void go(float2* v) {
-    const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
-    const float sg = INV ? 1.f : -1.f;  // exp(sg * i * theta)
-    float2 y[4][4];
-#pragma unroll
-    for (int m1 = 0; m1 < 4; ++m1) {
-      float2 t[4] = {v[m1], v[m1 + 4], v[m1 + 8], v[m1 + 12]};
-      Dft<4, INV>::go(t);
-#pragma unroll
-      for (int k1 = 0; k1 < 4; ++k1) y[m1][k1] = t[k1];
-    }
-    // twiddles W16^(m1 k1), angle 2 pi m1 k1 / 16, with cos/sin of multiples of pi/8
-    const float cs[10] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1};
-    const float sn[10] = {0.f, s1, h, c1, 1.f, c1, h, s1, 0.f, -s1};
-#pragma unroll
-    for (int m1 = 1; m1 < 4; ++m1)
-#pragma unroll
-      for (int k1 = 1; k1 < 4; ++k1) {
-        const int j = m1 * k1;  // <= 9
-        y[m1][k1] = cmul(y[m1][k1], make_float2(cs[j], sg * sn[j]));
-      }
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-      Dft<4, INV>::go(t);
-#pragma unroll
-      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
-    }
-  }
-};
-
-// N = 32 R point FFT of one line held by a warp, lane l holding x[l + 32 m]
-// in v[m].  With n = l + 32 m and k = k1 + R k2: an R-point DFT over m in
-// registers, the twiddle W_N^(l k1), then a 32-point DFT over l for every k1
-// by five radix-2 decimation-in-frequency stages with warp shuffles.  On
-// return v[k1] = X[k1 + R brev5(l)].
-template <int N, bool INV>
-__device__ __forceinline__ void fft_shfl(float2 (&v)[N / 32], const float2* __restrict__ tw, int lane) {
-  constexpr int R = N / 32;
-  Dft<R, INV>::go(v);
-#pragma unroll
-  for (int k1 = 1; k1 < R; ++k1) {
-    float2 w = tw[(lane * k1) % N];
-    if (INV) w.y = -w.y;
-    v[k1] = cmul(v[k1], w);
-  }
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool hi = (lane & h) != 0;
-    float2 w = tw[(lane & (h - 1)) * (N / (2 * h))];
-    if (INV) w.y = -w.y;
-#pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) {
-      float2 o;
-      o.x = __shfl_xor_sync(0xffffffffu, v[k1].x, h);
-      o.y = __shfl_xor_sync(0xffffffffu, v[k1].y, h);
-      v[k1] = hi ? cmul(make_float2(o.x - v[k1].x, o.y - v[k1].y), w) : make_float2(v[k1].x + o.x, v[k1].y + o.y);
-    }
-  }
-}
-
-__device__ __forceinline__ int brev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
-// shared-memory index with one float2 of padding per 32, which makes the
-// permuted writes after fft_shfl and the natural-order reads conflict-free
-__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
-
-__host__ __device__ constexpr bool use_shfl(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+// Shared-memory index of element i of a line: one float2 of padding per 8,
+// which leaves every Stockham stage's strided loads and stores at most
+// two-way bank conflicted for the supported lengths.
+__host__ __device__ __forceinline__ constexpr int pad8(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int padded_len(int n) { return n + n / 8; }
 
 template <int N, int R, int NS, bool INV>
 __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lane) {
@@ -205,7 +140,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lan
     const int j = lane + 32 * b;
     if (j < NB) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = buf[j + r * NB];
+      for (int r = 0; r < R; ++r) v[b][r] = buf[pad8(j + r * NB)];
     }
   }
   __syncwarp();
@@ -225,7 +160,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lan
       Dft<R, INV>::go(v[b]);
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[base + r * NS] = v[b][r];
+      for (int r = 0; r < R; ++r) buf[pad8(base + r * NS)] = v[b][r];
     }
   }
   __syncwarp();
@@ -271,44 +206,37 @@ constexpr int kRowWarps = 4;
 // One warp per (coil, k-space row).  Forward: FFT along x, k-side centring sign,
 // gather the row's samples (contiguous in the sorted list).  Rows without
 // samples are skipped.
+// The twiddle table, the row and the row's sample range are fetched before the
+// one CTA barrier, so their global-memory latencies overlap.
 template <int NX>
 __global__ void __launch_bounds__(kRowWarps * 32) k_rows_fwd_gather(
     const float2* __restrict__ data, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
     const int32_t* __restrict__ row_ptr, float2* __restrict__ y, int M, float ksign,
     const float2* __restrict__ tw_g) {
   __shared__ float2 tw[NX];
-  __shared__ float2 buf[kRowWarps][NX + NX / 32];
+  __shared__ float2 buf[kRowWarps][padded_len(NX)];
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long gr = (long)blockIdx.x * kRowWarps + warp;
-  if (gr >= (long)C * n_rows) return;
-  const int c = (int)(gr / n_rows), row = (int)(gr % n_rows);
-  const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
-  if (m0 == m1) return;
+  const bool in_range = gr < (long)C * n_rows;
+  const int c = in_range ? (int)(gr / n_rows) : 0, row = in_range ? (int)(gr % n_rows) : 0;
+  const int m0 = in_range ? row_ptr[row] : 0, m1 = in_range ? row_ptr[row + 1] : 0;
+  const bool work = in_range && m1 > m0;
   float2* b = buf[warp];
-  const float2* src = data + ((size_t)c * n_rows + row) * NX;
-  if constexpr (use_shfl(NX)) {
-    constexpr int R = NX / 32;
-    float2 v[R];
+  if (work) {
+    const float2* src = data + ((size_t)c * n_rows + row) * NX;
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = src[lane + 32 * m];
-    fft_shfl<NX, false>(v, tw, lane);
-    const int bl = R * brev5(lane);
-#pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) b[pad32(k1 + bl)] = v[k1];
-  } else {
-    for (int i = lane; i < NX; i += 32) b[i] = src[i];
-    __syncwarp();
-    Fft<NX, false>::go(b, tw, lane);
+    for (int i = lane; i < NX; i += 32) b[pad8(i)] = src[i];
   }
-  __syncwarp();
+  __syncthreads();
+  if (!work) return;
+  Fft<NX, false>::go(b, tw, lane);
   const int rpar = (row / ny + row % ny) & 1;  // (kz + ky) parity
   const size_t rbase = (size_t)row * NX;
   for (int m = m0 + lane; m < m1; m += 32) {
     const int kx = (int)(idx[m] - rbase);
     const float s = ((kx + rpar) & 1) ? -ksign : ksign;
-    const float2 v = b[use_shfl(NX) ? pad32(kx) : kx];
+    const float2 v = b[pad8(kx)];
     y[(size_t)c * M + m] = make_float2(v.x * s, v.y * s);
   }
 }
@@ -320,49 +248,34 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
     const int32_t* __restrict__ row_ptr, float2* __restrict__ data, int M, float ksign,
     const float2* __restrict__ tw_g) {
   __shared__ float2 tw[NX];
-  __shared__ float2 buf[kRowWarps][NX + NX / 32];
+  __shared__ float2 buf[kRowWarps][padded_len(NX)];
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long gr = (long)blockIdx.x * kRowWarps + warp;
-  if (gr >= (long)C * n_rows) return;
-  const int c = (int)(gr / n_rows), row = (int)(gr % n_rows);
-  const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
+  const bool in_range = gr < (long)C * n_rows;
+  const int c = in_range ? (int)(gr / n_rows) : 0, row = in_range ? (int)(gr % n_rows) : 0;
+  const int m0 = in_range ? row_ptr[row] : 0, m1 = in_range ? row_ptr[row + 1] : 0;
   float2* dst = data + ((size_t)c * n_rows + row) * NX;
-  if (m0 == m1) {
-    for (int i = lane; i < NX; i += 32) dst[i] = make_float2(0.f, 0.f);
-    return;
-  }
-  constexpr bool kShfl = use_shfl(NX);
   float2* b = buf[warp];
-  for (int i = lane; i < NX + NX / 32; i += 32) b[i] = make_float2(0.f, 0.f);
-  __syncwarp();
-  const int rpar = (row / ny + row % ny) & 1;
-  const size_t rbase = (size_t)row * NX;
-  for (int m = m0 + lane; m < m1; m += 32) {
-    const int kx = (int)(idx[m] - rbase);
-    const float s = ((kx + rpar) & 1) ? -ksign : ksign;
-    const float2 v = y[(size_t)c * M + m];
-    b[kShfl ? pad32(kx) : kx] = make_float2(v.x * s, v.y * s);
-  }
-  __syncwarp();
-  if constexpr (kShfl) {
-    constexpr int R = NX / 32;
-    float2 v[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = b[pad32(lane + 32 * m)];
-    fft_shfl<NX, true>(v, tw, lane);
+  if (in_range && m1 > m0) {
+    for (int i = lane; i < padded_len(NX); i += 32) b[i] = make_float2(0.f, 0.f);
     __syncwarp();
-    const int bl = R * brev5(lane);
-#pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) b[pad32(k1 + bl)] = v[k1];
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < R; ++m) dst[lane + 32 * m] = b[pad32(lane + 32 * m)];
-  } else {
-    Fft<NX, true>::go(b, tw, lane);
-    for (int i = lane; i < NX; i += 32) dst[i] = b[i];
+    const int rpar = (row / ny + row % ny) & 1;
+    const size_t rbase = (size_t)row * NX;
+    for (int m = m0 + lane; m < m1; m += 32) {
+      const int kx = (int)(idx[m] - rbase);
+      const float s = ((kx + rpar) & 1) ? -ksign : ksign;
+      const float2 v = y[(size_t)c * M + m];
+      b[pad8(kx)] = make_float2(v.x * s, v.y * s);
+    }
+  } else if (in_range) {
+    for (int i = lane; i < NX; i += 32) dst[i] = make_float2(0.f, 0.f);
   }
+  __syncthreads();
+  if (!(in_range && m1 > m0)) return;
+  Fft<NX, true>::go(b, tw, lane);
+#pragma unroll
+  for (int i = lane; i < NX; i += 32) dst[i] = b[pad8(i)];
 }
 
 constexpr int kColTile = 8;  // adjacent lines per CTA (one warp each)
@@ -374,10 +287,12 @@ constexpr int kColPad = 4;
 // line per warp), transforms and writes back.  Tiles are enumerated as
 // (slab, x-tile) with slab base offset = (slab / inner) * outer_stride +
 // (slab % inner) * inner_stride.
-// Column stride of the transposed tile: padded by one float2 per 32 (for the
-// shuffle FFT's reorder) and rounded to 2 mod 16 float2, which keeps the
-// transposing loads and stores (8 lines x 4 rows per warp) free of bank conflicts.
-__host__ __device__ constexpr int col_stride(int L) { return L + L / 32 + ((2 - (L + L / 32)) % 16 + 16) % 16; }
+// Column stride of the transposed tile: the padded line length rounded up to
+// 2 mod 16 float2, which keeps the transposing loads and stores (8 lines x 4
+// rows per warp) free of bank conflicts.
+__host__ __device__ constexpr int col_stride(int L) {
+  return padded_len(L) + ((2 - padded_len(L)) % 16 + 16) % 16;
+}
 
 template <int L, bool INV>
 __global__ void __launch_bounds__(kColTile * 32) k_fft_lines(float2* __restrict__ data, int nx,
@@ -385,7 +300,6 @@ __global__ void __launch_bounds__(kColTile * 32) k_fft_lines(float2* __restrict_
                                                             long outer_stride, long inner_stride,
                                                             const float2* __restrict__ tw_g) {
   constexpr int S = col_stride(L);
-  constexpr bool kShfl = use_shfl(L);
   __shared__ float2 tw[L];
   __shared__ float2 buf[kColTile * S];
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tw_g[i];
@@ -398,30 +312,15 @@ __global__ void __launch_bounds__(kColTile * 32) k_fft_lines(float2* __restrict_
   const int tid = threadIdx.x;
   for (int e = tid; e < L * kColTile; e += blockDim.x) {
     const int r = e / kColTile, cx = e % kColTile;
-    if (x0 + cx < nx) buf[cx * S + (kShfl ? pad32(r) : r)] = data[base + (size_t)r * stride + cx];
+    if (x0 + cx < nx) buf[cx * S + pad8(r)] = data[base + (size_t)r * stride + cx];
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  if (x0 + warp < nx) {
-    float2* b = buf + warp * S;
-    if constexpr (kShfl) {
-      constexpr int R = L / 32;
-      float2 v[R];
-#pragma unroll
-      for (int m = 0; m < R; ++m) v[m] = b[pad32(lane + 32 * m)];
-      fft_shfl<L, INV>(v, tw, lane);
-      __syncwarp();
-      const int bl = R * brev5(lane);
-#pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) b[pad32(k1 + bl)] = v[k1];
-    } else {
-      Fft<L, INV>::go(b, tw, lane);
-    }
-  }
+  if (x0 + warp < nx) Fft<L, INV>::go(buf + warp * S, tw, lane);
   __syncthreads();
   for (int e = tid; e < L * kColTile; e += blockDim.x) {
     const int r = e / kColTile, cx = e % kColTile;
-    if (x0 + cx < nx) data[base + (size_t)r * stride + cx] = buf[cx * S + (kShfl ? pad32(r) : r)];
+    if (x0 + cx < nx) data[base + (size_t)r * stride + cx] = buf[cx * S + pad8(r)];
   }
 }
 
@@ -551,32 +450,21 @@ template <int L, bool INV>
 __global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __restrict__ data, long n_rows,
                                                                     const float2* __restrict__ tw_g) {
   __shared__ float2 tw[L];
-  __shared__ float2 buf[kRowWarps][L + L / 32];
+  __shared__ float2 buf[kRowWarps][padded_len(L)];
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tw_g[i];
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long row = (long)blockIdx.x * kRowWarps + warp;
-  if (row >= n_rows) return;
-  float2* src = data + (size_t)row * L;
+  float2* src = data + (size_t)(row < n_rows ? row : 0) * L;
   float2* b = buf[warp];
-  if constexpr (use_shfl(L)) {
-    constexpr int R = L / 32;
-    float2 v[R];
+  if (row < n_rows) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = src[lane + 32 * m];
-    fft_shfl<L, INV>(v, tw, lane);
-    const int bl = R * brev5(lane);
-#pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) b[pad32(k1 + bl)] = v[k1];
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < R; ++m) src[lane + 32 * m] = b[pad32(lane + 32 * m)];
-  } else {
-    for (int i = lane; i < L; i += 32) b[i] = src[i];
-    __syncwarp();
-    Fft<L, INV>::go(b, tw, lane);
-    for (int i = lane; i < L; i += 32) src[i] = b[i];
+    for (int i = lane; i < L; i += 32) b[pad8(i)] = src[i];
   }
+  __syncthreads();
+  if (row >= n_rows) return;
+  Fft<L, INV>::go(b, tw, lane);
+#pragma unroll
+  for (int i = lane; i < L; i += 32) src[i] = b[pad8(i)];
 }
 
 template <bool INV>

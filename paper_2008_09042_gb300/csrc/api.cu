@@ -243,6 +243,7 @@ extern "C" mpi_status mpi_ctx_destroy(mpi_ctx* ctx) {
     cudaEventDestroy(ctx->ev_begin[i]);
     cudaEventDestroy(ctx->ev_end[i]);
   }
+  solver_cache_clear(ctx);
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->twiddles) cudaFree(ctx->twiddles);
   if (ctx->coef_img) cudaFree(ctx->coef_img);
@@ -436,6 +437,7 @@ extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
   if (!plan) return MPI_ERR_ARG;
   DeviceGuard g(plan->ctx->device);
   cudaStreamSynchronize(plan->ctx->stream);
+  solver_cache_forget(plan->ctx, plan);
   void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw,
                   plan->deap, plan->bin_ptr, plan->bin_perm};
   for (void* p : ptrs)
@@ -545,6 +547,7 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   if (!b) return MPI_ERR_ARG;
   DeviceGuard g(b->ctx->device);
   cudaStreamSynchronize(b->ctx->stream);
+  solver_cache_forget(b->ctx, b);
   if (b->U) cudaFree(b->U);
   if (b->Ubf) cudaFree(b->Ubf);
   tc_basis_release(b);

@@ -31,6 +31,7 @@ struct mpi_ctx {
   int num_sms = 0;
   int* dev_err = nullptr;  // device error word written by kernels whose waits time out
   void* coef_img = nullptr;  // BF16 coefficient operand image for the tensor-core expansion
+  void* solver_cache = nullptr;  // recorded solver graphs (solvers.cu)
   int64_t launches = 0;
   std::string err;
   // profiling: event pairs around launches while enabled
@@ -145,6 +146,10 @@ mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, in
 mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,
                           float2* partials, size_t partial_cap);
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS);
+
+// Drop recorded solver graphs that reference `object` (a plan or basis), or all of them.
+void solver_cache_forget(mpi_ctx* ctx, const void* object);
+void solver_cache_clear(mpi_ctx* ctx);
 
 // ------------------------------------------------------------ FFT passes
 

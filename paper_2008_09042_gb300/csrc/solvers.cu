@@ -10,6 +10,8 @@
 // the host; only the residual histories are copied back at the end.
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -580,27 +582,127 @@ mpi_status tv_prox_run(Solver& sv, const Grid3& g, long N, const float2* b, int 
 
 }  // namespace
 
-// ------------------------------------------------------------------ MPI-BL
+// ------------------------------------------------------- solver graph cache
+//
+// A solve enqueues thousands of small kernels; on small grids their launch
+// cost dominates.  Each solve is therefore recorded once into a CUDA graph
+// over solver buffers that the context keeps (keyed by plan, basis, coils,
+// precision and parameters), with its inputs copied into and its outputs
+// copied out of those buffers around one graph launch.  Destroying a plan or
+// basis drops the graphs that reference it; growing the context workspace
+// (which the graphs also reference) drops all of them.
 
-extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, const mpi_c32* y,
-                                      int C, const mpi_irgn_params* prm, mpi_c32* alpha_out, mpi_c32* p_out,
-                                      double* resid_out, mpi_precision prec) {
-  if (!ctx) return MPI_ERR_ARG;
-  if (!plan || !basis || !prm || !alpha_out || !p_out || C < 1 || (plan->M > 0 && !y))
-    return set_err(ctx, MPI_ERR_ARG, "sm_estimate: bad argument");
-  if (prm->n_outer < 0 || prm->n_cg < 0) return set_err(ctx, MPI_ERR_ARG, "negative iteration count");
-  cudaSetDevice(ctx->device);
-  const long N = plan->N, Cq = (long)C * basis->q, CM = (long)C * plan->M, X = N + Cq;
-  // x, dx, res, d, Ad, h (X each); ys, yt, r (CM each)
+namespace {
+
+struct SolverGraph {
+  int kind = 0;  // 0 = MPI-BL, 1 = MPI-L
+  const mpi_plan* plan = nullptr;
+  const mpi_basis* basis = nullptr;
+  int C = 0;
+  int prec = 0;
+  std::vector<unsigned char> key;
+  void* work = nullptr;  // ctx->work at capture time
   SolverMem mem;
   Solver sv;
-  float2* base;
-  double* hist;
-  TRY(alloc_solver(ctx, mem, 6 * X + 3 * std::max(CM, 1L), prm->n_outer + 1, sv, &base, &hist));
+  float2* base = nullptr;  // solver vectors
+  double* dbase = nullptr;
+  float2* in_y = nullptr;
+  float2* in_alpha = nullptr;
+  double* in_eps = nullptr;
+  float2* out_alpha = nullptr;
+  float2* out_p = nullptr;
+  double* hist = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+  ~SolverGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+struct SolverCache {
+  std::vector<SolverGraph*> entries;
+};
+
+SolverCache* cache_of(mpi_ctx* ctx) {
+  if (!ctx->solver_cache) ctx->solver_cache = new SolverCache();
+  return (SolverCache*)ctx->solver_cache;
+}
+
+SolverGraph* cache_find(mpi_ctx* ctx, int kind, const mpi_plan* plan, const mpi_basis* basis, int C, int prec,
+                        const void* prm, size_t prm_bytes) {
+  SolverCache* c = cache_of(ctx);
+  for (size_t i = 0; i < c->entries.size(); ++i) {
+    SolverGraph* e = c->entries[i];
+    if (e->kind == kind && e->plan == plan && e->basis == basis && e->C == C && e->prec == prec &&
+        e->key.size() == prm_bytes && memcmp(e->key.data(), prm, prm_bytes) == 0) {
+      if (e->work != ctx->work) {  // the workspace moved: the recorded kernels point at the old one
+        delete e;
+        c->entries.erase(c->entries.begin() + i);
+        return nullptr;
+      }
+      return e;
+    }
+  }
+  return nullptr;
+}
+
+void cache_insert(mpi_ctx* ctx, SolverGraph* g) {
+  SolverCache* c = cache_of(ctx);
+  constexpr size_t kMaxEntries = 8;
+  if (c->entries.size() >= kMaxEntries) {
+    delete c->entries.front();
+    c->entries.erase(c->entries.begin());
+  }
+  c->entries.push_back(g);
+}
+
+// Record `body` (which enqueues on ctx->stream) into a graph on a private stream.
+template <class F>
+mpi_status capture(mpi_ctx* ctx, SolverGraph* g, F body) {
+  cudaStream_t cap = nullptr, user = ctx->stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "solver capture stream");
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  ctx->stream = cap;
+  const int64_t l0 = ctx->launches;
+  mpi_status st = MPI_OK;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = body();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (st == MPI_OK && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st == MPI_OK && e2 != cudaSuccess) st = cuda_check(ctx, e2, "solver graph");
+  } else {
+    st = cuda_check(ctx, e, "solver capture begin");
+  }
+  g->kernels = ctx->launches - l0;
+  ctx->launches = l0;
+  ctx->stream = user;
+  ctx->profiling = prof;
+  cudaStreamDestroy(cap);
+  return st;
+}
+
+mpi_status launch_graph(mpi_ctx* ctx, SolverGraph* g) {
+  cudaError_t e = cudaGraphLaunch(g->exec, ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "solver graph launch");
+  ctx->launches += g->kernels;
+  return MPI_OK;
+}
+
+// ------------------------------------------------------------------ MPI-BL
+
+// Enqueue the IRGN solve.  Inputs: y (C x M).  Outputs: alpha_out, p_out, hist.
+mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C, const mpi_irgn_params* prm,
+                     mpi_precision prec, Solver& sv, float2* base, const float2* yc, float2* alpha_out,
+                     float2* p_out, double* hist) {
+  const long N = plan->N, Cq = (long)C * basis->q, CM = (long)C * plan->M, X = N + Cq;
   float2 *x = base, *dx = x + X, *res = dx + X, *d = res + X, *Ad = d + X, *h = Ad + X;
   float2 *ys = h + X, *yt = ys + std::max(CM, 1L), *r = yt + std::max(CM, 1L);
   float2 *p = x, *al = x + N;
-  auto* yc = (const float2*)y;
   // data scale: ys = y * target / ||y||
   if (CM > 0) {
     TRY(sv.dot(yc, nullptr, CM, FIN_SCALE, 0, prm->scale_target));
@@ -648,12 +750,65 @@ extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const 
     TRY(sv.lincomb(x, x, 1.f, dx, (float)prm->gamma, X));
   }
   // outputs: alpha, p / scale
-  TRY(sv.lincomb((float2*)alpha_out, al, 1.f, nullptr, 0.f, Cq));
-  TRY(sv.scale_dev((float2*)p_out, p, N, S_SCALE, 1));
+  TRY(sv.lincomb(alpha_out, al, 1.f, nullptr, 0.f, Cq));
+  TRY(sv.scale_dev(p_out, p, N, S_SCALE, 1));
+  return MPI_OK;
+}
+
+}  // namespace
+
+extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, const mpi_c32* y,
+                                      int C, const mpi_irgn_params* prm, mpi_c32* alpha_out, mpi_c32* p_out,
+                                      double* resid_out, mpi_precision prec) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!plan || !basis || !prm || !alpha_out || !p_out || C < 1 || (plan->M > 0 && !y))
+    return set_err(ctx, MPI_ERR_ARG, "sm_estimate: bad argument");
+  if (prm->n_outer < 0 || prm->n_cg < 0) return set_err(ctx, MPI_ERR_ARG, "negative iteration count");
+  cudaSetDevice(ctx->device);
+  TRY(mpi_ctx_reserve(ctx, plan, basis, C));
+  const long N = plan->N, Cq = (long)C * basis->q, CM = (long)C * plan->M, X = N + Cq;
+  const long CMs = std::max(CM, 1L);
+  SolverGraph* g = cache_find(ctx, 0, plan, basis, C, prec, prm, sizeof(*prm));
+  if (!g) {
+    g = new SolverGraph();
+    g->kind = 0;
+    g->plan = plan;
+    g->basis = basis;
+    g->C = C;
+    g->prec = prec;
+    g->key.assign((const unsigned char*)prm, (const unsigned char*)prm + sizeof(*prm));
+    // x, dx, res, d, Ad, h (X each); ys, yt, r (CM each); in_y, out_alpha, out_p
+    mpi_status st = alloc_solver(ctx, g->mem, 6 * X + 4 * CMs + Cq + N, prm->n_outer + 1, g->sv, &g->base, &g->dbase);
+    if (st) {
+      delete g;
+      return st;
+    }
+    g->in_y = g->base + 6 * X + 3 * CMs;
+    g->out_alpha = g->in_y + CMs;
+    g->out_p = g->out_alpha + Cq;
+    g->hist = g->dbase;
+    g->work = ctx->work;
+    st = capture(ctx, g, [&]() {
+      return irgn_body(ctx, plan, basis, C, prm, prec, g->sv, g->base, g->in_y, g->out_alpha, g->out_p, g->hist);
+    });
+    if (st) {
+      delete g;
+      return st;
+    }
+    cache_insert(ctx, g);
+  }
+  if (CM > 0)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(g->in_y, y, CM * sizeof(float2), cudaMemcpyDeviceToDevice, ctx->stream),
+                   "input copy"));
+  TRY(launch_graph(ctx, g));
+  TRY(cuda_check(ctx, cudaMemcpyAsync(alpha_out, g->out_alpha, Cq * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                      ctx->stream), "output copy"));
+  TRY(cuda_check(ctx, cudaMemcpyAsync(p_out, g->out_p, N * sizeof(float2), cudaMemcpyDeviceToDevice, ctx->stream),
+                 "output copy"));
   if (resid_out) {
     if (CM > 0)
-      TRY(cuda_check(ctx, cudaMemcpyAsync(resid_out, hist, (prm->n_outer + 1) * sizeof(double), cudaMemcpyDeviceToHost,
-                                          ctx->stream), "history copy"));
+      TRY(cuda_check(ctx, cudaMemcpyAsync(resid_out, g->hist, (prm->n_outer + 1) * sizeof(double),
+                                          cudaMemcpyDeviceToHost, ctx->stream), "history copy"));
     else
       for (int i = 0; i <= prm->n_outer; ++i) resid_out[i] = 0.0;
   }
@@ -662,38 +817,21 @@ extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const 
 
 // ------------------------------------------------------------------- MPI-L
 
-extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
-                                      const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
-                                      const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out,
-                                      mpi_precision prec) {
-  if (!ctx) return MPI_ERR_ARG;
-  if (!plan || !basis || !alpha || !eps || !prm || !p_out || C < 1 || (plan->M > 0 && !y))
-    return set_err(ctx, MPI_ERR_ARG, "image_solve: bad argument");
-  if (prm->n_outer < 0 || prm->n_cg < 0 || prm->n_tv < 0 || !(prm->rho0 > 0) || !(prm->tau > 0))
-    return set_err(ctx, MPI_ERR_ARG, "image_solve: bad parameters");
-  for (int c = 0; c < C; ++c)
-    if (!(eps[c] >= 0)) return set_err(ctx, MPI_ERR_ARG, "eps must be >= 0");
-  cudaSetDevice(ctx->device);
+namespace {
+
+// Enqueue the ADMM solve.  Inputs: alpha (C x q), y (C x M), eps_d (C, device).
+// Outputs: p_out, hist (n_outer x 3).
+mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C, const mpi_admm_params* prm,
+                     mpi_precision prec, Solver& sv, float2* base, double* dx, const mpi_c32* A, const float2* yc,
+                     const double* eps_d, float2* p_out, double* hist) {
   const Grid3 g = grid_of(plan);
   const long N = plan->N, M = plan->M, CM = (long)C * M, CMs = std::max(CM, 1L);
-  // image side: p, p_prev, u0, z0, rhs, t, r, d, Ad, tvx (10 N) + P, R (2 nd N)
-  // k-space: uk, zk, Apk, Apk_prev, wk (5 CM)
-  SolverMem mem;
-  Solver sv;
-  float2* base;
-  double* dx;
-  const size_t extra = (size_t)3 * prm->n_outer + 2 * (size_t)C + (size_t)C * kRedBlocks + 8;
-  TRY(alloc_solver(ctx, mem, 10 * N + 2 * (size_t)g.nd * N + 5 * CMs, extra, sv, &base, &dx));
   float2 *p = base, *p_prev = p + N, *u0 = p_prev + N, *z0 = u0 + N, *rhs = z0 + N, *t = rhs + N;
   float2 *r = t + N, *d = r + N, *Ad = d + N, *tvx = Ad + N, *P = tvx + N, *R = P + (size_t)g.nd * N;
   float2 *uk = R + (size_t)g.nd * N, *zk = uk + CMs, *Apk = zk + CMs, *Apk_prev = Apk + CMs, *wk = Apk_prev + CMs;
-  double* hist = dx;
-  double* eps_d = hist + 3 * (size_t)prm->n_outer;
-  double* fball = eps_d + C;
+  (void)tvx;
+  double* fball = dx;
   double* bpart = fball + C;
-  TRY(cuda_check(ctx, cudaMemcpyAsync(eps_d, eps, C * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "eps"));
-  const float2* yc = (const float2*)y;
-  const mpi_c32* A = alpha;
   TRY(sv.fill(p, make_float2(0.f, 0.f), N));
   TRY(sv.fill(u0, make_float2(0.f, 0.f), N));
   if (CM > 0) {
@@ -774,11 +912,96 @@ extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const 
     TRY(sv.scale_dev(u0, u0, N, S_UFAC, 0));
     if (CM > 0) TRY(sv.scale_dev(uk, uk, CM, S_UFAC, 0));
   }
-  TRY(sv.lincomb((float2*)p_out, p, 1.f, nullptr, 0.f, N));
+  return sv.lincomb(p_out, p, 1.f, nullptr, 0.f, N);
+}
+
+}  // namespace
+
+extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                      const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
+                                      const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out,
+                                      mpi_precision prec) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!plan || !basis || !alpha || !eps || !prm || !p_out || C < 1 || (plan->M > 0 && !y))
+    return set_err(ctx, MPI_ERR_ARG, "image_solve: bad argument");
+  if (prm->n_outer < 0 || prm->n_cg < 0 || prm->n_tv < 0 || !(prm->rho0 > 0) || !(prm->tau > 0))
+    return set_err(ctx, MPI_ERR_ARG, "image_solve: bad parameters");
+  for (int c = 0; c < C; ++c)
+    if (!(eps[c] >= 0)) return set_err(ctx, MPI_ERR_ARG, "eps must be >= 0");
+  cudaSetDevice(ctx->device);
+  TRY(mpi_ctx_reserve(ctx, plan, basis, C));
+  const Grid3 gr = grid_of(plan);
+  const long N = plan->N, M = plan->M, CM = (long)C * M, CMs = std::max(CM, 1L), Cq = (long)C * basis->q;
+  SolverGraph* g = cache_find(ctx, 1, plan, basis, C, prec, prm, sizeof(*prm));
+  if (!g) {
+    g = new SolverGraph();
+    g->kind = 1;
+    g->plan = plan;
+    g->basis = basis;
+    g->C = C;
+    g->prec = prec;
+    g->key.assign((const unsigned char*)prm, (const unsigned char*)prm + sizeof(*prm));
+    // image side: 10 N + 2 nd N; k-space: 5 CM; inputs y (CM), alpha (Cq); output p (N)
+    const size_t elems = 10 * N + 2 * (size_t)gr.nd * N + 5 * CMs + CMs + Cq + N;
+    const size_t extra = 2 * (size_t)C + (size_t)C * kRedBlocks + 3 * (size_t)prm->n_outer + C + 8;
+    mpi_status st = alloc_solver(ctx, g->mem, elems, extra, g->sv, &g->base, &g->dbase);
+    if (st) {
+      delete g;
+      return st;
+    }
+    float2* io = g->base + 10 * N + 2 * (size_t)gr.nd * N + 5 * CMs;
+    g->in_y = io;
+    g->in_alpha = io + CMs;
+    g->out_p = g->in_alpha + Cq;
+    double* scratch = g->dbase;                                   // fball, bpart
+    g->hist = scratch + 2 * (size_t)C + (size_t)C * kRedBlocks;  // [n_outer][3]
+    g->in_eps = g->hist + 3 * (size_t)prm->n_outer;
+    g->work = ctx->work;
+    st = capture(ctx, g, [&]() {
+      return admm_body(ctx, plan, basis, C, prm, prec, g->sv, g->base, scratch, (const mpi_c32*)g->in_alpha,
+                       g->in_y, g->in_eps, g->out_p, g->hist);
+    });
+    if (st) {
+      delete g;
+      return st;
+    }
+    cache_insert(ctx, g);
+  }
+  TRY(cuda_check(ctx, cudaMemcpyAsync(g->in_alpha, alpha, Cq * sizeof(float2), cudaMemcpyDeviceToDevice, ctx->stream),
+                 "input copy"));
+  if (CM > 0)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(g->in_y, y, CM * sizeof(float2), cudaMemcpyDeviceToDevice, ctx->stream),
+                   "input copy"));
+  TRY(cuda_check(ctx, cudaMemcpyAsync(g->in_eps, eps, C * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+                 "eps copy"));
+  TRY(launch_graph(ctx, g));
+  TRY(cuda_check(ctx, cudaMemcpyAsync(p_out, g->out_p, N * sizeof(float2), cudaMemcpyDeviceToDevice, ctx->stream),
+                 "output copy"));
   if (hist_out && prm->n_outer > 0)
-    TRY(cuda_check(ctx, cudaMemcpyAsync(hist_out, hist, 3 * (size_t)prm->n_outer * sizeof(double),
+    TRY(cuda_check(ctx, cudaMemcpyAsync(hist_out, g->hist, 3 * (size_t)prm->n_outer * sizeof(double),
                                         cudaMemcpyDeviceToHost, ctx->stream), "history copy"));
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "image_solve");
+}
+
+void solver_cache_forget(mpi_ctx* ctx, const void* object) {
+  if (!ctx || !ctx->solver_cache) return;
+  SolverCache* c = (SolverCache*)ctx->solver_cache;
+  for (size_t i = 0; i < c->entries.size();) {
+    if (c->entries[i]->plan == object || c->entries[i]->basis == object) {
+      delete c->entries[i];
+      c->entries.erase(c->entries.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+void solver_cache_clear(mpi_ctx* ctx) {
+  if (!ctx || !ctx->solver_cache) return;
+  SolverCache* c = (SolverCache*)ctx->solver_cache;
+  for (SolverGraph* e : c->entries) delete e;
+  delete c;
+  ctx->solver_cache = nullptr;
 }
 
 extern "C" mpi_status mpi_tv_prox(mpi_ctx* ctx, const mpi_plan* plan, const mpi_c32* v, double lam, int n_iter,

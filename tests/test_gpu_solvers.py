@@ -106,3 +106,25 @@ def test_image_solve_matches_oracle_admm(ctx, mp, prob):
                                    n_outer=50, n_cg=5, n_tv=10)
     assert nrmse(f64(p), p_ref) < 1e-3
     np.testing.assert_array_equal(hist[:, 2], h_ref[:, 2])  # same rho decisions
+
+
+def test_solver_graph_replay_is_deterministic(ctx, mp, prob):
+    # The second solve on the same geometry replays the recorded graph with new
+    # inputs copied in: results must match a fresh solve exactly.
+    plan = mp.Plan(ctx, (prob["ny"], prob["nx"]), sample_idx=prob["idx"])
+    B = mp.Basis(ctx, prob["U"].T)
+    y1 = c64(prob["y"])
+    y2 = c64(prob["y"] * 0.5 + 0.01)
+    a1, p1, h1 = mp.sm_estimate(ctx, plan, B, y1, prob["C"], n_outer=6, n_cg=5)
+    a2, p2, h2 = mp.sm_estimate(ctx, plan, B, y2, prob["C"], n_outer=6, n_cg=5)
+    a1b, p1b, h1b = mp.sm_estimate(ctx, plan, B, y1, prob["C"], n_outer=6, n_cg=5)
+    assert torch.equal(a1, a1b) and torch.equal(p1, p1b) and np.array_equal(h1, h1b)
+    assert not torch.equal(a1, a2)
+    # a new plan object at possibly the same address must not reuse stale graphs
+    del plan
+    plan2 = mp.Plan(ctx, (prob["ny"], prob["nx"]), sample_idx=prob["idx"])
+    a3, p3, _ = mp.sm_estimate(ctx, plan2, B, y1, prob["C"], n_outer=6, n_cg=5)
+    assert torch.equal(a1, a3) and torch.equal(p1, p3)
+    pa, ha = mp.image_solve(ctx, plan2, B, a1, y1, prob["eps"], n_outer=5, n_cg=3, n_tv=4)
+    pb, hb = mp.image_solve(ctx, plan2, B, a1, y1, prob["eps"], n_outer=5, n_cg=3, n_tv=4)
+    assert torch.equal(pa, pb) and np.array_equal(ha, hb)

@@ -179,8 +179,28 @@ def blas_threads():
         return os.cpu_count()
 
 
-def time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, steps, warmup, flush, stream):
-    """Mean ms of one forward + adjoint pair (CUDA events, L2 flushed between pairs)."""
+def reduce_max(value, device=None):
+    """Max of a scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, units_per_rank, slowest_ms):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (slowest_ms / 1000.0)
+
+
+def time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, steps, warmup, flush, stream, breakdown=None):
+    """Mean ms of one forward + adjoint pair (CUDA events, L2 flushed between pairs).
+
+    With ``breakdown`` (a dict), a second pass with the library's per-launch
+    events fills it with the mean ms per pair of each kernel family."""
     import torch
 
     C = a_d.shape[0]
@@ -201,6 +221,16 @@ def time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, steps, warmup, flush, strea
         e.synchronize()
         total += s.elapsed_time(e)
     ctx.synchronize()
+    if breakdown is not None:
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        for _ in range(steps):
+            flush.zero_()
+            mp.forward(ctx, plan, basis, a_d, p_d, prec, out=y)
+            mp.adjoint(ctx, plan, basis, a_d, y, prec, out=x)
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        breakdown.update({k: v[0] / steps for k, v in prof.items() if v[1]})
     return total / steps
 
 
@@ -219,8 +249,10 @@ def secondary_workloads(mp, ctx, dev, flush, stream, steps=10, warmup=3):
     a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 1).astype(np.complex64)).to(dev)
     p = torch.from_numpy(w.random_ellipses(n, n, seed=base + 2).ravel().astype(np.complex64)).to(dev)
     for prec in ("fp32", "bf16"):
-        ms = time_pairs(mp, ctx, plan, B, a, p, prec, steps, warmup, flush, stream)
-        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms}
+        bd = {}
+        ms = time_pairs(mp, ctx, plan, B, a, p, prec, steps, warmup, flush, stream, bd)
+        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms,
+                                        "kernel_ms_per_pair": bd}
     del plan, B
     # 3D 96 x 128 x 128, 32 coils, Tucker q = 256, ranks (32, 40, 40), 3D Poisson-disc R = 8
     cfg = w.workload("cart3d_128x128x96_c32_tucker256")
@@ -235,8 +267,10 @@ def secondary_workloads(mp, ctx, dev, flush, stream, steps=10, warmup=3):
                          .astype(np.complex64)).to(dev)
     ctx.reserve(plan, B, cfg["C"])
     for prec in ("fp32", "bf16"):
-        ms = time_pairs(mp, ctx, plan, B, a, p, prec, max(3, steps // 2), 2, flush, stream)
-        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms}
+        bd = {}
+        ms = time_pairs(mp, ctx, plan, B, a, p, prec, max(3, steps // 2), 2, flush, stream, bd)
+        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms,
+                                        "kernel_ms_per_pair": bd}
     del plan, B
     return out
 
@@ -425,14 +459,8 @@ def run_ours(args):
     clk = clocks.stop()
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    total_ms = sum(s.elapsed_time(e) for s, e in evs)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = reduce_max(sum(s.elapsed_time(e) for s, e in evs), dev)
+    value = replica_throughput(world, args.steps, total_ms)
 
     # ---- end to end: pinned host buffers, copies inside the timed region
     a_h = torch.from_numpy(alpha.astype(np.complex64)).pin_memory()
@@ -464,13 +492,8 @@ def run_ours(args):
         e.record(stream)
         e.synchronize()
         e2e_ms += s.elapsed_time(e)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * args.steps / (e2e_ms / 1000.0)
+    e2e_ms = reduce_max(e2e_ms, dev)
+    e2e_value = replica_throughput(world, args.steps, e2e_ms)
     h2d = (C * q + N + C * M) * 8
     d2h = (C * M + N) * 8
 

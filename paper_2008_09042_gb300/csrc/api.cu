@@ -438,8 +438,7 @@ extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
   DeviceGuard g(plan->ctx->device);
   cudaStreamSynchronize(plan->ctx->stream);
   solver_cache_forget(plan->ctx, plan);
-  void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw,
-                  plan->deap, plan->bin_ptr, plan->bin_perm};
+  void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw, plan->deap};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete plan;

@@ -62,9 +62,6 @@ struct mpi_plan {
   int32_t* gstart = nullptr;  // [M][2] first tap, array index in [0, G)
   float* gw = nullptr;        // [M][2][W] separable kernel weights
   float* deap = nullptr;      // [n] 1 / Phi(t), t = j - n/2
-  int32_t* bin_ptr = nullptr;  // spreading: samples sorted by grid tile
-  int32_t* bin_perm = nullptr;
-  int n_bins_x = 0, n_bins_y = 0;
 };
 
 struct mpi_basis {

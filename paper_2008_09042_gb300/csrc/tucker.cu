@@ -37,12 +37,14 @@ constexpr int kIB = 16;  // outputs along i per thread
 // Y[r][i][b] = sum_p X[r][p][b] M(i, p), with M(i, p) = F[i][p] (forward, F is I x P)
 // or conj(F[p][i]) (adjoint, F is P x I).  Threads run along b (coalesced);
 // each thread keeps kIB outputs along i in registers; M is staged in shared
-// memory as [P][kIB] for the CTA's i-block.
+// memory as [P][kIB] for the CTA's i-block.  The i-block is the fastest grid
+// index, so the CTAs that read the same X tile run together and all but the
+// first find it in L2.
 template <bool ADJ>
 __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, const float2* __restrict__ F, int R,
                                                 int P, int I, long B, float2* __restrict__ Y) {
   __shared__ float2 sM[128 * kIB];
-  const int i0 = blockIdx.z * kIB;
+  const int i0 = blockIdx.x * kIB;
   for (int e = threadIdx.x; e < P * kIB; e += blockDim.x) {
     const int p = e / kIB, ii = e % kIB;
     const int i = i0 + ii;
@@ -58,8 +60,8 @@ __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, co
     sM[e] = m;
   }
   __syncthreads();
-  const long b = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
+  const long b = (long)blockIdx.y * blockDim.x + threadIdx.x;
+  const int r = blockIdx.z;  // blockDim.x is B rounded to a warp multiple, at most 256
   if (b >= B || r >= R) return;
   float2 acc[kIB];
 #pragma unroll
@@ -162,11 +164,12 @@ __global__ void k_pointwise(ExpandArgs a, const float2* __restrict__ S, const fl
 
 mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, long B, float2* Y) {
   if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
-  const dim3 grid((unsigned)((B + 255) / 256), (unsigned)R, (unsigned)((I + kIB - 1) / kIB));
-  if (R > 65535 || grid.z > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
+  const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);  // no idle lanes when B = 128
+  const dim3 grid((unsigned)((I + kIB - 1) / kIB), (unsigned)((B + block - 1) / block), (unsigned)R);
+  if (R > 65535 || grid.y > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
   MPI_PROF(ctx, KF_EXPAND);
-  if (adj) k_mode_b<true><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
-  else k_mode_b<false><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
+  if (adj) k_mode_b<true><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
+  else k_mode_b<false><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
   MPI_LAUNCH_CHECK(ctx, "k_mode_b");
   return MPI_OK;
 }
@@ -174,9 +177,10 @@ mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int 
 mpi_status mode_last(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, float2* Y) {
   if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
   const unsigned grid = (unsigned)((R + 7) / 8);
+  const int block = std::min(256, (I + 31) / 32 * 32);  // threads run along i
   MPI_PROF(ctx, KF_EXPAND);
-  if (adj) k_mode_last<true><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, Y);
-  else k_mode_last<false><<<grid, 256, 0, ctx->stream>>>(X, F, R, P, I, Y);
+  if (adj) k_mode_last<true><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, Y);
+  else k_mode_last<false><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, Y);
   MPI_LAUNCH_CHECK(ctx, "k_mode_last");
   return MPI_OK;
 }

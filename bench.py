@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cart2d_256_c16_q128")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp32_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the radial/3D/recon lines")
     return ap.parse_args()
@@ -442,8 +442,6 @@ def run_ours(args):
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local_rank)
-    ctx.profile(True)
-    ctx.profile_read(reset=True)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -456,11 +454,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     launches = ctx.launches() - launches0
+    total_ms = reduce_max(sum(s.elapsed_time(e) for s, e in evs), dev)
+    value = replica_throughput(world, args.steps, total_ms)
+    # Per-launch kernel durations: the same K steps again, each launch bracketed by
+    # the library's own events on its stream.  A separate region, because the
+    # extra event records between launches slow the step they sit in.
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
     clk = clocks.stop()
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    total_ms = reduce_max(sum(s.elapsed_time(e) for s, e in evs), dev)
-    value = replica_throughput(world, args.steps, total_ms)
 
     # ---- end to end: pinned host buffers, copies inside the timed region
     a_h = torch.from_numpy(alpha.astype(np.complex64)).pin_memory()
@@ -502,34 +509,43 @@ def run_ours(args):
     ex_ms, ex_n = prof["expand"]
     fam_total = sum(v[0] for v in prof.values())
     ex_avg_s = ex_ms / max(ex_n, 1) / 1000.0
-    # per launch: read U (N q), alpha (C q), the image or per-coil data, write per-coil data or image
-    ex_bytes = (N * q + C * q + C * N + N) * (8 if args.prec == "fp32" else 4)
+    # per launch: read U (N q complex; 8 B per element in FP32, 4 B as BF16), alpha (C q),
+    # the image or the per-coil data (C N + N complex64), write the per-coil data or the image
+    u_bytes = 4 if args.prec == "bf16" else 8
+    ex_bytes = N * q * u_bytes + (C * q + C * N + N) * 8
     ex_flops = 8.0 * N * q * C
-    if args.prec == "fp32":
-        t_hbm = ex_bytes / (hbm_gbs * 1e9)
-        t_alu = ex_flops / (FP32_ALU_TFLOPS * 1e12)
-        if t_alu >= t_hbm:
-            roof = {"bound": "alu", "achieved": ex_flops / ex_avg_s / 1e12, "peak": FP32_ALU_TFLOPS,
-                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-        else:
-            roof = {"bound": "hbm", "achieved": ex_bytes / ex_avg_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
-                    "peak_source": f"{peak_src} HBM copy bandwidth"}
-    else:
-        roof = {"bound": "hbm", "achieved": ex_bytes / ex_avg_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+    t_hbm = ex_bytes / (hbm_gbs * 1e9)
+    hbm_roof = {"bound": "hbm", "achieved": ex_bytes / ex_avg_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
                 "peak_source": f"{peak_src} HBM copy bandwidth"}
+    if args.prec == "fp32_simt" and ex_flops / (FP32_ALU_TFLOPS * 1e12) >= t_hbm:
+        roof = {"bound": "alu", "achieved": ex_flops / ex_avg_s / 1e12, "peak": FP32_ALU_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+        kname = "k_expand (CUDA-core FFMA expansion fused with the point-wise products)"
+    elif args.prec == "fp32":
+        # three TF32 products per term; TF32 tensor rate = bf16 rate x 1.1 / 2.25 (nominal ratio)
+        tf32_tflops = bf16_tflops * 1.1 / 2.25
+        if 3 * ex_flops / (tf32_tflops * 1e12) > t_hbm:
+            roof = {"bound": "tensor", "achieved": 3 * ex_flops / ex_avg_s / 1e12, "peak": tf32_tflops,
+                    "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 x nominal tf32/bf16 ratio"}
+        else:
+            roof = hbm_roof
+        kname = "k_expand_tf32x3 (3xTF32 tcgen05 expansion fused with the point-wise products)"
+    else:
+        roof = hbm_roof
+        kname = "k_expand_tc (BF16 tcgen05 expansion fused with the point-wise products)"
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = "k_expand (basis expansion fused with the point-wise products)"
+    roof["kernel"] = kname
     roof["algorithmic_bytes_per_launch"] = ex_bytes
     roof["algorithmic_flops_per_launch"] = ex_flops
     roof["avg_launch_us"] = ex_avg_s * 1e6
     roof["share_of_kernel_time"] = ex_ms / fam_total if fam_total > 0 else None
-    roof["traffic"] = ncu_traffic("k_expand")
+    roof["traffic"] = ncu_traffic(kname.split()[0])
 
     line = {
         "metric": "MPI forward+adjoint operator pairs per second",
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16+f32",
+        "vs_baseline": None, "dtype": "bf16+f32" if args.prec == "bf16" else "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "C": C, "q": q, "M": M,
                    "mask": f"2D variable-density Poisson-disc R={cfg.get('R')} calib {cfg.get('calib')}",
@@ -538,12 +554,18 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "roofline": roof,
         "clocks": clk,
     }
     if not args.no_secondary:
         line["workloads"] = secondary_workloads(mp, ctx, dev, flush, stream)
+        for other in ("fp32", "fp32_simt", "bf16"):
+            if other != args.prec:
+                bd = {}
+                ms = time_pairs(mp, ctx, plan, basis, a_d, p_d, other, 10, 3, flush, stream, bd)
+                line["workloads"][f"{args.workload}/{other}"] = {"value": 1000.0 / ms, "unit": "pairs/s",
+                                                                 "ms_per_pair": ms, "kernel_ms_per_pair": bd}
         line["workloads"]["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
         line["recon"] = recon_per_slice(mp, ctx, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

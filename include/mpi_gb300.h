@@ -49,10 +49,14 @@ typedef enum {
 typedef enum { MPI_TRAJ_CARTESIAN = 0, MPI_TRAJ_RADIAL = 1 } mpi_traj_kind;
 
 /* Arithmetic of the basis expansion U alpha (the only dense contraction).
- * FP32: CUDA-core FFMA, FP32 in and out.  BF16: tensor cores, BF16 basis and
- * coefficients, FP32 accumulation.  FFT, gridding and reductions are FP32 in
- * both. */
-typedef enum { MPI_PREC_FP32 = 0, MPI_PREC_BF16 = 1 } mpi_precision;
+ * FP32: FP32 in and out at FP32 accuracy; on the tensor cores as three TF32
+ * products per term (hi*hi + hi*lo + lo*hi of the split operands, FP32
+ * accumulation) where the coefficient operand fits the kernel's shared-memory
+ * budget (2 C <= 256, or 4 C <= 256 for the Jacobian, and 2 q <= 256 or so),
+ * else on the CUDA cores.  BF16: tensor cores, BF16 basis and coefficients,
+ * FP32 accumulation.  FP32_SIMT: always the CUDA-core FFMA kernel.  FFT,
+ * gridding and reductions are FP32 in all three. */
+typedef enum { MPI_PREC_FP32 = 0, MPI_PREC_BF16 = 1, MPI_PREC_FP32_SIMT = 2 } mpi_precision;
 
 typedef struct mpi_ctx mpi_ctx;
 typedef struct mpi_plan mpi_plan;

@@ -97,17 +97,26 @@ mpi_status check_op(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, 
   if (plan->ctx != ctx || basis->ctx != ctx) return set_err(ctx, MPI_ERR_ARG, "plan/basis from another context");
   if (C < 1) return set_err(ctx, MPI_ERR_ARG, "C must be >= 1");
   if (basis->N != plan->N) return set_err(ctx, MPI_ERR_SHAPE, "basis N differs from plan N");
-  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return set_err(ctx, MPI_ERR_ARG, "bad precision");
+  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16 && prec != MPI_PREC_FP32_SIMT)
+    return set_err(ctx, MPI_ERR_ARG, "bad precision");
   const mpi_basis* eb = basis->tucker ? basis->core : basis;
   if (prec == MPI_PREC_BF16 && !eb->Ubf)
     return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + eb->bf16_err);
   return MPI_OK;
 }
 
+}  // namespace
+
+// FP32: the 3xTF32 tensor-core kernel where the shape fits its shared-memory
+// budget, else the CUDA-core FFMA kernel.  BF16: the BF16 tensor-core kernel.
+// FP32_SIMT: the FFMA kernel.
 mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec) {
   if (prec == MPI_PREC_BF16) return launch_expand_tc(ctx, basis, mode, a);
+  if (prec == MPI_PREC_FP32 && tf32_supported(basis, mode, a.C)) return launch_expand_tf32(ctx, basis, mode, a);
   return launch_expand(ctx, mode, a);
 }
+
+namespace {
 
 ExpandArgs base_args(const mpi_plan* plan, const mpi_basis* basis, int C) {
   ExpandArgs a;
@@ -489,6 +498,12 @@ extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N
     b->Ubf = nullptr;
     tc_basis_release(b);
   }
+  // FP32 operand copy for the 3xTF32 tensor-core path; without it FP32 runs on CUDA cores
+  if (tf32_basis_prepare(ctx, b) != MPI_OK) {
+    if (b->Uf32) cudaFree(b->Uf32);
+    b->Uf32 = nullptr;
+    tf32_basis_release(b);
+  }
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     mpi_status st = cuda_check(ctx, e, "basis conversion");
@@ -550,6 +565,8 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   if (b->U) cudaFree(b->U);
   if (b->Ubf) cudaFree(b->Ubf);
   tc_basis_release(b);
+  if (b->Uf32) cudaFree(b->Uf32);
+  tf32_basis_release(b);
   for (int k = 0; k < 3; ++k)
     if (b->F[k]) cudaFree(b->F[k]);
   if (b->core) mpi_basis_destroy(b->core);
@@ -563,7 +580,8 @@ extern "C" mpi_status mpi_basis_expand(mpi_ctx* ctx, const mpi_basis* basis, con
                                        mpi_c32* maps, mpi_precision prec) {
   if (!ctx) return MPI_ERR_ARG;
   if (!basis || bad_ptr(alpha) || bad_ptr(maps) || C < 1) return set_err(ctx, MPI_ERR_ARG, "bad argument");
-  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return set_err(ctx, MPI_ERR_ARG, "bad precision");
+  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16 && prec != MPI_PREC_FP32_SIMT)
+    return set_err(ctx, MPI_ERR_ARG, "bad precision");
   const mpi_basis* eb = basis->tucker ? basis->core : basis;
   if (prec == MPI_PREC_BF16 && !eb->Ubf)
     return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion unavailable: " + eb->bf16_err);
@@ -580,8 +598,7 @@ extern "C" mpi_status mpi_basis_expand(mpi_ctx* ctx, const mpi_basis* basis, con
   a.C = C;
   a.alpha = (const float2*)alpha;
   a.out = (float2*)maps;
-  if (prec == MPI_PREC_BF16) return launch_expand_tc(ctx, basis, EX_MAPS, a);
-  return launch_expand(ctx, EX_MAPS, a);
+  return expand(ctx, basis, EX_MAPS, a, prec);
 }
 
 extern "C" mpi_status mpi_forward(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,

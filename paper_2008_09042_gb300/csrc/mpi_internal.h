@@ -72,6 +72,9 @@ struct mpi_basis {
   size_t Ubf_bytes = 0;
   int Kp = 0;                    // padded K = round_up(2 q, 64)
   void* tmap = nullptr;          // CUtensorMap of Ubf (owned)
+  float* Uf32 = nullptr;         // FP32 operand copy [N][Kp32] (3xTF32 tensor-core path)
+  int Kp32 = 0;                  // round_up(2 q, 32)
+  void* tmap32 = nullptr;        // CUtensorMap of Uf32 (owned)
   std::string bf16_err;          // why the BF16 copy is missing, if it is
   // Tucker-factored basis (3D): N = n1 n2 n3; the core (r1 r2 r3 x q) is held
   // as an internal dense basis `core`; factors F[k] = U_k [n_k][r_k].
@@ -127,10 +130,17 @@ struct ExpandArgs {
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
+// Precision dispatch over the FFMA, 3xTF32 and BF16 expansion kernels.
+mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec);
 // BF16 tensor-core expansion (tcgen05); same modes and arguments.
 mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a);
 mpi_status tc_basis_prepare(mpi_ctx* ctx, mpi_basis* b);
 void tc_basis_release(mpi_basis* b);
+// FP32-accurate tensor-core expansion (3xTF32); same modes and arguments.
+mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a);
+bool tf32_supported(const mpi_basis* b, int mode, int C);
+mpi_status tf32_basis_prepare(mpi_ctx* ctx, mpi_basis* b);
+void tf32_basis_release(mpi_basis* b);
 // dalpha[c][j] = sum_n conj(U[j][n]) V[c][n]; partials in `work_partials`.
 mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
                        float2* dalpha, float2* work_partials, size_t partial_cap_elems);

@@ -212,7 +212,7 @@ mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, in
   a.C = C;
   a.alpha = alpha;
   a.out = g;
-  mpi_status st = prec == MPI_PREC_BF16 ? launch_expand_tc(ctx, b->core, EX_MAPS, a) : launch_expand(ctx, EX_MAPS, a);
+  mpi_status st = expand(ctx, b->core, EX_MAPS, a, prec);
   if (st) return st;
   if ((st = mode_last(ctx, false, g, b->F[2], C * r1 * r2, r3, n3, t1))) return st;
   if ((st = mode_b(ctx, false, t1, b->F[1], C * r1, r2, n2, n3, t2))) return st;

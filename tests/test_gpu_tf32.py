@@ -1,0 +1,111 @@
+"""GPU parity of the FP32 expansion on the tensor cores (3xTF32) against the FP64 oracle.
+
+MPI_PREC_FP32 runs the basis expansion as three TF32 products of the split
+operands (hi*hi + hi*lo + lo*hi), accumulated in FP32, wherever the coefficient
+operand fits the kernel's shared-memory budget, and on the CUDA cores otherwise;
+MPI_PREC_FP32_SIMT always takes the CUDA-core kernel.  Both must meet the FP32
+operator tolerance, relative L2 <= 1e-5 against the oracle.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as w
+from oracle import fourier, operator as op
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def c64(x):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x, dtype=np.complex64))).cuda()
+
+
+def f64(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import paper_2008_09042_gb300 as mp
+
+    return mp
+
+
+@pytest.fixture(scope="module")
+def ctx(mp):
+    return mp.Context(0)
+
+
+def _basis(N, q, seed):
+    rng = np.random.default_rng(seed)
+    U = np.linalg.qr(rng.normal(size=(N, q)) + 1j * rng.normal(size=(N, q)))[0]
+    return U.astype(np.complex64).astype(np.complex128)
+
+
+# ragged last pixel tile (N = 4000), K padded to the 32-element chunk (2q = 40,
+# 192, 320), one to eight K chunks, coefficient rows from 16 to 64
+@pytest.mark.parametrize("N,C,q", [(256, 4, 32), (4000, 3, 20), (65536, 16, 128), (8192, 32, 96), (4096, 12, 160)])
+def test_tf32_expand_shapes(ctx, mp, N, C, q):
+    U = _basis(N, q, N + C)
+    a = w.random_coefficients(C, q, seed=3).astype(np.complex64).astype(np.complex128)
+    B = mp.Basis(ctx, U.T)
+    ref = op.expand(U, a)
+    l0 = ctx.launches()
+    s_tc = f64(mp.basis_expand(ctx, B, c64(a), prec="fp32"))
+    l1 = ctx.launches()
+    s_simt = f64(mp.basis_expand(ctx, B, c64(a), prec="fp32_simt"))
+    l2 = ctx.launches()
+    ctx.synchronize()
+    assert l1 - l0 == 2, "FP32 expansion did not take the tensor-core kernel (coefficient image + expansion)"
+    assert l2 - l1 == 1
+    assert rel(s_tc, ref) < TOL
+    assert rel(s_simt, ref) < TOL
+    assert rel(s_tc, s_simt) < 5e-6
+
+
+def test_tf32_falls_back_to_cuda_cores_for_wide_coefficients(ctx, mp):
+    # 2C = 300 coefficient rows exceed the 256-row MMA: the FFMA kernel serves FP32
+    N, C, q = 2048, 150, 24
+    U = _basis(N, q, 5)
+    a = w.random_coefficients(C, q, seed=6).astype(np.complex64).astype(np.complex128)
+    B = mp.Basis(ctx, U.T)
+    l0 = ctx.launches()
+    s = f64(mp.basis_expand(ctx, B, c64(a), prec="fp32"))
+    assert ctx.launches() - l0 == 1
+    ctx.synchronize()
+    assert rel(s, op.expand(U, a)) < TOL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_simt"])
+@pytest.mark.parametrize("shape,C,q", [((64, 64), 4, 32), ((256, 256), 16, 128), ((128, 192), 32, 64)])
+def test_fp32_operator_family_matches_oracle(ctx, mp, prec, shape, C, q):
+    # forward, adjoint, Jacobian (coefficient rows doubled) and Jacobian-adjoint;
+    # at C = 32 the Jacobian's 128 coefficient rows leave the tensor-core kernel
+    # too little shared memory, so that one call runs on the CUDA cores
+    U = w.smooth_orthonormal_basis(shape[0], shape[1], q, seed=4).astype(np.complex64).astype(np.complex128)
+    mask = w.poisson_disc_mask(shape[0], shape[1], 4, calib=(12, 12), seed=5)
+    idx = w.mask_to_indices(mask)
+    Fs = fourier.CartesianSampling(shape, idx)
+    N = shape[0] * shape[1]
+    a = w.random_coefficients(C, q, seed=6).astype(np.complex64).astype(np.complex128)
+    p = w.random_image(N, seed=7).astype(np.complex64).astype(np.complex128)
+    dp = w.random_image(N, seed=8).astype(np.complex64).astype(np.complex128)
+    da = w.random_coefficients(C, q, seed=9).astype(np.complex64).astype(np.complex128)
+    r = w.random_coefficients(C, idx.size, seed=10, decay=False).astype(np.complex64).astype(np.complex128)
+    plan = mp.Plan(ctx, shape, sample_idx=idx)
+    B = mp.Basis(ctx, U.T)
+    ag, pg = c64(a), c64(p)
+    assert rel(f64(mp.forward(ctx, plan, B, ag, pg, prec=prec)), op.forward(Fs, U, a, p)) < TOL
+    assert rel(f64(mp.adjoint(ctx, plan, B, ag, c64(r), prec=prec)), op.adjoint(Fs, U, a, r)) < TOL
+    assert rel(f64(mp.jacobian(ctx, plan, B, ag, pg, c64(dp), c64(da), prec=prec)),
+               op.jacobian(Fs, U, a, p, dp, da)) < TOL
+    gp, ga = mp.jacobian_adjoint(ctx, plan, B, ag, pg, c64(r), prec=prec)
+    rp, ra = op.jacobian_adjoint(Fs, U, a, p, r)
+    assert rel(f64(gp), rp) < TOL and rel(f64(ga), ra) < TOL
+    ctx.synchronize()  # raises if a bounded wait ran out

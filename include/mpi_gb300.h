@@ -147,6 +147,16 @@ mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, const mpi_c3
                                  mpi_basis** out);
 mpi_status mpi_basis_destroy(mpi_basis* basis);
 
+/* Which kernel carries the dense contraction U alpha (for a Tucker basis, the
+ * core contraction) for C coils at precision `prec`; `jacobian` != 0 asks
+ * about the Jacobian's forward pass, which expands alpha and dalpha together.
+ * Returns MPI_EXPAND_FFMA (CUDA-core FP32), MPI_EXPAND_TF32X3 (tensor cores,
+ * FP32-accurate split) or MPI_EXPAND_BF16 (tensor cores, BF16 operands), or -1
+ * for a null basis, C < 1 or an unknown precision.  Host-side query: no device
+ * work. */
+enum { MPI_EXPAND_FFMA = 0, MPI_EXPAND_TF32X3 = 1, MPI_EXPAND_BF16 = 2 };
+int mpi_expand_path(const mpi_basis* basis, int C, int jacobian, mpi_precision prec);
+
 /* ------------------------------------------------------- operator (device) */
 
 /* maps[k] = U alpha_k for k < C (Eq. 5 inside F_s(.)).  alpha [C][q], maps [C][N]. */

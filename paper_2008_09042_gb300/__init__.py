@@ -17,6 +17,7 @@ from .api import (  # noqa: F401
     adjoint,
     basis_expand,
     basis_project,
+    expand_path,
     forward,
     jacobian,
     jacobian_adjoint,

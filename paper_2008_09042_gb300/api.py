@@ -245,6 +245,17 @@ def jacobian_adjoint(ctx, plan, basis, alpha, p, r, prec="fp32", out_p=None, out
     return out_p, out_alpha
 
 
+EXPAND_PATHS = {0: "ffma", 1: "tf32x3", 2: "bf16"}
+
+
+def expand_path(ctx, basis, C, prec="fp32", jacobian=False):
+    """Which kernel carries the contraction U alpha for C coils: "ffma", "tf32x3" or "bf16"."""
+    r = ctx.lib.mpi_expand_path(basis.h, int(C), int(bool(jacobian)), PREC[prec])
+    if r < 0:
+        raise ValueError("mpi_expand_path: bad arguments")
+    return EXPAND_PATHS[r]
+
+
 def basis_project(ctx, basis, maps):
     C = maps.shape[0]
     _need(maps, (C, basis.N), "maps")

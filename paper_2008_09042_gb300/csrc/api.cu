@@ -107,6 +107,22 @@ mpi_status check_op(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, 
 
 }  // namespace
 
+extern "C" int mpi_expand_path(const mpi_basis* basis, int C, int jacobian, mpi_precision prec) {
+  if (!basis || C < 1) return -1;
+  const mpi_basis* eb = basis->tucker ? basis->core : basis;
+  const int mode = jacobian ? EX_JFWD : EX_FWD;
+  switch (prec) {
+    case MPI_PREC_BF16:
+      return MPI_EXPAND_BF16;
+    case MPI_PREC_FP32:
+      return tf32_supported(eb, mode, C) ? MPI_EXPAND_TF32X3 : MPI_EXPAND_FFMA;
+    case MPI_PREC_FP32_SIMT:
+      return MPI_EXPAND_FFMA;
+    default:
+      return -1;
+  }
+}
+
 // FP32: the 3xTF32 tensor-core kernel where the shape fits its shared-memory
 // budget, else the CUDA-core FFMA kernel.  BF16: the BF16 tensor-core kernel.
 // FP32_SIMT: the FFMA kernel.
@@ -233,7 +249,6 @@ extern "C" mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_strea
     ctx->dev_err = (int*)((char*)ctx->twiddles + ((host.size() * sizeof(float2) + 127) & ~(size_t)127));
     e = cudaMemset(ctx->dev_err, 0, sizeof(int));
   }
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->coef_img, kCoefImgBytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (ctx->twiddles) cudaFree(ctx->twiddles);
@@ -255,7 +270,6 @@ extern "C" mpi_status mpi_ctx_destroy(mpi_ctx* ctx) {
   solver_cache_clear(ctx);
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->twiddles) cudaFree(ctx->twiddles);
-  if (ctx->coef_img) cudaFree(ctx->coef_img);
   delete ctx;
   return MPI_OK;
 }

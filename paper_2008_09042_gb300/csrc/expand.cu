@@ -56,6 +56,8 @@ constexpr int kPrefetch = 8;  // basis rows of U kept in flight per thread
 // over coils.
 template <int MODE, int CB>
 __global__ void __launch_bounds__(kExpandMaxThreads) k_expand(ExpandArgs a, int q_pad, int c_pad) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   extern __shared__ float4 smem4[];
   float2* sA = reinterpret_cast<float2*>(smem4);  // [q_pad][c_pad]
   float2* sD = sA + (size_t)q_pad * c_pad;         // [q_pad][c_pad], Jacobian only
@@ -175,7 +177,7 @@ mpi_status launch_mode(mpi_ctx* ctx, const ExpandArgs& a) {
   const int gy = adj_like ? 1 : (a.C + CB - 1) / CB;
   const long gx = std::min(grid, ((long)a.N + block - 1) / block);
   MPI_PROF(ctx, KF_EXPAND);
-  k_expand<MODE, CB><<<dim3((unsigned)gx, gy), block, smem, ctx->stream>>>(a, q_pad, c_pad);
+  launch_pdl(ctx, k_expand<MODE, CB>, dim3((unsigned)gx, gy), dim3(block), smem, a, q_pad, c_pad);
   MPI_LAUNCH_CHECK(ctx, "k_expand");
   return MPI_OK;
 }
@@ -194,6 +196,8 @@ template <int CT>
 __global__ void __launch_bounds__(kUhvThreads) k_uh_v(const float2* __restrict__ U, int N, int q,
                                                       const float2* __restrict__ V, int C, int c_begin,
                                                       int c_count, float2* __restrict__ partials) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   extern __shared__ float4 smem4[];
   float2* sU = reinterpret_cast<float2*>(smem4);  // [q][P + 1]
   float2* sV = sU + q * (kUhvP + 1);               // [P][c_count_pad]
@@ -245,6 +249,8 @@ __global__ void __launch_bounds__(kUhvThreads) k_uh_v(const float2* __restrict__
 
 __global__ void k_reduce_partials(const float2* __restrict__ partials, int nblk, int CQ,
                                   float2* __restrict__ out) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= CQ) return;
   float2 s = make_float2(0.f, 0.f);
@@ -295,12 +301,12 @@ mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2
     cudaError_t e = cudaFuncSetAttribute(k_uh_v<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "uh_v smem attribute");
     MPI_PROF(ctx, KF_UHV);
-  k_uh_v<CT><<<nblk, kUhvThreads, smem, ctx->stream>>>(U, N, q, V, C, c_begin, c_count, partials);
+  launch_pdl(ctx, k_uh_v<CT>, dim3(nblk), dim3(kUhvThreads), smem, U, N, q, V, C, c_begin, c_count, partials);
     MPI_LAUNCH_CHECK(ctx, "k_uh_v");
   }
   const int CQ = C * q;
   MPI_PROF(ctx, KF_UHV);
-  k_reduce_partials<<<(CQ + 255) / 256, 256, 0, ctx->stream>>>(partials, nblk, CQ, dalpha);
+  launch_pdl(ctx, k_reduce_partials, dim3((CQ + 255) / 256), dim3(256), 0, partials, nblk, CQ, dalpha);
   MPI_LAUNCH_CHECK(ctx, "k_reduce_partials");
   return MPI_OK;
 }

@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "mpi_internal.h"
+#include "ptx.cuh"
 
 namespace {
 
@@ -213,6 +214,8 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_fwd_gather(
     const float2* __restrict__ data, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
     const int32_t* __restrict__ row_ptr, float2* __restrict__ y, int M, float ksign,
     const float2* __restrict__ tw_g) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   __shared__ float2 tw[NX];
   __shared__ float2 buf[kRowWarps][padded_len(NX)];
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
@@ -247,6 +250,8 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
     const float2* __restrict__ y, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
     const int32_t* __restrict__ row_ptr, float2* __restrict__ data, int M, float ksign,
     const float2* __restrict__ tw_g) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   __shared__ float2 tw[NX];
   __shared__ float2 buf[kRowWarps][padded_len(NX)];
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
@@ -299,6 +304,8 @@ __global__ void __launch_bounds__(kColTile * 32) k_fft_lines(float2* __restrict_
                                                             long stride, int n_slabs, int inner,
                                                             long outer_stride, long inner_stride,
                                                             const float2* __restrict__ tw_g) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   constexpr int S = col_stride(L);
   __shared__ float2 tw[L];
   __shared__ float2 buf[kColTile * S];
@@ -335,8 +342,8 @@ mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride
   if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
 #define MPI_LINES_CASE(n)                                                                          \
   case n:                                                                                          \
-    k_fft_lines<n, INV><<<(unsigned)blocks, kColTile * 32, 0, ctx->stream>>>(                     \
-        data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw);                         \
+    launch_pdl(ctx, k_fft_lines<n, INV>, dim3((unsigned)blocks), dim3(kColTile * 32), 0, data, nx, stride,  \
+               n_slabs, inner, outer_stride, inner_stride, tw);                                    \
     break;
   MPI_PROF(ctx, KF_FFT_LINES);
   switch (L) {
@@ -387,8 +394,8 @@ mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const floa
   if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
 #define MPI_ROWS_CASE(n)                                                                          \
   case n:                                                                                         \
-    k_rows_fwd_gather<n><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(                  \
-        data, C, n_rows, plan->ny, plan->idx, plan->row_ptr, y, plan->M, ks, tw);                 \
+    launch_pdl(ctx, k_rows_fwd_gather<n>, dim3((unsigned)blocks), dim3(kRowWarps * 32), 0, data, C, n_rows, \
+               plan->ny, plan->idx, plan->row_ptr, y, plan->M, ks, tw);                           \
     break;
   MPI_PROF(ctx, KF_FFT_ROWS);
   switch (plan->nx) {
@@ -420,8 +427,8 @@ mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const flo
   if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
 #define MPI_ROWS_CASE(n)                                                                          \
   case n:                                                                                         \
-    k_rows_scatter_inv<n><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(                 \
-        y, C, n_rows, plan->ny, plan->idx, plan->row_ptr, data, plan->M, ks, tw);                 \
+    launch_pdl(ctx, k_rows_scatter_inv<n>, dim3((unsigned)blocks), dim3(kRowWarps * 32), 0, y, C, n_rows, \
+               plan->ny, plan->idx, plan->row_ptr, data, plan->M, ks, tw);                        \
     break;
   MPI_PROF(ctx, KF_FFT_ROWS);
   switch (plan->nx) {
@@ -449,6 +456,8 @@ namespace {
 template <int L, bool INV>
 __global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __restrict__ data, long n_rows,
                                                                     const float2* __restrict__ tw_g) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   __shared__ float2 tw[L];
   __shared__ float2 buf[kRowWarps][padded_len(L)];
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tw_g[i];
@@ -475,7 +484,8 @@ mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L)
   if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
 #define MPI_RI_CASE(n)                                                                           \
   case n:                                                                                        \
-    k_fft_rows_inplace<n, INV><<<(unsigned)blocks, kRowWarps * 32, 0, ctx->stream>>>(data, n_rows, tw); \
+    launch_pdl(ctx, k_fft_rows_inplace<n, INV>, dim3((unsigned)blocks), dim3(kRowWarps * 32), 0, data, n_rows, \
+               tw);                                                                               \
     break;
   MPI_PROF(ctx, KF_FFT_ROWS);
   switch (L) {

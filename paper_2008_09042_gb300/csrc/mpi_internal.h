@@ -15,7 +15,6 @@
 static const int kFftLengths[] = {16, 32, 48, 64, 96, 128, 192, 256, 320, 512};
 static const int kNumFftLengths = sizeof(kFftLengths) / sizeof(int);
 // Bytes reserved per context for the tensor-core coefficient operand image.
-static const size_t kCoefImgBytes = 256 * 512 * 2;
 
 // Kernel families for the optional per-launch event timing.
 enum KernelFamily { KF_EXPAND = 0, KF_UHV = 1, KF_FFT_ROWS = 2, KF_FFT_LINES = 3, KF_NUFFT = 4,
@@ -30,9 +29,9 @@ struct mpi_ctx {
   int tw_offset[kNumFftLengths] = {0};
   int num_sms = 0;
   int* dev_err = nullptr;  // device error word written by kernels whose waits time out
-  void* coef_img = nullptr;  // BF16 coefficient operand image for the tensor-core expansion
   void* solver_cache = nullptr;  // recorded solver graphs (solvers.cu)
   int64_t launches = 0;
+  bool pdl = true;  // launch operator kernels with programmatic stream serialization
   std::string err;
   // profiling: event pairs around launches while enabled
   bool profiling = false;
@@ -99,6 +98,26 @@ void prof_begin(mpi_ctx* ctx, int family);
 void prof_end(mpi_ctx* ctx);
 
 #define MPI_PROF(ctx, fam) prof_begin((ctx), (fam))
+
+// Launches `kern` on the context's stream with programmatic stream
+// serialization, so that its launch and its prologue overlap the tail of the
+// previous kernel.  Every kernel launched this way calls mpi_ptx::pdl_wait()
+// before touching global data that earlier stream work reads or writes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(mpi_ctx* ctx, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = ctx->pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 #define MPI_LAUNCH_CHECK(ctx, what)                                   \
   do {                                                                \

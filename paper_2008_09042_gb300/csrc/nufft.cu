@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "mpi_internal.h"
+#include "ptx.cuh"
 
 namespace {
 
@@ -76,6 +77,8 @@ __global__ void k_nufft_deap(int n, int G, int W, double beta, float* __restrict
 // v[c][y][x] * deap[y] * deap[x] * (-1)^(gx + gy) / n with (gy, gx) = (o + y, o + x).
 __global__ void k_nufft_pad(const float2* __restrict__ v, int C, int n, int G, const float* __restrict__ deap,
                             float2* __restrict__ grid) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t GG = (size_t)G * G;
   if (e >= (size_t)C * GG) return;
@@ -98,6 +101,8 @@ template <int W>
 __global__ void k_nufft_interp(const float2* __restrict__ grid, int C, int G, int M,
                                const int32_t* __restrict__ gstart, const float* __restrict__ gw,
                                float ksign, float2* __restrict__ y) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (size_t)C * M) return;
   const int c = (int)(e / M), m = (int)(e % M);
@@ -134,6 +139,8 @@ template <int W>
 __global__ void k_nufft_spread(const float2* __restrict__ y, int C, int G, int M,
                                const int32_t* __restrict__ gstart, const float* __restrict__ gw,
                                float ksign, float2* __restrict__ grid) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (size_t)C * M) return;
   const int c = (int)(e / M), m = (int)(e % M);
@@ -164,6 +171,8 @@ __global__ void k_nufft_spread(const float2* __restrict__ y, int C, int G, int M
 
 __global__ void k_nufft_crop(const float2* __restrict__ grid, int C, int n, int G, const float* __restrict__ deap,
                              float2* __restrict__ out) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nn = (size_t)n * n;
   if (e >= (size_t)C * nn) return;
@@ -215,7 +224,7 @@ mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, in
   const int n = plan->nx, G = plan->G, M = plan->M;
   const size_t total = (size_t)C * G * G;
   MPI_PROF(ctx, KF_NUFFT);
-  k_nufft_pad<<<blocks_for(total, 256), 256, 0, ctx->stream>>>(v, C, n, G, plan->deap, grid);
+  launch_pdl(ctx, k_nufft_pad, dim3(blocks_for(total, 256)), dim3(256), 0, v, C, n, G, plan->deap, grid);
   MPI_LAUNCH_CHECK(ctx, "k_nufft_pad");
   mpi_status st = launch_fft_cols(ctx, grid, C, 1, G, G, false);
   if (st) return st;
@@ -228,8 +237,8 @@ mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, in
   switch (plan->W) {
 #define MPI_W_CASE(w)                                                                                \
   case w:                                                                                            \
-    k_nufft_interp<w><<<blocks_for(cm, 256), 256, 0, ctx->stream>>>(grid, C, G, M, plan->gstart,    \
-                                                                   plan->gw, ks, y);                \
+    launch_pdl(ctx, k_nufft_interp<w>, dim3(blocks_for(cm, 256)), dim3(256), 0, grid, C, G, M,          \
+               plan->gstart, plan->gw, ks, y);                                                     \
     break;
     MPI_W_CASE(2) MPI_W_CASE(3) MPI_W_CASE(4) MPI_W_CASE(5) MPI_W_CASE(6) MPI_W_CASE(7) MPI_W_CASE(8)
 #undef MPI_W_CASE
@@ -252,8 +261,8 @@ mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, in
   switch (plan->W) {
 #define MPI_W_CASE(w)                                                                                \
   case w:                                                                                            \
-    k_nufft_spread<w><<<blocks_for(cm, 256), 256, 0, ctx->stream>>>(y, C, G, M, plan->gstart,       \
-                                                                    plan->gw, ks, grid);            \
+    launch_pdl(ctx, k_nufft_spread<w>, dim3(blocks_for(cm, 256)), dim3(256), 0, y, C, G, M,             \
+               plan->gstart, plan->gw, ks, grid);                                                  \
     break;
       MPI_W_CASE(2) MPI_W_CASE(3) MPI_W_CASE(4) MPI_W_CASE(5) MPI_W_CASE(6) MPI_W_CASE(7) MPI_W_CASE(8)
 #undef MPI_W_CASE
@@ -267,7 +276,8 @@ mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, in
   st = launch_fft_cols(ctx, grid, C, 1, G, G, true);
   if (st) return st;
   MPI_PROF(ctx, KF_NUFFT);
-  k_nufft_crop<<<blocks_for((size_t)C * n * n, 256), 256, 0, ctx->stream>>>(grid, C, n, G, plan->deap, out);
+  launch_pdl(ctx, k_nufft_crop, dim3(blocks_for((size_t)C * n * n, 256)), dim3(256), 0, grid, C, n, G,
+             plan->deap, out);
   MPI_LAUNCH_CHECK(ctx, "k_nufft_crop");
   return MPI_OK;
 }

@@ -58,6 +58,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return true;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while the previous kernel in the stream is still
+// running; pdl_wait() returns once that kernel has completed and its memory
+// is visible, and must precede every global access that depends on earlier
+// work (reads and writes).  pdl_trigger() lets the next such kernel start
+// launching.  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // 1D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
 // from global to shared memory; completion is signalled on `bar` as tx bytes.
 __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {

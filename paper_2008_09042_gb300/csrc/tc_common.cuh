@@ -2,6 +2,8 @@
 // descriptors, TMA / tcgen05 wrappers and the per-pixel epilogue.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cuda.h>
 
 #include "mpi_internal.h"
@@ -19,7 +21,6 @@ struct TcArgs {
   float scale;
   const float2* alpha;
   const float2* dalpha;
-  const void* coef_img;
   const float2* p;
   const float2* dp;
   const float2* w;
@@ -141,6 +142,84 @@ static __host__ __device__ __forceinline__ uint32_t sw128_offset_e(int r, int k,
   const int per_row = 128 / esize, per_unit = 16 / esize;
   const int kc = k / per_row, kk = k % per_row;
   return (uint32_t)(kc * rows * 128 + r * 128 + ((((kk / per_unit) ^ (r & 7))) << 4) + (kk % per_unit) * esize);
+}
+
+static __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+// The coefficient operand, written straight into shared memory in the swizzled
+// K-major layout by the four epilogue warps (etid = 0..127) while the first
+// tiles of U are still in flight.  Per coil c, row 2c is [Re a_c, -Im a_c] and
+// row 2c+1 is [Im a_c, Re a_c] over K = [0, q) | [q, 2q), so that accumulator
+// columns 2c, 2c+1 hold Re and Im of s_c; rows [half, half + 2C) hold dalpha
+// for the Jacobian; everything else is zero.  SPLIT (the 3xTF32 kernel): rows
+// [0, n_gemm) hold hi of those values and rows [n_gemm, 2 n_gemm) their lo
+// parts, as FP32; otherwise one block of BF16 rows.  Each step writes whole
+// 16-byte swizzle units (4 FP32 or 8 BF16 consecutive K values of a row pair).
+// Ends with the writes made visible to the tensor core and one arrival per
+// warp on `ready`.
+template <bool SPLIT>
+static __device__ void build_coef_smem(const TcArgs& a, unsigned char* sB, int Kp, bool with_dalpha, int etid,
+                                       uint64_t* ready) {
+  constexpr int E = SPLIT ? 4 : 8;        // K values per 16-byte unit
+  constexpr int esize = SPLIT ? 4 : 2;
+  const int rows = SPLIT ? 2 * a.n_gemm : a.n_gemm;
+  const int units = Kp / E;               // units along K per row
+  const int per_blk = a.C * units;
+  const int n_data = (with_dalpha ? 2 : 1) * per_blk;
+  // zero rows: [2C, half) always, [half + 2C, n_gemm) for the Jacobian, [2C, n_gemm) otherwise
+  const int z0 = with_dalpha ? a.half - 2 * a.C : a.n_gemm - 2 * a.C;
+  const int z1 = with_dalpha ? a.n_gemm - a.half - 2 * a.C : 0;
+  const int n_zero = (z0 + z1) * units;
+  for (int task = etid; task < n_data + n_zero; task += 128) {
+    if (task < n_data) {
+      const int blk = task >= per_blk;
+      const int t2 = task - blk * per_blk;
+      const int c = t2 / units, u = t2 - c * units;
+      const float2* src = (blk ? a.dalpha : a.alpha) + (size_t)c * a.q;
+      const int r0 = (blk ? a.half : 0) + 2 * c, k0 = u * E;
+      float re[E], im[E];  // rows r0 and r0 + 1
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = k0 + e;
+        float2 al = make_float2(0.f, 0.f);
+        if (k < 2 * a.q) al = src[k < a.q ? k : k - a.q];
+        re[e] = k < a.q ? al.x : (k < 2 * a.q ? -al.y : 0.f);
+        im[e] = k < a.q ? al.y : (k < 2 * a.q ? al.x : 0.f);
+      }
+      if (SPLIT) {
+        float4 h0, h1, l0, l1;
+        h0 = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
+        h1 = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
+        l0 = make_float4(re[0] - h0.x, re[1] - h0.y, re[2] - h0.z, re[3] - h0.w);
+        l1 = make_float4(im[0] - h1.x, im[1] - h1.y, im[2] - h1.z, im[3] - h1.w);
+        *reinterpret_cast<float4*>(sB + sw128_offset_e(r0, k0, rows, esize)) = h0;
+        *reinterpret_cast<float4*>(sB + sw128_offset_e(r0 + 1, k0, rows, esize)) = h1;
+        *reinterpret_cast<float4*>(sB + sw128_offset_e(r0 + a.n_gemm, k0, rows, esize)) = l0;
+        *reinterpret_cast<float4*>(sB + sw128_offset_e(r0 + 1 + a.n_gemm, k0, rows, esize)) = l1;
+      } else {
+        uint4 v0, v1;
+        __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(&v0);
+        __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(&v1);
+#pragma unroll
+        for (int e = 0; e < E / 2; ++e) {
+          p0[e] = __floats2bfloat162_rn(re[2 * e], re[2 * e + 1]);
+          p1[e] = __floats2bfloat162_rn(im[2 * e], im[2 * e + 1]);
+        }
+        *reinterpret_cast<uint4*>(sB + sw128_offset_e(r0, k0, rows, esize)) = v0;
+        *reinterpret_cast<uint4*>(sB + sw128_offset_e(r0 + 1, k0, rows, esize)) = v1;
+      }
+    } else {
+      const int t2 = task - n_data;
+      const int zr = t2 / units, u = t2 - zr * units;
+      const int r = zr < z0 ? 2 * a.C + zr : a.half + 2 * a.C + (zr - z0);
+      const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(sB + sw128_offset_e(r, u * E, rows, esize)) = zero;
+      if (SPLIT) *reinterpret_cast<uint4*>(sB + sw128_offset_e(r + a.n_gemm, u * E, rows, esize)) = zero;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+  __syncwarp();
+  if ((etid & 31) == 0) mpi_ptx::mbar_arrive(ready);
 }
 
 // Epilogue warps (4 of them, warp w owning TMEM lanes 32 (w % 4) ..): one pixel

@@ -15,9 +15,10 @@
 // accumulator and one thread issues tcgen05.mma (M = 128, N = padded 2C or 4C,
 // K = 16 per instruction); warps 2-5 read the accumulator with tcgen05.ld
 // (warp w owns TMEM lanes 32 (w % 4) ..) and apply the epilogue, one pixel per
-// thread.  The coefficient operand is built once per call in global memory, in
-// the swizzled shared-memory layout, and bulk-copied into each CTA.  Persistent
-// CTAs walk the pixel tiles; the ring is as deep as shared memory allows.
+// thread.  The epilogue warps first write the coefficient operand into shared
+// memory (swizzled K-major layout) while the first tiles of U are in flight.
+// Persistent CTAs walk the pixel tiles; the ring is as deep as shared memory
+// allows.
 // Every mbarrier wait is bounded (kWaitCycles); on a timeout the CTA records
 // the error, drains what it issued (bounded) and frees its TMEM.
 #include <cuda.h>
@@ -35,33 +36,6 @@ using namespace mpi_tc;
 constexpr int kKChunk = 64;  // BF16 elements per 128-byte swizzle row
 constexpr int kMaxStages = 12;
 constexpr int kThreads = 192;
-
-// The coefficient operand image, built once per call in global memory in the
-// exact swizzled shared-memory layout: rows [0, 2C) from alpha, rows
-// [half, half + 2C) from dalpha (Jacobian), zero elsewhere.
-__global__ void k_build_coef(TcArgs a, int with_dalpha, __nv_bfloat16* __restrict__ img) {
-  const int Kp = a.KC * kKChunk;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.n_gemm * Kp) return;
-  const int r = e / Kp, k = e % Kp;
-  float v = 0.f;
-  const float2* src = nullptr;
-  int rr = r;
-  if (r < 2 * a.C) {
-    src = a.alpha;
-  } else if (with_dalpha && r >= a.half && r < a.half + 2 * a.C) {
-    src = a.dalpha;
-    rr = r - a.half;
-  }
-  if (src && k < 2 * a.q) {
-    const int c = rr >> 1, im_row = rr & 1;
-    const int j = k < a.q ? k : k - a.q;
-    const float2 al = src[(size_t)c * a.q + j];
-    if (!im_row) v = k < a.q ? al.x : -al.y;  // row 2c: [Re a, -Im a]
-    else v = k < a.q ? al.y : al.x;             // row 2c+1: [Im a, Re a]
-  }
-  img[sw128_offset_e(r, k, a.n_gemm, 2) / 2] = __float2bfloat16_rn(v);
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a,
@@ -82,6 +56,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
   __shared__ int s_failed;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // Launched with programmatic stream serialization: set-up and the TMA stream of
+  // the (constant) basis start at once; only the epilogue warps, which read
+  // the coefficients and per-pixel data and write the outputs, wait for the
+  // previous kernel.
+  mpi_ptx::pdl_trigger();
   if (tid == 0) {
     s_failed = 0;
     for (int s = 0; s < stages; ++s) {
@@ -93,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
       mpi_ptx::mbar_init(&acc_empty[b], 4);
     }
     mpi_ptx::mbar_init(drain, 1);
-    mpi_ptx::mbar_init(bfull, 1);
+    mpi_ptx::mbar_init(bfull, 4);  // one arrival per epilogue warp once the coefficient operand is written
     mpi_ptx::fence_mbar_init();
   }
   if (warp == 1) {
@@ -110,9 +89,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
 
   const int n_tiles = (a.N + kTileM - 1) / kTileM;
   if (warp == 0 && lane == 0) {
-    // ---------------- producer: the coefficient operand image, then TMA tiles of U
-    mpi_ptx::mbar_arrive_expect_tx(bfull, b_bytes);
-    mpi_ptx::bulk_g2s(sB, a.coef_img, b_bytes, bfull);
+    // ---------------- producer: TMA tiles of U
     int it = 0;
     RingPos r;
     bool ok = true;
@@ -176,7 +153,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
     mpi_ptx::mbar_wait(drain, 0, a.err);
     if (!ok) s_failed = 1;
   } else if (warp >= 2) {
-    mpi_tc::tc_epilogue<MODE>(a, tmem, warp, lane, acc_full, acc_empty, n_tiles, &s_failed);
+    mpi_ptx::pdl_wait();  // alpha, p and w may come from the previous kernel
+    build_coef_smem<false>(a, sB, Kp, MODE == EX_JFWD, tid - 64, bfull);
+    tc_epilogue<MODE>(a, tmem, warp, lane, acc_full, acc_empty, n_tiles, &s_failed);
   }
   fence_before();
   __syncthreads();
@@ -291,12 +270,6 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   stages = std::min(stages, kMaxStages);
   if (stages < 2) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion: shared memory");
   const size_t smem = fixed + (size_t)stages * kStageBytes;
-  if ((size_t)a.n_gemm * b->Kp * 2 > kCoefImgBytes) return set_err(ctx, MPI_ERR_UNSUPPORTED, "coefficient image");
-  a.coef_img = ctx->coef_img;
-  MPI_PROF(ctx, KF_OTHER);
-  k_build_coef<<<(a.n_gemm * b->Kp + 255) / 256, 256, 0, ctx->stream>>>(a, mode == EX_JFWD,
-                                                                          (__nv_bfloat16*)ctx->coef_img);
-  MPI_LAUNCH_CHECK(ctx, "k_build_coef");
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
   const int grid = std::min(n_tiles, per_sm * std::max(ctx->num_sms, 1));
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap;
@@ -306,7 +279,7 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
     e = cudaFuncSetAttribute(k_expand_tc<m>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
     if (e != cudaSuccess) return cuda_check(ctx, e, "tc smem attribute");                                    \
     MPI_PROF(ctx, KF_EXPAND);                                                                                \
-    k_expand_tc<m><<<grid, kThreads, smem, ctx->stream>>>(map, a, stages);                                           \
+    launch_pdl(ctx, k_expand_tc<m>, dim3(grid), dim3(kThreads), smem, map, a, stages);                                           \
     break;
   switch (mode) {
     MPI_TC_CASE(EX_MAPS)

@@ -44,8 +44,6 @@ constexpr int kStageBytes32 = kBoxesPerStage * kBoxBytes32;
 constexpr int kThreads32 = 320;   // warp 0 TMA, 1 MMA, 2-5 epilogue, 6-9 converters
 constexpr size_t kSmemMax = 232448 - 128;  // 227 KB less room for the static shared word
 
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
-
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -58,35 +56,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_tf32_acc(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
   asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem_d), "l"(adesc), "l"(bdesc),
                "r"(idesc));
-}
-
-// The stacked coefficient operand [A_hi; A_lo]: rows [0, n_gemm) hold hi of the
-// coefficient rows (as in the BF16 kernel: [Re a, -Im a] / [Im a, Re a] per
-// coil, dalpha rows from `half` for the Jacobian), rows [n_gemm, 2 n_gemm) lo.
-__global__ void k_build_coef_tf32(TcArgs a, int with_dalpha, float* __restrict__ img) {
-  const int Kp = a.KC * kKChunk32;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.n_gemm * Kp) return;
-  const int r = e / Kp, k = e % Kp;
-  float v = 0.f;
-  const float2* src = nullptr;
-  int rr = r;
-  if (r < 2 * a.C) {
-    src = a.alpha;
-  } else if (with_dalpha && r >= a.half && r < a.half + 2 * a.C) {
-    src = a.dalpha;
-    rr = r - a.half;
-  }
-  if (src && k < 2 * a.q) {
-    const int c = rr >> 1, im_row = rr & 1;
-    const int j = k < a.q ? k : k - a.q;
-    const float2 al = src[(size_t)c * a.q + j];
-    if (!im_row) v = k < a.q ? al.x : -al.y;
-    else v = k < a.q ? al.y : al.x;
-  }
-  const float h = tf32_hi(v);
-  img[sw128_offset_e(r, k, 2 * a.n_gemm, 4) / 4] = h;
-  img[sw128_offset_e(r + a.n_gemm, k, 2 * a.n_gemm, 4) / 4] = v - h;
 }
 
 // 32 consecutive 32-bit TMEM columns of this warp's 32 lanes, one row per thread.
@@ -136,6 +105,11 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
   __shared__ int s_failed;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // Launched with programmatic stream serialization: set-up and the TMA stream of
+  // the (constant) basis start at once; only the epilogue warps, which read
+  // the coefficients and per-pixel data and write the outputs, wait for the
+  // previous kernel.
+  mpi_ptx::pdl_trigger();
   if (tid == 0) {
     s_failed = 0;
     for (int s = 0; s < stages; ++s) {
@@ -148,7 +122,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
       mpi_ptx::mbar_init(&acc_empty[b], 4);
     }
     mpi_ptx::mbar_init(drain, 1);
-    mpi_ptx::mbar_init(bfull, 1);
+    mpi_ptx::mbar_init(bfull, 4);  // one arrival per epilogue warp once the coefficient operand is written
     mpi_ptx::fence_mbar_init();
   }
   if (warp == 1) {
@@ -169,9 +143,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
   const int G = my_tiles * (a.KC / kBoxesPerStage);
 
   if (warp == 0 && lane == 0) {
-    // ---------------- producer: the stacked coefficient image, then TMA tiles of U
-    mpi_ptx::mbar_arrive_expect_tx(bfull, b_bytes);
-    mpi_ptx::bulk_g2s(sB, a.coef_img, b_bytes, bfull);
+    // ---------------- producer: TMA tiles of U
     RingPos r;
     int g = 0, kc = 0, t = (int)blockIdx.x;  // kc: first box of the stage
     for (; g < G; ++g) {
@@ -288,6 +260,8 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     mpi_ptx::mbar_wait(drain, 0, a.err);
     if (!ok) s_failed = 1;
   } else if (warp >= 2 && warp <= 5) {
+    mpi_ptx::pdl_wait();  // alpha, p and w may come from the previous kernel
+    build_coef_smem<true>(a, sB, Kp, MODE == EX_JFWD, tid - 64, bfull);
     tc_epilogue<MODE, true>(a, tmem, warp, lane, acc_full, acc_empty, n_tiles, &s_failed);
   }
   fence_before();
@@ -330,7 +304,6 @@ bool plan_tf32(const mpi_basis* b, int mode, int C, TfPlan* p) {
   while (acc_cols < 2 * p->n_gemm) acc_cols <<= 1;
   p->half_cols = acc_cols;
   p->b_bytes = 2 * (size_t)p->n_gemm * b->Kp32 * 4;
-  if (p->b_bytes > kCoefImgBytes) return false;
   // alignment slack + the stacked coefficient image + 3 barriers per stage and 6 more + TMEM slot
   const size_t fixed = 1024 + ((p->b_bytes + 1023) & ~(size_t)1023) + 8 * (3 * kMaxStages32 + 6) + 16;
   if (fixed + 2 * (size_t)kStageBytes32 > kSmemMax) return false;
@@ -421,11 +394,6 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.out = x.out;
   a.vout = x.vout;
   a.err = ctx->dev_err;
-  a.coef_img = ctx->coef_img;
-  MPI_PROF(ctx, KF_OTHER);
-  k_build_coef_tf32<<<(unsigned)((a.n_gemm * b->Kp32 + 255) / 256), 256, 0, ctx->stream>>>(a, mode == EX_JFWD,
-                                                                                           (float*)ctx->coef_img);
-  MPI_LAUNCH_CHECK(ctx, "k_build_coef_tf32");
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
   const int grid = std::min(n_tiles, std::max(ctx->num_sms, 1));
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap32;
@@ -435,7 +403,7 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
     e = cudaFuncSetAttribute(k_expand_tf32x3<m>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);  \
     if (e != cudaSuccess) return cuda_check(ctx, e, "tf32 smem attribute");                                  \
     MPI_PROF(ctx, KF_EXPAND);                                                                                \
-    k_expand_tf32x3<m><<<grid, kThreads32, pl.smem, ctx->stream>>>(map, a, pl.stages);                      \
+    launch_pdl(ctx, k_expand_tf32x3<m>, dim3(grid), dim3(kThreads32), pl.smem, map, a, pl.stages);                      \
     break;
   switch (mode) {
     MPI_TF_CASE(EX_MAPS)

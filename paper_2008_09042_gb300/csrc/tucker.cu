@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "mpi_internal.h"
+#include "ptx.cuh"
 
 namespace {
 
@@ -43,6 +44,8 @@ constexpr int kIB = 16;  // outputs along i per thread
 template <bool ADJ>
 __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, const float2* __restrict__ F, int R,
                                                 int P, int I, long B, float2* __restrict__ Y) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   __shared__ float2 sM[128 * kIB];
   const int i0 = blockIdx.x * kIB;
   for (int e = threadIdx.x; e < P * kIB; e += blockDim.x) {
@@ -88,6 +91,8 @@ __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, co
 template <bool ADJ>
 __global__ void __launch_bounds__(256) k_mode_last(const float2* __restrict__ X, const float2* __restrict__ F, int R,
                                                    int P, int I, float2* __restrict__ Y) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   constexpr int kRows = 8;
   __shared__ float2 sX[kRows * 128];
   const int r0 = blockIdx.x * kRows;
@@ -130,6 +135,8 @@ __device__ __forceinline__ float centre_sign(long n, int nx, int ny) {
 // Point-wise operator epilogues from materialised maps S (and dS) [C][N].
 template <int MODE>
 __global__ void k_pointwise(ExpandArgs a, const float2* __restrict__ S, const float2* __restrict__ dS) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
   for (long n = (long)blockIdx.x * blockDim.x + threadIdx.x; n < a.N; n += (long)gridDim.x * blockDim.x) {
     const float sg = (a.centre ? centre_sign(n, a.nx, a.ny) : 1.f) * a.scale;
     const float2 pv = a.p[n];
@@ -168,8 +175,8 @@ mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int 
   const dim3 grid((unsigned)((I + kIB - 1) / kIB), (unsigned)((B + block - 1) / block), (unsigned)R);
   if (R > 65535 || grid.y > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
   MPI_PROF(ctx, KF_EXPAND);
-  if (adj) k_mode_b<true><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
-  else k_mode_b<false><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, B, Y);
+  if (adj) launch_pdl(ctx, k_mode_b<true>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+  else launch_pdl(ctx, k_mode_b<false>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
   MPI_LAUNCH_CHECK(ctx, "k_mode_b");
   return MPI_OK;
 }
@@ -179,8 +186,8 @@ mpi_status mode_last(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, i
   const unsigned grid = (unsigned)((R + 7) / 8);
   const int block = std::min(256, (I + 31) / 32 * 32);  // threads run along i
   MPI_PROF(ctx, KF_EXPAND);
-  if (adj) k_mode_last<true><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, Y);
-  else k_mode_last<false><<<grid, block, 0, ctx->stream>>>(X, F, R, P, I, Y);
+  if (adj) launch_pdl(ctx, k_mode_last<true>, dim3(grid), dim3(block), 0, X, F, R, P, I, Y);
+  else launch_pdl(ctx, k_mode_last<false>, dim3(grid), dim3(block), 0, X, F, R, P, I, Y);
   MPI_LAUNCH_CHECK(ctx, "k_mode_last");
   return MPI_OK;
 }
@@ -239,10 +246,10 @@ mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const f
   const long blocks = std::min(((long)a.N + 255) / 256, 8L * std::max(ctx->num_sms, 1));
   MPI_PROF(ctx, KF_EXPAND);
   switch (mode) {
-    case EX_FWD: k_pointwise<EX_FWD><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
-    case EX_JFWD: k_pointwise<EX_JFWD><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
-    case EX_ADJ: k_pointwise<EX_ADJ><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
-    case EX_JADJ: k_pointwise<EX_JADJ><<<(unsigned)blocks, 256, 0, ctx->stream>>>(a, S, dS); break;
+    case EX_FWD: launch_pdl(ctx, k_pointwise<EX_FWD>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
+    case EX_JFWD: launch_pdl(ctx, k_pointwise<EX_JFWD>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
+    case EX_ADJ: launch_pdl(ctx, k_pointwise<EX_ADJ>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
+    case EX_JADJ: launch_pdl(ctx, k_pointwise<EX_JADJ>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
     default: return set_err(ctx, MPI_ERR_ARG, "pointwise mode");
   }
   MPI_LAUNCH_CHECK(ctx, "k_pointwise");

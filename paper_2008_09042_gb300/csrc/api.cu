@@ -28,6 +28,16 @@ bool fft_length_supported(int n) {
   return false;
 }
 
+void ctx_adopt(mpi_ctx* ctx, mpi_ctx** slot) { ctx->children.push_back(slot); }
+
+void ctx_release(mpi_ctx** slot) {
+  mpi_ctx* ctx = *slot;
+  if (!ctx) return;
+  auto& v = ctx->children;
+  v.erase(std::remove(v.begin(), v.end(), slot), v.end());
+  *slot = nullptr;
+}
+
 const float2* twiddle_table(const mpi_ctx* ctx, int n) {
   for (int i = 0; i < kNumFftLengths; ++i)
     if (kFftLengths[i] == n) return ctx->twiddles + ctx->tw_offset[i];
@@ -268,6 +278,7 @@ extern "C" mpi_status mpi_ctx_destroy(mpi_ctx* ctx) {
     cudaEventDestroy(ctx->ev_end[i]);
   }
   solver_cache_clear(ctx);
+  for (mpi_ctx** slot : ctx->children) *slot = nullptr;  // orphan the children still alive
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->twiddles) cudaFree(ctx->twiddles);
   delete ctx;
@@ -375,6 +386,7 @@ extern "C" mpi_status mpi_plan_create(mpi_ctx* ctx, const mpi_plan_desc* d, mpi_
   if (d->M < 0) return set_err(ctx, MPI_ERR_ARG, "M < 0");
   mpi_plan* plan = new mpi_plan();
   plan->ctx = ctx;
+  plan->device = ctx->device;
   plan->ndim = d->ndim;
   plan->nz = nz;
   plan->ny = ny;
@@ -452,15 +464,19 @@ extern "C" mpi_status mpi_plan_create(mpi_ctx* ctx, const mpi_plan_desc* d, mpi_
     mpi_plan_destroy(plan);
     return st;
   }
+  ctx_adopt(ctx, &plan->ctx);  // only a fully made plan is tracked
   *out = plan;
   return MPI_OK;
 }
 
 extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
   if (!plan) return MPI_ERR_ARG;
-  DeviceGuard g(plan->ctx->device);
-  cudaStreamSynchronize(plan->ctx->stream);
-  solver_cache_forget(plan->ctx, plan);
+  DeviceGuard g(plan->device);
+  if (plan->ctx) {  // else the context is gone, and it drained its stream when it went
+    cudaStreamSynchronize(plan->ctx->stream);
+    solver_cache_forget(plan->ctx, plan);
+    ctx_release(&plan->ctx);
+  }
   void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw, plan->deap};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -491,6 +507,7 @@ extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N
   DeviceGuard g(ctx->device);
   mpi_basis* b = new mpi_basis();
   b->ctx = ctx;
+  b->device = ctx->device;
   b->N = N;
   b->q = q;
   const size_t bytes = (size_t)N * q * sizeof(float2);
@@ -524,6 +541,7 @@ extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N
     mpi_basis_destroy(b);
     return st;
   }
+  ctx_adopt(ctx, &b->ctx);  // only a fully made basis is tracked
   *out = b;
   return MPI_OK;
 }
@@ -548,6 +566,7 @@ extern "C" mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, c
   if (st) return st;
   mpi_basis* b = new mpi_basis();
   b->ctx = ctx;
+  b->device = ctx->device;
   b->N = (int)N;
   b->q = q;
   b->tucker = true;
@@ -567,15 +586,19 @@ extern "C" mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, c
     mpi_basis_destroy(b);
     return st;
   }
+  ctx_adopt(ctx, &b->ctx);  // only a fully made basis is tracked
   *out = b;
   return MPI_OK;
 }
 
 extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   if (!b) return MPI_ERR_ARG;
-  DeviceGuard g(b->ctx->device);
-  cudaStreamSynchronize(b->ctx->stream);
-  solver_cache_forget(b->ctx, b);
+  DeviceGuard g(b->device);
+  if (b->ctx) {  // else the context is gone, and it drained its stream when it went
+    cudaStreamSynchronize(b->ctx->stream);
+    solver_cache_forget(b->ctx, b);
+    ctx_release(&b->ctx);
+  }
   if (b->U) cudaFree(b->U);
   if (b->Ubf) cudaFree(b->Ubf);
   tc_basis_release(b);

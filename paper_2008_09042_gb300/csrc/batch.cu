@@ -94,6 +94,7 @@ extern "C" mpi_status mpi_batch_create(mpi_ctx* ctx, const mpi_batch_slice* slic
     mpi_batch_destroy(bt);
     return st;
   }
+  ctx_adopt(ctx, &bt->ctx);
   *out = bt;
   return MPI_OK;
 }
@@ -112,6 +113,7 @@ extern "C" int64_t mpi_batch_kernel_count(const mpi_batch* bt) { return bt ? bt-
 
 extern "C" mpi_status mpi_batch_destroy(mpi_batch* bt) {
   if (!bt) return MPI_ERR_ARG;
+  ctx_release(&bt->ctx);
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->graph) cudaGraphDestroy(bt->graph);
   delete bt;

@@ -32,6 +32,11 @@ struct mpi_ctx {
   void* solver_cache = nullptr;  // recorded solver graphs (solvers.cu)
   int64_t launches = 0;
   bool pdl = true;  // launch operator kernels with programmatic stream serialization
+  // The `ctx` fields of the plans, bases and batches made on this context; the
+  // context clears them when it is destroyed, so that destroying a child after
+  // its context (in any order a caller's garbage collector picks) only frees
+  // the child's own memory.
+  std::vector<mpi_ctx**> children;
   std::string err;
   // profiling: event pairs around launches while enabled
   bool profiling = false;
@@ -45,6 +50,7 @@ struct mpi_ctx {
 
 struct mpi_plan {
   mpi_ctx* ctx = nullptr;
+  int device = 0;
   int ndim = 2;
   int nz = 1, ny = 0, nx = 0;
   int N = 0;
@@ -65,6 +71,7 @@ struct mpi_plan {
 
 struct mpi_basis {
   mpi_ctx* ctx = nullptr;
+  int device = 0;
   int N = 0, q = 0;
   float2* U = nullptr;  // [q][N] FP32 complex
   __nv_bfloat16* Ubf = nullptr;  // BF16 operand copy [N][Kp] (tensor-core path)
@@ -151,6 +158,9 @@ struct ExpandArgs {
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
 // Precision dispatch over the FFMA, 3xTF32 and BF16 expansion kernels.
 mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec);
+// Child bookkeeping (see mpi_ctx::children).
+void ctx_adopt(mpi_ctx* ctx, mpi_ctx** slot);
+void ctx_release(mpi_ctx** slot);
 // BF16 tensor-core expansion (tcgen05); same modes and arguments.
 mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a);
 mpi_status tc_basis_prepare(mpi_ctx* ctx, mpi_basis* b);

@@ -244,3 +244,24 @@ def test_radial_close_to_direct_nudft(ctx, mp):
     ref_kb = op.forward(cs["kb"], cs["U"], cs["a"], cs["p"])
     kb_err = rel(ref_kb, ref_exact)  # the gridding's own error, FP64
     assert rel(y, ref_exact) < kb_err + 1e-5
+
+
+def test_destroy_context_before_children(mp):
+    # a garbage collector may finalise a context before the plans, bases and
+    # batches made on it; destroying them afterwards must only free their memory
+    ctx2 = mp.Context(0)
+    n, C, q = 32, 2, 4
+    U = w.smooth_orthonormal_basis(n, n, q, seed=1)
+    idx = w.mask_to_indices(w.poisson_disc_mask(n, n, 4, calib=(8, 8), seed=2))
+    plan = mp.Plan(ctx2, (n, n), sample_idx=idx)
+    B = mp.Basis(ctx2, U.T)
+    a = c64(w.random_coefficients(C, q, seed=3))
+    p = c64(w.random_image(n * n, seed=4))
+    y = torch.empty((C, idx.size), dtype=torch.complex64, device="cuda")
+    x = torch.empty((n * n,), dtype=torch.complex64, device="cuda")
+    bt = mp.Batch(ctx2, [dict(plan=plan, basis=B, alpha=a, p=p, y=y, x=x)], kind="pair")
+    bt.run()
+    ctx2.close()
+    bt.close()
+    B.close()
+    plan.close()

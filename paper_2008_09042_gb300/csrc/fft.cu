@@ -283,67 +283,106 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
   for (int i = lane; i < NX; i += 32) dst[i] = b[pad8(i)];
 }
 
-constexpr int kColTile = 8;  // adjacent lines per CTA (one warp each)
-constexpr int kColPad = 4;
+constexpr int kLineWarps = 8;  // warps per CTA of the line pass
 
 // In-place FFT of lines of length L with element stride `stride`.  A CTA takes
-// kColTile lines that are adjacent in memory (consecutive x), loads them with
-// 64-byte row segments, transposes into shared memory (one contiguous padded
-// line per warp), transforms and writes back.  Tiles are enumerated as
-// (slab, x-tile) with slab base offset = (slab / inner) * outer_stride +
-// (slab % inner) * inner_stride.
-// Column stride of the transposed tile: the padded line length rounded up to
-// 2 mod 16 float2, which keeps the transposing loads and stores (8 lines x 4
-// rows per warp) free of bank conflicts.
-__host__ __device__ constexpr int col_stride(int L) {
-  return padded_len(L) + ((2 - padded_len(L)) % 16 + 16) % 16;
+// TILE lines that are adjacent in memory (consecutive x): it loads them as
+// TILE-element row segments (64, 128 or 256 bytes), transposes into shared
+// memory (one contiguous padded line each), transforms them (TILE / 8 lines
+// per warp) and writes back.  Wide tiles make long DRAM bursts for passes over
+// volumes that do not fit in L2; narrow ones give more CTAs for small grids.
+// Tiles are enumerated as (slab, x-tile) with slab base offset
+// (slab / inner) * outer_stride + (slab % inner) * inner_stride.
+// Column stride of the transposed tile: the padded line length rounded to
+// 2 mod 16 float2 for TILE <= 16 (a warp's transposing accesses then cover 8
+// or 16 lines x 4 or 2 rows) and to 1 mod 16 for TILE = 32 (32 lines of one
+// row); either way they take the minimum two shared-memory wavefronts.
+__host__ __device__ constexpr int col_stride(int L, int TILE) {
+  return padded_len(L) + (((TILE == 32 ? 1 : 2) - padded_len(L)) % 16 + 16) % 16;
 }
 
-template <int L, bool INV>
-__global__ void __launch_bounds__(kColTile * 32) k_fft_lines(float2* __restrict__ data, int nx,
-                                                            long stride, int n_slabs, int inner,
-                                                            long outer_stride, long inner_stride,
-                                                            const float2* __restrict__ tw_g) {
+template <int L, bool INV, int TILE>
+__global__ void __launch_bounds__(kLineWarps * 32) k_fft_lines(float2* __restrict__ data, int nx,
+                                                              long stride, int n_slabs, int inner,
+                                                              long outer_stride, long inner_stride,
+                                                              const float2* __restrict__ tw_g) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
-  constexpr int S = col_stride(L);
+  constexpr int S = col_stride(L, TILE);
+  constexpr int T = kLineWarps * 32;         // threads
+  constexpr int RSTEP = T / TILE;            // rows covered per pass of the CTA
+  constexpr int PER = (L + RSTEP - 1) / RSTEP;  // elements per thread
   __shared__ float2 tw[L];
-  __shared__ float2 buf[kColTile * S];
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tw_g[i];
-  const int x_tiles = (nx + kColTile - 1) / kColTile;
-  const long tile = blockIdx.x;
-  const int slab = (int)(tile / x_tiles);
-  const int x0 = (int)(tile % x_tiles) * kColTile;
+  __shared__ float2 buf[TILE * S];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < L; i += T) tw[i] = tw_g[i];
+  const int x_tiles = (nx + TILE - 1) / TILE;
+  const int tile = (int)blockIdx.x;
+  const int slab = tile / x_tiles;
+  const int x0 = (tile - slab * x_tiles) * TILE;
   if (slab >= n_slabs) return;
   const size_t base = (size_t)(slab / inner) * outer_stride + (size_t)(slab % inner) * inner_stride + x0;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < L * kColTile; e += blockDim.x) {
-    const int r = e / kColTile, cx = e % kColTile;
-    if (x0 + cx < nx) buf[cx * S + pad8(r)] = data[base + (size_t)r * stride + cx];
-  }
+  // thread -> (column cx, rows r0 + RSTEP u): all PER loads are issued before any is used
+  const int cx = tid % TILE, r0 = tid / TILE;
+  const bool ok = x0 + cx < nx;
+  const float2* src = data + base + cx;
+  float2 v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u)
+    if (ok && r0 + RSTEP * u < L) v[u] = src[(size_t)(r0 + RSTEP * u) * stride];
+#pragma unroll
+  for (int u = 0; u < PER; ++u)
+    if (ok && r0 + RSTEP * u < L) buf[cx * S + pad8(r0 + RSTEP * u)] = v[u];
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  if (x0 + warp < nx) Fft<L, INV>::go(buf + warp * S, tw, lane);
+  for (int line = warp; line < TILE; line += kLineWarps)
+    if (x0 + line < nx) Fft<L, INV>::go(buf + line * S, tw, lane);
   __syncthreads();
-  for (int e = tid; e < L * kColTile; e += blockDim.x) {
-    const int r = e / kColTile, cx = e % kColTile;
-    if (x0 + cx < nx) data[base + (size_t)r * stride + cx] = buf[cx * S + pad8(r)];
+  float2* dst = data + base + cx;
+#pragma unroll
+  for (int u = 0; u < PER; ++u)
+    if (ok && r0 + RSTEP * u < L) dst[(size_t)(r0 + RSTEP * u) * stride] = buf[cx * S + pad8(r0 + RSTEP * u)];
+}
+
+template <int L, bool INV, int TILE>
+void lines_launch(mpi_ctx* ctx, long blocks, float2* data, int nx, long stride, int n_slabs, int inner,
+                  long outer_stride, long inner_stride, const float2* tw) {
+  launch_pdl(ctx, k_fft_lines<L, INV, TILE>, dim3((unsigned)blocks), dim3(kLineWarps * 32), 0, data, nx, stride,
+             n_slabs, inner, outer_stride, inner_stride, tw);
+}
+
+// Tile width: the widest (longest row segments) that keeps at most 16 elements
+// per thread in the copy phases and still gives every SM four or more CTAs.
+int lines_tile(const mpi_ctx* ctx, int L, int nx, int n_slabs) {
+  const long want = 4L * std::max(ctx->num_sms, 1);
+  const int tiles[3] = {32, 16, 8};
+  for (int t : tiles) {
+    if (L * t / (kLineWarps * 32) > 16) continue;
+    if (t == 8 || (long)n_slabs * ((nx + t - 1) / t) >= want) return t;
   }
+  return 8;
 }
 
 template <bool INV>
 mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride, int n_slabs, int inner,
                           long outer_stride, long inner_stride) {
-  const int x_tiles = (nx + kColTile - 1) / kColTile;
+  const int tile = lines_tile(ctx, L, nx, n_slabs);
+  const int x_tiles = (nx + tile - 1) / tile;
   const long blocks = (long)n_slabs * x_tiles;
   if (blocks == 0) return MPI_OK;
   if (blocks > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many FFT tiles");
   const float2* tw = twiddle_table(ctx, L);
   if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
-#define MPI_LINES_CASE(n)                                                                          \
-  case n:                                                                                          \
-    launch_pdl(ctx, k_fft_lines<n, INV>, dim3((unsigned)blocks), dim3(kColTile * 32), 0, data, nx, stride,  \
-               n_slabs, inner, outer_stride, inner_stride, tw);                                    \
+#define MPI_LINES_CASE(n)                                                                                    \
+  case n:                                                                                                    \
+    if (n <= 128 && tile == 32)                                                                              \
+      lines_launch<n, INV, (n <= 128 ? 32 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,  \
+                                                inner_stride, tw);                                          \
+    else if (n <= 256 && tile == 16)                                                                         \
+      lines_launch<n, INV, (n <= 256 ? 16 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,  \
+                                                inner_stride, tw);                                          \
+    else                                                                                                     \
+      lines_launch<n, INV, 8>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw); \
     break;
   MPI_PROF(ctx, KF_FFT_LINES);
   switch (L) {

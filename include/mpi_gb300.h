@@ -150,6 +150,8 @@ mpi_status mpi_basis_destroy(mpi_basis* basis);
 /* Which kernel carries the dense contraction U alpha (for a Tucker basis, the
  * core contraction) for C coils at precision `prec`; `jacobian` != 0 asks
  * about the Jacobian's forward pass, which expands alpha and dalpha together.
+ * The forward-type passes run in coil groups when all C coils do not fit one
+ * tensor-core launch; the adjoint passes run on the CUDA cores in that case.
  * Returns MPI_EXPAND_FFMA (CUDA-core FP32), MPI_EXPAND_TF32X3 (tensor cores,
  * FP32-accurate split) or MPI_EXPAND_BF16 (tensor cores, BF16 operands), or -1
  * for a null basis, C < 1 or an unknown precision.  Host-side query: no device

@@ -125,7 +125,7 @@ extern "C" int mpi_expand_path(const mpi_basis* basis, int C, int jacobian, mpi_
     case MPI_PREC_BF16:
       return MPI_EXPAND_BF16;
     case MPI_PREC_FP32:
-      return tf32_supported(eb, mode, C) ? MPI_EXPAND_TF32X3 : MPI_EXPAND_FFMA;
+      return tf32_group(eb, mode, C) > 0 ? MPI_EXPAND_TF32X3 : MPI_EXPAND_FFMA;
     case MPI_PREC_FP32_SIMT:
       return MPI_EXPAND_FFMA;
     default:
@@ -138,7 +138,22 @@ extern "C" int mpi_expand_path(const mpi_basis* basis, int C, int jacobian, mpi_
 // FP32_SIMT: the FFMA kernel.
 mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec) {
   if (prec == MPI_PREC_BF16) return launch_expand_tc(ctx, basis, mode, a);
-  if (prec == MPI_PREC_FP32 && tf32_supported(basis, mode, a.C)) return launch_expand_tf32(ctx, basis, mode, a);
+  if (prec == MPI_PREC_FP32) {
+    const int g = tf32_group(basis, mode, a.C);
+    if (g == a.C) return launch_expand_tf32(ctx, basis, mode, a);
+    if (g > 0) {  // coil groups: each launch takes its slice of alpha (dalpha) and of the per-coil output
+      for (int c0 = 0; c0 < a.C; c0 += g) {
+        ExpandArgs ag = a;
+        ag.C = std::min(g, a.C - c0);
+        ag.alpha = a.alpha + (size_t)c0 * a.q;
+        if (a.dalpha) ag.dalpha = a.dalpha + (size_t)c0 * a.q;
+        ag.out = a.out + (size_t)c0 * a.N;
+        mpi_status st = launch_expand_tf32(ctx, basis, mode, ag);
+        if (st) return st;
+      }
+      return MPI_OK;
+    }
+  }
   return launch_expand(ctx, mode, a);
 }
 
@@ -219,6 +234,7 @@ mpi_status carve_work(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis
 mpi_status run_expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec,
                       const Work& w) {
   if (!basis->tucker) return expand(ctx, basis, mode, a, prec);
+  if (tucker_fusable(mode)) return tucker_fused(ctx, basis, mode, a, w.T, prec);
   mpi_status st = tucker_maps(ctx, basis, a.alpha, a.C, w.S, w.T, prec);
   if (st) return st;
   if (mode == EX_JFWD && (st = tucker_maps(ctx, basis, a.dalpha, a.C, w.dS, w.T, prec))) return st;

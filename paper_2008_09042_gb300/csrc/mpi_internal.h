@@ -168,6 +168,9 @@ void tc_basis_release(mpi_basis* b);
 // FP32-accurate tensor-core expansion (3xTF32); same modes and arguments.
 mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a);
 bool tf32_supported(const mpi_basis* b, int mode, int C);
+// Coils per launch of the 3xTF32 kernel: C when the whole call fits, else the
+// largest group that fits (forward-type modes only), or 0.
+int tf32_group(const mpi_basis* b, int mode, int C);
 mpi_status tf32_basis_prepare(mpi_ctx* ctx, mpi_basis* b);
 void tf32_basis_release(mpi_basis* b);
 // dalpha[c][j] = sum_n conj(U[j][n]) V[c][n]; partials in `work_partials`.
@@ -179,6 +182,11 @@ size_t uh_v_partial_elems(const mpi_ctx* ctx, int N, int q, int C);
 size_t tucker_work_elems(const mpi_basis* b, int C);
 mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
                        mpi_precision prec);
+// The forward pass of a Tucker basis with the last mode product fused with the
+// point-wise step (no per-coil maps stored); tucker_fusable says which modes.
+bool tucker_fusable(int mode);
+mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a, float2* tmp,
+                        mpi_precision prec);
 mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,
                           float2* partials, size_t partial_cap);
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS);

@@ -367,6 +367,16 @@ bool tf32_supported(const mpi_basis* b, int mode, int C) {
   return b->Uf32 && b->tmap32 && plan_tf32(b, mode, C, &p);
 }
 
+int tf32_group(const mpi_basis* b, int mode, int C) {
+  if (tf32_supported(b, mode, C)) return C;
+  // coils are independent in these modes, so they can run in groups whose
+  // coefficient operand and accumulators fit; the adjoint modes sum over coils
+  if (mode != EX_MAPS && mode != EX_FWD && mode != EX_JFWD) return 0;
+  for (int g = C - 1; g >= 1; --g)
+    if (tf32_supported(b, mode, g)) return g;
+  return 0;
+}
+
 mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& x) {
   TfPlan pl;
   if (!b->Uf32 || !b->tmap32 || !plan_tf32(b, mode, x.C, &pl))

@@ -11,8 +11,10 @@
 //      tensors smallest;
 // and the adjoint U^H v runs the conjugate-transposed mode products in the
 // reverse order followed by the core's U^H V contraction.  Mode products are
-// FP32 complex on CUDA cores; the per-coil maps are materialised in the context
-// workspace and combined with the image by a point-wise pass.
+// FP32 complex on CUDA cores.  The forward operator's last mode product is
+// fused with its point-wise step, so its per-coil maps are never stored; the
+// other passes materialise the maps in the context workspace and combine them
+// with the image in a point-wise kernel.
 #include <algorithm>
 
 #include "mpi_internal.h"
@@ -34,6 +36,7 @@ __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * 
 }
 
 constexpr int kIB = 16;  // outputs along i per thread
+constexpr int kPB = 8;   // contracted elements loaded per batch
 
 // Y[r][i][b] = sum_p X[r][p][b] M(i, p), with M(i, p) = F[i][p] (forward, F is I x P)
 // or conj(F[p][i]) (adjoint, F is P x I).  Threads run along b (coalesced);
@@ -46,8 +49,10 @@ __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, co
                                                 int P, int I, long B, float2* __restrict__ Y) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
-  __shared__ float2 sM[128 * kIB];
+  __shared__ float2 sM[(128 + kPB) * kIB];  // rows beyond P are zero (the last load batch)
   const int i0 = blockIdx.x * kIB;
+  for (int e = P * kIB + threadIdx.x; e < ((P + kPB - 1) / kPB) * kPB * kIB; e += blockDim.x)
+    sM[e] = make_float2(0.f, 0.f);
   for (int e = threadIdx.x; e < P * kIB; e += blockDim.x) {
     const int p = e / kIB, ii = e % kIB;
     const int i = i0 + ii;
@@ -70,14 +75,19 @@ __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, co
 #pragma unroll
   for (int ii = 0; ii < kIB; ++ii) acc[ii] = make_float2(0.f, 0.f);
   const float2* x = X + (size_t)r * P * B + b;
-  for (int p = 0; p < P; ++p) {
-    const float2 xv = x[(size_t)p * B];
-    const float4* mp = reinterpret_cast<const float4*>(sM + p * kIB);
+  for (int p0 = 0; p0 < P; p0 += kPB) {
+    float2 xv[kPB];  // the batch's loads are all issued before the first is used
 #pragma unroll
-    for (int i2 = 0; i2 < kIB / 2; ++i2) {
-      const float4 m = mp[i2];
-      cfma(acc[2 * i2], xv, make_float2(m.x, m.y));
-      cfma(acc[2 * i2 + 1], xv, make_float2(m.z, m.w));
+    for (int u = 0; u < kPB; ++u) xv[u] = p0 + u < P ? x[(size_t)(p0 + u) * B] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kPB; ++u) {
+      const float4* mp = reinterpret_cast<const float4*>(sM + (p0 + u) * kIB);
+#pragma unroll
+      for (int i2 = 0; i2 < kIB / 2; ++i2) {
+        const float4 m = mp[i2];
+        cfma(acc[2 * i2], xv[u], make_float2(m.x, m.y));
+        cfma(acc[2 * i2 + 1], xv[u], make_float2(m.z, m.w));
+      }
     }
   }
   float2* y = Y + (size_t)r * I * B + b;
@@ -169,6 +179,64 @@ __global__ void k_pointwise(ExpandArgs a, const float2* __restrict__ S, const fl
   }
 }
 
+// The x1 mode product fused with the forward operator's point-wise step:
+// v_c[n] = sign(n) scale * p[n] * sum_p X[c][p][b] F[i][p], with i the slowest
+// image axis and b = (y, x), so that voxel n = i B + b.  Same tiling as
+// k_mode_b (threads along b, kIB outputs along i per thread, one coil per
+// grid z), so the per-coil maps are never stored.
+__global__ void __launch_bounds__(256) k_mode1_fwd(const float2* __restrict__ X, const float2* __restrict__ F, int P,
+                                                   int I, long B, ExpandArgs a) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  __shared__ float2 sM[(128 + kPB) * kIB];  // M(i, p) = F[i][p] of the i-block; rows beyond P are zero
+  const int i0 = blockIdx.x * kIB;
+  for (int e = P * kIB + threadIdx.x; e < ((P + kPB - 1) / kPB) * kPB * kIB; e += blockDim.x)
+    sM[e] = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < P * kIB; e += blockDim.x) {
+    const int p = e / kIB, ii = e % kIB;
+    sM[e] = i0 + ii < I ? F[(size_t)(i0 + ii) * P + p] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const long b = (long)blockIdx.y * blockDim.x + threadIdx.x;
+  const int c = blockIdx.z;
+  if (b >= B || c >= a.C) return;
+  // the image values this thread multiplies, loaded before the contraction so
+  // that their latency overlaps it
+  float2 pv[kIB];
+#pragma unroll
+  for (int ii = 0; ii < kIB; ++ii) pv[ii] = i0 + ii < I ? a.p[(size_t)(i0 + ii) * B + b] : make_float2(0.f, 0.f);
+  float2 acc[kIB];
+#pragma unroll
+  for (int ii = 0; ii < kIB; ++ii) acc[ii] = make_float2(0.f, 0.f);
+  const float2* x = X + (size_t)c * P * B + b;
+  for (int p0 = 0; p0 < P; p0 += kPB) {
+    float2 xv[kPB];
+#pragma unroll
+    for (int u = 0; u < kPB; ++u) xv[u] = p0 + u < P ? x[(size_t)(p0 + u) * B] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kPB; ++u) {
+      const float4* mp = reinterpret_cast<const float4*>(sM + (p0 + u) * kIB);
+#pragma unroll
+      for (int i2 = 0; i2 < kIB / 2; ++i2) {
+        const float4 m = mp[i2];
+        cfma(acc[2 * i2], xv[u], make_float2(m.x, m.y));
+        cfma(acc[2 * i2 + 1], xv[u], make_float2(m.z, m.w));
+      }
+    }
+  }
+  // centring sign (-1)^(x + y + z) with z = i and b = y nx + x
+  const int sb = (int)((b % a.nx) + (b / a.nx)) & 1;
+#pragma unroll
+  for (int ii = 0; ii < kIB; ++ii) {
+    const int i = i0 + ii;
+    if (i >= I) continue;
+    const size_t n = (size_t)i * B + b;
+    const float sg = (a.centre && ((sb + i) & 1) ? -1.f : 1.f) * a.scale;
+    const float2 v = cmul(acc[ii], pv[ii]);
+    a.out[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
+  }
+}
+
 mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, long B, float2* Y) {
   if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
   const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);  // no idle lanes when B = 128
@@ -202,11 +270,13 @@ size_t tucker_work_elems(const mpi_basis* b, int C) {
   return (size_t)C * (R + t1 + t2);
 }
 
-// maps[c] = s_c for all coils (C x N), through the core contraction and the
-// three mode products; `tmp` holds C * (R + r1 r2 n3 + r1 n2 n3) elements.
-mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
-                       mpi_precision prec) {
-  const int n1 = b->n[0], n2 = b->n[1], n3 = b->n[2];
+namespace {
+
+// The core contraction and the x3, x2 mode products: t2 [C][r1][n2][n3] in `tmp`
+// (after g [C][R] and t1 [C][r1][r2][n3]); returns t2.
+mpi_status tucker_t2(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp, mpi_precision prec,
+                     float2** t2_out) {
+  const int n2 = b->n[1], n3 = b->n[2];
   const int r1 = b->r[0], r2 = b->r[1], r3 = b->r[2];
   const long R = (long)r1 * r2 * r3;
   float2* g = tmp;                                  // [C][r1][r2][r3]
@@ -223,7 +293,42 @@ mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, in
   if (st) return st;
   if ((st = mode_last(ctx, false, g, b->F[2], C * r1 * r2, r3, n3, t1))) return st;
   if ((st = mode_b(ctx, false, t1, b->F[1], C * r1, r2, n2, n3, t2))) return st;
-  return mode_b(ctx, false, t2, b->F[0], C, r1, n1, (long)n2 * n3, maps);
+  *t2_out = t2;
+  return MPI_OK;
+}
+
+}  // namespace
+
+// maps[c] = s_c for all coils (C x N), through the core contraction and the
+// three mode products; `tmp` holds C * (R + r1 r2 n3 + r1 n2 n3) elements.
+mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
+                       mpi_precision prec) {
+  float2* t2 = nullptr;
+  mpi_status st = tucker_t2(ctx, b, alpha, C, tmp, prec, &t2);
+  if (st) return st;
+  return mode_b(ctx, false, t2, b->F[0], C, b->r[0], b->n[0], (long)b->n[1] * b->n[2], maps);
+}
+
+bool tucker_fusable(int mode) { return mode == EX_FWD; }
+
+// The forward pass straight from alpha: core contraction, x3, x2, then the x1
+// product fused with the point-wise step.
+mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a, float2* tmp,
+                        mpi_precision prec) {
+  if (!tucker_fusable(mode)) return set_err(ctx, MPI_ERR_ARG, "fused Tucker pass: mode");
+  float2* t2 = nullptr;
+  mpi_status st = tucker_t2(ctx, b, a.alpha, a.C, tmp, prec, &t2);
+  if (st) return st;
+  const int P = b->r[0], I = b->n[0];
+  const long B = (long)b->n[1] * b->n[2];
+  if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
+  const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);
+  const dim3 grid((unsigned)((I + kIB - 1) / kIB), (unsigned)((B + block - 1) / block), (unsigned)a.C);
+  if (grid.y > 65535 || a.C > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
+  MPI_PROF(ctx, KF_EXPAND);
+  launch_pdl(ctx, k_mode1_fwd, grid, dim3(block), 0, t2, b->F[0], P, I, B, a);
+  MPI_LAUNCH_CHECK(ctx, "k_mode1_fwd");
+  return MPI_OK;
 }
 
 // dalpha[c] = U^H v_c (C x q): conjugate-transposed mode products, then the core's U^H V.

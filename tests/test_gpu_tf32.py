@@ -69,14 +69,17 @@ def test_tf32_expand_shapes(ctx, mp, N, C, q):
     assert rel(s_tc, s_simt) < 5e-6
 
 
-def test_tf32_falls_back_to_cuda_cores_for_wide_coefficients(ctx, mp):
-    # 2C = 300 coefficient rows exceed the 256-row MMA: the FFMA kernel serves FP32
+def test_tf32_coil_groups_for_wide_coefficients(ctx, mp):
+    # 2C = 300 coefficient rows exceed one MMA's N: the coils run in groups on
+    # the tensor cores, and the result is the same expansion
     N, C, q = 2048, 150, 24
     U = _basis(N, q, 5)
     a = w.random_coefficients(C, q, seed=6).astype(np.complex64).astype(np.complex128)
     B = mp.Basis(ctx, U.T)
-    assert mp.expand_path(ctx, B, C, "fp32") == "ffma"
+    assert mp.expand_path(ctx, B, C, "fp32") == "tf32x3"
+    l0 = ctx.launches()
     s = f64(mp.basis_expand(ctx, B, c64(a), prec="fp32"))
+    assert ctx.launches() - l0 >= 2  # more than one group
     ctx.synchronize()
     assert rel(s, op.expand(U, a)) < TOL
 
@@ -86,7 +89,7 @@ def test_tf32_falls_back_to_cuda_cores_for_wide_coefficients(ctx, mp):
 def test_fp32_operator_family_matches_oracle(ctx, mp, prec, shape, C, q):
     # forward, adjoint, Jacobian (coefficient rows doubled) and Jacobian-adjoint;
     # at C = 32 the Jacobian's stacked [hi; lo] rows (256) leave no room for a
-    # double-buffered accumulator, so that one call runs on the CUDA cores
+    # double-buffered accumulator, so that one call runs in two coil groups
     U = w.smooth_orthonormal_basis(shape[0], shape[1], q, seed=4).astype(np.complex64).astype(np.complex128)
     mask = w.poisson_disc_mask(shape[0], shape[1], 4, calib=(12, 12), seed=5)
     idx = w.mask_to_indices(mask)
@@ -101,7 +104,7 @@ def test_fp32_operator_family_matches_oracle(ctx, mp, prec, shape, C, q):
     B = mp.Basis(ctx, U.T)
     if prec == "fp32":
         assert mp.expand_path(ctx, B, C, prec) == "tf32x3"
-        assert mp.expand_path(ctx, B, C, prec, jacobian=True) == ("ffma" if C == 32 else "tf32x3")
+        assert mp.expand_path(ctx, B, C, prec, jacobian=True) == "tf32x3"  # C = 32 runs in coil groups
     ag, pg = c64(a), c64(p)
     assert rel(f64(mp.forward(ctx, plan, B, ag, pg, prec=prec)), op.forward(Fs, U, a, p)) < TOL
     assert rel(f64(mp.adjoint(ctx, plan, B, ag, c64(r), prec=prec)), op.adjoint(Fs, U, a, r)) < TOL

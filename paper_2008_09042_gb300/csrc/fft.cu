@@ -204,11 +204,11 @@ MPI_FFT_PLAN(512, 8, 8, 8)
 
 constexpr int kRowWarps = 4;
 
-// One warp per (coil, k-space row).  Forward: FFT along x, k-side centring sign,
-// gather the row's samples (contiguous in the sorted list).  Rows without
-// samples are skipped.
-// The twiddle table, the row and the row's sample range are fetched before the
-// one CTA barrier, so their global-memory latencies overlap.
+// One warp per (coil, k-space row), the warps striding over all rows (the grid
+// is capped at a few CTAs per SM: volumes have hundreds of thousands of rows,
+// most of them without samples, and one CTA each would make the pass bound by
+// CTA launches).  Forward: FFT along x, k-side centring sign, gather the row's
+// samples (contiguous in the sorted list); rows without samples are skipped.
 template <int NX>
 __global__ void __launch_bounds__(kRowWarps * 32) k_rows_fwd_gather(
     const float2* __restrict__ data, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
@@ -219,32 +219,39 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_fwd_gather(
   __shared__ float2 tw[NX];
   __shared__ float2 buf[kRowWarps][padded_len(NX)];
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long gr = (long)blockIdx.x * kRowWarps + warp;
-  const bool in_range = gr < (long)C * n_rows;
-  const int c = in_range ? (int)(gr / n_rows) : 0, row = in_range ? (int)(gr % n_rows) : 0;
-  const int m0 = in_range ? row_ptr[row] : 0, m1 = in_range ? row_ptr[row + 1] : 0;
-  const bool work = in_range && m1 > m0;
-  float2* b = buf[warp];
-  if (work) {
-    const float2* src = data + ((size_t)c * n_rows + row) * NX;
-#pragma unroll
-    for (int i = lane; i < NX; i += 32) b[pad8(i)] = src[i];
-  }
   __syncthreads();
-  if (!work) return;
-  Fft<NX, false>::go(b, tw, lane);
-  const int rpar = (row / ny + row % ny) & 1;  // (kz + ky) parity
-  const size_t rbase = (size_t)row * NX;
-  for (int m = m0 + lane; m < m1; m += 32) {
-    const int kx = (int)(idx[m] - rbase);
-    const float s = ((kx + rpar) & 1) ? -ksign : ksign;
-    const float2 v = b[pad8(kx)];
-    y[(size_t)c * M + m] = make_float2(v.x * s, v.y * s);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* b = buf[warp];
+  const int total = C * n_rows;
+  for (int gr = blockIdx.x * kRowWarps + warp; gr < total; gr += gridDim.x * kRowWarps) {
+    const int c = gr / n_rows, row = gr - c * n_rows;
+    const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
+    if (m1 <= m0) continue;  // warp-uniform
+    const float2* src = data + ((size_t)c * n_rows + row) * NX;
+    constexpr int PL = (NX + 31) / 32;
+    float2 v[PL];
+#pragma unroll
+    for (int u = 0; u < PL; ++u)
+      if (lane + 32 * u < NX) v[u] = src[lane + 32 * u];
+#pragma unroll
+    for (int u = 0; u < PL; ++u)
+      if (lane + 32 * u < NX) b[pad8(lane + 32 * u)] = v[u];
+    __syncwarp();
+    Fft<NX, false>::go(b, tw, lane);
+    const int rpar = (row / ny + row % ny) & 1;  // (kz + ky) parity
+    const size_t rbase = (size_t)row * NX;
+    for (int m = m0 + lane; m < m1; m += 32) {
+      const int kx = (int)(idx[m] - rbase);
+      const float sg = ((kx + rpar) & 1) ? -ksign : ksign;
+      const float2 t = b[pad8(kx)];
+      y[(size_t)c * M + m] = make_float2(t.x * sg, t.y * sg);
+    }
+    __syncwarp();  // the buffer is refilled for the next row
   }
 }
 
-// Adjoint: zero-fill the row from its samples (with the k-side sign), inverse FFT.
+// Adjoint: zero-fill the row from its samples (with the k-side sign), inverse
+// FFT; rows without samples are written as zeros.  Same row striding.
 template <int NX>
 __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
     const float2* __restrict__ y, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
@@ -255,32 +262,33 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
   __shared__ float2 tw[NX];
   __shared__ float2 buf[kRowWarps][padded_len(NX)];
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long gr = (long)blockIdx.x * kRowWarps + warp;
-  const bool in_range = gr < (long)C * n_rows;
-  const int c = in_range ? (int)(gr / n_rows) : 0, row = in_range ? (int)(gr % n_rows) : 0;
-  const int m0 = in_range ? row_ptr[row] : 0, m1 = in_range ? row_ptr[row + 1] : 0;
-  float2* dst = data + ((size_t)c * n_rows + row) * NX;
   float2* b = buf[warp];
-  if (in_range && m1 > m0) {
+  const int total = C * n_rows;
+  for (int gr = blockIdx.x * kRowWarps + warp; gr < total; gr += gridDim.x * kRowWarps) {
+    const int c = gr / n_rows, row = gr - c * n_rows;
+    const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
+    float2* dst = data + ((size_t)c * n_rows + row) * NX;
+    if (m1 <= m0) {  // warp-uniform
+      for (int i = lane; i < NX; i += 32) dst[i] = make_float2(0.f, 0.f);
+      continue;
+    }
     for (int i = lane; i < padded_len(NX); i += 32) b[i] = make_float2(0.f, 0.f);
     __syncwarp();
     const int rpar = (row / ny + row % ny) & 1;
     const size_t rbase = (size_t)row * NX;
     for (int m = m0 + lane; m < m1; m += 32) {
       const int kx = (int)(idx[m] - rbase);
-      const float s = ((kx + rpar) & 1) ? -ksign : ksign;
-      const float2 v = y[(size_t)c * M + m];
-      b[pad8(kx)] = make_float2(v.x * s, v.y * s);
+      const float sg = ((kx + rpar) & 1) ? -ksign : ksign;
+      const float2 t = y[(size_t)c * M + m];
+      b[pad8(kx)] = make_float2(t.x * sg, t.y * sg);
     }
-  } else if (in_range) {
-    for (int i = lane; i < NX; i += 32) dst[i] = make_float2(0.f, 0.f);
+    __syncwarp();
+    Fft<NX, true>::go(b, tw, lane);
+    for (int i = lane; i < NX; i += 32) dst[i] = b[pad8(i)];
+    __syncwarp();
   }
-  __syncthreads();
-  if (!(in_range && m1 > m0)) return;
-  Fft<NX, true>::go(b, tw, lane);
-#pragma unroll
-  for (int i = lane; i < NX; i += 32) dst[i] = b[pad8(i)];
 }
 
 constexpr int kLineWarps = 8;  // warps per CTA of the line pass
@@ -302,7 +310,7 @@ __host__ __device__ constexpr int col_stride(int L, int TILE) {
 }
 
 template <int L, bool INV, int TILE>
-__global__ void __launch_bounds__(kLineWarps * 32) k_fft_lines(float2* __restrict__ data, int nx,
+__global__ void __launch_bounds__(kLineWarps * 32, 3) k_fft_lines(float2* __restrict__ data, int nx,
                                                               long stride, int n_slabs, int inner,
                                                               long outer_stride, long inner_stride,
                                                               const float2* __restrict__ tw_g) {
@@ -427,7 +435,8 @@ mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const floa
                                   float2* y) {
   if (plan->M == 0 || C == 0) return MPI_OK;
   const int n_rows = plan->n_rows;
-  const long blocks = ((long)C * n_rows + kRowWarps - 1) / kRowWarps;
+  if ((long)C * n_rows > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many k-space rows");
+  const long blocks = std::min(((long)C * n_rows + kRowWarps - 1) / kRowWarps, 16L * std::max(ctx->num_sms, 1));
   const float ks = axis_sign(plan->nx) * axis_sign(plan->ny) * (plan->ndim == 3 ? axis_sign(plan->nz) : 1.f);
   const float2* tw = twiddle_table(ctx, plan->nx);
   if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
@@ -460,7 +469,8 @@ mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const flo
                                    float2* data) {
   if (C == 0) return MPI_OK;
   const int n_rows = plan->n_rows;
-  const long blocks = ((long)C * n_rows + kRowWarps - 1) / kRowWarps;
+  if ((long)C * n_rows > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many k-space rows");
+  const long blocks = std::min(((long)C * n_rows + kRowWarps - 1) / kRowWarps, 16L * std::max(ctx->num_sms, 1));
   const float ks = axis_sign(plan->nx) * axis_sign(plan->ny) * (plan->ndim == 3 ? axis_sign(plan->nz) : 1.f);
   const float2* tw = twiddle_table(ctx, plan->nx);
   if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");

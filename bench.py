@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp32_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the radial/3D/recon lines")
+    ap.add_argument("--profile-workload", default=None,
+                    help="only run --steps forward+adjoint pairs of this workload (radial2d_*, cart3d_*), "
+                         "untimed, for an external profiler")
     return ap.parse_args()
 
 
@@ -582,10 +585,48 @@ def run_ours(args):
     return 0
 
 
+def profile_workload(args):
+    """Forward+adjoint pairs of one secondary workload, nothing timed: the command
+    an external profiler (ncu) wraps to capture that workload's kernels."""
+    import torch
+    import paper_2008_09042_gb300 as mp
+
+    dev = torch.device("cuda", 0)
+    ctx = mp.Context(0)
+    base = w.BASE_SEED
+    cfg = w.workload(args.profile_workload)
+    if cfg["name"].startswith("cart3d"):
+        dims = cfg["dims"]
+        core, fac = w.smooth_tucker_basis(dims, cfg["ranks"], cfg["q"], seed=base)
+        mask = w.poisson_disc_mask_3d(*dims, R=cfg["R"], calib=cfg["calib"], seed=base + 1)
+        plan = mp.Plan(ctx, dims, sample_idx=w.mask_to_indices(mask))
+        B = mp.TuckerBasis(ctx, core, fac)
+        p = w.random_ellipses(dims[1], dims[2], nz=dims[0], seed=base + 3).ravel()
+    elif cfg["name"].startswith("radial2d"):
+        n = cfg["dims"][0]
+        k = w.golden_angle_radial(cfg["spokes"], cfg["readout"]).astype(np.float32)
+        plan = mp.Plan(ctx, (n, n), traj=k, kb_width=cfg["W"], oversamp=cfg["sigma"])
+        B = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, cfg["q"], seed=base).T)
+        p = w.random_ellipses(n, n, seed=base + 2).ravel()
+    else:
+        raise SystemExit(f"--profile-workload: {cfg['name']} is not a radial2d_* or cart3d_* workload")
+    a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 2).astype(np.complex64)).to(dev)
+    pd = torch.from_numpy(p.astype(np.complex64)).to(dev)
+    ctx.reserve(plan, B, cfg["C"])
+    for _ in range(args.steps):
+        y = mp.forward(ctx, plan, B, a, pd, args.prec)
+        mp.adjoint(ctx, plan, B, a, y, args.prec)
+    ctx.synchronize()
+    print(f"{cfg['name']}: {args.steps} forward+adjoint pairs ({args.prec})", flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_workload:
+        return profile_workload(args)
     return run_ours(args)
 
 

@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cuda.h>
+
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -147,7 +149,7 @@ mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandAr
         ag.C = std::min(g, a.C - c0);
         ag.alpha = a.alpha + (size_t)c0 * a.q;
         if (a.dalpha) ag.dalpha = a.dalpha + (size_t)c0 * a.q;
-        ag.out = a.out + (size_t)c0 * a.N;
+        ag.out = a.out + (a.tuck_B ? (size_t)c0 * a.tuck_B : (size_t)c0 * a.N);
         mpi_status st = launch_expand_tf32(ctx, basis, mode, ag);
         if (st) return st;
       }
@@ -234,7 +236,10 @@ mpi_status carve_work(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis
 mpi_status run_expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandArgs& a, mpi_precision prec,
                       const Work& w) {
   if (!basis->tucker) return expand(ctx, basis, mode, a, prec);
-  if (tucker_fusable(mode)) return tucker_fused(ctx, basis, mode, a, w.T, prec);
+  // With the x1 product on the CUDA cores, the forward fuses it with its
+  // point-wise step; on the tensor cores the maps are written and combined below.
+  if (tucker_fusable(mode) && !tucker_x1_on_tensor_cores(basis, a.C, prec))
+    return tucker_fused(ctx, basis, mode, a, w.T, prec);
   mpi_status st = tucker_maps(ctx, basis, a.alpha, a.C, w.S, w.T, prec);
   if (st) return st;
   if (mode == EX_JFWD && (st = tucker_maps(ctx, basis, a.dalpha, a.C, w.dS, w.T, prec))) return st;
@@ -623,6 +628,7 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   for (int k = 0; k < 3; ++k)
     if (b->F[k]) cudaFree(b->F[k]);
   if (b->core) mpi_basis_destroy(b->core);
+  delete (CUtensorMap*)b->op_map;
   delete b;
   return MPI_OK;
 }

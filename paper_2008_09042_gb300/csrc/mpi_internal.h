@@ -88,6 +88,11 @@ struct mpi_basis {
   int n[3] = {0, 0, 0}, r[3] = {0, 0, 0};
   float2* F[3] = {nullptr, nullptr, nullptr};
   mpi_basis* core = nullptr;
+  // Tensor map of the flattened x1 operand in the workspace (tucker.cu), kept
+  // while the workspace address, coil count and precision stay the same.
+  void* op_map = nullptr;
+  const void* op_map_ptr = nullptr;
+  int op_map_C = -1, op_map_prec = -1;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -153,6 +158,10 @@ struct ExpandArgs {
   float2* out = nullptr;       // maps / v [C][N], or image [N]
   float2* vout = nullptr;      // Jacobian adjoint: conj(p) w [C][N]
   int* err = nullptr;          // device error word (bounded-wait timeouts)
+  // Maps-mode output remap for a flattened Tucker operand (tensor-core kernels
+  // only): pixel n = c B + b of coil row i goes to out[c tuck_stride + i B + b].
+  int tuck_B = 0;
+  long tuck_stride = 0;
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
@@ -173,6 +182,10 @@ bool tf32_supported(const mpi_basis* b, int mode, int C);
 int tf32_group(const mpi_basis* b, int mode, int C);
 mpi_status tf32_basis_prepare(mpi_ctx* ctx, mpi_basis* b);
 void tf32_basis_release(mpi_basis* b);
+// Tensor maps of a K-major operand [rows][Kp] (BF16 or FP32) laid out as the
+// tensor-core kernels read their basis copies; `map` is a CUtensorMap.
+bool tc_encode_operand_map(void* map, void* ptr, long rows, int Kp);
+bool tf32_encode_operand_map(void* map, void* ptr, long rows, int Kp);
 // dalpha[c][j] = sum_n conj(U[j][n]) V[c][n]; partials in `work_partials`.
 mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
                        float2* dalpha, float2* work_partials, size_t partial_cap_elems);
@@ -185,6 +198,8 @@ mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, in
 // The forward pass of a Tucker basis with the last mode product fused with the
 // point-wise step (no per-coil maps stored); tucker_fusable says which modes.
 bool tucker_fusable(int mode);
+// Whether the x1 mode product of this basis runs on the tensor-core kernels.
+bool tucker_x1_on_tensor_cores(const mpi_basis* b, int C, mpi_precision prec);
 mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a, float2* tmp,
                         mpi_precision prec);
 mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,

@@ -27,6 +27,8 @@ struct TcArgs {
   float2* out;
   float2* vout;
   int* err;
+  int tuck_B;         // maps mode: output remap for a flattened Tucker operand (0: none)
+  long tuck_stride;
 };
 
 // Position in a ring of `n` shared-memory stages: slot and the parity of the
@@ -247,6 +249,13 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
       const int nn = valid ? n : 0;
       const float sg = (a.centre ? centre_sign(nn, a.nx, a.ny) : 1.f) * a.scale;
       const float2 pimg = (MODE != EX_MAPS) ? a.p[nn] : make_float2(0.f, 0.f);
+      // maps mode: where coil c of pixel n goes ([C][N], or the Tucker remap)
+      size_t maps_base = (size_t)n, maps_cstride = (size_t)a.N;
+      if (MODE == EX_MAPS && a.tuck_B) {
+        const long nb = nn / a.tuck_B;
+        maps_base = (size_t)nb * a.tuck_stride + (size_t)(nn - nb * a.tuck_B);
+        maps_cstride = (size_t)a.tuck_B;
+      }
       const float2 dpi = (MODE == EX_JFWD) ? a.dp[nn] : make_float2(0.f, 0.f);
       float2 pacc = make_float2(0.f, 0.f);
       const int n_chunks = (2 * a.C + 15) / 16;
@@ -288,7 +297,7 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
           const bool cv = valid && c < a.C;
           const float2 s = make_float2(r[2 * i], r[2 * i + 1]);
           if (MODE == EX_MAPS) {
-            if (cv) a.out[(size_t)c * a.N + n] = s;
+            if (cv) a.out[maps_base + (size_t)c * maps_cstride] = s;
           } else if (MODE == EX_FWD) {
             const float2 v = cmul(s, pimg);
             if (cv) a.out[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);

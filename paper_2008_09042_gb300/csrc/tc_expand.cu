@@ -221,6 +221,23 @@ mpi_status tc_basis_prepare(mpi_ctx* ctx, mpi_basis* b) {
   return MPI_OK;
 }
 
+bool tc_encode_operand_map(void* map, void* ptr, long rows, int Kp) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+  if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {(cuuint32_t)kKChunk, (cuuint32_t)kTileM};
+  const cuuint32_t estr[2] = {1, 1};
+  return ((EncodeTiledFn)fn)((CUtensorMap*)map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void tc_basis_release(mpi_basis* b) {
   delete (CUtensorMap*)b->tmap;
   b->tmap = nullptr;
@@ -255,6 +272,8 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.out = x.out;
   a.vout = x.vout;
   a.err = ctx->dev_err;
+  a.tuck_B = x.tuck_B;
+  a.tuck_stride = x.tuck_stride;
   const size_t b_bytes = round_up(a.n_gemm * b->Kp * 2, 1024);
   // Two CTAs per SM (one's epilogue overlaps the other's loads) when each can
   // still keep four or more stages in flight within half of the SM's shared
@@ -263,7 +282,7 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   const size_t half_sm = 112 * 1024, whole_sm = 227 * 1024 - 128;
   int stages = half_sm > fixed ? (int)((half_sm - fixed) / kStageBytes) : 0;
   int per_sm = 2;
-  if (stages < 4) {
+  if (stages < 4 || a.tmem_cols > 256) {  // two CTAs per SM must both hold their TMEM columns
     per_sm = 1;
     stages = whole_sm > fixed ? (int)((whole_sm - fixed) / kStageBytes) : 0;
   }

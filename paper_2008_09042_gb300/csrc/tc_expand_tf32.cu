@@ -357,6 +357,23 @@ mpi_status tf32_basis_prepare(mpi_ctx* ctx, mpi_basis* b) {
   return MPI_OK;
 }
 
+bool tf32_encode_operand_map(void* map, void* ptr, long rows, int Kp) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+  if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kKChunk32, (cuuint32_t)kTileM};
+  const cuuint32_t estr[2] = {1, 1};
+  return ((EncodeTiledFn)fn)((CUtensorMap*)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void tf32_basis_release(mpi_basis* b) {
   delete (CUtensorMap*)b->tmap32;
   b->tmap32 = nullptr;
@@ -404,6 +421,8 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.out = x.out;
   a.vout = x.vout;
   a.err = ctx->dev_err;
+  a.tuck_B = x.tuck_B;
+  a.tuck_stride = x.tuck_stride;
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
   const int grid = std::min(n_tiles, std::max(ctx->num_sms, 1));
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap32;

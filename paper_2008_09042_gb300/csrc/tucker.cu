@@ -10,11 +10,17 @@
 //      first (x3 U3, then x2 U2, then x1 U1), which keeps the intermediate
 //      tensors smallest;
 // and the adjoint U^H v runs the conjugate-transposed mode products in the
-// reverse order followed by the core's U^H V contraction.  Mode products are
-// FP32 complex on CUDA cores.  The forward operator's last mode product is
-// fused with its point-wise step, so its per-coil maps are never stored; the
-// other passes materialise the maps in the context workspace and combine them
-// with the image in a point-wise kernel.
+// reverse order followed by the core's U^H V contraction.  The x3 and x2 mode
+// products are FP32 complex on CUDA cores.  The x1 product, which carries most
+// of the arithmetic, runs on the tensor-core expansion kernels (3xTF32 for FP32,
+// BF16): over all coils it is a dense expansion whose basis rows are the
+// positions (c, y, x) of T2 with K = r1 and whose coefficient rows are the rows
+// of U1.  Its maps are combined with the image in a point-wise kernel.  Where
+// the tensor-core kernels cannot take it, the forward's x1 product runs on the
+// CUDA cores fused with the point-wise step.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "mpi_internal.h"
@@ -237,6 +243,33 @@ __global__ void __launch_bounds__(256) k_mode1_fwd(const float2* __restrict__ X,
   }
 }
 
+// The x1 product's operand for the tensor-core expansion kernels: t2
+// [C][r1][B] (complex) rewritten as K-major rows op[(c B + b)][k], k < r1 the
+// real part of t2[c][k][b], r1 <= k < 2 r1 the imaginary part, zero up to Kp.
+// A CTA transposes a 32-position block of one coil through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_x1_operand(const float2* __restrict__ t2, int r1, long B, int Kp,
+                                                    T* __restrict__ op) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  __shared__ float2 tile[128][33];  // [k][position], padded against bank conflicts
+  const int c = blockIdx.y;
+  const long b0 = (long)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32 threads
+  for (int k = ty; k < r1; k += 8)
+    tile[k][tx] = b0 + tx < B ? t2[((size_t)c * r1 + k) * B + b0 + tx] : make_float2(0.f, 0.f);
+  __syncthreads();
+  // each warp writes whole rows: position b0 + j, elements k = lane, lane + 32, ...
+  for (int j = ty; j < 32 && b0 + j < B; j += 8) {
+    T* row = op + ((size_t)c * B + b0 + j) * Kp;
+    for (int k = tx; k < Kp; k += 32) {
+      const float v = k < r1 ? tile[k][j].x : (k < 2 * r1 ? tile[k - r1][j].y : 0.f);
+      if constexpr (sizeof(T) == 2) row[k] = __float2bfloat16_rn(v);
+      else row[k] = v;
+    }
+  }
+}
+
 mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, long B, float2* Y) {
   if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
   const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);  // no idle lanes when B = 128
@@ -262,12 +295,20 @@ mpi_status mode_last(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, i
 
 }  // namespace
 
-size_t tucker_work_elems(const mpi_basis* b, int C) {
-  if (!b->tucker) return 0;
+namespace {
+int x1_kp(const mpi_basis* b) { return (2 * b->r[0] + 63) / 64 * 64; }
+size_t x1_op_offset(const mpi_basis* b, int C) {  // float2 elements before the x1 operand, 256-byte aligned
   const size_t R = (size_t)b->r[0] * b->r[1] * b->r[2];
   const size_t t1 = (size_t)b->r[0] * b->r[1] * b->n[2];
   const size_t t2 = (size_t)b->r[0] * b->n[1] * b->n[2];
-  return (size_t)C * (R + t1 + t2);
+  return ((size_t)C * (R + t1 + t2) + 31) / 32 * 32;
+}
+}  // namespace
+
+size_t tucker_work_elems(const mpi_basis* b, int C) {
+  if (!b->tucker) return 0;
+  // core and mode-product intermediates, then the x1 operand (FP32, Kp floats per position)
+  return x1_op_offset(b, C) + (size_t)C * b->n[1] * b->n[2] * (x1_kp(b) / 2) + 32;
 }
 
 namespace {
@@ -299,14 +340,100 @@ mpi_status tucker_t2(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int 
 
 }  // namespace
 
+namespace {
+
+// A basis view over the flattened x1 operand: N' = C B rows (coil-major), q = r1,
+// with the operand in the layout of the tensor-core kernels' own basis copies.
+void x1_view(const mpi_basis* b, int C, mpi_precision prec, void* op, void* map, mpi_basis* fb) {
+  fb->ctx = b->ctx;
+  fb->device = b->device;
+  fb->N = C * b->n[1] * b->n[2];
+  fb->q = b->r[0];
+  if (prec == MPI_PREC_BF16) {
+    fb->Ubf = (__nv_bfloat16*)op;
+    fb->Kp = x1_kp(b);
+    fb->tmap = map;
+  } else {
+    fb->Uf32 = (float*)op;
+    fb->Kp32 = x1_kp(b);
+    fb->tmap32 = map;
+  }
+}
+
+}  // namespace
+
+bool tucker_x1_on_tensor_cores(const mpi_basis* b, int C, mpi_precision prec) {
+  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return false;
+  const long rows = (long)C * b->n[1] * b->n[2];
+  if (rows > 0x7fffffffL - 128 || b->n[0] > 128) return false;  // one MMA holds 2 n1 <= 256 coefficient rows
+  if (prec == MPI_PREC_BF16) return true;
+  mpi_basis fb;  // shape-only view: the 3xTF32 kernel must take the n1 coefficient rows in coil groups
+  x1_view(b, C, prec, (void*)256, (void*)256, &fb);
+  const bool ok = tf32_group(&fb, EX_MAPS, b->n[0]) > 0;
+  fb.Uf32 = nullptr;
+  fb.tmap32 = nullptr;
+  return ok;
+}
+
 // maps[c] = s_c for all coils (C x N), through the core contraction and the
-// three mode products; `tmp` holds C * (R + r1 r2 n3 + r1 n2 n3) elements.
+// three mode products; `tmp` holds tucker_work_elems(b, C) elements.  The x1
+// product runs on the tensor-core expansion kernels where it can (per coil it
+// is a dense expansion with T2_c^T as the basis and the rows of U1 as the
+// coefficients), else on the CUDA cores.
 mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
                        mpi_precision prec) {
   float2* t2 = nullptr;
   mpi_status st = tucker_t2(ctx, b, alpha, C, tmp, prec, &t2);
   if (st) return st;
-  return mode_b(ctx, false, t2, b->F[0], C, b->r[0], b->n[0], (long)b->n[1] * b->n[2], maps);
+  const long B = (long)b->n[1] * b->n[2];
+  if (!tucker_x1_on_tensor_cores(b, C, prec))
+    return mode_b(ctx, false, t2, b->F[0], C, b->r[0], b->n[0], B, maps);
+  const int Kp = x1_kp(b);
+  void* op = (void*)(((uintptr_t)(tmp + x1_op_offset(b, C)) + 255) & ~(uintptr_t)255);  // TMA wants 16-byte alignment
+  const dim3 grid((unsigned)((B + 31) / 32), (unsigned)C);
+  MPI_PROF(ctx, KF_EXPAND);
+  if (prec == MPI_PREC_BF16)
+    launch_pdl(ctx, k_x1_operand<__nv_bfloat16>, grid, dim3(256), 0, (const float2*)t2, b->r[0], B, Kp,
+               (__nv_bfloat16*)op);
+  else
+    launch_pdl(ctx, k_x1_operand<float>, grid, dim3(256), 0, (const float2*)t2, b->r[0], B, Kp, (float*)op);
+  MPI_LAUNCH_CHECK(ctx, "k_x1_operand");
+  // the operand's tensor map, re-encoded only when the workspace, C or precision change
+  mpi_basis* mb = const_cast<mpi_basis*>(b);
+  if (!mb->op_map) mb->op_map = new CUtensorMap;
+  if (mb->op_map_ptr != op || mb->op_map_C != C || mb->op_map_prec != (int)prec) {
+    const bool ok = prec == MPI_PREC_BF16 ? tc_encode_operand_map(mb->op_map, op, (long)C * B, Kp)
+                                          : tf32_encode_operand_map(mb->op_map, op, (long)C * B, Kp);
+    if (!ok) {
+      mb->op_map_ptr = nullptr;
+      return set_err(ctx, MPI_ERR_UNSUPPORTED, "x1 operand tensor map");
+    }
+    mb->op_map_ptr = op;
+    mb->op_map_C = C;
+    mb->op_map_prec = (int)prec;
+  }
+  mpi_basis fb;
+  x1_view(b, C, prec, op, mb->op_map, &fb);
+  ExpandArgs a;
+  a.N = fb.N;
+  a.q = b->r[0];
+  a.C = b->n[0];
+  a.alpha = b->F[0];  // U1 [n1][r1]: row i is coefficient row i
+  a.out = maps;
+  a.tuck_B = (int)B;
+  a.tuck_stride = (long)b->n[0] * B;
+  // The tensor-core kernels start streaming their basis before waiting on the
+  // previous kernel; this basis is the operand just written, so launch them in
+  // plain stream order.
+  const bool pdl = ctx->pdl;
+  ctx->pdl = false;
+  st = expand(ctx, &fb, EX_MAPS, a, prec);
+  ctx->pdl = pdl;
+  fb.Ubf = nullptr;  // the view owns nothing
+  fb.Uf32 = nullptr;
+  fb.tmap = nullptr;
+  fb.tmap32 = nullptr;
+  return st;
 }
 
 bool tucker_fusable(int mode) { return mode == EX_FWD; }

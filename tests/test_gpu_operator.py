@@ -110,6 +110,23 @@ def test_cartesian_full_size_256_c16_q128(ctx, mp):
     _check_all(ctx, mp, cs)
 
 
+def test_cartesian_3d_volume_pipelined_line_passes(ctx, mp):
+    # a 32 x 64 x 128 volume with 20 coils: thousands of 32-line tiles per pass,
+    # which the library runs on persistent, software-pipelined CTAs
+    shape, C, q = (32, 64, 128), 20, 4
+    rng = np.random.default_rng(21)
+    N = int(np.prod(shape))
+    U = np.linalg.qr(rng.normal(size=(N, q)) + 1j * rng.normal(size=(N, q)))[0]
+    mask = w.poisson_disc_mask_3d(*shape, R=4, calib=(8, 8), seed=22)
+    cs = _case(ctx, mp, shape, C, q, mask, U=U, seed=23)
+    U, Fs, a, p, plan, B = cs["U"], cs["Fs"], cs["a"], cs["p"], cs["plan"], cs["B"]
+    ag, pg = c64(a), c64(p)
+    assert rel(f64(mp.forward(ctx, plan, B, ag, pg)), op.forward(Fs, U, a, p)) < TOL
+    r = w.random_coefficients(C, cs["M"], seed=24, decay=False).astype(np.complex64).astype(np.complex128)
+    assert rel(f64(mp.adjoint(ctx, plan, B, ag, c64(r))), op.adjoint(Fs, U, a, r)) < TOL
+    ctx.synchronize()
+
+
 def test_fully_sampled_and_empty(ctx, mp):
     full = np.ones((32, 32), dtype=bool)
     cs = _case(ctx, mp, (32, 32), 3, 8, full, seed=9)

@@ -96,7 +96,7 @@ size_t partial_elems(const mpi_ctx* ctx, const mpi_basis* basis, int C) {
 size_t op_work_bytes(const mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C) {
   const size_t cn = (size_t)C * plan->N;
   size_t grid = 0;
-  if (plan->kind == MPI_TRAJ_RADIAL) grid = (size_t)C * plan->G * plan->G;
+  if (plan->kind == MPI_TRAJ_RADIAL) grid = nufft_grid_elems(plan, C);
   size_t partial = partial_elems(ctx, basis, C);
   size_t tucker = (basis && basis->tucker) ? 2 * cn + tucker_work_elems(basis, C) : 0;
   return (2 * cn + grid + partial + tucker) * sizeof(float2) + 4096;
@@ -221,7 +221,7 @@ mpi_status carve_work(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis
   float2* base = (float2*)ctx->work;
   w->A = base;
   w->B = base + cn;
-  size_t grid = plan->kind == MPI_TRAJ_RADIAL ? (size_t)C * plan->G * plan->G : 0;
+  size_t grid = plan->kind == MPI_TRAJ_RADIAL ? nufft_grid_elems(plan, C) : 0;
   w->grid = base + 2 * cn;
   w->partials = base + 2 * cn + grid;
   w->partial_cap = partial_elems(ctx, basis, C);
@@ -498,7 +498,8 @@ extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
     solver_cache_forget(plan->ctx, plan);
     ctx_release(&plan->ctx);
   }
-  void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw, plan->deap};
+  void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw, plan->deap, plan->cell_ptr,
+                  plan->cell_rank, plan->cell_sx, plan->cell_w, plan->cell_dense};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete plan;

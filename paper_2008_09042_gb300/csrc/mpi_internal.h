@@ -67,6 +67,17 @@ struct mpi_plan {
   int32_t* gstart = nullptr;  // [M][2] first tap, array index in [0, G)
   float* gw = nullptr;        // [M][2][W] separable kernel weights
   float* deap = nullptr;      // [n] 1 / Phi(t), t = j - n/2
+  // Spreading index: the samples in order of their first-tap cell sy * G + sx
+  // (stable in m; cell_rank [M] gives each sample's position), CSR offsets per
+  // cell (cell_ptr [G * G + 1]), each sorted sample's sx (cell_sx [M]) and
+  // weights (cell_w [M][2][W]), and the cells whose W x W window holds many
+  // samples (cell_dense [n_dense], spread one warp per cell).
+  int32_t* cell_ptr = nullptr;
+  int32_t* cell_rank = nullptr;
+  int32_t* cell_sx = nullptr;
+  float* cell_w = nullptr;
+  int32_t* cell_dense = nullptr;
+  int n_dense = 0;
 };
 
 struct mpi_basis {
@@ -226,6 +237,9 @@ mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const flo
 // ------------------------------------------------------------- NUFFT (radial)
 
 mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host);
+// Radial workspace: the C oversampled grids, then the coil-grouped sorted copy
+// of the k-space samples that spreading reads.
+size_t nufft_grid_elems(const mpi_plan* plan, int C);
 mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* img_deap_src, int C,
                          float2* y, float2* grid);
 mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C,

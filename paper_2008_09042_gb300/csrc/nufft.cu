@@ -9,14 +9,17 @@
 //   3. interpolate at kappa = k G / (2 pi) with the separable kernel
 //      phi(u) = I0(beta sqrt(1 - (2u/W)^2)) / I0(beta) over the W grid points
 //      floor(kappa) - W/2 + 1 ... floor(kappa) + W/2 (periodic).
-// The adjoint runs the transposed steps: spread (float2 atomics), inverse FFTs,
-// crop with the sign and deapodisation.
+// The adjoint runs the transposed steps: spread, inverse FFTs, crop with the
+// sign and deapodisation.  Spreading is output-driven: each grid cell sums the
+// samples whose W x W footprint covers it, found through a per-plan CSR of the
+// samples by first-tap cell, so no cell is written twice and no atomics run.
 // beta = pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8) (Beatty et al. 2005);
 // Phi(t) = W sinh(z) / (z I0(beta)), z = sqrt(beta^2 - (pi W t / G)^2).
 // Grid positions, start taps and weights are computed once per plan in FP64.
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "mpi_internal.h"
 #include "ptx.cuh"
@@ -135,38 +138,150 @@ __global__ void k_nufft_interp(const float2* __restrict__ grid, int C, int G, in
   y[e] = make_float2(acc.x * ksign, acc.y * ksign);
 }
 
-template <int W>
-__global__ void k_nufft_spread(const float2* __restrict__ y, int C, int G, int M,
-                               const int32_t* __restrict__ gstart, const float* __restrict__ gw,
-                               float ksign, float2* __restrict__ grid) {
+constexpr int kSpreadCoils = 4;   // coils a spreading thread accumulates (one group of four)
+constexpr int kSpreadDense = 24;  // cells with more samples in their window go to the warp kernel
+
+int spread_coils_padded(int C) { return (C + 3) / 4 * 4; }
+
+// ys[cell_rank[m]][c] = ksign * y[c][m] for c < C, zero for C <= c < Cp (C
+// padded to a multiple of four): the samples in first-tap-cell order, the
+// coils of one sample contiguous.  Reads follow y's layout; writes scatter.
+__global__ void k_nufft_sort_y(const float2* __restrict__ y, int C, int Cp, int M,
+                               const int32_t* __restrict__ cell_rank, float ksign, float2* __restrict__ ys) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)C * M) return;
+  if (e >= (size_t)Cp * M) return;
   const int c = (int)(e / M), m = (int)(e % M);
-  const int sx = gstart[2 * m], sy = gstart[2 * m + 1];
-  float wx[W], wy[W];
-#pragma unroll
-  for (int a = 0; a < W; ++a) {
-    wx[a] = gw[(size_t)(2 * m) * W + a];
-    wy[a] = gw[(size_t)(2 * m + 1) * W + a];
+  float2 v = make_float2(0.f, 0.f);
+  if (c < C) {
+    const float2 t = y[e];
+    v = make_float2(t.x * ksign, t.y * ksign);
   }
-  const float2 yv = y[e];
-  const float2 v = make_float2(yv.x * ksign, yv.y * ksign);
-  float2* gc = grid + (size_t)c * G * G;
+  ys[(size_t)cell_rank[m] * Cp + c] = v;
+}
+
+// The samples that reach grid cell (gy, gx) from first-tap row sy = gy - a:
+// first taps (sy, gx - b), b = 0 .. W-1, one CSR range [r[0], r[1]) and, when
+// the window wraps past column 0 (G >= 2W: once at most), a second [r[2], r[3]).
+template <int W>
+__device__ __forceinline__ void spread_row_ranges(const int32_t* __restrict__ rp, int gx, int G, int r[4]) {
+  const int lo = gx - (W - 1);
+  r[1] = rp[gx + 1];
+  if (lo >= 0) {
+    r[0] = rp[lo];
+    r[2] = r[3] = 0;
+  } else {
+    r[0] = rp[0];
+    r[2] = rp[G + lo];
+    r[3] = rp[G];
+  }
+}
+
+// One sample's term: weight phi_x(b) phi_y(a) with b = gx - sx (mod G) read
+// from the sample's own first tap, times four coils of ys.
+template <int W>
+__device__ __forceinline__ void spread_term(const float* __restrict__ cell_w, const int32_t* __restrict__ cell_sx,
+                                            const float4* __restrict__ yc, int ystride, int k, int gx, int a,
+                                            int G, float acc[8]) {
+  int b = gx - cell_sx[k];
+  if (b < 0) b += G;
+  const float w = cell_w[k * 2 * W + b] * cell_w[k * 2 * W + W + a];
+  const float4 u = yc[k * ystride], v = yc[k * ystride + 1];
+  acc[0] = fmaf(w, u.x, acc[0]);
+  acc[1] = fmaf(w, u.y, acc[1]);
+  acc[2] = fmaf(w, u.z, acc[2]);
+  acc[3] = fmaf(w, u.w, acc[3]);
+  acc[4] = fmaf(w, v.x, acc[4]);
+  acc[5] = fmaf(w, v.y, acc[5]);
+  acc[6] = fmaf(w, v.z, acc[6]);
+  acc[7] = fmaf(w, v.w, acc[7]);
+}
+
+__device__ __forceinline__ void spread_store(float2* __restrict__ grid, int C, int G, int c0, int gy, int gx,
+                                             const float acc[8]) {
+  const float s = ((gx + gy) & 1) ? -1.f : 1.f;  // the k-side sign (-1)^(gx + gy)
+#pragma unroll
+  for (int j = 0; j < kSpreadCoils; ++j)
+    if (c0 + j < C) grid[((size_t)(c0 + j) * G + gy) * G + gx] = make_float2(s * acc[2 * j], s * acc[2 * j + 1]);
+}
+
+// Output-driven spreading, sparse cells: thread (gy, gx, coil group) sums the
+// samples whose W x W footprint covers its cell, i.e. whose first tap is
+// (gy - a, gx - b) (mod G) for 0 <= a, b < W, and stores the cell once; no
+// atomics.  A cell whose window holds more than kSpreadDense samples is left
+// to k_nufft_spread_dense (its thread would hold the CTA up).
+template <int W>
+__global__ void __launch_bounds__(256, 4) k_nufft_spread(const float4* __restrict__ ys, int C, int Cp, int G,
+                                                         const int32_t* __restrict__ cell_ptr,
+                                                         const int32_t* __restrict__ cell_sx,
+                                                         const float* __restrict__ cell_w,
+                                                         float2* __restrict__ grid) {
+  mpi_ptx::pdl_trigger();
+  const int gx = blockIdx.x * 32 + threadIdx.x, gy = blockIdx.y * 8 + threadIdx.y;
+  const int c0 = blockIdx.z * kSpreadCoils;
+  mpi_ptx::pdl_wait();
+  if (gx >= G || gy >= G) return;
+  int n = 0;
 #pragma unroll
   for (int a = 0; a < W; ++a) {
-    int gy = sy + a;
-    if (gy >= G) gy -= G;
-    const float2 va = make_float2(v.x * wy[a], v.y * wy[a]);
-#pragma unroll
-    for (int b = 0; b < W; ++b) {
-      int gx = sx + b;
-      if (gx >= G) gx -= G;
-      const float w = ((gx + gy) & 1) ? -wx[b] : wx[b];
-      atomicAdd(gc + (size_t)gy * G + gx, make_float2(va.x * w, va.y * w));
+    int sy = gy - a;
+    if (sy < 0) sy += G;
+    int r[4];
+    spread_row_ranges<W>(cell_ptr + sy * G, gx, G, r);
+    n += r[1] - r[0] + r[3] - r[2];
+  }
+  if (n > kSpreadDense) return;
+  const int ystride = Cp / 2;
+  const float4* yc = ys + c0 / 2;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (n > 0) {
+    for (int a = 0; a < W; ++a) {  // the ranges again (L1 hits), rather than W x 4 live registers
+      int sy = gy - a;
+      if (sy < 0) sy += G;
+      int r[4];
+      spread_row_ranges<W>(cell_ptr + sy * G, gx, G, r);
+      for (int k = r[0]; k < r[1]; ++k) spread_term<W>(cell_w, cell_sx, yc, ystride, k, gx, a, G, acc);
+      for (int k = r[2]; k < r[3]; ++k) spread_term<W>(cell_w, cell_sx, yc, ystride, k, gx, a, G, acc);
     }
   }
+  spread_store(grid, C, G, c0, gy, gx, acc);
+}
+
+// Output-driven spreading, dense cells (the plan's list of cells whose window
+// holds more than kSpreadDense samples): warp (cell, coil group), the lanes
+// taking every 32nd sample of each row range, then a butterfly sum.
+template <int W>
+__global__ void __launch_bounds__(256) k_nufft_spread_dense(const float4* __restrict__ ys, int C, int Cp, int G,
+                                                            const int32_t* __restrict__ cell_ptr,
+                                                            const int32_t* __restrict__ cell_sx,
+                                                            const float* __restrict__ cell_w,
+                                                            const int32_t* __restrict__ dense, int n_dense,
+                                                            float2* __restrict__ grid) {
+  mpi_ptx::pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int c0 = blockIdx.y * kSpreadCoils;
+  mpi_ptx::pdl_wait();
+  if (i >= n_dense) return;
+  const int cell = dense[i], gy = cell / G, gx = cell % G;
+  const int ystride = Cp / 2;
+  const float4* yc = ys + c0 / 2;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    int sy = gy - a;
+    if (sy < 0) sy += G;
+    int r[4];
+    spread_row_ranges<W>(cell_ptr + sy * G, gx, G, r);
+    for (int k = r[0] + lane; k < r[1]; k += 32) spread_term<W>(cell_w, cell_sx, yc, ystride, k, gx, a, G, acc);
+    for (int k = r[2] + lane; k < r[3]; k += 32) spread_term<W>(cell_w, cell_sx, yc, ystride, k, gx, a, G, acc);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+  if (lane == 0) spread_store(grid, C, G, c0, gy, gx, acc);
 }
 
 __global__ void k_nufft_crop(const float2* __restrict__ grid, int C, int n, int G, const float* __restrict__ deap,
@@ -195,6 +310,10 @@ unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse);
 
+size_t nufft_grid_elems(const mpi_plan* plan, int C) {
+  return (size_t)C * plan->G * plan->G + (size_t)spread_coils_padded(C) * plan->M;
+}
+
 mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host) {
   const int M = plan->M, W = plan->W, G = plan->G, n = plan->nx;
   const double sigma = (double)G / n;
@@ -217,7 +336,61 @@ mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host)
   MPI_PROF(ctx, KF_NUFFT);
   k_nufft_deap<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(n, G, W, beta, plan->deap);
   MPI_LAUNCH_CHECK(ctx, "k_nufft_deap");
-  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "nufft plan setup");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "nufft plan setup");
+  // Spreading CSR, built from the device's own first taps and weights (so it
+  // agrees with the interpolation bit for bit): a counting sort of the samples
+  // by first-tap cell sy * G + sx, stable in the sample index.
+  if (M > 0) {
+    std::vector<int32_t> gs((size_t)2 * M);
+    std::vector<float> w((size_t)2 * M * W);
+    e = cudaMemcpy(gs.data(), plan->gstart, gs.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(w.data(), plan->gw, w.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "nufft spreading index");
+    const size_t GG = (size_t)G * G;
+    std::vector<int32_t> ptr(GG + 1, 0), samp(M), rank(M), sx(M), dense;
+    std::vector<float> cw((size_t)2 * M * W);
+    for (int m = 0; m < M; ++m) ++ptr[(size_t)gs[2 * m + 1] * G + gs[2 * m] + 1];
+    for (size_t t = 0; t < GG; ++t) ptr[t + 1] += ptr[t];
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int m = 0; m < M; ++m) {
+      const int k = fill[(size_t)gs[2 * m + 1] * G + gs[2 * m]]++;
+      samp[k] = m;
+      rank[m] = k;
+      sx[k] = gs[2 * m];
+      std::copy(w.begin() + (size_t)2 * m * W, w.begin() + (size_t)(2 * m + 2) * W, cw.begin() + (size_t)2 * k * W);
+    }
+    // Cells whose W x W window of first taps holds more than kSpreadDense
+    // samples (a radial trajectory's centre), counted the way the kernels do.
+    for (int gy = 0; gy < G; ++gy)
+      for (int gx = 0; gx < G; ++gx) {
+        long cnt = 0;
+        for (int a = 0; a < W; ++a) {
+          const int sy = (gy - a + G) % G;
+          for (int b = 0; b < W; ++b) {
+            const size_t t = (size_t)sy * G + (gx - b + G) % G;
+            cnt += ptr[t + 1] - ptr[t];
+          }
+        }
+        if (cnt > kSpreadDense) dense.push_back(gy * G + gx);
+      }
+    plan->n_dense = (int)dense.size();
+    e = cudaMalloc(&plan->cell_ptr, ptr.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&plan->cell_rank, (size_t)M * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&plan->cell_sx, (size_t)M * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&plan->cell_w, cw.size() * sizeof(float));
+    if (e == cudaSuccess && !dense.empty()) e = cudaMalloc(&plan->cell_dense, dense.size() * sizeof(int32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(plan->cell_ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(plan->cell_rank, rank.data(), (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(plan->cell_sx, sx.data(), (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(plan->cell_w, cw.data(), cw.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !dense.empty())
+      e = cudaMemcpy(plan->cell_dense, dense.data(), dense.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "nufft spreading index");
+  }
+  return MPI_OK;
 }
 
 mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, int C, float2* y, float2* grid) {
@@ -252,17 +425,33 @@ mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, in
 mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C, float2* out, float2* grid) {
   const int n = plan->nx, G = plan->G, M = plan->M;
   const size_t total = (size_t)C * G * G;
-  cudaError_t e = cudaMemsetAsync(grid, 0, total * sizeof(float2), ctx->stream);
-  if (e != cudaSuccess) return cuda_check(ctx, e, "grid clear");
-  if (M > 0) {
+  if (M == 0) {
+    cudaError_t e = cudaMemsetAsync(grid, 0, total * sizeof(float2), ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "grid clear");
+  } else {
     const float ks = axis_sign(G) * axis_sign(G);
-    const size_t cm = (size_t)C * M;
+    const int Cp = spread_coils_padded(C);
+    float2* ys = grid + total;  // nufft_grid_elems reserves the sorted copy after the grid
     MPI_PROF(ctx, KF_NUFFT);
-  switch (plan->W) {
-#define MPI_W_CASE(w)                                                                                \
-  case w:                                                                                            \
-    launch_pdl(ctx, k_nufft_spread<w>, dim3(blocks_for(cm, 256)), dim3(256), 0, y, C, G, M,             \
-               plan->gstart, plan->gw, ks, grid);                                                  \
+    launch_pdl(ctx, k_nufft_sort_y, dim3(blocks_for((size_t)M * Cp, 256)), dim3(256), 0, y, C, Cp, M,
+               plan->cell_rank, ks, ys);
+    MPI_LAUNCH_CHECK(ctx, "k_nufft_sort_y");
+    const unsigned groups = (unsigned)(Cp / kSpreadCoils);
+    const dim3 sgrid((unsigned)((G + 31) / 32), (unsigned)((G + 7) / 8), groups);
+    const dim3 dgrid((unsigned)((plan->n_dense + 7) / 8), groups);
+    const float4* ys4 = (const float4*)ys;
+    switch (plan->W) {
+#define MPI_W_CASE(w)                                                                                      \
+  case w:                                                                                                  \
+    MPI_PROF(ctx, KF_NUFFT);                                                                               \
+    launch_pdl(ctx, k_nufft_spread<w>, sgrid, dim3(32, 8), 0, ys4, C, Cp, G, plan->cell_ptr, plan->cell_sx,  \
+               plan->cell_w, grid);                                                                        \
+    if (plan->n_dense > 0) {                                                                               \
+      MPI_LAUNCH_CHECK(ctx, "k_nufft_spread");                                                             \
+      MPI_PROF(ctx, KF_NUFFT);                                                                             \
+      launch_pdl(ctx, k_nufft_spread_dense<w>, dgrid, dim3(256), 0, ys4, C, Cp, G, plan->cell_ptr,          \
+                 plan->cell_sx, plan->cell_w, plan->cell_dense, plan->n_dense, grid);                      \
+    }                                                                                                      \
     break;
       MPI_W_CASE(2) MPI_W_CASE(3) MPI_W_CASE(4) MPI_W_CASE(5) MPI_W_CASE(6) MPI_W_CASE(7) MPI_W_CASE(8)
 #undef MPI_W_CASE

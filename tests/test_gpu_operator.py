@@ -253,6 +253,31 @@ def test_radial_operator_matches_fp64_gridding(ctx, mp, n, C, q, spokes, readout
     assert rel(f64(gp), rp) < TOL and rel(f64(ga), ra) < TOL
 
 
+@pytest.mark.parametrize("W,C,sigma", [(2, 5, 2.0), (3, 1, 2.0), (4, 4, 1.5), (7, 9, 2.0), (8, 2, 1.5), (6, 19, 2.0)])
+def test_radial_kernel_widths_and_wrapped_windows(ctx, mp, W, C, sigma):
+    # Every kernel width the plan accepts; coil counts that leave a ragged group
+    # of four and one beyond sixteen (two coil chunks) in the spreading; a
+    # 48-point grid (not a multiple of the 32-cell strips); and samples on the
+    # k-space edge whose W x W footprints wrap around the grid's first row and
+    # column.
+    n, q = 32, 4
+    rng = np.random.default_rng(50 + W)
+    k = np.concatenate([
+        w.golden_angle_radial(8, 64),
+        rng.uniform(-np.pi, np.pi, size=(200, 2)),
+        np.array([[-np.pi, -np.pi], [-np.pi, 0.0], [0.0, -np.pi], [np.pi * 0.999, -np.pi * 0.999]]),
+    ]).astype(np.float32)
+    U = w.smooth_orthonormal_basis(n, n, q, seed=W).astype(np.complex64).astype(np.complex128)
+    a = w.random_coefficients(C, q, seed=W + 1).astype(np.complex64).astype(np.complex128)
+    p = w.random_image(n * n, seed=W + 2).astype(np.complex64).astype(np.complex128)
+    r = w.random_coefficients(C, k.shape[0], seed=W + 3, decay=False).astype(np.complex64).astype(np.complex128)
+    plan = mp.Plan(ctx, (n, n), traj=k, kb_width=W, oversamp=sigma)
+    B = mp.Basis(ctx, U.T)
+    kb = nufft.KBGriddingNUFFT((n, n), k.astype(np.float64), W=W, sigma=sigma)
+    assert rel(f64(mp.forward(ctx, plan, B, c64(a), c64(p))), op.forward(kb, U, a, p)) < TOL
+    assert rel(f64(mp.adjoint(ctx, plan, B, c64(a), c64(r))), op.adjoint(kb, U, a, r)) < TOL
+
+
 def test_radial_close_to_direct_nudft(ctx, mp):
     cs = _radial_case(ctx, mp, 64, 2, 8, 24, 128)
     ex = fourier.DirectNUDFT((64, 64), cs["k"].astype(np.float64))

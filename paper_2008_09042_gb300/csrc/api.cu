@@ -499,7 +499,8 @@ extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
     ctx_release(&plan->ctx);
   }
   void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw, plan->deap, plan->cell_ptr,
-                  plan->cell_rank, plan->cell_sx, plan->cell_w, plan->cell_dense};
+                  plan->cell_rank, plan->cell_sx, plan->cell_w, plan->cell_dense,
+                  plan->tile_items, plan->tile_samples};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete plan;

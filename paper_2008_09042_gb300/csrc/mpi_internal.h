@@ -78,6 +78,12 @@ struct mpi_plan {
   float* cell_w = nullptr;
   int32_t* cell_dense = nullptr;
   int n_dense = 0;
+  // Interpolation work list: the samples sorted by the 32 x 32 tile of their
+  // first tap (tile_samples [M]); items [n_tile_items][3] = (tile, first
+  // sorted sample, count), dense tiles split into chunks.
+  int32_t* tile_items = nullptr;
+  int32_t* tile_samples = nullptr;
+  int n_tile_items = 0;
 };
 
 struct mpi_basis {

@@ -8,7 +8,8 @@
 //      so the two signs make the centred DFT of the grid);
 //   3. interpolate at kappa = k G / (2 pi) with the separable kernel
 //      phi(u) = I0(beta sqrt(1 - (2u/W)^2)) / I0(beta) over the W grid points
-//      floor(kappa) - W/2 + 1 ... floor(kappa) + W/2 (periodic).
+//      floor(kappa) - W/2 + 1 ... floor(kappa) + W/2 (periodic), reading the
+//      grid through shared-memory tiles (samples binned by first-tap tile).
 // The adjoint runs the transposed steps: spread, inverse FFTs, crop with the
 // sign and deapodisation.  Spreading is output-driven: each grid cell sums the
 // samples whose W x W footprint covers it, found through a per-plan CSR of the
@@ -100,15 +101,32 @@ __global__ void k_nufft_pad(const float2* __restrict__ v, int C, int n, int G, c
   grid[e] = out;
 }
 
+constexpr int kInterpTile = 32;    // first-tap tile of the shared-memory interpolation
+constexpr int kInterpChunk = 256;  // samples per interpolation work item (one per thread)
+
+// Interpolation through shared memory: CTA (item, coil) takes a chunk of at
+// most kInterpChunk of the samples whose first tap lies in one 32 x 32 tile
+// (the plan's tile-sorted list).  Each thread loads its sample's first tap
+// and weights (before waiting on the kernel that writes the grid), the CTA
+// copies the grid cells the chunk reads, (32 + W - 1)^2 from the tile's corner
+// (periodic), into shared memory with coalesced loads, and each thread forms
+// its sample's W x W sum there.
 template <int W>
-__global__ void k_nufft_interp(const float2* __restrict__ grid, int C, int G, int M,
-                               const int32_t* __restrict__ gstart, const float* __restrict__ gw,
-                               float ksign, float2* __restrict__ y) {
+__global__ void __launch_bounds__(kInterpChunk) k_nufft_interp_tiled(const float2* __restrict__ grid, int C, int G,
+                                                                     int M, const int32_t* __restrict__ gstart,
+                                                                     const float* __restrict__ gw, float ksign,
+                                                                     const int32_t* __restrict__ items,
+                                                                     const int32_t* __restrict__ samples,
+                                                                     float2* __restrict__ y) {
   mpi_ptx::pdl_trigger();
-  mpi_ptx::pdl_wait();
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)C * M) return;
-  const int c = (int)(e / M), m = (int)(e % M);
+  constexpr int TT = kInterpTile + W - 1;
+  __shared__ float2 tile[TT * TT];
+  const int it = blockIdx.x, c = blockIdx.y;
+  const int t = items[3 * it], s0 = items[3 * it + 1], cnt = items[3 * it + 2];
+  const int tpr = (G + kInterpTile - 1) / kInterpTile;
+  const int oy = (t / tpr) * kInterpTile, ox = (t % tpr) * kInterpTile;
+  const bool active = (int)threadIdx.x < cnt;
+  const int m = samples[s0 + (active ? (int)threadIdx.x : 0)];
   const int sx = gstart[2 * m], sy = gstart[2 * m + 1];
   float wx[W], wy[W];
 #pragma unroll
@@ -116,26 +134,31 @@ __global__ void k_nufft_interp(const float2* __restrict__ grid, int C, int G, in
     wx[a] = gw[(size_t)(2 * m) * W + a];
     wy[a] = gw[(size_t)(2 * m + 1) * W + a];
   }
+  mpi_ptx::pdl_wait();
   const float2* gc = grid + (size_t)c * G * G;
+  for (int e = threadIdx.x; e < TT * TT; e += blockDim.x) {
+    const int r = e / TT, q = e % TT;
+    tile[e] = gc[(size_t)((oy + r) % G) * G + (ox + q) % G];
+  }
+  __syncthreads();
+  if (!active) return;
+  const float2* tp = tile + (sy - oy) * TT + (sx - ox);
+  const bool odd = (sx + sy) & 1;  // (-1)^(gx + gy); G is even, so wrapping keeps the parity
   float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
   for (int a = 0; a < W; ++a) {
-    int gy = sy + a;
-    if (gy >= G) gy -= G;
     float2 racc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int b = 0; b < W; ++b) {
-      int gx = sx + b;
-      if (gx >= G) gx -= G;
-      const float2 g = gc[(size_t)gy * G + gx];
-      const float w = ((gx + gy) & 1) ? -wx[b] : wx[b];
+      const float2 g = tp[a * TT + b];
+      const float w = (((a + b) & 1) != odd) ? -wx[b] : wx[b];
       racc.x = fmaf(w, g.x, racc.x);
       racc.y = fmaf(w, g.y, racc.y);
     }
     acc.x = fmaf(wy[a], racc.x, acc.x);
     acc.y = fmaf(wy[a], racc.y, acc.y);
   }
-  y[e] = make_float2(acc.x * ksign, acc.y * ksign);
+  y[(size_t)c * M + m] = make_float2(acc.x * ksign, acc.y * ksign);
 }
 
 constexpr int kSpreadCoils = 4;   // coils a spreading thread accumulates (one group of four)
@@ -388,6 +411,28 @@ mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host)
     if (e == cudaSuccess) e = cudaMemcpy(plan->cell_w, cw.data(), cw.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !dense.empty())
       e = cudaMemcpy(plan->cell_dense, dense.data(), dense.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    // Interpolation work list: a counting sort of the samples by the 32 x 32
+    // tile of their first tap, then one item per chunk of a tile's samples.
+    const int tpr = (G + kInterpTile - 1) / kInterpTile, n_tiles = tpr * tpr;
+    std::vector<int32_t> tcount(n_tiles + 1, 0), tsorted(M), items;
+    for (int m = 0; m < M; ++m)
+      ++tcount[(gs[2 * m + 1] / kInterpTile) * tpr + gs[2 * m] / kInterpTile + 1];
+    for (int t = 0; t < n_tiles; ++t) tcount[t + 1] += tcount[t];
+    std::vector<int32_t> tfill(tcount.begin(), tcount.end() - 1);
+    for (int m = 0; m < M; ++m) tsorted[tfill[(gs[2 * m + 1] / kInterpTile) * tpr + gs[2 * m] / kInterpTile]++] = m;
+    for (int t = 0; t < n_tiles; ++t)
+      for (int s0 = tcount[t]; s0 < tcount[t + 1]; s0 += kInterpChunk) {
+        items.push_back(t);
+        items.push_back(s0);
+        items.push_back(std::min(kInterpChunk, tcount[t + 1] - s0));
+      }
+    plan->n_tile_items = (int)(items.size() / 3);
+    if (e == cudaSuccess) e = cudaMalloc(&plan->tile_items, items.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&plan->tile_samples, (size_t)M * sizeof(int32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(plan->tile_items, items.data(), items.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(plan->tile_samples, tsorted.data(), (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_check(ctx, e, "nufft spreading index");
   }
   return MPI_OK;
@@ -405,13 +450,13 @@ mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, in
   if (st) return st;
   if (M == 0) return MPI_OK;
   const float ks = axis_sign(G) * axis_sign(G);
-  const size_t cm = (size_t)C * M;
+  const dim3 igrid((unsigned)plan->n_tile_items, (unsigned)C);
   MPI_PROF(ctx, KF_NUFFT);
   switch (plan->W) {
 #define MPI_W_CASE(w)                                                                                \
   case w:                                                                                            \
-    launch_pdl(ctx, k_nufft_interp<w>, dim3(blocks_for(cm, 256)), dim3(256), 0, grid, C, G, M,          \
-               plan->gstart, plan->gw, ks, y);                                                     \
+    launch_pdl(ctx, k_nufft_interp_tiled<w>, igrid, dim3(kInterpChunk), 0,                                         \
+               grid, C, G, M, plan->gstart, plan->gw, ks, plan->tile_items, plan->tile_samples, y);         \
     break;
     MPI_W_CASE(2) MPI_W_CASE(3) MPI_W_CASE(4) MPI_W_CASE(5) MPI_W_CASE(6) MPI_W_CASE(7) MPI_W_CASE(8)
 #undef MPI_W_CASE

@@ -310,7 +310,7 @@ __host__ __device__ constexpr int col_stride(int L, int TILE) {
 }
 
 template <int L, bool INV, int TILE>
-__global__ void __launch_bounds__(kLineWarps * 32, 3) k_fft_lines(float2* __restrict__ data, int nx,
+__global__ void __launch_bounds__(kLineWarps * 32, (L * TILE <= 2048) ? 4 : (L * TILE >= 4096 ? 2 : 3)) k_fft_lines(float2* __restrict__ data, int nx,
                                                               long stride, int n_slabs, int inner,
                                                               long outer_stride, long inner_stride,
                                                               const float2* __restrict__ tw_g) {

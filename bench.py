@@ -472,23 +472,17 @@ def run_ours(args):
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
 
-    # ---- end to end: pinned host buffers, copies inside the timed region
+    # ---- end to end through the C ABI's host-buffer calls (mpi_forward_host,
+    # mpi_adjoint_host): pinned host inputs in, host outputs back, each call
+    # returning once its result is in host memory.  Host wall clock per step.
     a_h = torch.from_numpy(alpha.astype(np.complex64)).pin_memory()
     p_h = torch.from_numpy(p.astype(np.complex64)).pin_memory()
     y_h = torch.empty((C, M), dtype=torch.complex64).pin_memory()
     x_h = torch.empty((N,), dtype=torch.complex64).pin_memory()
-    a_e = torch.empty_like(a_d)
-    p_e = torch.empty_like(p_d)
-    y_e = torch.empty_like(y_d)
 
     def e2e_step():
-        a_e.copy_(a_h, non_blocking=True)
-        p_e.copy_(p_h, non_blocking=True)
-        mp.forward(ctx, plan, basis, a_e, p_e, args.prec, out=y_d)
-        y_h.copy_(y_d, non_blocking=True)
-        y_e.copy_(y_h, non_blocking=True)
-        mp.adjoint(ctx, plan, basis, a_e, y_e, args.prec, out=x_d)
-        x_h.copy_(x_d, non_blocking=True)
+        mp.forward_host(ctx, plan, basis, a_h, p_h, args.prec, out=y_h)
+        mp.adjoint_host(ctx, plan, basis, a_h, y_h, args.prec, out=x_h)
 
     for _ in range(args.warmup):
         e2e_step()
@@ -496,15 +490,13 @@ def run_ours(args):
     e2e_ms = 0.0
     for _ in range(args.steps):
         flush.zero_()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         e2e_step()
-        e.record(stream)
-        e.synchronize()
-        e2e_ms += s.elapsed_time(e)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms = reduce_max(e2e_ms, dev)
     e2e_value = replica_throughput(world, args.steps, e2e_ms)
-    h2d = (C * q + N + C * M) * 8
+    h2d = (2 * C * q + N + C * M) * 8  # alpha for each call, p, y
     d2h = (C * M + N) * 8
 
     # ---- roofline of the dominant kernel (the basis expansion, forward and adjoint launches)

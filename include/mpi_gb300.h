@@ -176,6 +176,24 @@ mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basi
                        const mpi_c32* alpha, int C, const mpi_c32* y, mpi_c32* p_out,
                        mpi_precision prec);
 
+/* mpi_forward and mpi_adjoint on HOST buffers (the same operators, Eq. 5 and the
+ * adjoint of Eq. 1 in p, and the same layouts:
+ * alpha [C][q]; forward p [N] -> y [C][M]; adjoint y [C][M] -> p_out [N]).  The
+ * kernels read and write pinned (page-locked, mapped) host buffers in place,
+ * over the coherent CPU-GPU link; pageable buffers are copied through a device
+ * staging buffer that the context owns (grown on demand, freed with the
+ * context).  The call runs the operator on the context's stream and
+ * synchronises the stream before it returns, so the output is ready in host
+ * memory.  Errors: as mpi_forward / mpi_adjoint;
+ * MPI_ERR_OOM if the staging buffer cannot be allocated; MPI_ERR_CUDA if a copy
+ * fails.  Not for use inside stream capture (it synchronises). */
+mpi_status mpi_forward_host(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                            const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y,
+                            mpi_precision prec);
+mpi_status mpi_adjoint_host(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                            const mpi_c32* alpha, int C, const mpi_c32* y, mpi_c32* p_out,
+                            mpi_precision prec);
+
 /* dy = J(p, alpha)[dp; dalpha] = [F_s(U alpha_k (.) dp + p (.) U dalpha_k)]_k (Eq. 7). */
 mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
                         const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* dp,

@@ -19,6 +19,8 @@ from .api import (  # noqa: F401
     basis_project,
     expand_path,
     forward,
+    forward_host,
+    adjoint_host,
     jacobian,
     jacobian_adjoint,
     image_solve,

@@ -221,6 +221,42 @@ def adjoint(ctx, plan, basis, alpha, y, prec="fp32", out=None):
     return out
 
 
+def _need_host(t, shape, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.complex64 or t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous complex64 CPU tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def forward_host(ctx, plan, basis, alpha, p, prec="fp32", out=None):
+    """forward() on host tensors: the library copies the inputs in and y out
+    (mpi_forward_host); returns when y is ready in host memory."""
+    C = alpha.shape[0]
+    _need_host(alpha, (C, basis.q), "alpha")
+    _need_host(p, (plan.N,), "p")
+    out = out if out is not None else torch.empty((C, plan.M), dtype=torch.complex64)
+    _need_host(out, (C, plan.M), "out")
+    check(ctx.h, ctx.lib.mpi_forward_host(ctx.h, plan.h, basis.h, _ptr(alpha), C, _ptr(p), _ptr(out),
+                                          PREC[prec]))
+    return out
+
+
+def adjoint_host(ctx, plan, basis, alpha, y, prec="fp32", out=None):
+    """adjoint() on host tensors (mpi_adjoint_host); returns when the image is
+    ready in host memory."""
+    C = alpha.shape[0]
+    _need_host(alpha, (C, basis.q), "alpha")
+    _need_host(y, (C, plan.M), "y")
+    out = out if out is not None else torch.empty((plan.N,), dtype=torch.complex64)
+    _need_host(out, (plan.N,), "out")
+    check(ctx.h, ctx.lib.mpi_adjoint_host(ctx.h, plan.h, basis.h, _ptr(alpha), C, _ptr(y), _ptr(out),
+                                          PREC[prec]))
+    return out
+
+
 def jacobian(ctx, plan, basis, alpha, p, dp, dalpha, prec="fp32", out=None):
     C = alpha.shape[0]
     for t, s, n in ((alpha, (C, basis.q), "alpha"), (dalpha, (C, basis.q), "dalpha"),

@@ -301,6 +301,7 @@ extern "C" mpi_status mpi_ctx_destroy(mpi_ctx* ctx) {
   solver_cache_clear(ctx);
   for (mpi_ctx** slot : ctx->children) *slot = nullptr;  // orphan the children still alive
   if (ctx->work) cudaFree(ctx->work);
+  if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->twiddles) cudaFree(ctx->twiddles);
   delete ctx;
   return MPI_OK;
@@ -694,6 +695,102 @@ extern "C" mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   a.w = w.A;
   a.out = (float2*)p_out;
   return run_expand(ctx, basis, EX_ADJ, a, prec, w);
+}
+
+namespace {
+
+// Device staging for the host-buffer calls: grown like the workspace, with a
+// stream sync before the old buffer is freed.
+mpi_status ensure_stage(mpi_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->stage_bytes) return MPI_OK;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "staging sync");
+  if (ctx->stage) cudaFree(ctx->stage);
+  ctx->stage = nullptr;
+  ctx->stage_bytes = 0;
+  e = cudaMalloc(&ctx->stage, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, MPI_ERR_OOM, "staging allocation failed");
+  }
+  ctx->stage_bytes = bytes;
+  return MPI_OK;
+}
+
+// Device address of a host buffer the GPU can access in place (pinned and
+// mapped, e.g. from cudaHostAlloc), or null for pageable memory.  On GB300 the
+// kernels then read and write it directly over the coherent CPU-GPU link.
+const void* mapped_host(const void* h) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// One host-buffer operator call.  Pinned buffers are used in place; pageable
+// ones go through the staging buffer: alpha [C][q] and the input (n_in
+// elements) copied in, the output (n_out elements) copied back.  `op` runs on
+// the device addresses; the call waits for the stream before returning.
+template <class Op>
+mpi_status host_call(mpi_ctx* ctx, const mpi_basis* basis, int C, const mpi_c32* alpha, const mpi_c32* in,
+                     size_t n_in, mpi_c32* out, size_t n_out, Op op) {
+  const size_t n_alpha = (size_t)C * basis->q;
+  const mpi_c32* da = (const mpi_c32*)mapped_host(alpha);
+  const mpi_c32* di = n_in ? (const mpi_c32*)mapped_host(in) : in;
+  mpi_c32* dout = n_out ? (mpi_c32*)mapped_host(out) : out;
+  const size_t a_off = 0, i_off = (n_alpha + 1) & ~(size_t)1, o_off = i_off + ((n_in + 1) & ~(size_t)1);
+  if (!da || !di || !dout) {
+    mpi_status st = ensure_stage(ctx, (o_off + n_out) * sizeof(mpi_c32));
+    if (st) return st;
+  }
+  mpi_c32* d = (mpi_c32*)ctx->stage;
+  cudaError_t e = cudaSuccess;
+  if (!da) {
+    e = cudaMemcpyAsync(d + a_off, alpha, n_alpha * sizeof(mpi_c32), cudaMemcpyHostToDevice, ctx->stream);
+    da = d + a_off;
+  }
+  if (e == cudaSuccess && !di) {
+    e = cudaMemcpyAsync(d + i_off, in, n_in * sizeof(mpi_c32), cudaMemcpyHostToDevice, ctx->stream);
+    di = d + i_off;
+  }
+  if (e != cudaSuccess) return cuda_check(ctx, e, "host input copy");
+  const bool copy_out = !dout;
+  if (copy_out) dout = d + o_off;
+  mpi_status st = op(da, di, dout);
+  if (st) return st;
+  if (copy_out) e = cudaMemcpyAsync(out, dout, n_out * sizeof(mpi_c32), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return e == cudaSuccess ? MPI_OK : cuda_check(ctx, e, "host output copy");
+}
+
+}  // namespace
+
+extern "C" mpi_status mpi_forward_host(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                       const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y,
+                                       mpi_precision prec) {
+  mpi_status st = check_op(ctx, plan, basis, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p) || (plan->M > 0 && bad_ptr(y))) return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  DeviceGuard g(ctx->device);
+  return host_call(ctx, basis, C, alpha, p, (size_t)plan->N, y, (size_t)C * plan->M,
+                   [&](const mpi_c32* da, const mpi_c32* dp, mpi_c32* dy) {
+                     return mpi_forward(ctx, plan, basis, da, C, dp, dy, prec);
+                   });
+}
+
+extern "C" mpi_status mpi_adjoint_host(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                       const mpi_c32* alpha, int C, const mpi_c32* y, mpi_c32* p_out,
+                                       mpi_precision prec) {
+  mpi_status st = check_op(ctx, plan, basis, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p_out) || (plan->M > 0 && bad_ptr(y))) return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  DeviceGuard g(ctx->device);
+  return host_call(ctx, basis, C, alpha, y, (size_t)C * plan->M, p_out, (size_t)plan->N,
+                   [&](const mpi_c32* da, const mpi_c32* dy, mpi_c32* dp) {
+                     return mpi_adjoint(ctx, plan, basis, da, C, dy, dp, prec);
+                   });
 }
 
 extern "C" mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,

@@ -25,6 +25,8 @@ struct mpi_ctx {
   cudaStream_t stream = nullptr;
   void* work = nullptr;  // scratch between kernel passes
   size_t work_bytes = 0;
+  void* stage = nullptr;  // device copies of host-buffer calls' inputs and outputs
+  size_t stage_bytes = 0;
   float2* twiddles = nullptr;  // all tables back to back
   int tw_offset[kNumFftLengths] = {0};
   int num_sms = 0;

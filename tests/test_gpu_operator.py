@@ -209,6 +209,35 @@ def test_bad_arguments_rejected_before_launch(ctx, mp):
         mp.Plan(ctx, (30, 32), sample_idx=np.array([0], dtype=np.int32))  # unsupported length
 
 
+@pytest.mark.parametrize("pinned", [False, True, "mixed"])
+def test_host_buffer_calls_match_device_calls(ctx, mp, pinned):
+    # mpi_forward_host / mpi_adjoint_host run the same kernels, on pinned host
+    # buffers in place and on staged copies of pageable ones: results equal the
+    # device-pointer calls bit for bit, and the oracle within the FP32
+    # tolerance.  Pageable, pinned, and pinned alpha with pageable data.
+    mask = w.poisson_disc_mask(64, 96, 4, calib=(12, 12), seed=60)
+    cs = _case(ctx, mp, (64, 96), 5, 12, mask, seed=61)
+    C, M = cs["C"], cs["M"]
+    r = w.random_coefficients(C, M, seed=62, decay=False).astype(np.complex64)
+
+    def host(x, pin):
+        t = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64)))
+        return t.pin_memory() if pin else t
+
+    a_h = host(cs["a"], bool(pinned))
+    p_h, r_h = host(cs["p"], pinned is True), host(r, pinned is True)
+    y_h = mp.forward_host(ctx, cs["plan"], cs["B"], a_h, p_h)
+    x_h = mp.adjoint_host(ctx, cs["plan"], cs["B"], a_h, r_h)
+    assert not y_h.is_cuda and not x_h.is_cuda
+    y_d = mp.forward(ctx, cs["plan"], cs["B"], a_h.cuda(), p_h.cuda())
+    x_d = mp.adjoint(ctx, cs["plan"], cs["B"], a_h.cuda(), r_h.cuda())
+    assert torch.equal(y_h, y_d.cpu()) and torch.equal(x_h, x_d.cpu())
+    assert rel(y_h.numpy(), op.forward(cs["Fs"], cs["U"], cs["a"], cs["p"])) < TOL
+    assert rel(x_h.numpy(), op.adjoint(cs["Fs"], cs["U"], cs["a"], r.astype(np.complex128))) < TOL
+    with pytest.raises(TypeError):
+        mp.forward_host(ctx, cs["plan"], cs["B"], a_h.cuda(), p_h)
+
+
 def test_launch_count_grows(ctx, mp):
     before = ctx.launches()
     mask = w.poisson_disc_mask(32, 32, 3, calib=(8, 8), seed=20)

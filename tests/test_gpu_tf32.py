@@ -48,9 +48,12 @@ def _basis(N, q, seed):
     return U.astype(np.complex64).astype(np.complex128)
 
 
-# ragged last pixel tile (N = 4000), K padded to the 32-element chunk (2q = 40,
-# 192, 320), one to eight K chunks, coefficient rows from 16 to 64
-@pytest.mark.parametrize("N,C,q", [(256, 4, 32), (4000, 3, 20), (65536, 16, 128), (8192, 32, 96), (4096, 12, 160)])
+# ragged last pixel tile (N = 4000, 23260, 38396), K padded to the 32-element
+# chunk (2q = 40, 192, 320), one to eight K chunks, coefficient rows from 16 to
+# 64; more tiles than CTAs, with a short (N = 23260) and a long (N = 38396) last
+# wave on 152 SMs.
+@pytest.mark.parametrize("N,C,q", [(256, 4, 32), (4000, 3, 20), (65536, 16, 128), (8192, 32, 96), (4096, 12, 160),
+                                   (23260, 5, 40), (38396, 4, 24)])
 def test_tf32_expand_shapes(ctx, mp, N, C, q):
     U = _basis(N, q, N + C)
     a = w.random_coefficients(C, q, seed=3).astype(np.complex64).astype(np.complex128)

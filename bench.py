@@ -155,6 +155,31 @@ def ncu_traffic(kernel):
     return d["bytes_per_launch"] if sha == d.get("source_sha") else None
 
 
+def size_matched_read(nbytes, flush, stream, reps=10):
+    """The read ceiling at the expansion's own working-set size: a device-wide
+    torch reduction over `nbytes` of FP32 after the same L2 flush the timed
+    steps use (the flush leaves L2 full of dirty lines, whose write-back every
+    cold read pays for).  Median of `reps`, CUDA events on `stream`."""
+    import torch
+    x = torch.ones(max(int(nbytes) // 4, 1), dtype=torch.float32, device=flush.device)
+    for _ in range(3):
+        x.sum()
+    ts = []
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            x.sum()
+            e.record(stream)
+            e.synchronize()
+            ts.append(s.elapsed_time(e) * 1e-3)
+    t = statistics.median(ts)
+    del x
+    return {"bytes": int(nbytes), "us": t * 1e6, "GB/s": nbytes / t / 1e9,
+            "how": "torch.sum over the same bytes (fp32) after the same 256 MiB L2 flush, median of 10"}
+
+
 def cpu_oracle_pairs(cfg, U, idx, alpha, p, budget_s=12.0, max_pairs=200):
     """Forward+adjoint pairs/s of the FP64 oracle on this host (bounded sample)."""
     from oracle import fourier, operator as op
@@ -535,6 +560,7 @@ def run_ours(args):
     roof["avg_launch_us"] = ex_avg_s * 1e6
     roof["share_of_kernel_time"] = ex_ms / fam_total if fam_total > 0 else None
     roof["traffic"] = ncu_traffic(kname.split()[0])
+    roof["size_matched_read"] = size_matched_read(ex_bytes, flush, stream)
 
     line = {
         "metric": "MPI forward+adjoint operator pairs per second",

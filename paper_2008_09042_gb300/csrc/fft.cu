@@ -412,6 +412,95 @@ mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride
   return MPI_OK;
 }
 
+// Line pass along y over the oversampled radial grid [C][G][G] (L = G) with the
+// centred n x n window folded in, in place of separate zero-pad and crop
+// passes.  Each grid cell of the window (gy, gx) = (o + y, o + x) carries the
+// factor deap[y] deap[x] / n (-1)^(gx + gy).  Forward (src set): the column is
+// formed on the fly from the image [C][n][n] (zero outside the window) and its
+// transform written to the grid.  Inverse (dst set): the grid column's
+// transform is stored only inside the window, scaled, into the image
+// [C][n][n]; the grid is not written back.  Tiles of 8 columns; a tile wholly
+// outside the window writes zeros (forward) or nothing (inverse).
+struct LineWin {
+  const float2* src;
+  float2* dst;
+  const float* deap;
+  int n, o;
+};
+
+template <int L, bool INV>
+__global__ void __launch_bounds__(kLineWarps * 32, (L * 8 <= 2048) ? 4 : (L * 8 >= 4096 ? 2 : 3))
+    k_fft_lines_win(float2* __restrict__ grid, int C, LineWin win, const float2* __restrict__ tw_g) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  constexpr int TILE = 8;
+  constexpr int S = col_stride(L, TILE);
+  constexpr int T = kLineWarps * 32;
+  constexpr int RSTEP = T / TILE;
+  constexpr int PER = (L + RSTEP - 1) / RSTEP;
+  __shared__ float2 tw[L];
+  __shared__ float2 buf[TILE * S];
+  constexpr int x_tiles = L / TILE;
+  const int c = (int)blockIdx.x / x_tiles, x0 = ((int)blockIdx.x % x_tiles) * TILE;
+  if (c >= C) return;
+  const bool tile_in = x0 < win.o + win.n && x0 + TILE > win.o;  // CTA-uniform
+  if (INV && !tile_in) return;
+  const int tid = threadIdx.x, cx = tid % TILE, r0 = tid / TILE;
+  const int gx = x0 + cx, xi = gx - win.o;
+  const bool colin = xi >= 0 && xi < win.n;
+  float2* gcol = grid + (size_t)c * L * L + gx;
+  if (!INV && !tile_in) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (r0 + RSTEP * u < L) gcol[(size_t)(r0 + RSTEP * u) * L] = make_float2(0.f, 0.f);
+    return;
+  }
+  for (int i = tid; i < L; i += T) tw[i] = tw_g[i];
+  float2 v[PER];
+  if (!INV) {
+    const float2* src = win.src + (size_t)c * win.n * win.n + xi;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int r = r0 + RSTEP * u, yi = r - win.o;
+      v[u] = make_float2(0.f, 0.f);
+      if (r < L && colin && yi >= 0 && yi < win.n) {
+        const float2 val = src[(size_t)yi * win.n];
+        float f = win.deap[yi] * win.deap[xi] / (float)win.n;
+        if ((gx + r) & 1) f = -f;
+        v[u] = make_float2(val.x * f, val.y * f);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (r0 + RSTEP * u < L) v[u] = gcol[(size_t)(r0 + RSTEP * u) * L];
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u)
+    if (r0 + RSTEP * u < L) buf[cx * S + pad8(r0 + RSTEP * u)] = v[u];
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int line = warp; line < TILE; line += kLineWarps) Fft<L, INV>::go(buf + line * S, tw, lane);
+  __syncthreads();
+  if (!INV) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (r0 + RSTEP * u < L) gcol[(size_t)(r0 + RSTEP * u) * L] = buf[cx * S + pad8(r0 + RSTEP * u)];
+  } else {
+    float2* dst = win.dst + (size_t)c * win.n * win.n + xi;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int r = r0 + RSTEP * u, yi = r - win.o;
+      if (r < L && colin && yi >= 0 && yi < win.n) {
+        const float2 t = buf[cx * S + pad8(r)];
+        float f = win.deap[yi] * win.deap[xi] / (float)win.n;
+        if ((gx + r) & 1) f = -f;
+        dst[(size_t)yi * win.n] = make_float2(t.x * f, t.y * f);
+      }
+    }
+  }
+}
+
 float axis_sign(int n) { return ((n / 2) & 1) ? -1.f : 1.f; }
 
 }  // namespace
@@ -421,6 +510,41 @@ mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, in
   const long plane = (long)ny * nx;
   if (inverse) return lines_dispatch<true>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0);
   return lines_dispatch<false>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0);
+}
+
+mpi_status launch_fft_cols_window(mpi_ctx* ctx, float2* grid, int C, int G, const float2* src, float2* dst,
+                                  const float* deap, int n, bool inverse) {
+  if (C == 0) return MPI_OK;
+  const long blocks = (long)C * (G / 8);
+  if (blocks > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many FFT tiles");
+  const float2* tw = twiddle_table(ctx, G);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  const LineWin win{src, dst, deap, n, G / 2 - n / 2};
+#define MPI_WIN_CASE(L)                                                                                    \
+  case L:                                                                                                  \
+    if (inverse)                                                                                           \
+      launch_pdl(ctx, k_fft_lines_win<L, true>, dim3((unsigned)blocks), dim3(kLineWarps * 32), 0, grid, C, win, tw); \
+    else                                                                                                   \
+      launch_pdl(ctx, k_fft_lines_win<L, false>, dim3((unsigned)blocks), dim3(kLineWarps * 32), 0, grid, C, win, tw); \
+    break;
+  MPI_PROF(ctx, KF_FFT_LINES);
+  switch (G) {
+    MPI_WIN_CASE(16)
+    MPI_WIN_CASE(32)
+    MPI_WIN_CASE(48)
+    MPI_WIN_CASE(64)
+    MPI_WIN_CASE(96)
+    MPI_WIN_CASE(128)
+    MPI_WIN_CASE(192)
+    MPI_WIN_CASE(256)
+    MPI_WIN_CASE(320)
+    MPI_WIN_CASE(512)
+    default:
+      return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  }
+#undef MPI_WIN_CASE
+  MPI_LAUNCH_CHECK(ctx, "k_fft_lines_win");
+  return MPI_OK;
 }
 
 mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse) {

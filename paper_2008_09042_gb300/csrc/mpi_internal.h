@@ -233,6 +233,11 @@ void solver_cache_clear(mpi_ctx* ctx);
 
 // In-place FFT along the y axis of `data` [C][nz][ny][nx] (unnormalised).
 mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);
+// FFT along y over the oversampled radial grid [C][G][G] with the centred
+// n x n window folded in: forward reads the image src [C][n][n] (padding,
+// deapodisation and sign on the fly); inverse writes only the window into dst.
+mpi_status launch_fft_cols_window(mpi_ctx* ctx, float2* grid, int C, int G, const float2* src, float2* dst,
+                                  const float* deap, int n, bool inverse);
 // In-place FFT along z of [C][nz][ny][nx].
 mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);
 // Forward: FFT along x of every row, centring sign on k, gather of the sampled points.

@@ -11,7 +11,8 @@
 //      floor(kappa) - W/2 + 1 ... floor(kappa) + W/2 (periodic), reading the
 //      grid through shared-memory tiles (samples binned by first-tap tile).
 // The adjoint runs the transposed steps: spread, inverse FFTs, crop with the
-// sign and deapodisation.  Spreading is output-driven: each grid cell sums the
+// sign and deapodisation (the zero-padding of step 1 and the crop are folded
+// into the FFT pass along y).  Spreading is output-driven: each grid cell sums the
 // samples whose W x W footprint covers it, found through a per-plan CSR of the
 // samples by first-tap cell, so no cell is written twice and no atomics run.
 // beta = pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8) (Beatty et al. 2005);
@@ -75,30 +76,6 @@ __global__ void k_nufft_deap(int n, int G, int W, double beta, float* __restrict
   }
   phi = W * phi / bessel_i0(beta);
   deap[j] = (float)(1.0 / phi);
-}
-
-// grid[c] = 0 outside the centred n x n window; inside,
-// v[c][y][x] * deap[y] * deap[x] * (-1)^(gx + gy) / n with (gy, gx) = (o + y, o + x).
-__global__ void k_nufft_pad(const float2* __restrict__ v, int C, int n, int G, const float* __restrict__ deap,
-                            float2* __restrict__ grid) {
-  mpi_ptx::pdl_trigger();
-  mpi_ptx::pdl_wait();
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t GG = (size_t)G * G;
-  if (e >= (size_t)C * GG) return;
-  const int c = (int)(e / GG);
-  const int g = (int)(e % GG);
-  const int gy = g / G, gx = g % G;
-  const int o = G / 2 - n / 2;
-  const int y = gy - o, x = gx - o;
-  float2 out = make_float2(0.f, 0.f);
-  if (y >= 0 && y < n && x >= 0 && x < n) {
-    const float2 val = v[(size_t)c * n * n + (size_t)y * n + x];
-    float s = deap[y] * deap[x] / (float)n;
-    if ((gx + gy) & 1) s = -s;
-    out = make_float2(val.x * s, val.y * s);
-  }
-  grid[e] = out;
 }
 
 constexpr int kInterpTile = 32;    // first-tap tile of the shared-memory interpolation
@@ -307,24 +284,6 @@ __global__ void __launch_bounds__(256) k_nufft_spread_dense(const float4* __rest
   if (lane == 0) spread_store(grid, C, G, c0, gy, gx, acc);
 }
 
-__global__ void k_nufft_crop(const float2* __restrict__ grid, int C, int n, int G, const float* __restrict__ deap,
-                             float2* __restrict__ out) {
-  mpi_ptx::pdl_trigger();
-  mpi_ptx::pdl_wait();
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t nn = (size_t)n * n;
-  if (e >= (size_t)C * nn) return;
-  const int c = (int)(e / nn);
-  const int j = (int)(e % nn);
-  const int y = j / n, x = j % n;
-  const int o = G / 2 - n / 2;
-  const int gy = o + y, gx = o + x;
-  const float2 g = grid[(size_t)c * G * G + (size_t)gy * G + gx];
-  float s = deap[y] * deap[x] / (float)n;
-  if ((gx + gy) & 1) s = -s;
-  out[e] = make_float2(g.x * s, g.y * s);
-}
-
 float axis_sign(int n) { return ((n / 2) & 1) ? -1.f : 1.f; }
 
 unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -440,11 +399,8 @@ mpi_status nufft_plan_init(mpi_ctx* ctx, mpi_plan* plan, const float* traj_host)
 
 mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, int C, float2* y, float2* grid) {
   const int n = plan->nx, G = plan->G, M = plan->M;
-  const size_t total = (size_t)C * G * G;
-  MPI_PROF(ctx, KF_NUFFT);
-  launch_pdl(ctx, k_nufft_pad, dim3(blocks_for(total, 256)), dim3(256), 0, v, C, n, G, plan->deap, grid);
-  MPI_LAUNCH_CHECK(ctx, "k_nufft_pad");
-  mpi_status st = launch_fft_cols(ctx, grid, C, 1, G, G, false);
+  // zero-pad with deapodisation and sign, folded into the pass along y
+  mpi_status st = launch_fft_cols_window(ctx, grid, C, G, v, nullptr, plan->deap, n, false);
   if (st) return st;
   st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, false);
   if (st) return st;
@@ -507,11 +463,6 @@ mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, in
   }
   mpi_status st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, true);
   if (st) return st;
-  st = launch_fft_cols(ctx, grid, C, 1, G, G, true);
-  if (st) return st;
-  MPI_PROF(ctx, KF_NUFFT);
-  launch_pdl(ctx, k_nufft_crop, dim3(blocks_for((size_t)C * n * n, 256)), dim3(256), 0, grid, C, n, G,
-             plan->deap, out);
-  MPI_LAUNCH_CHECK(ctx, "k_nufft_crop");
-  return MPI_OK;
+  // the inverse pass along y stores only the centred window, with deapodisation and sign
+  return launch_fft_cols_window(ctx, grid, C, G, nullptr, out, plan->deap, n, true);
 }

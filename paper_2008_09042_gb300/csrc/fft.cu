@@ -625,10 +625,13 @@ mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const flo
 
 namespace {
 
-// In-place FFT of contiguous lines of length L, one warp per line.
+// In-place FFT of contiguous lines of length L, one warp per line; only the
+// elements [keep_lo, keep_hi) of each transformed line are stored back (the
+// radial adjoint keeps the columns that its cropping pass along y reads).
 template <int L, bool INV>
 __global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __restrict__ data, long n_rows,
-                                                                    const float2* __restrict__ tw_g) {
+                                                                    const float2* __restrict__ tw_g, int keep_lo,
+                                                                    int keep_hi) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
   __shared__ float2 tw[L];
@@ -646,11 +649,12 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __r
   if (row >= n_rows) return;
   Fft<L, INV>::go(b, tw, lane);
 #pragma unroll
-  for (int i = lane; i < L; i += 32) src[i] = b[pad8(i)];
+  for (int i = lane; i < L; i += 32)
+    if (i >= keep_lo && i < keep_hi) src[i] = b[pad8(i)];
 }
 
 template <bool INV>
-mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L) {
+mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L, int keep_lo, int keep_hi) {
   const long blocks = (n_rows + kRowWarps - 1) / kRowWarps;
   if (blocks == 0) return MPI_OK;
   const float2* tw = twiddle_table(ctx, L);
@@ -658,7 +662,7 @@ mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L)
 #define MPI_RI_CASE(n)                                                                           \
   case n:                                                                                        \
     launch_pdl(ctx, k_fft_rows_inplace<n, INV>, dim3((unsigned)blocks), dim3(kRowWarps * 32), 0, data, n_rows, \
-               tw);                                                                               \
+               tw, keep_lo, keep_hi);                                                             \
     break;
   MPI_PROF(ctx, KF_FFT_ROWS);
   switch (L) {
@@ -682,7 +686,9 @@ mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L)
 
 }  // namespace
 
-mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse) {
-  if (inverse) return rows_inplace_dispatch<true>(ctx, data, n_rows, L);
-  return rows_inplace_dispatch<false>(ctx, data, n_rows, L);
+mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse, int keep_lo,
+                                   int keep_hi) {
+  if (keep_hi < 0) keep_hi = L;
+  if (inverse) return rows_inplace_dispatch<true>(ctx, data, n_rows, L, keep_lo, keep_hi);
+  return rows_inplace_dispatch<false>(ctx, data, n_rows, L, keep_lo, keep_hi);
 }

@@ -290,7 +290,9 @@ unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse);
+// keep_lo, keep_hi: the elements of each transformed line stored back (default: all)
+mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse, int keep_lo = 0,
+                                   int keep_hi = -1);
 
 size_t nufft_grid_elems(const mpi_plan* plan, int C) {
   return (size_t)C * plan->G * plan->G + (size_t)spread_coils_padded(C) * plan->M;
@@ -461,7 +463,8 @@ mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, in
     }
     MPI_LAUNCH_CHECK(ctx, "k_nufft_spread");
   }
-  mpi_status st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, true);
+  // only the columns of the centred window reach the cropping pass along y
+  mpi_status st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, true, G / 2 - n / 2, G / 2 - n / 2 + n);
   if (st) return st;
   // the inverse pass along y stores only the centred window, with deapodisation and sign
   return launch_fft_cols_window(ctx, grid, C, G, nullptr, out, plan->deap, n, true);

@@ -420,7 +420,8 @@ mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride
 // transform written to the grid.  Inverse (dst set): the grid column's
 // transform is stored only inside the window, scaled, into the image
 // [C][n][n]; the grid is not written back.  Tiles of 8 columns; a tile wholly
-// outside the window writes zeros (forward) or nothing (inverse).
+// outside the window does nothing: forward, those grid columns are zero and
+// the row pass that follows reads them as zeros without loading them.
 struct LineWin {
   const float2* src;
   float2* dst;
@@ -444,17 +445,11 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * 8 <= 2048) ? 4 : (L * 8 
   const int c = (int)blockIdx.x / x_tiles, x0 = ((int)blockIdx.x % x_tiles) * TILE;
   if (c >= C) return;
   const bool tile_in = x0 < win.o + win.n && x0 + TILE > win.o;  // CTA-uniform
-  if (INV && !tile_in) return;
   const int tid = threadIdx.x, cx = tid % TILE, r0 = tid / TILE;
   const int gx = x0 + cx, xi = gx - win.o;
   const bool colin = xi >= 0 && xi < win.n;
   float2* gcol = grid + (size_t)c * L * L + gx;
-  if (!INV && !tile_in) {
-#pragma unroll
-    for (int u = 0; u < PER; ++u)
-      if (r0 + RSTEP * u < L) gcol[(size_t)(r0 + RSTEP * u) * L] = make_float2(0.f, 0.f);
-    return;
-  }
+  if (!tile_in) return;  // forward: those columns are zero, and the row pass reads them as such
   for (int i = tid; i < L; i += T) tw[i] = tw_g[i];
   float2 v[PER];
   if (!INV) {
@@ -625,13 +620,15 @@ mpi_status launch_rows_scatter_inv(mpi_ctx* ctx, const mpi_plan* plan, const flo
 
 namespace {
 
-// In-place FFT of contiguous lines of length L, one warp per line; only the
-// elements [keep_lo, keep_hi) of each transformed line are stored back (the
-// radial adjoint keeps the columns that its cropping pass along y reads).
+// In-place FFT of contiguous lines of length L, one warp per line.  Elements
+// outside [load_lo, load_hi) are taken as zero without being read (the radial
+// forward's padded columns), and only [keep_lo, keep_hi) of each transformed
+// line is stored back (the radial adjoint keeps the columns that its cropping
+// pass along y reads).
 template <int L, bool INV>
 __global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __restrict__ data, long n_rows,
-                                                                    const float2* __restrict__ tw_g, int keep_lo,
-                                                                    int keep_hi) {
+                                                                    const float2* __restrict__ tw_g, int load_lo,
+                                                                    int load_hi, int keep_lo, int keep_hi) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
   __shared__ float2 tw[L];
@@ -643,7 +640,8 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __r
   float2* b = buf[warp];
   if (row < n_rows) {
 #pragma unroll
-    for (int i = lane; i < L; i += 32) b[pad8(i)] = src[i];
+    for (int i = lane; i < L; i += 32)
+      b[pad8(i)] = (i >= load_lo && i < load_hi) ? src[i] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   if (row >= n_rows) return;
@@ -654,7 +652,8 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_fft_rows_inplace(float2* __r
 }
 
 template <bool INV>
-mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L, int keep_lo, int keep_hi) {
+mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L, int load_lo, int load_hi,
+                                 int keep_lo, int keep_hi) {
   const long blocks = (n_rows + kRowWarps - 1) / kRowWarps;
   if (blocks == 0) return MPI_OK;
   const float2* tw = twiddle_table(ctx, L);
@@ -662,7 +661,7 @@ mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L,
 #define MPI_RI_CASE(n)                                                                           \
   case n:                                                                                        \
     launch_pdl(ctx, k_fft_rows_inplace<n, INV>, dim3((unsigned)blocks), dim3(kRowWarps * 32), 0, data, n_rows, \
-               tw, keep_lo, keep_hi);                                                             \
+               tw, load_lo, load_hi, keep_lo, keep_hi);                                           \
     break;
   MPI_PROF(ctx, KF_FFT_ROWS);
   switch (L) {
@@ -686,9 +685,10 @@ mpi_status rows_inplace_dispatch(mpi_ctx* ctx, float2* data, long n_rows, int L,
 
 }  // namespace
 
-mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse, int keep_lo,
-                                   int keep_hi) {
+mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse, int load_lo,
+                                   int load_hi, int keep_lo, int keep_hi) {
+  if (load_hi < 0) load_hi = L;
   if (keep_hi < 0) keep_hi = L;
-  if (inverse) return rows_inplace_dispatch<true>(ctx, data, n_rows, L, keep_lo, keep_hi);
-  return rows_inplace_dispatch<false>(ctx, data, n_rows, L, keep_lo, keep_hi);
+  if (inverse) return rows_inplace_dispatch<true>(ctx, data, n_rows, L, load_lo, load_hi, keep_lo, keep_hi);
+  return rows_inplace_dispatch<false>(ctx, data, n_rows, L, load_lo, load_hi, keep_lo, keep_hi);
 }

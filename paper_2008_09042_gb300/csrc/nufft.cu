@@ -290,9 +290,10 @@ unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+// load_lo, load_hi: the elements of each line read (the rest taken as zero);
 // keep_lo, keep_hi: the elements of each transformed line stored back (default: all)
-mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse, int keep_lo = 0,
-                                   int keep_hi = -1);
+mpi_status launch_fft_rows_inplace(mpi_ctx* ctx, float2* data, long n_rows, int L, bool inverse, int load_lo = 0,
+                                   int load_hi = -1, int keep_lo = 0, int keep_hi = -1);
 
 size_t nufft_grid_elems(const mpi_plan* plan, int C) {
   return (size_t)C * plan->G * plan->G + (size_t)spread_coils_padded(C) * plan->M;
@@ -404,7 +405,9 @@ mpi_status nufft_forward(mpi_ctx* ctx, const mpi_plan* plan, const float2* v, in
   // zero-pad with deapodisation and sign, folded into the pass along y
   mpi_status st = launch_fft_cols_window(ctx, grid, C, G, v, nullptr, plan->deap, n, false);
   if (st) return st;
-  st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, false);
+  // the pass along y wrote only the window's columns; the rest are zero
+  const int o = G / 2 - n / 2;
+  st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, false, o, o + n);
   if (st) return st;
   if (M == 0) return MPI_OK;
   const float ks = axis_sign(G) * axis_sign(G);
@@ -464,7 +467,8 @@ mpi_status nufft_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, in
     MPI_LAUNCH_CHECK(ctx, "k_nufft_spread");
   }
   // only the columns of the centred window reach the cropping pass along y
-  mpi_status st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, true, G / 2 - n / 2, G / 2 - n / 2 + n);
+  const int o = G / 2 - n / 2;
+  mpi_status st = launch_fft_rows_inplace(ctx, grid, (long)C * G, G, true, 0, G, o, o + n);
   if (st) return st;
   // the inverse pass along y stores only the centred window, with deapodisation and sign
   return launch_fft_cols_window(ctx, grid, C, G, nullptr, out, plan->deap, n, true);

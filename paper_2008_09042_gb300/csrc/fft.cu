@@ -151,12 +151,15 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lan
     if (j < NB) {
       const int k = j % NS;
       if (NS > 1) {
+        // w^r for r = 1 .. R-1 from one table read: w^r = w^(r/2) w^(r - r/2),
+        // so each power is at most three products deep (a few ulp)
+        float2 w[R];
+        w[1] = tw[k * (N / (NS * R))];
+        if (INV) w[1].y = -w[1].y;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = tw[(r * k * (N / (NS * R))) % N];
-          if (INV) w.y = -w.y;
-          v[b][r] = cmul(v[b][r], w);
-        }
+        for (int r = 2; r < R; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
       }
       Dft<R, INV>::go(v[b]);
       const int base = (j / NS) * NS * R + k;

@@ -131,14 +131,17 @@ struct Dft<5, INV> {
 __host__ __device__ __forceinline__ constexpr int pad8(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int padded_len(int n) { return n + n / 8; }
 
-template <int N, int R, int NS, bool INV>
+// One radix-R Stockham stage of an N-point line held in shared memory, its
+// N / R butterflies spread over LANES lanes (a warp, or half a warp for short
+// lines, two lines per warp).
+template <int N, int R, int NS, bool INV, int LANES>
 __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lane) {
   constexpr int NB = N / R;
-  constexpr int PER = (NB + 31) / 32;
+  constexpr int PER = (NB + LANES - 1) / LANES;
   float2 v[PER][R];
 #pragma unroll
   for (int b = 0; b < PER; ++b) {
-    const int j = lane + 32 * b;
+    const int j = lane + LANES * b;
     if (j < NB) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = buf[pad8(j + r * NB)];
@@ -147,7 +150,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lan
   __syncwarp();
 #pragma unroll
   for (int b = 0; b < PER; ++b) {
-    const int j = lane + 32 * b;
+    const int j = lane + LANES * b;
     if (j < NB) {
       const int k = j % NS;
       if (NS > 1) {
@@ -170,17 +173,17 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw, int lan
   __syncwarp();
 }
 
-template <int N, bool INV, int NS, int R, int... Rest>
+template <int N, bool INV, int LANES, int NS, int R, int... Rest>
 struct Run {
   static __device__ __forceinline__ void go(float2* b, const float2* tw, int lane) {
-    fft_stage<N, R, NS, INV>(b, tw, lane);
-    Run<N, INV, NS * R, Rest...>::go(b, tw, lane);
+    fft_stage<N, R, NS, INV, LANES>(b, tw, lane);
+    Run<N, INV, LANES, NS * R, Rest...>::go(b, tw, lane);
   }
 };
-template <int N, bool INV, int NS, int R>
-struct Run<N, INV, NS, R> {
+template <int N, bool INV, int LANES, int NS, int R>
+struct Run<N, INV, LANES, NS, R> {
   static __device__ __forceinline__ void go(float2* b, const float2* tw, int lane) {
-    fft_stage<N, R, NS, INV>(b, tw, lane);
+    fft_stage<N, R, NS, INV, LANES>(b, tw, lane);
   }
 };
 
@@ -189,8 +192,9 @@ struct Fft;
 #define MPI_FFT_PLAN(n, ...)                                                    \
   template <bool INV>                                                           \
   struct Fft<n, INV> {                                                          \
+    template <int LANES = 32>                                                   \
     static __device__ __forceinline__ void go(float2* b, const float2* tw, int lane) { \
-      Run<n, INV, 1, __VA_ARGS__>::go(b, tw, lane);                             \
+      Run<n, INV, LANES, 1, __VA_ARGS__>::go(b, tw, lane);                      \
     }                                                                           \
   };
 MPI_FFT_PLAN(16, 4, 4)
@@ -296,6 +300,21 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
 
 constexpr int kLineWarps = 8;  // warps per CTA of the line pass
 
+// The FFTs of a line pass's TILE lines, in shared memory at buf + line * S.
+// Lines of up to 128 points take half a warp each (no stage of theirs has more
+// than 16 butterflies), two lines per warp; every line of the tile is
+// transformed, whether or not it is stored, so both halves of a warp run the
+// same stages.
+template <int L, bool INV, int TILE, int S>
+__device__ __forceinline__ void fft_tile_lines(float2* buf, const float2* tw, int warp, int lane) {
+  if constexpr (L <= 128) {
+    for (int line = 2 * warp + (lane >> 4); line < TILE; line += 2 * kLineWarps)
+      Fft<L, INV>::template go<16>(buf + line * S, tw, lane & 15);
+  } else {
+    for (int line = warp; line < TILE; line += kLineWarps) Fft<L, INV>::go(buf + line * S, tw, lane);
+  }
+}
+
 // In-place FFT of lines of length L with element stride `stride`.  A CTA takes
 // TILE lines that are adjacent in memory (consecutive x): it loads them as
 // TILE-element row segments (64, 128 or 256 bytes), transposes into shared
@@ -346,8 +365,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * TILE <= 2048) ? 4 : (L *
     if (ok && r0 + RSTEP * u < L) buf[cx * S + pad8(r0 + RSTEP * u)] = v[u];
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  for (int line = warp; line < TILE; line += kLineWarps)
-    if (x0 + line < nx) Fft<L, INV>::go(buf + line * S, tw, lane);
+  fft_tile_lines<L, INV, TILE, S>(buf, tw, warp, lane);
   __syncthreads();
   float2* dst = data + base + cx;
 #pragma unroll
@@ -478,7 +496,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * 8 <= 2048) ? 4 : (L * 8 
     if (r0 + RSTEP * u < L) buf[cx * S + pad8(r0 + RSTEP * u)] = v[u];
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  for (int line = warp; line < TILE; line += kLineWarps) Fft<L, INV>::go(buf + line * S, tw, lane);
+  fft_tile_lines<L, INV, TILE, S>(buf, tw, warp, lane);
   __syncthreads();
   if (!INV) {
 #pragma unroll

@@ -185,7 +185,7 @@ mpi_status kspace_to_image(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, 
   if (plan->kind == MPI_TRAJ_RADIAL) return nufft_adjoint(ctx, plan, y, C, w, grid);
   mpi_status st = launch_rows_scatter_inv(ctx, plan, y, C, w);
   if (st) return st;
-  st = launch_fft_cols(ctx, w, C, plan->nz, plan->ny, plan->nx, true);
+  st = launch_fft_cols(ctx, w, C, plan->nz, plan->ny, plan->nx, true, plan->row_has);
   if (st) return st;
   if (plan->ndim == 3) st = launch_fft_z(ctx, w, C, plan->nz, plan->ny, plan->nx, true);
   return st;
@@ -442,9 +442,20 @@ extern "C" mpi_status mpi_plan_create(mpi_ctx* ctx, const mpi_plan_desc* d, mpi_
       while (m < d->M && d->sample_idx[m] < end) ++m;
     }
     row_ptr[plan->n_rows] = m;
+    // row mask only where some k-space row has no samples (3D masks sample
+    // whole readouts at a fraction of the (kz, ky) rows)
+    std::vector<uint8_t> row_has(plan->n_rows);
+    bool any_empty = false;
+    for (int r = 0; r < plan->n_rows; ++r) {
+      row_has[r] = row_ptr[r + 1] > row_ptr[r] ? 1 : 0;
+      any_empty |= !row_has[r];
+    }
     cudaError_t e = cudaMalloc(&plan->row_ptr, row_ptr.size() * sizeof(int32_t));
     if (e == cudaSuccess)
       e = cudaMemcpy(plan->row_ptr, row_ptr.data(), row_ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && any_empty) e = cudaMalloc(&plan->row_has, row_has.size());
+    if (e == cudaSuccess && any_empty)
+      e = cudaMemcpy(plan->row_has, row_has.data(), row_has.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && d->M > 0) {
       e = cudaMalloc(&plan->idx, (size_t)d->M * sizeof(int32_t));
       if (e == cudaSuccess)
@@ -499,7 +510,7 @@ extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
     solver_cache_forget(plan->ctx, plan);
     ctx_release(&plan->ctx);
   }
-  void* ptrs[] = {plan->idx, plan->row_ptr, plan->traj, plan->gstart, plan->gw, plan->deap, plan->cell_ptr,
+  void* ptrs[] = {plan->idx, plan->row_ptr, plan->row_has, plan->traj, plan->gstart, plan->gw, plan->deap, plan->cell_ptr,
                   plan->cell_rank, plan->cell_sx, plan->cell_w, plan->cell_dense,
                   plan->tile_items, plan->tile_samples};
   for (void* p : ptrs)

@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_fwd_gather(
 }
 
 // Adjoint: zero-fill the row from its samples (with the k-side sign), inverse
-// FFT; rows without samples are written as zeros.  Same row striding.
+// FFT.  Rows without samples are not written: the pass along y that follows
+// reads them as zeros.  Same row striding.
 template <int NX>
 __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
     const float2* __restrict__ y, int C, int n_rows, int ny, const int32_t* __restrict__ idx,
@@ -277,10 +278,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_rows_scatter_inv(
     const int c = gr / n_rows, row = gr - c * n_rows;
     const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
     float2* dst = data + ((size_t)c * n_rows + row) * NX;
-    if (m1 <= m0) {  // warp-uniform
-      for (int i = lane; i < NX; i += 32) dst[i] = make_float2(0.f, 0.f);
-      continue;
-    }
+    if (m1 <= m0) continue;  // warp-uniform
     for (int i = lane; i < padded_len(NX); i += 32) b[i] = make_float2(0.f, 0.f);
     __syncwarp();
     const int rpar = (row / ny + row % ny) & 1;
@@ -335,7 +333,8 @@ template <int L, bool INV, int TILE>
 __global__ void __launch_bounds__(kLineWarps * 32, (L * TILE <= 2048) ? 4 : (L * TILE >= 4096 ? 2 : 3)) k_fft_lines(float2* __restrict__ data, int nx,
                                                               long stride, int n_slabs, int inner,
                                                               long outer_stride, long inner_stride,
-                                                              const float2* __restrict__ tw_g) {
+                                                              const float2* __restrict__ tw_g,
+                                                              const uint8_t* __restrict__ rmask, int mask_nz) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
   constexpr int S = col_stride(L, TILE);
@@ -360,6 +359,15 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * TILE <= 2048) ? 4 : (L *
 #pragma unroll
   for (int u = 0; u < PER; ++u)
     if (ok && r0 + RSTEP * u < L) v[u] = src[(size_t)(r0 + RSTEP * u) * stride];
+  if (INV && rmask) {
+    // rows of this slab without samples (rmask[z * L + r] == 0, z = slab %
+    // mask_nz) are taken as zeros, whatever the buffer holds there: the
+    // adjoint's row pass does not write them
+    const uint8_t* rm = rmask + (size_t)(slab % mask_nz) * L;
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (r0 + RSTEP * u < L && !rm[r0 + RSTEP * u]) v[u] = make_float2(0.f, 0.f);
+  }
 #pragma unroll
   for (int u = 0; u < PER; ++u)
     if (ok && r0 + RSTEP * u < L) buf[cx * S + pad8(r0 + RSTEP * u)] = v[u];
@@ -369,15 +377,17 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * TILE <= 2048) ? 4 : (L *
   __syncthreads();
   float2* dst = data + base + cx;
 #pragma unroll
-  for (int u = 0; u < PER; ++u)
-    if (ok && r0 + RSTEP * u < L) dst[(size_t)(r0 + RSTEP * u) * stride] = buf[cx * S + pad8(r0 + RSTEP * u)];
+  for (int u = 0; u < PER; ++u) {
+    const int r = r0 + RSTEP * u;
+    if (ok && r < L) dst[(size_t)r * stride] = buf[cx * S + pad8(r)];
+  }
 }
 
 template <int L, bool INV, int TILE>
 void lines_launch(mpi_ctx* ctx, long blocks, float2* data, int nx, long stride, int n_slabs, int inner,
-                  long outer_stride, long inner_stride, const float2* tw) {
+                  long outer_stride, long inner_stride, const float2* tw, const uint8_t* rmask, int mask_nz) {
   launch_pdl(ctx, k_fft_lines<L, INV, TILE>, dim3((unsigned)blocks), dim3(kLineWarps * 32), 0, data, nx, stride,
-             n_slabs, inner, outer_stride, inner_stride, tw);
+             n_slabs, inner, outer_stride, inner_stride, tw, rmask, mask_nz);
 }
 
 // Tile width: the widest (longest row segments) that keeps at most 16 elements
@@ -394,7 +404,7 @@ int lines_tile(const mpi_ctx* ctx, int L, int nx, int n_slabs) {
 
 template <bool INV>
 mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride, int n_slabs, int inner,
-                          long outer_stride, long inner_stride) {
+                          long outer_stride, long inner_stride, const uint8_t* rmask = nullptr, int mask_nz = 1) {
   const int tile = lines_tile(ctx, L, nx, n_slabs);
   const int x_tiles = (nx + tile - 1) / tile;
   const long blocks = (long)n_slabs * x_tiles;
@@ -406,12 +416,13 @@ mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride
   case n:                                                                                                    \
     if (n <= 128 && tile == 32)                                                                              \
       lines_launch<n, INV, (n <= 128 ? 32 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,  \
-                                                inner_stride, tw);                                          \
+                                                inner_stride, tw, rmask, mask_nz);                          \
     else if (n <= 256 && tile == 16)                                                                         \
       lines_launch<n, INV, (n <= 256 ? 16 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,  \
-                                                inner_stride, tw);                                          \
+                                                inner_stride, tw, rmask, mask_nz);                          \
     else                                                                                                     \
-      lines_launch<n, INV, 8>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw); \
+      lines_launch<n, INV, 8>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw,   \
+                              rmask, mask_nz);                                                              \
     break;
   MPI_PROF(ctx, KF_FFT_LINES);
   switch (L) {
@@ -521,11 +532,12 @@ float axis_sign(int n) { return ((n / 2) & 1) ? -1.f : 1.f; }
 
 }  // namespace
 
-mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse) {
-  // lines along y: stride nx; slabs = (c, z); base = slab * ny * nx
+mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse,
+                           const uint8_t* row_has) {
+  // lines along y: stride nx; slabs = (c, z); base = slab * ny * nx; row mask [z][y]
   const long plane = (long)ny * nx;
-  if (inverse) return lines_dispatch<true>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0);
-  return lines_dispatch<false>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0);
+  if (inverse) return lines_dispatch<true>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0, row_has, nz);
+  return lines_dispatch<false>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0, row_has, nz);
 }
 
 mpi_status launch_fft_cols_window(mpi_ctx* ctx, float2* grid, int C, int G, const float2* src, float2* dst,

@@ -62,6 +62,7 @@ struct mpi_plan {
   // first sample of that row (rows + 1 entries).
   int32_t* idx = nullptr;
   int32_t* row_ptr = nullptr;
+  uint8_t* row_has = nullptr;  // [n_rows]: 1 where the k-space row has samples; null when every row has some
   int n_rows = 0;
   // Radial (Kaiser-Bessel gridding)
   int W = 0, G = 0;
@@ -232,7 +233,11 @@ void solver_cache_clear(mpi_ctx* ctx);
 // ------------------------------------------------------------ FFT passes
 
 // In-place FFT along the y axis of `data` [C][nz][ny][nx] (unnormalised).
-mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);
+// FFT along y of [C][nz][ny][nx].  With row_has ([nz][ny], 1 where the
+// k-space row has samples; inverse only): rows without samples are read as
+// zeros (the adjoint's row pass does not write them).
+mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse,
+                           const uint8_t* row_has = nullptr);
 // FFT along y over the oversampled radial grid [C][G][G] with the centred
 // n x n window folded in: forward reads the image src [C][n][n] (padding,
 // deapodisation and sign on the fly); inverse writes only the window into dst.

@@ -238,6 +238,28 @@ def test_host_buffer_calls_match_device_calls(ctx, mp, pinned):
         mp.forward_host(ctx, cs["plan"], cs["B"], a_h.cuda(), p_h)
 
 
+def test_cartesian_rows_without_samples(ctx, mp):
+    # Only every third k-space row is sampled: the adjoint's row pass skips the
+    # empty rows and the pass along y reads them as zeros (the plan's row mask),
+    # after a call that filled the workspace with non-zero values.
+    shape = (96, 64)
+    mask = np.zeros(shape, dtype=bool)
+    mask[::3, :] = True
+    mask[40:56, 24:40] = True  # calibration block: some rows sampled in part
+    cs = _case(ctx, mp, shape, 4, 10, mask, seed=70)
+    C, M = cs["C"], cs["M"]
+    r = w.random_coefficients(C, M, seed=71, decay=False).astype(np.complex64).astype(np.complex128)
+    ag, pg = c64(cs["a"]), c64(cs["p"])
+    mp.forward(ctx, cs["plan"], cs["B"], ag, pg)  # leaves non-zero data in the workspace
+    x = mp.adjoint(ctx, cs["plan"], cs["B"], ag, c64(r))
+    assert rel(f64(x), op.adjoint(cs["Fs"], cs["U"], cs["a"], r)) < TOL
+    y = mp.forward(ctx, cs["plan"], cs["B"], ag, pg)
+    assert rel(f64(y), op.forward(cs["Fs"], cs["U"], cs["a"], cs["p"])) < TOL
+    gp, ga = mp.jacobian_adjoint(ctx, cs["plan"], cs["B"], ag, pg, c64(r))
+    rp, ra = op.jacobian_adjoint(cs["Fs"], cs["U"], cs["a"], cs["p"], r)
+    assert rel(f64(gp), rp) < TOL and rel(f64(ga), ra) < TOL
+
+
 def test_launch_count_grows(ctx, mp):
     before = ctx.launches()
     mask = w.poisson_disc_mask(32, 32, 3, calib=(8, 8), seed=20)

@@ -748,26 +748,27 @@ template <class Op>
 mpi_status host_call(mpi_ctx* ctx, const mpi_basis* basis, int C, const mpi_c32* alpha, const mpi_c32* in,
                      size_t n_in, mpi_c32* out, size_t n_out, Op op) {
   const size_t n_alpha = (size_t)C * basis->q;
+  // an empty input or output (no samples) is passed through as given
   const mpi_c32* da = (const mpi_c32*)mapped_host(alpha);
   const mpi_c32* di = n_in ? (const mpi_c32*)mapped_host(in) : in;
   mpi_c32* dout = n_out ? (mpi_c32*)mapped_host(out) : out;
+  const bool stage_a = !da, stage_i = n_in && !di, copy_out = n_out && !dout;
   const size_t a_off = 0, i_off = (n_alpha + 1) & ~(size_t)1, o_off = i_off + ((n_in + 1) & ~(size_t)1);
-  if (!da || !di || !dout) {
+  if (stage_a || stage_i || copy_out) {
     mpi_status st = ensure_stage(ctx, (o_off + n_out) * sizeof(mpi_c32));
     if (st) return st;
   }
   mpi_c32* d = (mpi_c32*)ctx->stage;
   cudaError_t e = cudaSuccess;
-  if (!da) {
+  if (stage_a) {
     e = cudaMemcpyAsync(d + a_off, alpha, n_alpha * sizeof(mpi_c32), cudaMemcpyHostToDevice, ctx->stream);
     da = d + a_off;
   }
-  if (e == cudaSuccess && !di) {
+  if (e == cudaSuccess && stage_i) {
     e = cudaMemcpyAsync(d + i_off, in, n_in * sizeof(mpi_c32), cudaMemcpyHostToDevice, ctx->stream);
     di = d + i_off;
   }
   if (e != cudaSuccess) return cuda_check(ctx, e, "host input copy");
-  const bool copy_out = !dout;
   if (copy_out) dout = d + o_off;
   mpi_status st = op(da, di, dout);
   if (st) return st;

@@ -238,6 +238,20 @@ def test_host_buffer_calls_match_device_calls(ctx, mp, pinned):
         mp.forward_host(ctx, cs["plan"], cs["B"], a_h.cuda(), p_h)
 
 
+def test_host_buffer_calls_without_samples(ctx, mp):
+    # a plan with no samples: the forward's y and the adjoint's input are empty
+    n, q, C = 32, 4, 3
+    U = w.smooth_orthonormal_basis(n, n, q, seed=80)
+    plan = mp.Plan(ctx, (n, n), sample_idx=np.zeros(0, dtype=np.int32))
+    B = mp.Basis(ctx, U.T)
+    a = torch.from_numpy(w.random_coefficients(C, q, seed=81).astype(np.complex64)).pin_memory()
+    p = torch.from_numpy(w.random_image(n * n, seed=82).astype(np.complex64))
+    y = mp.forward_host(ctx, plan, B, a, p)
+    assert tuple(y.shape) == (C, 0)
+    x = mp.adjoint_host(ctx, plan, B, a, y)
+    assert torch.count_nonzero(x).item() == 0
+
+
 def test_cartesian_rows_without_samples(ctx, mp):
     # Only every third k-space row is sampled: the adjoint's row pass skips the
     # empty rows and the pass along y reads them as zeros (the plan's row mask),

@@ -82,6 +82,10 @@ mpi_status mpi_ctx_reserve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* 
 const char* mpi_last_error(const mpi_ctx* ctx);
 /* Number of kernels this context has launched since creation (for accounting). */
 int64_t mpi_ctx_launch_count(const mpi_ctx* ctx);
+/* Bytes of device memory the context currently holds for its growable workspace
+ * and host-call staging buffer (0 until an operator call or mpi_ctx_reserve
+ * grows them); -1 for a null context.  Library bookkeeping, no paper passage. */
+int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx);
 /* Per-launch device timing: while enabled, every kernel the context launches is
  * bracketed by two CUDA events on the context's stream (16384 launches at most
  * between reads; later ones are not timed).  mpi_ctx_profile_read synchronises
@@ -206,11 +210,17 @@ mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* bas
  * the driver's allocator (cudaMalloc may synchronise the device and can fail at
  * an unpredictable point).  mpi_forward may grow the context workspace; this
  * call never allocates: its [C][N] intermediate lives in a 16 MiB static device
- * array inside the library, held by every GPU that loads the library until the
- * process exits.  Limit: C * N <= 2,097,152, else MPI_ERR_SHAPE (nothing is
- * launched).  Radial plans return MPI_ERR_UNSUPPORTED.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call,
+ * array inside the library.  mpi_ctx_create loads the module holding that array
+ * on its device (the driver loads modules lazily, and the first use would
+ * otherwise reserve the 16 MiB inside this call); from then on every GPU with a
+ * context holds the array until the process exits.  Each call asks for the
+ * array's device address (cudaGetSymbolAddress, no allocation once the module
+ * is resident) with the context's device current; after a device reset the
+ * first call loads the module again.  Make the first call before any stream
+ * capture.  Limit: C * N <= 2,097,152, else MPI_ERR_SHAPE (nothing is
+ * launched).  Radial plans and Tucker bases return MPI_ERR_UNSUPPORTED.  The
+ * expansion is mpi_forward's FP32 one (3xTF32 tensor cores where the shape
+ * fits).  Every call,
  * from any context, shares the one array: calls whose work overlaps on the GPU
  * (different streams, or concurrent host threads) race and corrupt each other's
  * results; serialise them.  The caller still passes every input and output

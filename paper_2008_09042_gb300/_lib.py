@@ -21,7 +21,7 @@ PREC = {"fp32": 0, "bf16": 1, "fp32_simt": 2}
 # Every symbol include/mpi_gb300.h declares.
 EXPORTS = [
     "mpi_ctx_create", "mpi_ctx_destroy", "mpi_ctx_set_stream", "mpi_ctx_synchronize", "mpi_ctx_reserve",
-    "mpi_last_error", "mpi_ctx_launch_count", "mpi_ctx_profile", "mpi_ctx_profile_read", "mpi_plan_create", "mpi_plan_destroy", "mpi_plan_grid_index",
+    "mpi_last_error", "mpi_ctx_launch_count", "mpi_ctx_workspace_bytes", "mpi_ctx_profile", "mpi_ctx_profile_read", "mpi_plan_create", "mpi_plan_destroy", "mpi_plan_grid_index",
     "mpi_basis_load_dense", "mpi_basis_load_tucker", "mpi_basis_destroy", "mpi_basis_expand", "mpi_forward", "mpi_adjoint",
     "mpi_jacobian", "mpi_jacobian_adjoint", "mpi_basis_project", "mpi_sm_estimate", "mpi_image_solve",
     "mpi_tv_prox", "mpi_forward_noalloc", "mpi_batch_create", "mpi_batch_run", "mpi_batch_kernel_count",
@@ -123,6 +123,8 @@ def load(path=LIB_PATH):
     lib.mpi_last_error.restype = ctypes.c_char_p
     lib.mpi_ctx_launch_count.argtypes = [vp]
     lib.mpi_ctx_launch_count.restype = i64
+    lib.mpi_ctx_workspace_bytes.argtypes = [vp]
+    lib.mpi_ctx_workspace_bytes.restype = i64
     lib.mpi_batch_kernel_count.argtypes = [vp]
     lib.mpi_batch_kernel_count.restype = i64
     _lib = lib

@@ -52,6 +52,10 @@ class Context:
     def launches(self):
         return int(self.lib.mpi_ctx_launch_count(self.h))
 
+    def workspace_bytes(self):
+        """Device bytes held by the context's growable workspace and staging buffer."""
+        return int(self.lib.mpi_ctx_workspace_bytes(self.h))
+
     FAMILIES = {"expand": 0, "uh_v": 1, "fft_rows": 2, "fft_lines": 3, "nufft": 4, "solver": 5, "other": 6}
 
     def profile(self, enable=True):

@@ -280,6 +280,10 @@ extern "C" mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_strea
     ctx->dev_err = (int*)((char*)ctx->twiddles + ((host.size() * sizeof(float2) + 127) & ~(size_t)127));
     e = cudaMemset(ctx->dev_err, 0, sizeof(int));
   }
+  // The allocation-free forward's static scratch lives in a module of its own,
+  // which the driver would otherwise load (and reserve 16 MiB for) at that
+  // call's first use; load it now, while allocating is allowed.
+  if (e == cudaSuccess) e = noalloc_preload();
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (ctx->twiddles) cudaFree(ctx->twiddles);
@@ -392,6 +396,10 @@ extern "C" const char* mpi_last_error(const mpi_ctx* ctx) {
 }
 
 extern "C" int64_t mpi_ctx_launch_count(const mpi_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+extern "C" int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx) {
+  return ctx ? (int64_t)(ctx->work_bytes + ctx->stage_bytes) : -1;
+}
 
 // ------------------------------------------------------------------- plan
 

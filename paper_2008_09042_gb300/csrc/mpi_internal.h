@@ -226,6 +226,10 @@ mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int
                           float2* partials, size_t partial_cap);
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS);
 
+// Loads the module holding the allocation-free forward's static scratch on the
+// current device (noalloc.cu); called once per context at creation.
+cudaError_t noalloc_preload();
+
 // Drop recorded solver graphs that reference `object` (a plan or basis), or all of them.
 void solver_cache_forget(mpi_ctx* ctx, const void* object);
 void solver_cache_clear(mpi_ctx* ctx);

@@ -7,10 +7,8 @@
 // (cudaMalloc may synchronise the device and can fail at an unpredictable point
 // under memory pressure).  mpi_forward grows the context workspace on demand;
 // this entry point never allocates: the per-coil intermediate lives in
-// g_noalloc_scratch below, which every GPU that loads the library holds until
-// the process exits.
-#include <mutex>
-
+// g_noalloc_scratch below, which every GPU on which a context of this library
+// is created holds from that moment until the process exits.
 #include "mpi_internal.h"
 
 namespace {
@@ -20,31 +18,29 @@ namespace {
 constexpr size_t kNoallocScratchElems = (size_t)2 << 20;
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoallocScratchElems];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-float2* g_noalloc_ptr[kMaxDevices] = {nullptr};
-
 // Device address of the scratch array on the current device.  In host code
-// g_noalloc_scratch is only a host-side stand-in, so the real address is looked
-// up once per device with that device current.
+// g_noalloc_scratch is only a host-side stand-in, so the real address is asked
+// for with the device current.  The driver loads the library's modules lazily:
+// the first lookup on a device loads the module that holds the array, which
+// reserves its 16 MiB.  mpi_ctx_create does that first lookup (noalloc_preload),
+// so that an mpi_forward_noalloc call only reads the address of a module that is
+// already resident.  The address is looked up on every call, not cached, so a
+// module loaded anew after a device reset is found where it now is.
 mpi_status noalloc_scratch(mpi_ctx* ctx, float2** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_check(ctx, e, "noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return set_err(ctx, MPI_ERR_UNSUPPORTED, "noalloc: device index too large");
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) return cuda_check(ctx, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
-                                                            "noalloc: cudaGetSymbolAddress");
-    g_noalloc_ptr[dev] = (float2*)p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return cuda_check(ctx, e == cudaSuccess ? cudaErrorInvalidSymbol : e, "noalloc: cudaGetSymbolAddress");
+  *out = (float2*)p;
   return MPI_OK;
 }
 
 }  // namespace
+
+cudaError_t noalloc_preload() {
+  void* p = nullptr;
+  return cudaGetSymbolAddress(&p, g_noalloc_scratch);
+}
 
 extern "C" mpi_status mpi_forward_noalloc(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
                                           const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y) {
@@ -65,7 +61,10 @@ extern "C" mpi_status mpi_forward_noalloc(mpi_ctx* ctx, const mpi_plan* plan, co
   mpi_status st = noalloc_scratch(ctx, &v);
   if (st) return st;
   // The expansion pass writes all C * N scratch entries before the FFT passes
-  // read them, so nothing left from an earlier call needs clearing.
+  // read them, so nothing left from an earlier call needs clearing.  The FP32
+  // expansion is the same one mpi_forward runs (3xTF32 on the tensor cores where
+  // the shape fits, else the CUDA-core kernel); its operand copy and tensor map
+  // were made with the basis, so it allocates nothing here.
   ExpandArgs a;
   a.U = basis->U;
   a.N = basis->N;
@@ -78,7 +77,7 @@ extern "C" mpi_status mpi_forward_noalloc(mpi_ctx* ctx, const mpi_plan* plan, co
   a.alpha = (const float2*)alpha;
   a.p = (const float2*)p;
   a.out = v;
-  if ((st = launch_expand(ctx, EX_FWD, a))) return st;
+  if ((st = expand(ctx, basis, EX_FWD, a, MPI_PREC_FP32))) return st;
   if (plan->ndim == 3 && (st = launch_fft_z(ctx, v, C, plan->nz, plan->ny, plan->nx, false))) return st;
   if ((st = launch_fft_cols(ctx, v, C, plan->nz, plan->ny, plan->nx, false))) return st;
   return launch_rows_fwd_gather(ctx, plan, v, C, (float2*)y);

@@ -26,6 +26,37 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def _slice(mp, ctx, n=256, q=64):
+    plan = mp.Plan(ctx, (n, n), sample_idx=w.mask_to_indices(w.poisson_disc_mask(n, n, 6, calib=(24, 24), seed=1)))
+    basis = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, q, seed=2).T)
+    return plan, basis
+
+
+def test_forward_noalloc_first_call_leaves_workspace_empty():
+    # On a fresh context, before any other operator call: the allocation-free
+    # forward must not grow the context's workspace, and its result must match
+    # the allocating forward's (called afterwards).
+    import paper_2008_09042_gb300 as mp
+    from paper_2008_09042_gb300 import _lib
+
+    lib = _lib.load()
+    ctx = mp.Context(0)
+    n, C, q = 256, 16, 64
+    plan, basis = _slice(mp, ctx, n, q)
+    assert ctx.workspace_bytes() == 0
+    a = torch.from_numpy(w.random_coefficients(C, q, seed=30).astype(np.complex64)).cuda()
+    p = torch.from_numpy(w.random_image(n * n, seed=31).astype(np.complex64)).cuda()
+    y = torch.full((C, plan.M), float("nan"), dtype=torch.complex64, device="cuda")
+    vp = ctypes.c_void_p
+    st = lib.mpi_forward_noalloc(ctx.h, plan.h, basis.h, vp(a.data_ptr()), C, vp(p.data_ptr()), vp(y.data_ptr()))
+    assert st == 0, lib.mpi_last_error(ctx.h)
+    ctx.synchronize()
+    assert ctx.workspace_bytes() == 0
+    y_ref = mp.forward(ctx, plan, basis, a, p)
+    torch.cuda.synchronize()
+    assert _rel(y, y_ref) < TOL
+
+
 def test_forward_noalloc_matches_forward_twice():
     import paper_2008_09042_gb300 as mp
     from paper_2008_09042_gb300 import _lib
@@ -33,8 +64,7 @@ def test_forward_noalloc_matches_forward_twice():
     lib = _lib.load()
     ctx = mp.Context(0)
     n, C, q = 256, 16, 64
-    plan = mp.Plan(ctx, (n, n), sample_idx=w.mask_to_indices(w.poisson_disc_mask(n, n, 6, calib=(24, 24), seed=1)))
-    basis = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, q, seed=2).T)
+    plan, basis = _slice(mp, ctx, n, q)
     vp = ctypes.c_void_p
     for call in range(2):
         a = torch.from_numpy(w.random_coefficients(C, q, seed=10 + call).astype(np.complex64)).cuda()

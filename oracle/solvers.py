@@ -68,15 +68,18 @@ def cg(apply_A, b, x0, n_iter):
 
 
 def irgn(Fs, U, y, C, q, n_outer=20, n_cg=10, a0=1.0, b0=1.0, decay=0.5,
-         floor=1e-6, gamma=1.0, scale_target=100.0):
-    """MPI-BL: returns (p, alpha, history of ||y - G(x^n)|| in the scaled units)."""
+         floor=1e-6, gamma=1.0, scale_target=100.0, p0=None, alpha0=None):
+    """MPI-BL: returns (p, alpha, history of ||y - G(x^n)|| in the scaled units).
+
+    ``p0`` / ``alpha0`` replace the default start (p = 1, alpha = 0); ``p0`` is
+    given in the units of the scaled data."""
     y = np.asarray(y, dtype=np.complex128)
     N = Fs.N
     ny = np.linalg.norm(y)
     scale = scale_target / ny if ny > 0 else 1.0
     ys = y * scale
-    p = np.ones(N, dtype=np.complex128)
-    alpha = np.zeros((C, q), dtype=np.complex128)
+    p = np.ones(N, dtype=np.complex128) if p0 is None else np.array(p0, dtype=np.complex128)
+    alpha = np.zeros((C, q), dtype=np.complex128) if alpha0 is None else np.array(alpha0, dtype=np.complex128)
     hist = []
     for n in range(n_outer):
         an = max(a0 * decay ** n, floor)
@@ -160,8 +163,12 @@ def project_ball(z, y, eps):
     return y + (eps / np.maximum(nrm, eps))[:, None] * d
 
 
-def admm_tv(Fs, s, y, eps, shape, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0, tau=2.0):
-    """MPI-L: returns (p, history of (primal, dual, rho))."""
+def admm_tv(Fs, s, y, eps, shape, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0, tau=2.0, trace=None):
+    """MPI-L: returns (p, history of (primal, dual, rho)).
+
+    ``trace``, if given, is called as trace(event, rho, u0, uk) after each dual
+    update (event "dual") and after each change of rho (event "rho"), with
+    copies of the scaled dual variables."""
     s = np.asarray(s, dtype=np.complex128)
     y = np.asarray(y, dtype=np.complex128)
     eps = np.asarray(eps, dtype=np.float64)
@@ -190,6 +197,8 @@ def admm_tv(Fs, s, y, eps, shape, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0
         Apk = Fs.fwd(s * p[None, :])
         u0 = u0 + p - z0n
         uk = uk + Apk - zkn
+        if trace is not None:
+            trace("dual", rho, u0.copy(), uk.copy())
         r_norm = np.sqrt(np.linalg.norm(p - z0n) ** 2 + np.linalg.norm(Apk - zkn) ** 2)
         s_norm = rho * np.sqrt(np.linalg.norm(p - p_prev) ** 2 + np.linalg.norm(Apk - Apk_prev) ** 2)
         hist.append((r_norm, s_norm, rho))
@@ -197,10 +206,14 @@ def admm_tv(Fs, s, y, eps, shape, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0
             rho *= tau
             u0 = u0 / tau
             uk = uk / tau
+            if trace is not None:
+                trace("rho", rho, u0.copy(), uk.copy())
         elif s_norm > mu * r_norm:
             rho /= tau
             u0 = u0 * tau
             uk = uk * tau
+            if trace is not None:
+                trace("rho", rho, u0.copy(), uk.copy())
     return p, np.array(hist)
 
 

@@ -1,21 +1,25 @@
 """Benchmark of the Maxwell Parallel Imaging encoding operator on GB300.
 
 Metric: forward + adjoint operator pairs per second (one mpi_forward plus one
-mpi_adjoint of the Maxwell-parameterised bilinear operator, Eq. 5 and its
-adjoint) on the 2D Cartesian 256 x 256, 16-coil, q = 128 workload with a
-variable-density Poisson-disc mask (R = 6, 24 x 24 calibration), complex64 data.
+mpi_adjoint of the Maxwell-parameterised bilinear operator, Eq. 5, and its
+adjoint).  The headline workload is the largest single-GPU configuration: the
+3D Cartesian 96 x 128 x 128 volume with 32 coils, a Tucker-factored basis
+(q = 256, ranks 32 / 40 / 40) and a 3D Poisson-disc mask (R = 8, 24 x 24
+calibration), complex64 data.  The 2D Cartesian 256^2 / 16-coil slice, the
+radial slice, the 64-slice batched exam and the reconstruction times are
+secondary lines under "workloads".
 
-One step = one forward + one adjoint on one slice, inputs resident in HBM.  L2
-(129 MB) is flushed between timed steps by writing a 256 MiB buffer, because
-the 67 MB FP32 basis would otherwise stay L2-resident.  Steps are timed with
-CUDA events on the library's stream; the expansion kernel's own launches are
-timed with per-launch events inside the same region (the library's profiling
-hook) for the roofline entry.
+One step = one forward + one adjoint with the inputs resident in HBM.  A
+256 MiB buffer is written between timed steps (L2 flush; the 3D volume's
+403 MB intermediates exceed L2 anyway).  Steps are timed with CUDA events on
+the library's stream.  A second run of the same steps brackets every kernel
+launch with the library's own events (on its stream) for the per-kernel times
+and the roofline entry of the dominant kernel.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
-Multi-GPU: independent replicas (one slice per rank, no collective on the data
-path); the value is the pairs of all ranks over the slowest rank's time.
+Multi-GPU: independent replicas (one volume per rank, no collective on the
+data path); the value is the pairs of all ranks over the slowest rank's time.
 """
 
 import argparse
@@ -36,6 +40,7 @@ import numpy as np  # noqa: E402
 
 import workloads as w  # noqa: E402
 
+HEADLINE = "cart3d_128x128x96_c32_tucker256"
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
@@ -46,16 +51,15 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cart2d_256_c16_q128")
+    ap.add_argument("--workload", default=HEADLINE, choices=[HEADLINE, "cart2d_256_c16_q128"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp32_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-secondary", action="store_true", help="skip the radial/3D/recon lines")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 2D/radial/batched/recon lines")
     ap.add_argument("--profile-workload", default=None,
-                    help="only run --steps forward+adjoint pairs of this workload (radial2d_*, cart3d_*), "
-                         "untimed, for an external profiler")
+                    help="only run --steps forward+adjoint pairs of this workload, untimed, for an external profiler")
     return ap.parse_args()
 
 
@@ -63,23 +67,109 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
-def make_inputs(name, seed_offset=0):
-    cfg = w.workload(name)
-    if cfg["kind"] != "cartesian":
-        raise SystemExit(f"bench workload {name} is not a 2D Cartesian slice")
-    ny, nx = cfg["dims"]
-    C, q = cfg["C"], cfg["q"]
-    base = w.BASE_SEED + seed_offset
-    U = w.smooth_orthonormal_basis(ny, nx, q, seed=base)
-    if cfg["mask"] == "poisson":
-        mask = w.poisson_disc_mask(ny, nx, cfg["R"], calib=cfg["calib"], seed=base + 1)
-    else:
-        mask = w.vd_lines_mask(ny, nx, cfg["R"], cfg["acs"], seed=base + 1)
-    idx = w.mask_to_indices(mask)
-    alpha = w.random_coefficients(C, q, seed=base + 2)
-    p = w.random_ellipses(ny, nx, seed=base + 3).ravel().astype(np.complex128)
-    return cfg, U, idx, alpha, p
+# ----------------------------------------------------------------- workloads
 
+def make_case(name, seed_offset=0):
+    """Seeded host inputs of one workload (a dense 2D slice or the 3D Tucker volume)."""
+    cfg = w.workload(name)
+    base = w.BASE_SEED + seed_offset
+    C, q = cfg["C"], cfg["q"]
+    case = dict(name=name, cfg=cfg, C=C, q=q, dims=tuple(cfg["dims"]))
+    if cfg["kind"] == "cartesian":
+        ny, nx = cfg["dims"]
+        case["U"] = w.smooth_orthonormal_basis(ny, nx, q, seed=base)
+        if cfg["mask"] == "poisson":
+            mask = w.poisson_disc_mask(ny, nx, cfg["R"], calib=cfg["calib"], seed=base + 1)
+        else:
+            mask = w.vd_lines_mask(ny, nx, cfg["R"], cfg["acs"], seed=base + 1)
+        case["p"] = w.random_ellipses(ny, nx, seed=base + 3).ravel().astype(np.complex128)
+        case["alpha"] = w.random_coefficients(C, q, seed=base + 2)
+        case["tucker"] = False
+        case["mask_desc"] = f"2D variable-density Poisson-disc R={cfg['R']} calib {cfg['calib']}"
+    elif cfg["kind"] == "cartesian3d":
+        dims = cfg["dims"]
+        case["core"], case["fac"] = w.smooth_tucker_basis(dims, cfg["ranks"], q, seed=base)
+        mask = w.poisson_disc_mask_3d(*dims, R=cfg["R"], calib=cfg["calib"], seed=base + 1)
+        case["alpha"] = w.random_coefficients(C, q, seed=base + 2)
+        case["p"] = w.random_ellipses(dims[1], dims[2], nz=dims[0], seed=base + 3).ravel().astype(np.complex128)
+        case["tucker"] = True
+        case["ranks"] = tuple(cfg["ranks"])
+        case["mask_desc"] = (f"3D Poisson-disc over (ky, kz) R={cfg['R']} calib {cfg['calib']}, kx fully sampled")
+    else:
+        raise SystemExit(f"{name}: not a Cartesian workload")
+    idx = w.mask_to_indices(mask)
+    case["idx"] = idx
+    case["N"] = int(np.prod(case["dims"]))
+    case["M"] = int(idx.size)
+    # fraction of k-space rows (x lines) holding samples
+    nx = case["dims"][-1]
+    rows = np.unique(idx // nx)
+    case["row_frac"] = rows.size / (case["N"] // nx)
+    return case
+
+
+def gpu_objects(mp, ctx, dev, case):
+    import torch
+
+    plan = mp.Plan(ctx, case["dims"], sample_idx=case["idx"])
+    basis = mp.TuckerBasis(ctx, case["core"], case["fac"]) if case["tucker"] else mp.Basis(ctx, case["U"].T)
+    ctx.reserve(plan, basis, case["C"])
+    a_d = torch.from_numpy(case["alpha"].astype(np.complex64)).to(dev)
+    p_d = torch.from_numpy(case["p"].astype(np.complex64)).to(dev)
+    return plan, basis, a_d, p_d
+
+
+def basis_bytes(case, prec):
+    """Bytes of the basis one expansion pass must read (dense U, or the Tucker core)."""
+    ub = 4 if prec == "bf16" else 8
+    if case["tucker"]:
+        r1, r2, r3 = case["ranks"]
+        return r1 * r2 * r3 * case["q"] * ub
+    return case["N"] * case["q"] * ub
+
+
+def pair_algorithmic_bytes(case, prec):
+    """Algorithmic bytes of one forward + adjoint pair: per direction, the basis
+    (or Tucker core) once, the per-coil image-side product once (C N complex64),
+    the k-space samples (C M complex64), the image and the coefficients."""
+    C, N, M, q = case["C"], case["N"], case["M"], case["q"]
+    return 2 * (basis_bytes(case, prec) + 8 * C * N + 8 * C * M + 8 * N + 8 * C * q)
+
+
+def kernel_bytes_per_pair(case, prec):
+    """Algorithmic DRAM bytes per forward + adjoint pair of each kernel (by the
+    name the library's per-kernel timing reports), for the roofline entry."""
+    C, N, M, q = case["C"], case["N"], case["M"], case["q"]
+    V = 8 * C * N          # one complex64 volume (or slice) per coil
+    Y = 8 * C * M          # the k-space samples
+    P = 8 * N              # the image
+    f = case["row_frac"]   # k-space rows with samples
+    out = {
+        "k_fft_lines<z,fwd>": 2 * V, "k_fft_lines<z,inv>": 2 * V,
+        "k_fft_lines<y,fwd>": V * (1 + f), "k_fft_lines<y,inv>": V * (1 + f),
+        "k_rows_fwd_gather": f * V + Y, "k_rows_scatter_inv": Y + f * V,
+        "k_pointwise<fwd>": 2 * V + P, "k_pointwise<adj>": 2 * V + P,
+    }
+    if case["tucker"]:
+        n1, n2, n3 = case["dims"]
+        r1, r2, r3 = case["ranks"]
+        R = r1 * r2 * r3
+        ob = 2 if prec == "bf16" else 4
+        tc = "k_expand_tc" if prec == "bf16" else "k_expand_tf32x3"
+        # per pair: the forward's and the adjoint's map chains
+        out[f"{tc}<tucker core>"] = 2 * (basis_bytes(case, prec) + 8 * C * q + 8 * C * R)
+        out["k_mode_last"] = 2 * (8 * C * R + 8 * C * r1 * r2 * n3)
+        out["k_mode_b"] = 2 * (8 * C * r1 * r2 * n3 + 8 * C * r1 * n2 * n3)
+        out["k_x1_operand"] = 2 * (8 * C * r1 * n2 * n3 + ob * C * n2 * n3 * 2 * r1)
+        out[f"{tc}<tucker x1>"] = 2 * (ob * C * n2 * n3 * 2 * r1 + V)
+    else:
+        per = basis_bytes(case, prec) + 8 * C * q + V + P
+        for k in ("k_expand_tf32x3", "k_expand_tc", "k_expand"):
+            out[k] = 2 * per
+    return out
+
+
+# ------------------------------------------------------------- measurement
 
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while running."""
@@ -141,70 +231,18 @@ def load_peaks():
     return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it still matches
-    the kernel's source; else None."""
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, if it was taken on the kernel's current source; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path)).get(kernel)
+    d = json.load(open(path)).get(f"{workload}/{kernel}")
     if not d:
         return None
     src = os.path.join(ROOT, "paper_2008_09042_gb300", "csrc", d["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     return d["bytes_per_launch"] if sha == d.get("source_sha") else None
-
-
-def size_matched_read(nbytes, flush, stream, reps=10):
-    """The read ceiling at the expansion's own working-set size: a device-wide
-    torch reduction over `nbytes` of FP32 after the same L2 flush the timed
-    steps use (the flush leaves L2 full of dirty lines, whose write-back every
-    cold read pays for).  Median of `reps`, CUDA events on `stream`."""
-    import torch
-    x = torch.ones(max(int(nbytes) // 4, 1), dtype=torch.float32, device=flush.device)
-    for _ in range(3):
-        x.sum()
-    ts = []
-    with torch.cuda.stream(stream):
-        for _ in range(reps):
-            flush.zero_()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            x.sum()
-            e.record(stream)
-            e.synchronize()
-            ts.append(s.elapsed_time(e) * 1e-3)
-    t = statistics.median(ts)
-    del x
-    return {"bytes": int(nbytes), "us": t * 1e6, "GB/s": nbytes / t / 1e9,
-            "how": "torch.sum over the same bytes (fp32) after the same 256 MiB L2 flush, median of 10"}
-
-
-def cpu_oracle_pairs(cfg, U, idx, alpha, p, budget_s=12.0, max_pairs=200):
-    """Forward+adjoint pairs/s of the FP64 oracle on this host (bounded sample)."""
-    from oracle import fourier, operator as op
-
-    Fs = fourier.CartesianSampling(cfg["dims"], idx)
-    n = 0
-    t0 = time.perf_counter()
-    while n < max_pairs:
-        y = op.forward(Fs, U, alpha, p)
-        op.adjoint(Fs, U, alpha, y)
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return n / dt, n, dt
-
-
-def blas_threads():
-    try:
-        from threadpoolctl import threadpool_info
-
-        info = threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] or [1])
-    except Exception:
-        return os.cpu_count()
 
 
 def reduce_max(value, device=None):
@@ -224,51 +262,152 @@ def replica_throughput(world, units_per_rank, slowest_ms):
     return world * units_per_rank / (slowest_ms / 1000.0)
 
 
-def time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, steps, warmup, flush, stream, breakdown=None):
-    """Mean ms of one forward + adjoint pair (CUDA events, L2 flushed between pairs).
+def run_pair(mp, ctx, plan, basis, a_d, p_d, prec, y, x):
+    mp.forward(ctx, plan, basis, a_d, p_d, prec, out=y)
+    mp.adjoint(ctx, plan, basis, a_d, y, prec, out=x)
 
-    With ``breakdown`` (a dict), a second pass with the library's per-launch
-    events fills it with the mean ms per pair of each kernel family."""
+
+def time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, steps, warmup, flush, stream):
+    """Mean ms of one forward + adjoint pair (CUDA events, L2 flushed between pairs)."""
     import torch
 
     C = a_d.shape[0]
     y = torch.empty((C, plan.M), dtype=torch.complex64, device=a_d.device)
     x = torch.empty((plan.N,), dtype=torch.complex64, device=a_d.device)
     for _ in range(warmup):
-        mp.forward(ctx, plan, basis, a_d, p_d, prec, out=y)
-        mp.adjoint(ctx, plan, basis, a_d, y, prec, out=x)
+        run_pair(mp, ctx, plan, basis, a_d, p_d, prec, y, x)
     torch.cuda.synchronize()
     total = 0.0
     for _ in range(steps):
         flush.zero_()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        mp.forward(ctx, plan, basis, a_d, p_d, prec, out=y)
-        mp.adjoint(ctx, plan, basis, a_d, y, prec, out=x)
+        run_pair(mp, ctx, plan, basis, a_d, p_d, prec, y, x)
         e.record(stream)
         e.synchronize()
         total += s.elapsed_time(e)
     ctx.synchronize()
-    if breakdown is not None:
-        ctx.profile(True)
-        ctx.profile_read(reset=True)
-        for _ in range(steps):
-            flush.zero_()
-            mp.forward(ctx, plan, basis, a_d, p_d, prec, out=y)
-            mp.adjoint(ctx, plan, basis, a_d, y, prec, out=x)
-        prof = ctx.profile_read(reset=True)
-        ctx.profile(False)
-        breakdown.update({k: v[0] / steps for k, v in prof.items() if v[1]})
     return total / steps
 
 
-def secondary_workloads(mp, ctx, dev, flush, stream, steps=10, warmup=3):
-    """Forward+adjoint pairs/s on the other workloads (radial, 3D Tucker, 64^2)."""
+def kernel_profile(mp, ctx, plan, basis, a_d, p_d, prec, steps, flush):
+    """Per-kernel device time over `steps` pairs, each launch bracketed by the
+    library's events on its stream: {name: {ms_per_pair, launches_per_pair,
+    us_per_launch}} and the family sums."""
     import torch
 
+    C = a_d.shape[0]
+    y = torch.empty((C, plan.M), dtype=torch.complex64, device=a_d.device)
+    x = torch.empty((plan.N,), dtype=torch.complex64, device=a_d.device)
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    for _ in range(steps):
+        flush.zero_()
+        run_pair(mp, ctx, plan, basis, a_d, p_d, prec, y, x)
+    fam, kern = ctx.profile_read(reset=True, kernels=True)
+    ctx.profile(False)
+    per = {k: {"ms_per_pair": v[0] / steps, "launches_per_pair": v[1] / steps, "us_per_launch": 1e3 * v[0] / v[1]}
+           for k, v in kern.items() if v[1]}
+    return per, {k: v[0] / steps for k, v in fam.items() if v[1]}
+
+
+def roofline_entry(case, prec, per_kernel, hbm_gbs, peak_src, workload):
+    """Roofline of the dominant kernel (largest share of the pair's kernel time)
+    whose algorithmic bytes are tabulated; every kernel is HBM-bound here."""
+    table = kernel_bytes_per_pair(case, prec)
+    total = sum(v["ms_per_pair"] for v in per_kernel.values())
+    ranked = sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms_per_pair"])
+    for name, v in ranked:
+        if name not in table:
+            continue
+        b_launch = table[name] / v["launches_per_pair"]
+        t_launch = v["us_per_launch"] * 1e-6
+        achieved = b_launch / t_launch / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+                "traffic": ncu_traffic(name, workload), "kernel": name,
+                "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": b_launch, "avg_launch_us": v["us_per_launch"],
+                "launches_per_pair": v["launches_per_pair"],
+                "share_of_kernel_time": v["ms_per_pair"] / total if total else None,
+                "dominant_overall": ranked[0][0]}
+    return None
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_pairs(case, budget_s=15.0, sample_coils=None, max_pairs=50):
+    """Forward+adjoint pairs/s of the FP64 oracle in its fast mode (scipy.fft
+    with every host core, threaded BLAS) on this host, over a bounded sample:
+    whole pairs restricted to `sample_coils` coils (the per-coil work dominates;
+    the value is scaled to whole pairs by sample_coils / C)."""
+    from oracle import fourier, operator as op, tucker
+
+    C = case["C"]
+    cs = min(sample_coils or C, C)
+    Fs = fourier.CartesianSamplingFFT(case["dims"], case["idx"])
+    U = tucker.TuckerBasis(case["core"], case["fac"]) if case["tucker"] else case["U"]
+    a = case["alpha"][:cs]
+    p = case["p"]
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_pairs:
+        y = op.forward(Fs, U, a, p)
+        op.adjoint(Fs, U, a, y)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    value = n * (cs / C) / dt
+    desc = (f"{n} forward+adjoint pairs of the {case['name']} workload restricted to {cs} of its {C} coils "
+            f"({dt:.1f} s; value scaled by {cs}/{C}); complex128 numpy oracle, fast mode: scipy.fft with "
+            f"{os.cpu_count()} workers, threaded BLAS")
+    return value, desc
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def host_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [os.cpu_count() or 1])
+    except Exception:
+        return os.cpu_count()
+
+
+# --------------------------------------------------------- secondary lines
+
+def slice_line(mp, ctx, dev, flush, stream, name, prec_list=("fp32", "bf16"), steps=10, warmup=3):
+    """A 2D Cartesian workload: pairs/s per precision, with the roofline of its
+    dominant kernel."""
+    case = make_case(name)
+    plan, basis, a_d, p_d = gpu_objects(mp, ctx, dev, case)
+    hbm, _, src = load_peaks()
     out = {}
+    for prec in prec_list:
+        ms = time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, steps, warmup, flush, stream)
+        per, _ = kernel_profile(mp, ctx, plan, basis, a_d, p_d, prec, steps, flush)
+        out[prec] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms,
+                     "roofline": roofline_entry(case, prec, per, hbm, src, name),
+                     "kernels": {k: round(v["ms_per_pair"] * 1e3, 2) for k, v in per.items()},
+                     "pair_hbm_frac": pair_algorithmic_bytes(case, prec) / (ms * 1e-3) / 1e9 / hbm}
+    return out
+
+
+def radial_line(mp, ctx, dev, flush, stream, steps=10, warmup=3):
+    """radial 256^2, 12 coils, q = 96, 64 golden-angle spokes x 512 samples, KB W = 6, sigma = 2."""
+    import torch
+
     base = w.BASE_SEED
-    # radial 256^2, 12 coils, q = 96, 64 golden-angle spokes x 512 samples, KB W = 6, sigma = 2
     cfg = w.workload("radial2d_256_c12_q96")
     n = cfg["dims"][0]
     k = w.golden_angle_radial(cfg["spokes"], cfg["readout"]).astype(np.float32)
@@ -276,37 +415,20 @@ def secondary_workloads(mp, ctx, dev, flush, stream, steps=10, warmup=3):
     B = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, cfg["q"], seed=base).T)
     a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 1).astype(np.complex64)).to(dev)
     p = torch.from_numpy(w.random_ellipses(n, n, seed=base + 2).ravel().astype(np.complex64)).to(dev)
+    out = {}
     for prec in ("fp32", "bf16"):
-        bd = {}
-        ms = time_pairs(mp, ctx, plan, B, a, p, prec, steps, warmup, flush, stream, bd)
-        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms,
-                                        "kernel_ms_per_pair": bd}
-    del plan, B
-    # 3D 96 x 128 x 128, 32 coils, Tucker q = 256, ranks (32, 40, 40), 3D Poisson-disc R = 8
-    cfg = w.workload("cart3d_128x128x96_c32_tucker256")
-    dims = cfg["dims"]
-    core, fac = w.smooth_tucker_basis(dims, cfg["ranks"], cfg["q"], seed=base)
-    mask = w.poisson_disc_mask_3d(*dims, R=cfg["R"], calib=cfg["calib"], seed=base + 1)
-    plan = mp.Plan(ctx, dims, sample_idx=w.mask_to_indices(mask))
-    B = mp.TuckerBasis(ctx, core, fac)
-    N = int(np.prod(dims))
-    a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 2).astype(np.complex64)).to(dev)
-    p = torch.from_numpy(w.random_ellipses(dims[1], dims[2], nz=dims[0], seed=base + 3).ravel()
-                         .astype(np.complex64)).to(dev)
-    ctx.reserve(plan, B, cfg["C"])
-    for prec in ("fp32", "bf16"):
-        bd = {}
-        ms = time_pairs(mp, ctx, plan, B, a, p, prec, max(3, steps // 2), 2, flush, stream, bd)
-        out[f"{cfg['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms,
-                                        "kernel_ms_per_pair": bd}
-    del plan, B
+        ms = time_pairs(mp, ctx, plan, B, a, p, prec, steps, warmup, flush, stream)
+        per, _ = kernel_profile(mp, ctx, plan, B, a, p, prec, steps, flush)
+        out[prec] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms,
+                     "kernels": {k: round(v["ms_per_pair"] * 1e3, 2) for k, v in per.items()}}
     return out
 
 
 def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
     """The 64-slice mixed exam: grids from {128, 192, 256, 320}^2, coils from
     {8, 16, 32}, q by grid size, Poisson-disc R in 4..8; all slices' forward +
-    adjoint replayed as one CUDA graph.  Returns slices/s per precision."""
+    adjoint replayed as one CUDA graph.  Slice pairs/s per precision, and the
+    exam's algorithmic bytes over its time against HBM peak."""
     import torch
 
     cfg = w.workload("batched2d_64slices")
@@ -316,6 +438,7 @@ def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
     Rs = rng.integers(cfg["R_range"][0], cfg["R_range"][1] + 1, size=cfg["slices"])
     bases, masks = {}, {}
     slices = []
+    exam_bytes = {"fp32": 0, "bf16": 0}
     for i in range(cfg["slices"]):
         n, C, R = int(sizes[i]), int(coils[i]), int(Rs[i])
         q = cfg["q_by_size"][n]
@@ -330,6 +453,10 @@ def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
         slices.append(dict(plan=plan, basis=bases[n], alpha=a, p=p,
                            y=torch.empty((C, plan.M), dtype=torch.complex64, device=dev),
                            x=torch.empty((n * n,), dtype=torch.complex64, device=dev)))
+        for prec in exam_bytes:
+            ub = 4 if prec == "bf16" else 8
+            exam_bytes[prec] += 2 * (n * n * q * ub + 8 * C * n * n + 8 * C * plan.M + 8 * n * n + 8 * C * q)
+    hbm, _, src = load_peaks()
     out = {"slices": cfg["slices"], "coils_total": int(coils.sum()),
            "grid_counts": {int(k): int((sizes == k).sum()) for k in cfg["sizes"]}}
     for prec in ("fp32", "bf16"):
@@ -348,8 +475,13 @@ def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
             total += s.elapsed_time(e)
         ctx.synchronize()
         ms = total / steps
+        achieved = exam_bytes[prec] / (ms * 1e-3) / 1e9
         out[prec] = {"value": cfg["slices"] * 1000.0 / ms, "unit": "slice pairs/s", "ms_per_exam": ms,
-                     "graph_kernels": batch.kernels()}
+                     "graph_kernels": batch.kernels(),
+                     "roofline": {"bound": "hbm", "kernel": "whole exam (every kernel of the replayed graph)",
+                                  "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                  "algorithmic_bytes_per_exam": exam_bytes[prec], "traffic": None,
+                                  "peak_source": f"{src} HBM copy bandwidth"}}
         batch.close()
     return out
 
@@ -394,32 +526,41 @@ def recon_per_slice(mp, ctx, dev, prec_list=("fp32", "bf16"), reps=2):
     return {"workload": cfg["name"], "iterations": "20 IRGN x 10 CG + 50 ADMM x 5 CG x 10 TV", **res}
 
 
+# --------------------------------------------------------------------- arms
+
 def run_reference(args):
+    """The oracle (this build's reference arm: the paper ships no code) timed on
+    the host cores in its fast mode; each step one forward+adjoint pair of the
+    workload restricted to a few coils, the value scaled to whole pairs."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    cfg, U, idx, alpha, p = make_inputs(args.workload)
-    from oracle import fourier, operator as op
+    case = make_case(args.workload)
+    from oracle import fourier, operator as op, tucker
 
-    Fs = fourier.CartesianSampling(cfg["dims"], idx)
+    C = case["C"]
+    cs = min(4, C)
+    Fs = fourier.CartesianSamplingFFT(case["dims"], case["idx"])
+    U = tucker.TuckerBasis(case["core"], case["fac"]) if case["tucker"] else case["U"]
+    a, p = case["alpha"][:cs], case["p"]
     for _ in range(args.warmup):
-        op.adjoint(Fs, U, alpha, op.forward(Fs, U, alpha, p))
+        op.adjoint(Fs, U, a, op.forward(Fs, U, a, p))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        op.adjoint(Fs, U, alpha, op.forward(Fs, U, alpha, p))
+        op.adjoint(Fs, U, a, op.forward(Fs, U, a, p))
     dt = time.perf_counter() - t0
-    value = args.steps / dt
-    cores = blas_threads()
+    value = args.steps * (cs / C) / dt
+    sample = (f"each step one forward+adjoint pair of the {case['name']} workload restricted to {cs} of its {C} "
+              f"coils (value scaled by {cs}/{C}); complex128 numpy oracle, fast mode: scipy.fft with "
+              f"{os.cpu_count()} workers, threaded BLAS")
     line = {
         "impl": "reference", "metric": "MPI forward+adjoint operator pairs per second",
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "N": int(np.prod(cfg["dims"])), "C": cfg["C"], "q": cfg["q"],
-                   "M": int(idx.size)},
-        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} full forward+adjoint pairs of the workload (complex128, "
-                                   f"explicit DFT matrices, numpy BLAS)"},
+        "config": {"workload": case["name"], "N": case["N"], "C": C, "q": case["q"], "M": case["M"]},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": host_threads(), "kind": "oracle",
+                         "cpu": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -438,24 +579,18 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     import paper_2008_09042_gb300 as mp
 
-    cfg, U, idx, alpha, p = make_inputs(args.workload, seed_offset=rank)
-    C, q = cfg["C"], cfg["q"]
-    N, M = U.shape[0], int(idx.size)
+    case = make_case(args.workload, seed_offset=rank)
+    C, q, N, M = case["C"], case["q"], case["N"], case["M"]
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = mp.Context(local_rank, stream=stream)
-    plan = mp.Plan(ctx, cfg["dims"], sample_idx=idx)
-    basis = mp.Basis(ctx, U.T)
-    ctx.reserve(plan, basis, C)
-    a_d = torch.from_numpy(alpha.astype(np.complex64)).to(dev)
-    p_d = torch.from_numpy(p.astype(np.complex64)).to(dev)
+    plan, basis, a_d, p_d = gpu_objects(mp, ctx, dev, case)
     y_d = torch.empty((C, M), dtype=torch.complex64, device=dev)
     x_d = torch.empty((N,), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step():
-        mp.forward(ctx, plan, basis, a_d, p_d, args.prec, out=y_d)
-        mp.adjoint(ctx, plan, basis, a_d, y_d, args.prec, out=x_d)
+        run_pair(mp, ctx, plan, basis, a_d, p_d, args.prec, y_d, x_d)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -487,21 +622,14 @@ def run_ours(args):
     # Per-launch kernel durations: the same K steps again, each launch bracketed by
     # the library's own events on its stream.  A separate region, because the
     # extra event records between launches slow the step they sit in.
-    ctx.profile(True)
-    ctx.profile_read(reset=True)
-    for k in range(args.steps):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
+    per_kernel, families = kernel_profile(mp, ctx, plan, basis, a_d, p_d, args.prec, args.steps, flush)
     clk = clocks.stop()
-    prof = ctx.profile_read(reset=True)
-    ctx.profile(False)
 
     # ---- end to end through the C ABI's host-buffer calls (mpi_forward_host,
     # mpi_adjoint_host): pinned host inputs in, host outputs back, each call
     # returning once its result is in host memory.  Host wall clock per step.
-    a_h = torch.from_numpy(alpha.astype(np.complex64)).pin_memory()
-    p_h = torch.from_numpy(p.astype(np.complex64)).pin_memory()
+    a_h = torch.from_numpy(case["alpha"].astype(np.complex64)).pin_memory()
+    p_h = torch.from_numpy(case["p"].astype(np.complex64)).pin_memory()
     y_h = torch.empty((C, M), dtype=torch.complex64).pin_memory()
     x_h = torch.empty((N,), dtype=torch.complex64).pin_memory()
 
@@ -524,76 +652,53 @@ def run_ours(args):
     h2d = (2 * C * q + N + C * M) * 8  # alpha for each call, p, y
     d2h = (C * M + N) * 8
 
-    # ---- roofline of the dominant kernel (the basis expansion, forward and adjoint launches)
     hbm_gbs, bf16_tflops, peak_src = load_peaks()
-    ex_ms, ex_n = prof["expand"]
-    fam_total = sum(v[0] for v in prof.values())
-    ex_avg_s = ex_ms / max(ex_n, 1) / 1000.0
-    # per launch: read U (N q complex; 8 B per element in FP32, 4 B as BF16), alpha (C q),
-    # the image or the per-coil data (C N + N complex64), write the per-coil data or the image
-    u_bytes = 4 if args.prec == "bf16" else 8
-    ex_bytes = N * q * u_bytes + (C * q + C * N + N) * 8
-    ex_flops = 8.0 * N * q * C
-    t_hbm = ex_bytes / (hbm_gbs * 1e9)
-    hbm_roof = {"bound": "hbm", "achieved": ex_bytes / ex_avg_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
-                "peak_source": f"{peak_src} HBM copy bandwidth"}
-    if args.prec == "fp32_simt" and ex_flops / (FP32_ALU_TFLOPS * 1e12) >= t_hbm:
-        roof = {"bound": "alu", "achieved": ex_flops / ex_avg_s / 1e12, "peak": FP32_ALU_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-        kname = "k_expand (CUDA-core FFMA expansion fused with the point-wise products)"
-    elif args.prec == "fp32":
-        # three TF32 products per term; TF32 tensor rate = bf16 rate x 1.1 / 2.25 (nominal ratio)
-        tf32_tflops = bf16_tflops * 1.1 / 2.25
-        if 3 * ex_flops / (tf32_tflops * 1e12) > t_hbm:
-            roof = {"bound": "tensor", "achieved": 3 * ex_flops / ex_avg_s / 1e12, "peak": tf32_tflops,
-                    "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 x nominal tf32/bf16 ratio"}
-        else:
-            roof = hbm_roof
-        kname = "k_expand_tf32x3 (3xTF32 tcgen05 expansion fused with the point-wise products)"
+    roof = roofline_entry(case, args.prec, per_kernel, hbm_gbs, peak_src, case["name"])
+    pair_bytes = pair_algorithmic_bytes(case, args.prec)
+    ms_pair = total_ms / args.steps
+    if case["tucker"]:
+        basis_desc = (f"smooth orthonormal stand-in of the Maxwell basis shape, Tucker-factored: core "
+                      f"{case['ranks']} x q={q}, factors {case['dims'][0]}x{case['ranks'][0]}, "
+                      f"{case['dims'][1]}x{case['ranks'][1]}, {case['dims'][2]}x{case['ranks'][2]} (complex64)")
     else:
-        roof = hbm_roof
-        kname = "k_expand_tc (BF16 tcgen05 expansion fused with the point-wise products)"
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = kname
-    roof["algorithmic_bytes_per_launch"] = ex_bytes
-    roof["algorithmic_flops_per_launch"] = ex_flops
-    roof["avg_launch_us"] = ex_avg_s * 1e6
-    roof["share_of_kernel_time"] = ex_ms / fam_total if fam_total > 0 else None
-    roof["traffic"] = ncu_traffic(kname.split()[0])
-    roof["size_matched_read"] = size_matched_read(ex_bytes, flush, stream)
-
+        basis_desc = "smooth orthonormal stand-in of the Maxwell basis shape (complex64 [q][N])"
     line = {
         "metric": "MPI forward+adjoint operator pairs per second",
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": ms_pair, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16+f32" if args.prec == "bf16" else "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "N": N, "C": C, "q": q, "M": M,
-                   "mask": f"2D variable-density Poisson-disc R={cfg.get('R')} calib {cfg.get('calib')}",
-                   "basis": "smooth orthonormal stand-in of the Maxwell basis shape (complex64 [q][N])",
-                   "expansion_precision": args.prec, "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}"},
+        "config": {"workload": case["name"], "dims": list(case["dims"]), "N": N, "C": C, "q": q, "M": M,
+                   "mask": case["mask_desc"], "basis": basis_desc, "expansion_precision": args.prec,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "roofline": roof,
+        "pair_roofline": {"bound": "hbm", "algorithmic_bytes_per_pair": pair_bytes,
+                          "achieved": pair_bytes / (ms_pair * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                          "frac": pair_bytes / (ms_pair * 1e-3) / 1e9 / hbm_gbs},
+        "kernel_us_per_pair": {k: round(v["ms_per_pair"] * 1e3, 1) for k, v in
+                               sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms_per_pair"])},
         "clocks": clk,
     }
     if not args.no_secondary:
-        line["workloads"] = secondary_workloads(mp, ctx, dev, flush, stream)
-        for other in ("fp32", "fp32_simt", "bf16"):
-            if other != args.prec:
-                bd = {}
-                ms = time_pairs(mp, ctx, plan, basis, a_d, p_d, other, 10, 3, flush, stream, bd)
-                line["workloads"][f"{args.workload}/{other}"] = {"value": 1000.0 / ms, "unit": "pairs/s",
-                                                                 "ms_per_pair": ms, "kernel_ms_per_pair": bd}
-        line["workloads"]["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
+        wl = {}
+        others = {HEADLINE, "cart2d_256_c16_q128"} - {case["name"]}
+        for other in sorted(others):
+            wl[other] = slice_line(mp, ctx, dev, flush, stream, other) if other != HEADLINE else None
+        if case["name"] == HEADLINE:
+            for prec in ("bf16",):
+                ms = time_pairs(mp, ctx, plan, basis, a_d, p_d, prec, max(3, args.steps // 2), 2, flush, stream)
+                wl[f"{case['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms}
+        wl = {k: v for k, v in wl.items() if v is not None}
+        wl["radial2d_256_c12_q96"] = radial_line(mp, ctx, dev, flush, stream)
+        wl["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
+        line["workloads"] = wl
         line["recon"] = recon_per_slice(mp, ctx, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, n, dt = cpu_oracle_pairs(cfg, U, idx, alpha, p)
-        line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": blas_threads(), "kind": "oracle",
-                                "sample": f"{n} forward+adjoint pairs of the same workload in {dt:.1f} s "
-                                          f"(complex128 numpy oracle)"}
+        v, desc = cpu_oracle_pairs(case, sample_coils=4 if case["tucker"] else None)
+        line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": host_threads(), "kind": "oracle",
+                                "cpu": cpu_model(), "sample": desc}
     if world > 1:
         import torch.distributed as dist
 
@@ -604,38 +709,32 @@ def run_ours(args):
 
 
 def profile_workload(args):
-    """Forward+adjoint pairs of one secondary workload, nothing timed: the command
-    an external profiler (ncu) wraps to capture that workload's kernels."""
+    """Forward+adjoint pairs of one workload, nothing timed: the command an
+    external profiler (ncu) wraps to capture that workload's kernels."""
     import torch
     import paper_2008_09042_gb300 as mp
 
     dev = torch.device("cuda", 0)
     ctx = mp.Context(0)
     base = w.BASE_SEED
-    cfg = w.workload(args.profile_workload)
-    if cfg["name"].startswith("cart3d"):
-        dims = cfg["dims"]
-        core, fac = w.smooth_tucker_basis(dims, cfg["ranks"], cfg["q"], seed=base)
-        mask = w.poisson_disc_mask_3d(*dims, R=cfg["R"], calib=cfg["calib"], seed=base + 1)
-        plan = mp.Plan(ctx, dims, sample_idx=w.mask_to_indices(mask))
-        B = mp.TuckerBasis(ctx, core, fac)
-        p = w.random_ellipses(dims[1], dims[2], nz=dims[0], seed=base + 3).ravel()
-    elif cfg["name"].startswith("radial2d"):
+    name = args.profile_workload
+    if name.startswith("radial2d"):
+        cfg = w.workload(name)
         n = cfg["dims"][0]
         k = w.golden_angle_radial(cfg["spokes"], cfg["readout"]).astype(np.float32)
         plan = mp.Plan(ctx, (n, n), traj=k, kb_width=cfg["W"], oversamp=cfg["sigma"])
         B = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, cfg["q"], seed=base).T)
-        p = w.random_ellipses(n, n, seed=base + 2).ravel()
+        a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 2).astype(np.complex64)).to(dev)
+        pd = torch.from_numpy(w.random_ellipses(n, n, seed=base + 2).ravel().astype(np.complex64)).to(dev)
+        ctx.reserve(plan, B, cfg["C"])
     else:
-        raise SystemExit(f"--profile-workload: {cfg['name']} is not a radial2d_* or cart3d_* workload")
-    a = torch.from_numpy(w.random_coefficients(cfg["C"], cfg["q"], seed=base + 2).astype(np.complex64)).to(dev)
-    pd = torch.from_numpy(p.astype(np.complex64)).to(dev)
-    ctx.reserve(plan, B, cfg["C"])
+        case = make_case(name)
+        plan, B, a, pd = gpu_objects(mp, ctx, dev, case)
     for _ in range(args.steps):
         y = mp.forward(ctx, plan, B, a, pd, args.prec)
         mp.adjoint(ctx, plan, B, a, y, args.prec)
     ctx.synchronize()
-    print(f"{cfg['name']}: {args.steps} forward+adjoint pairs ({args.prec})", flush=True)
+    print(f"{name}: {args.steps} forward+adjoint pairs ({args.prec})", flush=True)
     return 0
 
 

@@ -96,6 +96,13 @@ int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx);
 mpi_status mpi_ctx_profile(mpi_ctx* ctx, int enable);
 mpi_status mpi_ctx_profile_read(mpi_ctx* ctx, int family, double* ms_out, int64_t* launches_out,
                                 int reset);
+/* Per-kernel sums of the same timing: entry `index` (0, 1, ... in order of first
+ * launch) gives the kernel's name (valid until the next reset), its summed device
+ * time (ms) and its timed launches since the last reset.  Synchronises the
+ * stream.  MPI_ERR_ARG once `index` is past the last kernel.  Library
+ * bookkeeping, no paper passage. */
+mpi_status mpi_ctx_profile_kernel(mpi_ctx* ctx, int index, const char** name_out, double* ms_out,
+                                  int64_t* launches_out);
 
 /* ------------------------------------------------------------------- plan */
 

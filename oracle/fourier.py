@@ -65,6 +65,41 @@ class CartesianSampling:
         return idft(k.reshape(lead + self.shape), len(self.shape)).reshape(lead + (self.N,))
 
 
+class CartesianSamplingFFT(CartesianSampling):
+    """The same F_s as ``CartesianSampling`` with the centred DFT taken by FFTs
+    (``scipy.fft``, ``workers`` threads): the oracle's fast mode, used only to
+    time a CPU baseline.  The centred transform is the plain DFT of the
+    index-shifted array, shifted back: F_c v = fftshift(fft(ifftshift(v))) with
+    the unitary scale; pinned against the explicit matrices by the tests."""
+
+    def __init__(self, shape, idx, workers=None):
+        super().__init__(shape, idx)
+        import os
+
+        self.workers = workers or os.cpu_count()
+
+    def _fft(self, v, inverse):
+        import scipy.fft as sfft
+
+        axes = tuple(range(v.ndim - len(self.shape), v.ndim))
+        v = sfft.ifftshift(v, axes=axes)
+        v = (sfft.ifftn if inverse else sfft.fftn)(v, axes=axes, norm="ortho", workers=self.workers)
+        return sfft.fftshift(v, axes=axes)
+
+    def fwd(self, v):
+        v = np.asarray(v, dtype=np.complex128)
+        lead = v.shape[:-1]
+        k = self._fft(v.reshape(lead + self.shape), False).reshape(lead + (self.N,))
+        return k[..., self.idx]
+
+    def adj(self, y):
+        y = np.asarray(y, dtype=np.complex128)
+        lead = y.shape[:-1]
+        k = np.zeros(lead + (self.N,), dtype=np.complex128)
+        k[..., self.idx] = y
+        return self._fft(k.reshape(lead + self.shape), True).reshape(lead + (self.N,))
+
+
 class DirectNUDFT:
     """Direct non-uniform DFT for 2D radial sampling.
 

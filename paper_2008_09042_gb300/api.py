@@ -61,19 +61,31 @@ class Context:
     def profile(self, enable=True):
         check(self.h, self.lib.mpi_ctx_profile(self.h, 1 if enable else 0))
 
-    def profile_read(self, reset=False):
-        """{family: (ms, launches)} summed since the last reset."""
+    def profile_read(self, reset=False, kernels=False):
+        """{family: (ms, launches)} summed since the last reset; with ``kernels``
+        also {kernel name: (ms, launches)}, returned as a second value."""
         out = {}
         for name, fam in self.FAMILIES.items():
             ms = ctypes.c_double()
             n = ctypes.c_int64()
             check(self.h, self.lib.mpi_ctx_profile_read(self.h, fam, ctypes.byref(ms), ctypes.byref(n), 0))
             out[name] = (ms.value, n.value)
+        per_kernel = {}
+        if kernels:
+            i = 0
+            while True:
+                nm = ctypes.c_char_p()
+                ms = ctypes.c_double()
+                n = ctypes.c_int64()
+                if self.lib.mpi_ctx_profile_kernel(self.h, i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(n)):
+                    break
+                per_kernel[nm.value.decode()] = (ms.value, n.value)
+                i += 1
         if reset:
             ms = ctypes.c_double()
             n = ctypes.c_int64()
             check(self.h, self.lib.mpi_ctx_profile_read(self.h, 0, ctypes.byref(ms), ctypes.byref(n), 1))
-        return out
+        return (out, per_kernel) if kernels else out
 
     def reserve(self, plan, basis, C):
         check(self.h, self.lib.mpi_ctx_reserve(self.h, plan.h, basis.h, C))

@@ -69,10 +69,11 @@ void prof_begin(mpi_ctx* ctx, int family) {
   ctx->pending_family = family;
 }
 
-void prof_end(mpi_ctx* ctx) {
+void prof_end(mpi_ctx* ctx, const char* name) {
   if (!ctx->profiling || ctx->pending_family < 0 || ctx->ev_used >= (int)ctx->ev_begin.size()) return;
   cudaEventRecord(ctx->ev_end[ctx->ev_used], ctx->stream);
   ctx->ev_family[ctx->ev_used] = ctx->pending_family;
+  ctx->ev_name[ctx->ev_used] = name;
   ctx->ev_used++;
   ctx->pending_family = -1;
 }
@@ -198,7 +199,7 @@ mpi_status image_to_kspace(mpi_ctx* ctx, const mpi_plan* plan, float2* v, int C,
   mpi_status st = MPI_OK;
   if (plan->ndim == 3) st = launch_fft_z(ctx, v, C, plan->nz, plan->ny, plan->nx, false);
   if (st) return st;
-  st = launch_fft_cols(ctx, v, C, plan->nz, plan->ny, plan->nx, false);
+  st = launch_fft_cols(ctx, v, C, plan->nz, plan->ny, plan->nx, false, plan->row_has);
   if (st) return st;
   return launch_rows_fwd_gather(ctx, plan, v, C, y);
 }
@@ -349,6 +350,7 @@ extern "C" mpi_status mpi_ctx_profile(mpi_ctx* ctx, int enable) {
     ctx->ev_begin.resize(kProfileSlots);
     ctx->ev_end.resize(kProfileSlots);
     ctx->ev_family.assign(kProfileSlots, 0);
+    ctx->ev_name.assign(kProfileSlots, nullptr);
     for (int i = 0; i < kProfileSlots; ++i) {
       if (cudaEventCreate(&ctx->ev_begin[i]) != cudaSuccess || cudaEventCreate(&ctx->ev_end[i]) != cudaSuccess) {
         cudaGetLastError();
@@ -363,22 +365,41 @@ extern "C" mpi_status mpi_ctx_profile(mpi_ctx* ctx, int enable) {
   return MPI_OK;
 }
 
+namespace {
+
+// Folds the timed launches recorded since the last fold into the per-family
+// and per-kernel sums (the caller has synchronised the stream).
+void prof_fold(mpi_ctx* ctx) {
+  for (int i = 0; i < ctx->ev_used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->ev_begin[i], ctx->ev_end[i]) == cudaSuccess) {
+      ctx->prof_ms[ctx->ev_family[i]] += t;
+      ctx->prof_launches[ctx->ev_family[i]] += 1;
+      const std::string nm = ctx->ev_name[i] ? ctx->ev_name[i] : "?";
+      auto it = std::find_if(ctx->prof_kernels.begin(), ctx->prof_kernels.end(),
+                             [&](const std::pair<std::string, std::pair<double, int64_t>>& k) { return k.first == nm; });
+      if (it == ctx->prof_kernels.end()) {
+        ctx->prof_kernels.push_back({nm, {0.0, 0}});
+        it = ctx->prof_kernels.end() - 1;
+      }
+      it->second.first += t;
+      it->second.second += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  ctx->ev_used = 0;
+}
+
+}  // namespace
+
 extern "C" mpi_status mpi_ctx_profile_read(mpi_ctx* ctx, int family, double* ms, int64_t* launches, int reset) {
   if (!ctx) return MPI_ERR_ARG;
   if (family < 0 || family >= KF_COUNT || !ms || !launches) return set_err(ctx, MPI_ERR_ARG, "bad profile query");
   DeviceGuard g(ctx->device);
   mpi_status st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "profile sync");
   if (st) return st;
-  for (int i = 0; i < ctx->ev_used; ++i) {
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, ctx->ev_begin[i], ctx->ev_end[i]) == cudaSuccess) {
-      ctx->prof_ms[ctx->ev_family[i]] += t;
-      ctx->prof_launches[ctx->ev_family[i]] += 1;
-    } else {
-      cudaGetLastError();
-    }
-  }
-  ctx->ev_used = 0;
+  prof_fold(ctx);
   *ms = ctx->prof_ms[family];
   *launches = ctx->prof_launches[family];
   if (reset) {
@@ -386,7 +407,24 @@ extern "C" mpi_status mpi_ctx_profile_read(mpi_ctx* ctx, int family, double* ms,
       ctx->prof_ms[k] = 0;
       ctx->prof_launches[k] = 0;
     }
+    ctx->prof_kernels.clear();
   }
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_ctx_profile_kernel(mpi_ctx* ctx, int index, const char** name, double* ms,
+                                             int64_t* launches) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (!name || !ms || !launches) return set_err(ctx, MPI_ERR_ARG, "bad profile query");
+  DeviceGuard g(ctx->device);
+  mpi_status st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "profile sync");
+  if (st) return st;
+  prof_fold(ctx);
+  if (index < 0 || index >= (int)ctx->prof_kernels.size()) return MPI_ERR_ARG;
+  const auto& k = ctx->prof_kernels[index];
+  *name = k.first.c_str();
+  *ms = k.second.first;
+  *launches = k.second.second;
   return MPI_OK;
 }
 

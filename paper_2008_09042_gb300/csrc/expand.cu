@@ -178,7 +178,7 @@ mpi_status launch_mode(mpi_ctx* ctx, const ExpandArgs& a) {
   const long gx = std::min(grid, ((long)a.N + block - 1) / block);
   MPI_PROF(ctx, KF_EXPAND);
   launch_pdl(ctx, k_expand<MODE, CB>, dim3((unsigned)gx, gy), dim3(block), smem, a, q_pad, c_pad);
-  MPI_LAUNCH_CHECK(ctx, "k_expand");
+  MPI_LAUNCH_CHECK(ctx, a.kname ? a.kname : "k_expand");
   return MPI_OK;
 }
 

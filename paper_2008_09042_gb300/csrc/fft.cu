@@ -355,18 +355,17 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * TILE <= 2048) ? 4 : (L *
   const int cx = tid % TILE, r0 = tid / TILE;
   const bool ok = x0 + cx < nx;
   const float2* src = data + base + cx;
+  // With a row mask (rmask[z * L + r], z = slab % mask_nz: 1 where k-space row r
+  // of this slab has samples): inverse, the rows without samples are taken as
+  // zeros without being read, whatever the buffer holds there (the adjoint's
+  // row pass does not write them); forward, only the rows with samples are
+  // stored (the row pass that follows reads no other row).
+  const uint8_t* rm = rmask ? rmask + (size_t)(slab % mask_nz) * L : nullptr;
   float2 v[PER];
 #pragma unroll
-  for (int u = 0; u < PER; ++u)
-    if (ok && r0 + RSTEP * u < L) v[u] = src[(size_t)(r0 + RSTEP * u) * stride];
-  if (INV && rmask) {
-    // rows of this slab without samples (rmask[z * L + r] == 0, z = slab %
-    // mask_nz) are taken as zeros, whatever the buffer holds there: the
-    // adjoint's row pass does not write them
-    const uint8_t* rm = rmask + (size_t)(slab % mask_nz) * L;
-#pragma unroll
-    for (int u = 0; u < PER; ++u)
-      if (r0 + RSTEP * u < L && !rm[r0 + RSTEP * u]) v[u] = make_float2(0.f, 0.f);
+  for (int u = 0; u < PER; ++u) {
+    const int r = r0 + RSTEP * u;
+    if (ok && r < L) v[u] = (INV && rm && !rm[r]) ? make_float2(0.f, 0.f) : src[(size_t)r * stride];
   }
 #pragma unroll
   for (int u = 0; u < PER; ++u)
@@ -379,7 +378,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * TILE <= 2048) ? 4 : (L *
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int r = r0 + RSTEP * u;
-    if (ok && r < L) dst[(size_t)r * stride] = buf[cx * S + pad8(r)];
+    if (ok && r < L && (INV || !rm || rm[r])) dst[(size_t)r * stride] = buf[cx * S + pad8(r)];
   }
 }
 
@@ -403,8 +402,9 @@ int lines_tile(const mpi_ctx* ctx, int L, int nx, int n_slabs) {
 }
 
 template <bool INV>
-mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride, int n_slabs, int inner,
-                          long outer_stride, long inner_stride, const uint8_t* rmask = nullptr, int mask_nz = 1) {
+mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, int nx, long stride, int n_slabs,
+                          int inner, long outer_stride, long inner_stride, const uint8_t* rmask = nullptr,
+                          int mask_nz = 1) {
   const int tile = lines_tile(ctx, L, nx, n_slabs);
   const int x_tiles = (nx + tile - 1) / tile;
   const long blocks = (long)n_slabs * x_tiles;
@@ -440,7 +440,7 @@ mpi_status lines_dispatch(mpi_ctx* ctx, float2* data, int L, int nx, long stride
       return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
   }
 #undef MPI_LINES_CASE
-  MPI_LAUNCH_CHECK(ctx, "k_fft_lines");
+  MPI_LAUNCH_CHECK(ctx, name);
   return MPI_OK;
 }
 
@@ -536,8 +536,8 @@ mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, in
                            const uint8_t* row_has) {
   // lines along y: stride nx; slabs = (c, z); base = slab * ny * nx; row mask [z][y]
   const long plane = (long)ny * nx;
-  if (inverse) return lines_dispatch<true>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0, row_has, nz);
-  return lines_dispatch<false>(ctx, data, ny, nx, nx, C * nz, 1, plane, 0, row_has, nz);
+  if (inverse) return lines_dispatch<true>(ctx, "k_fft_lines<y,inv>", data, ny, nx, nx, C * nz, 1, plane, 0, row_has, nz);
+  return lines_dispatch<false>(ctx, "k_fft_lines<y,fwd>", data, ny, nx, nx, C * nz, 1, plane, 0, row_has, nz);
 }
 
 mpi_status launch_fft_cols_window(mpi_ctx* ctx, float2* grid, int C, int G, const float2* src, float2* dst,
@@ -579,8 +579,8 @@ mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int n
   // lines along z: stride ny * nx; slabs = (c, y); base = c * vol + y * nx
   const long plane = (long)ny * nx;
   const long vol = plane * nz;
-  if (inverse) return lines_dispatch<true>(ctx, data, nz, nx, plane, C * ny, ny, vol, nx);
-  return lines_dispatch<false>(ctx, data, nz, nx, plane, C * ny, ny, vol, nx);
+  if (inverse) return lines_dispatch<true>(ctx, "k_fft_lines<z,inv>", data, nz, nx, plane, C * ny, ny, vol, nx);
+  return lines_dispatch<false>(ctx, "k_fft_lines<z,fwd>", data, nz, nx, plane, C * ny, ny, vol, nx);
 }
 
 mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const float2* data, int C,

@@ -44,6 +44,8 @@ struct mpi_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_begin, ev_end;
   std::vector<int> ev_family;
+  std::vector<const char*> ev_name;  // kernel name of each timed launch (string literals)
+  std::vector<std::pair<std::string, std::pair<double, int64_t>>> prof_kernels;  // per-name sums
   int ev_used = 0;
   int pending_family = -1;
   double prof_ms[KF_COUNT] = {0};
@@ -126,8 +128,9 @@ bool fft_length_supported(int n);
 
 // Record the start event of the next launch (when profiling is on).
 void prof_begin(mpi_ctx* ctx, int family);
-// Record the end event of the launch just issued.
-void prof_end(mpi_ctx* ctx);
+// Record the end event of the launch just issued (`name`: the kernel's name,
+// a string literal, for the per-kernel sums).
+void prof_end(mpi_ctx* ctx, const char* name = nullptr);
 
 #define MPI_PROF(ctx, fam) prof_begin((ctx), (fam))
 
@@ -154,7 +157,7 @@ inline cudaError_t launch_pdl(mpi_ctx* ctx, void (*kern)(KArgs...), dim3 grid, d
 #define MPI_LAUNCH_CHECK(ctx, what)                                   \
   do {                                                                \
     (ctx)->launches++;                                                \
-    prof_end(ctx);                                                    \
+    prof_end((ctx), (what));                                          \
     cudaError_t e__ = cudaGetLastError();                             \
     if (e__ != cudaSuccess) return cuda_check((ctx), e__, (what));    \
   } while (0)
@@ -182,6 +185,7 @@ struct ExpandArgs {
   // only): pixel n = c B + b of coil row i goes to out[c tuck_stride + i B + b].
   int tuck_B = 0;
   long tuck_stride = 0;
+  const char* kname = nullptr;  // name of the launch in the per-kernel timing (default: the kernel's)
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
@@ -237,9 +241,10 @@ void solver_cache_clear(mpi_ctx* ctx);
 // ------------------------------------------------------------ FFT passes
 
 // In-place FFT along the y axis of `data` [C][nz][ny][nx] (unnormalised).
-// FFT along y of [C][nz][ny][nx].  With row_has ([nz][ny], 1 where the
-// k-space row has samples; inverse only): rows without samples are read as
-// zeros (the adjoint's row pass does not write them).
+// With row_has ([nz][ny], 1 where the k-space row has samples): inverse, rows
+// without samples are read as zeros (the adjoint's row pass does not write
+// them); forward, only rows with samples are stored (the row pass reads no
+// other row).
 mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse,
                            const uint8_t* row_has = nullptr);
 // FFT along y over the oversampled radial grid [C][G][G] with the centred

@@ -1048,15 +1048,15 @@ extern "C" mpi_status mpi_basis_project(mpi_ctx* ctx, const mpi_basis* basis, co
     MPI_PROF(ctx, KF_OTHER);
     k_gram<<<dim3((q + 7) / 8, q), dim3(32, 8), 0, ctx->stream>>>(basis->U, N, q, G);
     ctx->launches++;
-    prof_end(ctx);
+    prof_end(ctx, "k_gram");
     MPI_PROF(ctx, KF_OTHER);
     k_uh_s<<<dim3((C + 7) / 8, q), dim3(32, 8), 0, ctx->stream>>>(basis->U, N, q, (const float2*)maps, C, rhs);
     ctx->launches++;
-    prof_end(ctx);
+    prof_end(ctx, "k_uh_s");
     MPI_PROF(ctx, KF_OTHER);
     k_cholesky_solve<<<1, 1024, 0, ctx->stream>>>(G, q, rhs, C, (float2*)alpha, status);
     ctx->launches++;
-    prof_end(ctx);
+    prof_end(ctx, "k_cholesky_solve");
     e = cudaGetLastError();
   }
   int hstat = 0;

@@ -310,6 +310,6 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
       return set_err(ctx, MPI_ERR_ARG, "unknown expansion mode");
   }
 #undef MPI_TC_CASE
-  MPI_LAUNCH_CHECK(ctx, "k_expand_tc");
+  MPI_LAUNCH_CHECK(ctx, x.kname ? x.kname : "k_expand_tc");
   return MPI_OK;
 }

@@ -444,6 +444,6 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
       return set_err(ctx, MPI_ERR_ARG, "unknown expansion mode");
   }
 #undef MPI_TF_CASE
-  MPI_LAUNCH_CHECK(ctx, "k_expand_tf32x3");
+  MPI_LAUNCH_CHECK(ctx, x.kname ? x.kname : "k_expand_tf32x3");
   return MPI_OK;
 }

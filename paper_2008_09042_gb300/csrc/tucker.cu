@@ -330,6 +330,7 @@ mpi_status tucker_t2(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int 
   a.C = C;
   a.alpha = alpha;
   a.out = g;
+  a.kname = prec == MPI_PREC_BF16 ? "k_expand_tc<tucker core>" : "k_expand_tf32x3<tucker core>";
   mpi_status st = expand(ctx, b->core, EX_MAPS, a, prec);
   if (st) return st;
   if ((st = mode_last(ctx, false, g, b->F[2], C * r1 * r2, r3, n3, t1))) return st;
@@ -422,6 +423,7 @@ mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, in
   a.out = maps;
   a.tuck_B = (int)B;
   a.tuck_stride = (long)b->n[0] * B;
+  a.kname = prec == MPI_PREC_BF16 ? "k_expand_tc<tucker x1>" : "k_expand_tf32x3<tucker x1>";
   // The tensor-core kernels start streaming their basis before waiting on the
   // previous kernel; this basis is the operand just written, so launch them in
   // plain stream order.
@@ -477,13 +479,26 @@ mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS) {
   const long blocks = std::min(((long)a.N + 255) / 256, 8L * std::max(ctx->num_sms, 1));
   MPI_PROF(ctx, KF_EXPAND);
+  const char* name = "k_pointwise";
   switch (mode) {
-    case EX_FWD: launch_pdl(ctx, k_pointwise<EX_FWD>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
-    case EX_JFWD: launch_pdl(ctx, k_pointwise<EX_JFWD>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
-    case EX_ADJ: launch_pdl(ctx, k_pointwise<EX_ADJ>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
-    case EX_JADJ: launch_pdl(ctx, k_pointwise<EX_JADJ>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS); break;
+    case EX_FWD:
+      launch_pdl(ctx, k_pointwise<EX_FWD>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS);
+      name = "k_pointwise<fwd>";
+      break;
+    case EX_JFWD:
+      launch_pdl(ctx, k_pointwise<EX_JFWD>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS);
+      name = "k_pointwise<jfwd>";
+      break;
+    case EX_ADJ:
+      launch_pdl(ctx, k_pointwise<EX_ADJ>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS);
+      name = "k_pointwise<adj>";
+      break;
+    case EX_JADJ:
+      launch_pdl(ctx, k_pointwise<EX_JADJ>, dim3((unsigned)blocks), dim3(256), 0, a, S, dS);
+      name = "k_pointwise<jadj>";
+      break;
     default: return set_err(ctx, MPI_ERR_ARG, "pointwise mode");
   }
-  MPI_LAUNCH_CHECK(ctx, "k_pointwise");
+  MPI_LAUNCH_CHECK(ctx, name);
   return MPI_OK;
 }

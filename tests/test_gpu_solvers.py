@@ -128,3 +128,21 @@ def test_solver_graph_replay_is_deterministic(ctx, mp, prob):
     pa, ha = mp.image_solve(ctx, plan2, B, a1, y1, prob["eps"], n_outer=5, n_cg=3, n_tv=4)
     pb, hb = mp.image_solve(ctx, plan2, B, a1, y1, prob["eps"], n_outer=5, n_cg=3, n_tv=4)
     assert torch.equal(pa, pb) and np.array_equal(ha, hb)
+
+
+def test_bf16_solvers_against_oracle(ctx, mp, prob):
+    # The BF16 path (BF16 basis expansion on the tensor cores, FP32 elsewhere)
+    # against the FP64 oracle's reconstructions: NRMSE <= 1e-2.
+    plan = mp.Plan(ctx, (prob["ny"], prob["nx"]), sample_idx=prob["idx"])
+    B = mp.Basis(ctx, prob["U"].T)
+    a, p, hist = mp.sm_estimate(ctx, plan, B, c64(prob["y"]), prob["C"], n_outer=20, n_cg=10, prec="bf16")
+    p_ref, a_ref, h_ref = solvers.irgn(prob["Fs"], prob["U"], prob["y"], prob["C"], prob["q"], n_outer=20, n_cg=10)
+    ci = op.expand(prob["U"], f64(a)) * f64(p)[None]
+    ci_ref = op.expand(prob["U"], a_ref) * p_ref[None]
+    assert nrmse(ci, ci_ref) < 1e-2
+    at = prob["a_true"].astype(np.complex64).astype(np.complex128)
+    x, _ = mp.image_solve(ctx, plan, B, c64(at), c64(prob["y"]), prob["eps"], n_outer=50, n_cg=5, n_tv=10,
+                          prec="bf16")
+    x_ref, _ = solvers.admm_tv(prob["Fs"], op.expand(prob["U"], at), prob["y"], prob["eps"],
+                               (prob["ny"], prob["nx"]), n_outer=50, n_cg=5, n_tv=10)
+    assert nrmse(f64(x), x_ref) < 1e-2

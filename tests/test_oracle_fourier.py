@@ -157,3 +157,18 @@ def test_kb_nufft_adjoint():
     lhs = np.vdot(kb.fwd(v), y)
     rhs = np.vdot(v, kb.adj(y))
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("shape", [(8, 12), (16, 32, 48), (6, 10, 4)])
+def test_fast_mode_equals_explicit_matrices(shape):
+    # the oracle's FFT fast mode (used only to time the CPU baseline) computes the
+    # same F_s and F_s^H as the explicit separable DFT matrices
+    rng = np.random.default_rng(7)
+    N = int(np.prod(shape))
+    idx = np.sort(rng.choice(N, N // 3, replace=False))
+    slow = fourier.CartesianSampling(shape, idx)
+    fast = fourier.CartesianSamplingFFT(shape, idx, workers=2)
+    v = rng.normal(size=(3, N)) + 1j * rng.normal(size=(3, N))
+    y = rng.normal(size=(3, idx.size)) + 1j * rng.normal(size=(3, idx.size))
+    np.testing.assert_allclose(fast.fwd(v), slow.fwd(v), atol=1e-12)
+    np.testing.assert_allclose(fast.adj(y), slow.adj(y), atol=1e-12)

@@ -162,6 +162,11 @@ def kernel_bytes_per_pair(case, prec):
         out["k_mode_b"] = 2 * (8 * C * r1 * r2 * n3 + 8 * C * r1 * n2 * n3)
         out["k_x1_operand"] = 2 * (8 * C * r1 * n2 * n3 + ob * C * n2 * n3 * 2 * r1)
         out[f"{tc}<tucker x1>"] = 2 * (ob * C * n2 * n3 * 2 * r1 + V)
+        # the fused x1 kernels: operand in; forward: image in, DFT'd volume out;
+        # adjoint: per-coil data in, image out
+        pk = "bf16" if prec == "bf16" else "tf32x3"
+        out[f"k_tucker_x1<{pk},fwd+dft_z>"] = ob * C * n2 * n3 * 2 * r1 + P + V
+        out[f"k_tucker_x1<{pk},adj>"] = ob * C * n2 * n3 * 2 * r1 + V + P
     else:
         per = basis_bytes(case, prec) + 8 * C * q + V + P
         for k in ("k_expand_tf32x3", "k_expand_tc", "k_expand"):

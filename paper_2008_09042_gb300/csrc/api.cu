@@ -733,6 +733,16 @@ extern "C" mpi_status mpi_forward(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   a.alpha = (const float2*)alpha;
   a.p = (const float2*)p;
   a.out = w.A;
+  if (tucker_x1_fused_supported(basis, plan, C, prec)) {
+    // x1 product, point-wise step and the DFT along z in one tensor-core pass,
+    // then the passes along y and x
+    void* op = nullptr;
+    void* map = nullptr;
+    if ((st = tucker_x1_operand(ctx, basis, a.alpha, C, w.T, prec, &op, &map))) return st;
+    if ((st = tucker_x1_fused_launch(ctx, basis, plan, false, C, map, a.p, nullptr, w.A, a.scale, prec))) return st;
+    if ((st = launch_fft_cols(ctx, w.A, C, plan->nz, plan->ny, plan->nx, false, plan->row_has))) return st;
+    return launch_rows_fwd_gather(ctx, plan, w.A, C, (float2*)y);
+  }
   if ((st = run_expand(ctx, basis, EX_FWD, a, prec, w))) return st;
   return image_to_kspace(ctx, plan, w.A, C, (float2*)y, w.grid);
 }
@@ -751,6 +761,13 @@ extern "C" mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   a.alpha = (const float2*)alpha;
   a.w = w.A;
   a.out = (float2*)p_out;
+  if (tucker_x1_fused_supported(basis, plan, C, prec)) {
+    // the maps' x1 product fused with the sum over coils of conj(s_c) w_c
+    void* op = nullptr;
+    void* map = nullptr;
+    if ((st = tucker_x1_operand(ctx, basis, a.alpha, C, w.T, prec, &op, &map))) return st;
+    return tucker_x1_fused_launch(ctx, basis, plan, true, C, map, nullptr, a.w, a.out, a.scale, prec);
+  }
   return run_expand(ctx, basis, EX_ADJ, a, prec, w);
 }
 

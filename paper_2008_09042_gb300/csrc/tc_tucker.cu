@@ -1,0 +1,640 @@
+// The x1 mode product of a Tucker-factored basis ("A Compression Scheme for
+// Maxwell Basis", the contraction printed under Eq. 19) on the tensor cores,
+// fused with the operator steps around it on a 3D Cartesian grid:
+//
+//   forward  (Eq. 5):  v_c[z][b] = sign(z, b) scale p[z][b] sum_a U1[z][a] T_c[a][b],
+//                      then the DFT of v_c along z, written as vhat_c[kz][b];
+//   adjoint:           x[z][b]  = sign(z, b) scale sum_c conj(s_c[z][b]) w_c[z][b],
+//                      s_c[z][b] = sum_a U1[z][a] T_c[a][b],
+//
+// with T_c = G alpha_c x3 U3 x2 U2 (the core contraction and the other two mode
+// products, made before this kernel), b = (y, x) the position in a z-plane, and
+// w_c the per-coil image-side data after the inverse FFT passes.  The coil maps
+// are never stored.
+//
+// GEMM: the flattened operand rows are the positions (c, b) (K = [Re T | Im T]
+// over a), the coefficient rows are U1's rows real-ified as in the dense
+// expansion, so accumulator columns 2z, 2z + 1 of row (c, b) hold Re and Im of
+// s_c[z][b].  A 128-row tile is 128 consecutive positions of one coil.  FP32:
+// 3xTF32 (raw tile as hi, lo(T) staged in tensor memory by four converter
+// warps, hi and lo coefficient rows as two MMAs into one accumulator); BF16:
+// one kind::f16 MMA per K step.  Double-buffered accumulator in tensor memory.
+//
+// Epilogue warps: 4 per 32 values of z (warps 6 .. 6 + 4 N1 / 32 - 1, the warp
+// index mod 4 picking its 32 tensor-memory lanes).
+//  - forward: the DFT of length N1 = 8 R along z is done per position (one
+//    thread) through tensor memory: for each j1 < 8 the R values
+//    z = j1 + 8 j2 are read, multiplied by the image and the centring sign,
+//    transformed (R-point DFT in registers), twiddled by w_N1^(j1 k2) and
+//    written back to the same columns; after a barrier of the epilogue warps
+//    each k2 < R reads its 8 values (16 consecutive columns), takes the 8-point
+//    DFT and stores vhat[k2 + R k1], k1 < 8.  The j1 and k2 work is split over
+//    the epilogue warps of a lane quarter.
+//  - adjoint: each thread accumulates its 32 values of z over the coils in
+//    registers; the CTA owns one 128-position block and runs through its tiles
+//    coil by coil (grid = positions / 128), writing the image at the end.
+// Every mbarrier wait is bounded; an epilogue decision that depends on a wait
+// is made uniform over the epilogue warps with a reducing barrier.
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "mpi_internal.h"
+#include "ptx.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+using namespace mpi_tc;
+
+constexpr int kTxFwd = 0;  // forward with the DFT along z
+constexpr int kTxAdj = 1;  // adjoint, summed over coils
+constexpr int kEpi0 = 6;   // first epilogue warp
+constexpr int kKp = 64;    // operand K: 2 r1 <= 64
+constexpr int kBox32 = kTileM * 128;  // 128 rows x 32 FP32
+constexpr size_t kSmemCap = 232448 - 1024;
+
+struct TxArgs {
+  int rows;      // C B operand rows
+  int B;         // positions per z-plane (n2 n3), a multiple of 128
+  int C;         // coils
+  int nx, ny;    // the position b = y nx + x, for the centring sign
+  int centre;
+  float scale;
+  const float2* p;   // image [N1][B]
+  const float2* w;   // adjoint input [C][N1][B]
+  float2* out;       // forward: vhat [C][N1][B]; adjoint: image [N1][B]
+  const float2* tw;  // exp(-2 pi i m / N1), m < N1
+  int* err;
+  int tmem_cols;
+  int stages;
+  TcArgs coef;       // coefficient builder: C = N1 rows of U1, q = r1, alpha = U1
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Forward DFTs in registers, X[k] = sum_n x[n] exp(-2 pi i n k / R).
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  const float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+__device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2) {
+  // exp(-2 pi i / 3) = -1/2 - i sqrt(3)/2
+  const float s = 0.86602540378443865f;
+  const float2 t = cadd(x1, x2), d = csub(x1, x2);
+  const float2 m = make_float2(x0.x - 0.5f * t.x, x0.y - 0.5f * t.y);
+  const float2 isd = make_float2(s * d.y, -s * d.x);  // -i s d
+  x0 = cadd(x0, t);
+  x1 = cadd(m, isd);
+  x2 = csub(m, isd);
+}
+
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  const float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
+  const float2 s13 = cadd(x1, x3), d13 = mul_mi(csub(x1, x3));
+  x0 = cadd(s02, s13);
+  x2 = csub(s02, s13);
+  x1 = cadd(d02, d13);
+  x3 = csub(d02, d13);
+}
+
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  // radix-2 split: 4-point DFTs of the even and odd samples, then the combine
+  // with exp(-2 pi i m / 8), m < 4
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4(e0, e1, e2, e3);
+  dft4(o0, o1, o2, o3);
+  const float h = 0.70710678118654752f;
+  o1 = make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));   // x exp(-i pi/4)
+  o2 = mul_mi(o2);                                           // x -i
+  o3 = make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));  // x exp(-3 i pi/4)
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+// 12 = 3 x 4: n = 3 n2 + n1, k = k1 + 4 k2; 4-point DFTs over n2, twiddles
+// exp(-2 pi i n1 k1 / 12), 3-point DFTs over n1.
+__device__ __forceinline__ void dft12(float2 (&v)[12]) {
+  float2 y[3][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 3; ++n1) {
+    y[n1][0] = v[n1];
+    y[n1][1] = v[3 + n1];
+    y[n1][2] = v[6 + n1];
+    y[n1][3] = v[9 + n1];
+    dft4(y[n1][0], y[n1][1], y[n1][2], y[n1][3]);
+  }
+  const float c30 = 0.86602540378443865f;  // cos(pi/6)
+  // n1 = 1: m = k1 (0..3); n1 = 2: m = 2 k1 (0, 2, 4, 6)
+  y[1][1] = cmulf(y[1][1], make_float2(c30, -0.5f));
+  y[1][2] = cmulf(y[1][2], make_float2(0.5f, -c30));
+  y[1][3] = mul_mi(y[1][3]);
+  y[2][1] = cmulf(y[2][1], make_float2(0.5f, -c30));
+  y[2][2] = cmulf(y[2][2], make_float2(-0.5f, -c30));
+  y[2][3] = make_float2(-y[2][3].x, -y[2][3].y);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    dft3(y[0][k1], y[1][k1], y[2][k1]);
+    v[k1] = y[0][k1];
+    v[k1 + 4] = y[1][k1];
+    v[k1 + 8] = y[2][k1];
+  }
+}
+
+// 16 = 4 x 4: n = 4 n2 + n1, k = k1 + 4 k2; twiddles exp(-2 pi i n1 k1 / 16).
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+  float2 y[4][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    y[n1][0] = v[n1];
+    y[n1][1] = v[4 + n1];
+    y[n1][2] = v[8 + n1];
+    y[n1][3] = v[12 + n1];
+    dft4(y[n1][0], y[n1][1], y[n1][2], y[n1][3]);
+  }
+  const float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  const float2 w1 = make_float2(c1, -s1), w2 = make_float2(h, -h), w3 = make_float2(s1, -c1);
+  const float2 w6 = make_float2(-h, -h), w9 = make_float2(-c1, s1);
+  y[1][1] = cmulf(y[1][1], w1);
+  y[1][2] = cmulf(y[1][2], w2);
+  y[1][3] = cmulf(y[1][3], w3);
+  y[2][1] = cmulf(y[2][1], w2);
+  y[2][2] = mul_mi(y[2][2]);
+  y[2][3] = cmulf(y[2][3], w6);
+  y[3][1] = cmulf(y[3][1], w3);
+  y[3][2] = cmulf(y[3][2], w6);
+  y[3][3] = cmulf(y[3][3], w9);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    dft4(y[0][k1], y[1][k1], y[2][k1], y[3][k1]);
+    v[k1] = y[0][k1];
+    v[k1 + 4] = y[1][k1];
+    v[k1 + 8] = y[2][k1];
+    v[k1 + 12] = y[3][k1];
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void dft_r(float2 (&v)[R]) {
+  if constexpr (R == 8) dft8(v);
+  else if constexpr (R == 12) dft12(v);
+  else dft16(v);
+}
+
+// Two consecutive 32-bit TMEM columns of this warp's lanes (one complex value).
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float2& v) {
+  uint32_t a, b;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
+  v = make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(__float_as_uint(v.x)),
+               "r"(__float_as_uint(v.y))
+               : "memory");
+}
+__device__ __forceinline__ void fence_reg2(float2& v) { asm volatile("" : "+f"(v.x), "+f"(v.y)); }
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+      "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+      "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_tf32_tmem_a(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc) {
+  asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;" ::"r"(d), "r"(a), "l"(b), "r"(idesc));
+}
+
+// Barrier over the `n` epilogue threads (named barrier 1) that also returns
+// whether any of them passed `flag` != 0.
+__device__ __forceinline__ bool epi_bar_any(int flag, int n) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"(flag), "r"(n)
+      : "memory");
+  return out != 0;
+}
+
+__device__ __forceinline__ float pos_sign(int z, int b, int nx) {
+  return ((z + b % nx + b / nx) & 1) ? -1.f : 1.f;
+}
+
+// ------------------------------------------------------------------- kernel
+
+template <int PREC, int MODE, int N1>
+__global__ void __launch_bounds__((kEpi0 + 4 * (N1 / 32)) * 32, 1)
+    k_tucker_x1(const __grid_constant__ CUtensorMap tmap, TxArgs a) {
+  constexpr bool TF = PREC == 0;
+  constexpr int NSUB = N1 / 32;          // epilogue warps per lane quarter
+  constexpr int NEPI = 4 * NSUB;
+  constexpr int NG = 2 * N1;             // accumulator columns
+  constexpr int R = N1 / 8;              // the DFT along z is 8 x R
+  constexpr int STAGE = TF ? 2 * kBox32 : kTileM * 128;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int stages = a.stages;
+  constexpr uint32_t b_bytes = TF ? 2u * NG * kKp * 4 : (uint32_t)NG * kKp * 2;
+  constexpr uint32_t b_pad = (b_bytes + 1023) & ~1023u;
+  unsigned char* sB = smem;
+  unsigned char* sA = smem + b_pad;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sA + (size_t)stages * STAGE);
+  uint64_t* conv = full + stages;
+  uint64_t* empty = conv + stages;
+  uint64_t* acc_full = empty + stages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;   // [2]
+  uint64_t* drain = acc_empty + 2;
+  uint64_t* bfull = drain + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bfull + 1);
+  __shared__ float2 s_tw[N1];
+  __shared__ int s_failed;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the operand is written by the previous kernel in the stream
+  mpi_ptx::pdl_wait();
+  mpi_ptx::pdl_trigger();
+  if (tid == 0) {
+    s_failed = 0;
+    for (int s = 0; s < stages; ++s) {
+      mpi_ptx::mbar_init(&full[s], 1);
+      mpi_ptx::mbar_init(&conv[s], 4);
+      mpi_ptx::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mpi_ptx::mbar_init(&acc_full[b], 1);
+      mpi_ptx::mbar_init(&acc_empty[b], NEPI);
+    }
+    mpi_ptx::mbar_init(drain, 1);
+    mpi_ptx::mbar_init(bfull, 4);
+    mpi_ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     mpi_ptx::smem_addr(tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem_lo = tmem + 2u * NG;  // lo(T) slots: 64 columns per stage (FP32)
+  const int n_tiles = a.rows / kTileM;
+  const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer: one stage (the whole K = 64) per tile
+    RingPos r;
+    int g = 0;
+    for (int t = blockIdx.x; g < my_tiles; ++g, t += gridDim.x) {
+      if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err)) break;
+      unsigned char* dst = sA + (size_t)r.s * STAGE;
+      mpi_ptx::mbar_arrive_expect_tx(&full[r.s], STAGE);
+      if (TF) {
+        tma_load_2d(dst, &tmap, 0, t * kTileM, &full[r.s]);
+        tma_load_2d(dst + kBox32, &tmap, 32, t * kTileM, &full[r.s]);
+      } else {
+        tma_load_2d(dst, &tmap, 0, t * kTileM, &full[r.s]);
+      }
+      r.next(stages);
+    }
+    if (g < my_tiles) {
+      s_failed = 1;
+      for (int h = (g > stages ? g - stages : 0); h < g; ++h)  // fills still in flight (bounded)
+        mpi_ptx::mbar_wait(&full[h % stages], (uint32_t)((h / stages) & 1), nullptr);
+    }
+  } else if (TF && warp >= 2 && warp <= 5) {
+    // ---------------- converters: lo(x) of tile row 32 (warp % 4) + lane into TMEM
+    const int row = (warp & 3) * 32 + lane;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    RingPos r;
+    for (int g = 0; g < my_tiles; ++g) {
+      const bool got = mpi_ptx::mbar_wait(&full[r.s], r.ph, a.err);
+      if (!__all_sync(0xffffffffu, got)) {
+        s_failed = 1;
+        break;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4* x = reinterpret_cast<const float4*>(sA + (size_t)r.s * STAGE + h * kBox32 + row * 128);
+        float lo[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 v = x[j ^ (row & 7)];
+          lo[4 * j + 0] = v.x - tf32_hi(v.x);
+          lo[4 * j + 1] = v.y - tf32_hi(v.y);
+          lo[4 * j + 2] = v.z - tf32_hi(v.z);
+          lo[4 * j + 3] = v.w - tf32_hi(v.w);
+        }
+        tmem_st32(tmem_lo + lane_base + (uint32_t)(r.s * 64 + 32 * h), lo);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mpi_ptx::mbar_arrive(&conv[r.s]);
+      r.next(stages);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint64_t a0 = sdesc_sw128(mpi_ptx::smem_addr(sA));
+    const uint64_t b0 = sdesc_sw128(mpi_ptx::smem_addr(sB));
+    RingPos r;
+    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err);
+    for (int tc = 0; tc < my_tiles && ok; ++tc) {
+      const int buf = tc & 1;
+      const uint32_t tacc = tmem + (uint32_t)(buf * NG);
+      if (!mpi_ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), a.err)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      const int s = r.s;
+      if (!mpi_ptx::mbar_wait(&full[s], r.ph, a.err)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint64_t ad = a0 + (uint32_t)(s * (STAGE >> 4));
+      if (TF) {
+        const uint32_t idesc = idesc_tf32(kTileM, NG);
+        constexpr uint32_t b_chunk = (uint32_t)(2 * NG * 128) >> 4;  // [hi; lo] rows per 32-element K chunk
+        constexpr uint32_t lo_off = (uint32_t)(NG * 128) >> 4;
+        constexpr uint32_t box = kBox32 >> 4;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint64_t adk = ad + h * box + 2 * ks, bdk = b0 + h * b_chunk + 2 * ks;
+            mma_tf32(tacc, adk, bdk, idesc, (h | ks) != 0);
+            mma_tf32(tacc, adk, bdk + lo_off, idesc, 1);
+          }
+        if (!mpi_ptx::mbar_wait(&conv[s], r.ph, a.err)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t la = tmem_lo + (uint32_t)(s * 64);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            mma_tf32_tmem_a(tacc, la + 32 * h + 8 * ks, b0 + h * b_chunk + 2 * ks, idesc);
+      } else {
+        const uint32_t idesc = idesc_bf16(kTileM, NG);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) mma_bf16(tacc, ad + 2 * ks, b0 + 2 * ks, idesc, ks != 0);
+      }
+      mma_commit(&empty[s]);
+      mma_commit(&acc_full[buf]);
+      r.next(stages);
+    }
+    mma_commit(drain);
+    mpi_ptx::mbar_wait(drain, 0, a.err);
+    if (!ok) s_failed = 1;
+  } else if (warp >= kEpi0) {
+    // ---------------- epilogue
+    const int e = warp - kEpi0;
+    const int qd = warp & 3, sub = e >> 2;
+    const int row = qd * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    constexpr int NT = NEPI * 32;
+    if (e < 4) build_coef_smem<TF>(a.coef, sB, kKp, false, e * 32 + lane, bfull);
+    for (int i = e * 32 + lane; i < N1; i += NT) s_tw[i] = a.tw[i];
+    epi_bar_any(0, NT);  // twiddles visible to every epilogue warp
+    float2 pacc[32];
+    if (MODE == kTxAdj) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) pacc[j] = make_float2(0.f, 0.f);
+    }
+    int b = 0;
+    bool failed = false;
+    int tc = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      const bool got = mpi_ptx::mbar_wait(&acc_full[buf], (uint32_t)((tc >> 1) & 1), a.err);
+      if (epi_bar_any(!got, NT)) {
+        failed = true;
+        s_failed = 1;
+        break;
+      }
+      fence_after();
+      const int n = t * kTileM + row;
+      const int c = n / a.B;
+      b = n - c * a.B;
+      const uint32_t tbase = tmem + lane_base + (uint32_t)(buf * NG);
+      if (MODE == kTxFwd) {
+        const float sb = ((b % a.nx + b / a.nx) & 1) ? -1.f : 1.f;
+        // stage 1: the 8 sub-DFTs of length R over z = j1 + 8 j2, in place
+        constexpr int J1_PER = (8 + NSUB - 1) / NSUB;
+        for (int j1 = sub * J1_PER; j1 < min(8, (sub + 1) * J1_PER); ++j1) {
+          float2 v[R], pv[R];
+#pragma unroll
+          for (int j2 = 0; j2 < R; ++j2) pv[j2] = a.p[(size_t)(j1 + 8 * j2) * a.B + b];
+#pragma unroll
+          for (int j2 = 0; j2 < R; ++j2) tmem_ld2(tbase + 2u * (j1 + 8 * j2), v[j2]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j2 = 0; j2 < R; ++j2) {
+            fence_reg2(v[j2]);
+            const int z = j1 + 8 * j2;
+            const float sg = (a.centre && (z & 1) ? -sb : (a.centre ? sb : 1.f)) * a.scale;
+            v[j2] = cscale(cmulf(v[j2], pv[j2]), sg);
+          }
+          dft_r<R>(v);
+#pragma unroll
+          for (int k2 = 1; k2 < R; ++k2) v[k2] = cmulf(v[k2], s_tw[(j1 * k2) % N1]);
+#pragma unroll
+          for (int k2 = 0; k2 < R; ++k2) tmem_st2(tbase + 2u * (j1 + 8 * k2), v[k2]);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_before();
+        epi_bar_any(0, NT);
+        fence_after();
+        // stage 2: the 8-point DFTs over j1 for each k2; output kz = k2 + R k1
+        constexpr int K2_PER = (R + NSUB - 1) / NSUB;
+        float2* o = a.out + (size_t)c * N1 * a.B + b;
+        for (int k2 = sub * K2_PER; k2 < min(R, (sub + 1) * K2_PER); ++k2) {
+          uint32_t raw[16];
+          tmem_ld16_start(tbase + 16u * k2, raw);
+          tmem_wait_ld();
+          reg_fence16(raw);
+          float2 u[8];
+#pragma unroll
+          for (int j1 = 0; j1 < 8; ++j1) u[j1] = make_float2(__uint_as_float(raw[2 * j1]), __uint_as_float(raw[2 * j1 + 1]));
+          dft8(u);
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) o[(size_t)(k2 + R * k1) * a.B] = u[k1];
+        }
+      } else {
+        // adjoint: conj(s_c) w_c for this thread's 32 values of z, summed over coils
+        const float2* wp = a.w + (size_t)c * N1 * a.B + (size_t)(32 * sub) * a.B + b;
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          float2 wv[8];  // this chunk's loads, issued before the accumulator read
+#pragma unroll
+          for (int i = 0; i < 8; ++i) wv[i] = wp[(size_t)(8 * ch + i) * a.B];
+          uint32_t raw[16];
+          tmem_ld16_start(tbase + (uint32_t)(64 * sub + 16 * ch), raw);
+          tmem_wait_ld();
+          reg_fence16(raw);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float2 s = make_float2(__uint_as_float(raw[2 * i]), __uint_as_float(raw[2 * i + 1]));
+            const float2 wz = wv[i];
+            pacc[8 * ch + i].x += s.x * wz.x + s.y * wz.y;
+            pacc[8 * ch + i].y += s.x * wz.y - s.y * wz.x;
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mpi_ptx::mbar_arrive(&acc_empty[buf]);
+    }
+    if (MODE == kTxAdj && !failed && my_tiles > 0) {
+      // the CTA's tiles are every coil of one 128-position block: write the image
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int z = 32 * sub + j;
+        const float sg = (a.centre ? pos_sign(z, b, a.nx) : 1.f) * a.scale;
+        a.out[(size_t)z * a.B + b] = cscale(pacc[j], sg);
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+template <int PREC, int MODE, int N1>
+constexpr int tx_threads() {
+  return (kEpi0 + 4 * (N1 / 32)) * 32;
+}
+
+template <int PREC, int N1>
+size_t tx_smem(int stages) {
+  constexpr int NG = 2 * N1;
+  const size_t b_bytes = PREC == 0 ? 2 * (size_t)NG * kKp * 4 : (size_t)NG * kKp * 2;
+  const size_t stage = PREC == 0 ? 2 * kBox32 : kTileM * 128;
+  return 1024 + ((b_bytes + 1023) & ~(size_t)1023) + stages * stage + 8 * (3 * stages + 6) + 16;
+}
+
+template <int PREC, int MODE, int N1>
+mpi_status tx_launch(mpi_ctx* ctx, const CUtensorMap* map, TxArgs& a, int grid) {
+  // ring depth: as many stages as fit (at most 4), at least 2
+  int stages = 4;
+  while (stages > 2 && tx_smem<PREC, N1>(stages) > kSmemCap) --stages;
+  const size_t smem = tx_smem<PREC, N1>(stages);
+  if (smem > kSmemCap) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker x1 kernel: shared memory");
+  constexpr int NG = 2 * N1;
+  int cols = PREC == 0 ? 2 * NG + 64 * stages : 2 * NG;
+  if (PREC == 0 && cols > 512) {
+    stages = 2;
+    cols = 2 * NG + 128;
+  }
+  if (cols > 512) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker x1 kernel: tensor memory");
+  int tcols = 32;
+  while (tcols < cols) tcols <<= 1;
+  a.tmem_cols = tcols;
+  a.stages = stages;
+  auto kern = k_tucker_x1<PREC, MODE, N1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tx_smem<PREC, N1>(stages));
+  if (e != cudaSuccess) return cuda_check(ctx, e, "Tucker x1 smem attribute");
+  MPI_PROF(ctx, KF_EXPAND);
+  launch_pdl(ctx, kern, dim3(grid), dim3(tx_threads<PREC, MODE, N1>()), tx_smem<PREC, N1>(stages), *map, a);
+  MPI_LAUNCH_CHECK(ctx, MODE == kTxFwd ? (PREC == 0 ? "k_tucker_x1<tf32x3,fwd+dft_z>" : "k_tucker_x1<bf16,fwd+dft_z>")
+                                       : (PREC == 0 ? "k_tucker_x1<tf32x3,adj>" : "k_tucker_x1<bf16,adj>"));
+  return MPI_OK;
+}
+
+}  // namespace
+
+bool tucker_x1_fused_supported(const mpi_basis* b, const mpi_plan* plan, int C, mpi_precision prec) {
+  if (!b->tucker || !plan || plan->kind != MPI_TRAJ_CARTESIAN || plan->ndim != 3) return false;
+  if (prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) return false;
+  const int n1 = b->n[0];
+  if (!(n1 == 64 || n1 == 96 || (n1 == 128 && prec == MPI_PREC_BF16))) return false;
+  if (2 * b->r[0] > kKp) return false;
+  const long B = (long)b->n[1] * b->n[2];
+  if (B % kTileM || (long)C * B > 0x7fffffffL) return false;
+  // the adjoint's grid is one CTA per 128-position block
+  if (B / kTileM > 65535) return false;
+  return plan->nz == b->n[0] && plan->ny == b->n[1] && plan->nx == b->n[2];
+}
+
+// x1 product fused with the forward's point-wise step and the DFT along z (fwd)
+// or with the adjoint's conj(s) w sum over coils (adj).  `op` is the flattened
+// operand [C B][64] (FP32 or BF16, from k_x1_operand) and `map` its tensor map.
+mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_plan* plan, bool adjoint, int C,
+                                  const void* map, const float2* p, const float2* w, float2* out, float scale,
+                                  mpi_precision prec) {
+  TxArgs a;
+  const long B = (long)b->n[1] * b->n[2];
+  a.rows = (int)(C * B);
+  a.B = (int)B;
+  a.C = C;
+  a.nx = plan->nx;
+  a.ny = plan->ny;
+  a.centre = 1;
+  a.scale = scale;
+  a.p = p;
+  a.w = w;
+  a.out = out;
+  a.tw = twiddle_table(ctx, b->n[0]);
+  a.err = ctx->dev_err;
+  if (!a.tw) return set_err(ctx, MPI_ERR_SHAPE, "Tucker x1: no twiddle table for n1");
+  TcArgs& cf = a.coef;
+  cf = TcArgs{};
+  cf.C = b->n[0];
+  cf.q = b->r[0];
+  cf.n_gemm = 2 * b->n[0];
+  cf.half = cf.n_gemm;
+  cf.alpha = b->F[0];
+  const int n_tiles = (int)(C * B / kTileM);
+  const int grid = adjoint ? (int)(B / kTileM) : std::min(n_tiles, std::max(ctx->num_sms, 1));
+  const CUtensorMap* m = (const CUtensorMap*)map;
+  const bool bf = prec == MPI_PREC_BF16;
+#define MPI_TX(P, M, N)                                   \
+  if (b->n[0] == N) return tx_launch<P, M, N>(ctx, m, a, grid);
+  if (!adjoint && !bf) { MPI_TX(0, kTxFwd, 64) MPI_TX(0, kTxFwd, 96) }
+  if (!adjoint && bf) { MPI_TX(1, kTxFwd, 64) MPI_TX(1, kTxFwd, 96) MPI_TX(1, kTxFwd, 128) }
+  if (adjoint && !bf) { MPI_TX(0, kTxAdj, 64) MPI_TX(0, kTxAdj, 96) }
+  if (adjoint && bf) { MPI_TX(1, kTxAdj, 64) MPI_TX(1, kTxAdj, 96) MPI_TX(1, kTxAdj, 128) }
+#undef MPI_TX
+  return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker x1: unsupported n1");
+}

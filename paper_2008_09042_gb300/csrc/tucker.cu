@@ -376,19 +376,17 @@ bool tucker_x1_on_tensor_cores(const mpi_basis* b, int C, mpi_precision prec) {
   return ok;
 }
 
-// maps[c] = s_c for all coils (C x N), through the core contraction and the
-// three mode products; `tmp` holds tucker_work_elems(b, C) elements.  The x1
-// product runs on the tensor-core expansion kernels where it can (per coil it
-// is a dense expansion with T2_c^T as the basis and the rows of U1 as the
-// coefficients), else on the CUDA cores.
-mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
-                       mpi_precision prec) {
+// The flattened x1 operand of alpha's coil maps: the core contraction, the x3
+// and x2 mode products and the rewrite of T2 [C][r1][n2 n3] as K-major rows
+// [(c, b)][Kp] (FP32 or BF16) at a 256-byte aligned place in `tmp`; returns the
+// operand and its tensor map (re-encoded only when the workspace, C or the
+// precision change).
+mpi_status tucker_x1_operand(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp,
+                             mpi_precision prec, void** op_out, void** map_out) {
   float2* t2 = nullptr;
   mpi_status st = tucker_t2(ctx, b, alpha, C, tmp, prec, &t2);
   if (st) return st;
   const long B = (long)b->n[1] * b->n[2];
-  if (!tucker_x1_on_tensor_cores(b, C, prec))
-    return mode_b(ctx, false, t2, b->F[0], C, b->r[0], b->n[0], B, maps);
   const int Kp = x1_kp(b);
   void* op = (void*)(((uintptr_t)(tmp + x1_op_offset(b, C)) + 255) & ~(uintptr_t)255);  // TMA wants 16-byte alignment
   const dim3 grid((unsigned)((B + 31) / 32), (unsigned)C);
@@ -399,7 +397,6 @@ mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, in
   else
     launch_pdl(ctx, k_x1_operand<float>, grid, dim3(256), 0, (const float2*)t2, b->r[0], B, Kp, (float*)op);
   MPI_LAUNCH_CHECK(ctx, "k_x1_operand");
-  // the operand's tensor map, re-encoded only when the workspace, C or precision change
   mpi_basis* mb = const_cast<mpi_basis*>(b);
   if (!mb->op_map) mb->op_map = new CUtensorMap;
   if (mb->op_map_ptr != op || mb->op_map_C != C || mb->op_map_prec != (int)prec) {
@@ -413,8 +410,31 @@ mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, in
     mb->op_map_C = C;
     mb->op_map_prec = (int)prec;
   }
+  *op_out = op;
+  *map_out = mb->op_map;
+  return MPI_OK;
+}
+
+// maps[c] = s_c for all coils (C x N), through the core contraction and the
+// three mode products; `tmp` holds tucker_work_elems(b, C) elements.  The x1
+// product runs on the tensor-core expansion kernels where it can (per coil it
+// is a dense expansion with T2_c^T as the basis and the rows of U1 as the
+// coefficients), else on the CUDA cores.
+mpi_status tucker_maps(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* maps, float2* tmp,
+                       mpi_precision prec) {
+  const long B = (long)b->n[1] * b->n[2];
+  if (!tucker_x1_on_tensor_cores(b, C, prec)) {
+    float2* t2 = nullptr;
+    mpi_status st = tucker_t2(ctx, b, alpha, C, tmp, prec, &t2);
+    if (st) return st;
+    return mode_b(ctx, false, t2, b->F[0], C, b->r[0], b->n[0], B, maps);
+  }
+  void* op = nullptr;
+  void* map = nullptr;
+  mpi_status st = tucker_x1_operand(ctx, b, alpha, C, tmp, prec, &op, &map);
+  if (st) return st;
   mpi_basis fb;
-  x1_view(b, C, prec, op, mb->op_map, &fb);
+  x1_view(b, C, prec, op, map, &fb);
   ExpandArgs a;
   a.N = fb.N;
   a.q = b->r[0];

@@ -97,3 +97,32 @@ def test_tucker_full_size_maps_and_adjointness(ctx, mp):
     rhs = torch.vdot(p.to(torch.complex128), x.to(torch.complex128)).item()
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
     ctx.synchronize()
+
+
+@pytest.mark.parametrize("dims,ranks,prec", [
+    ((64, 32, 64), (16, 8, 8), "fp32"),     # n1 = 64, r1 < 32 (zero-padded K)
+    ((64, 32, 64), (32, 12, 10), "bf16"),
+    ((96, 16, 64), (24, 8, 8), "fp32"),
+    ((128, 16, 64), (32, 8, 8), "bf16"),    # n1 = 128: BF16 only on the fused kernel
+    ((128, 16, 64), (32, 8, 8), "fp32"),    # ... FP32 takes the unfused passes
+])
+def test_tucker_fused_x1_shapes(ctx, mp, dims, ranks, prec):
+    # forward and adjoint through the x1 kernel fused with the point-wise step and
+    # the DFT along z (forward) or the sum over coils (adjoint), every coil count
+    # path, against the oracle
+    tol = 1e-5 if prec == "fp32" else 5e-3
+    q, C = 20, 5
+    core, fac = _tucker(dims, ranks, q, seed=21)
+    tb = tucker.TuckerBasis(core, fac)
+    idx = w.mask_to_indices(w.poisson_disc_mask_3d(*dims, R=4, calib=(8, 8), seed=22))
+    Fs = fourier.CartesianSampling(dims, idx)
+    N = int(np.prod(dims))
+    a = w.random_coefficients(C, q, seed=23).astype(np.complex64).astype(np.complex128)
+    p = w.random_image(N, seed=24).astype(np.complex64).astype(np.complex128)
+    r = w.random_coefficients(C, idx.size, seed=25, decay=False).astype(np.complex64).astype(np.complex128)
+    plan = mp.Plan(ctx, dims, sample_idx=idx)
+    B = mp.TuckerBasis(ctx, core, fac)
+    for rep in range(2):  # a second call reuses the cached operand tensor map
+        assert rel(f64(mp.forward(ctx, plan, B, c64(a), c64(p), prec=prec)), op.forward(Fs, tb, a, p)) < tol
+        assert rel(f64(mp.adjoint(ctx, plan, B, c64(a), c64(r), prec=prec)), op.adjoint(Fs, tb, a, r)) < tol
+    ctx.synchronize()

@@ -685,6 +685,7 @@ def run_ours(args):
         "kernel_us_per_pair": {k: round(v["ms_per_pair"] * 1e3, 1) for k, v in
                                sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms_per_pair"])},
         "clocks": clk,
+        "autotune": ctx.tuning_records(),
     }
     if not args.no_secondary:
         wl = {}

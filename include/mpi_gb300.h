@@ -86,6 +86,17 @@ int64_t mpi_ctx_launch_count(const mpi_ctx* ctx);
  * and host-call staging buffer (0 until an operator call or mpi_ctx_reserve
  * grows them); -1 for a null context.  Library bookkeeping, no paper passage. */
 int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx);
+/* Launch-shape autotuning (on by default).  The first operator call that runs an
+ * FFT line pass of a new shape (length, stride, line count, row mask) times each
+ * candidate tile width of that pass with CUDA events on a free workspace buffer
+ * (never while the stream is being captured, never in mpi_forward_noalloc) and
+ * keeps the fastest for the context's later calls.  enable = 0 switches tuning
+ * off (untuned shapes take a fixed default).  mpi_ctx_tuning_record returns the
+ * text of the `index`-th decision (shape, candidates and their times; valid for
+ * the context's lifetime), MPI_ERR_ARG past the last.  Library machinery, no
+ * paper passage. */
+mpi_status mpi_ctx_set_autotune(mpi_ctx* ctx, int enable);
+mpi_status mpi_ctx_tuning_record(const mpi_ctx* ctx, int index, const char** text_out);
 /* Per-launch device timing: while enabled, every kernel the context launches is
  * bracketed by two CUDA events on the context's stream (16384 launches at most
  * between reads; later ones are not timed).  mpi_ctx_profile_read synchronises

@@ -52,6 +52,18 @@ class Context:
     def launches(self):
         return int(self.lib.mpi_ctx_launch_count(self.h))
 
+    def set_autotune(self, enable=True):
+        check(self.h, self.lib.mpi_ctx_set_autotune(self.h, 1 if enable else 0))
+
+    def tuning_records(self):
+        """Text of every launch-shape decision the autotuner made on this context."""
+        out = []
+        while True:
+            t = ctypes.c_char_p()
+            if self.lib.mpi_ctx_tuning_record(self.h, len(out), ctypes.byref(t)):
+                return out
+            out.append(t.value.decode())
+
     def workspace_bytes(self):
         """Device bytes held by the context's growable workspace and staging buffer."""
         return int(self.lib.mpi_ctx_workspace_bytes(self.h))

@@ -53,6 +53,8 @@ mpi_status ensure_work(mpi_ctx* ctx, size_t bytes) {
   if (ctx->work) cudaFree(ctx->work);
   ctx->work = nullptr;
   ctx->work_bytes = 0;
+  ctx->tune_scratch = nullptr;
+  ctx->tune_scratch_bytes = 0;
   const size_t want = std::max(bytes, (size_t)1 << 20);
   e = cudaMalloc(&ctx->work, want);
   if (e != cudaSuccess) {
@@ -222,6 +224,9 @@ mpi_status carve_work(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis
   float2* base = (float2*)ctx->work;
   w->A = base;
   w->B = base + cn;
+  // the line passes run on A; B is free while they run (the autotuner's scratch)
+  ctx->tune_scratch = w->B;
+  ctx->tune_scratch_bytes = cn * sizeof(float2);
   size_t grid = plan->kind == MPI_TRAJ_RADIAL ? nufft_grid_elems(plan, C) : 0;
   w->grid = base + 2 * cn;
   w->partials = base + 2 * cn + grid;
@@ -434,6 +439,19 @@ extern "C" const char* mpi_last_error(const mpi_ctx* ctx) {
 }
 
 extern "C" int64_t mpi_ctx_launch_count(const mpi_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+extern "C" mpi_status mpi_ctx_set_autotune(mpi_ctx* ctx, int enable) {
+  if (!ctx) return MPI_ERR_ARG;
+  ctx->autotune = enable != 0;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_ctx_tuning_record(const mpi_ctx* ctx, int index, const char** text_out) {
+  if (!ctx || !text_out) return MPI_ERR_ARG;
+  if (index < 0 || index >= (int)ctx->tuned.size()) return MPI_ERR_ARG;
+  *text_out = ctx->tuned[index].what.c_str();
+  return MPI_OK;
+}
 
 extern "C" int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx) {
   return ctx ? (int64_t)(ctx->work_bytes + ctx->stage_bytes) : -1;
@@ -807,13 +825,15 @@ const void* mapped_host(const void* h) {
 // ones go through the staging buffer: alpha [C][q] and the input (n_in
 // elements) copied in, the output (n_out elements) copied back.  `op` runs on
 // the device addresses; the call waits for the stream before returning.
+// `reread_in`: the kernels read the input more than once (the 3D forward reads
+// the image once per coil), so it is copied to the device even when pinned.
 template <class Op>
 mpi_status host_call(mpi_ctx* ctx, const mpi_basis* basis, int C, const mpi_c32* alpha, const mpi_c32* in,
-                     size_t n_in, mpi_c32* out, size_t n_out, Op op) {
+                     size_t n_in, mpi_c32* out, size_t n_out, Op op, bool reread_in = false) {
   const size_t n_alpha = (size_t)C * basis->q;
   // an empty input or output (no samples) is passed through as given
   const mpi_c32* da = (const mpi_c32*)mapped_host(alpha);
-  const mpi_c32* di = n_in ? (const mpi_c32*)mapped_host(in) : in;
+  const mpi_c32* di = n_in ? (reread_in ? nullptr : (const mpi_c32*)mapped_host(in)) : in;
   mpi_c32* dout = n_out ? (mpi_c32*)mapped_host(out) : out;
   const bool stage_a = !da, stage_i = n_in && !di, copy_out = n_out && !dout;
   const size_t a_off = 0, i_off = (n_alpha + 1) & ~(size_t)1, o_off = i_off + ((n_in + 1) & ~(size_t)1);
@@ -852,7 +872,8 @@ extern "C" mpi_status mpi_forward_host(mpi_ctx* ctx, const mpi_plan* plan, const
   return host_call(ctx, basis, C, alpha, p, (size_t)plan->N, y, (size_t)C * plan->M,
                    [&](const mpi_c32* da, const mpi_c32* dp, mpi_c32* dy) {
                      return mpi_forward(ctx, plan, basis, da, C, dp, dy, prec);
-                   });
+                   },
+                   tucker_x1_fused_supported(basis, plan, C, prec));
 }
 
 extern "C" mpi_status mpi_adjoint_host(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,

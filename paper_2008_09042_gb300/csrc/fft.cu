@@ -15,6 +15,8 @@
 // exp(-+2 pi i / (Ns R)), takes an R-point DFT and writes output r to
 // (j div Ns) Ns R + (j mod Ns) + r Ns.  Each lane keeps its butterflies in
 // registers across a __syncwarp, so the stage runs in place.
+#include <stdio.h>
+
 #include <algorithm>
 
 #include "mpi_internal.h"
@@ -401,30 +403,26 @@ int lines_tile(const mpi_ctx* ctx, int L, int nx, int n_slabs) {
   return 8;
 }
 
+// Launch of one line pass with tile width `tile` (8, 16 or 32 lines); false
+// when the length / tile pair is not compiled.
 template <bool INV>
-mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, int nx, long stride, int n_slabs,
-                          int inner, long outer_stride, long inner_stride, const uint8_t* rmask = nullptr,
-                          int mask_nz = 1) {
-  const int tile = lines_tile(ctx, L, nx, n_slabs);
-  const int x_tiles = (nx + tile - 1) / tile;
-  const long blocks = (long)n_slabs * x_tiles;
-  if (blocks == 0) return MPI_OK;
-  if (blocks > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many FFT tiles");
-  const float2* tw = twiddle_table(ctx, L);
-  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
-#define MPI_LINES_CASE(n)                                                                                    \
-  case n:                                                                                                    \
-    if (n <= 128 && tile == 32)                                                                              \
-      lines_launch<n, INV, (n <= 128 ? 32 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,  \
-                                                inner_stride, tw, rmask, mask_nz);                          \
-    else if (n <= 256 && tile == 16)                                                                         \
-      lines_launch<n, INV, (n <= 256 ? 16 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,  \
-                                                inner_stride, tw, rmask, mask_nz);                          \
-    else                                                                                                     \
-      lines_launch<n, INV, 8>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw,   \
-                              rmask, mask_nz);                                                              \
-    break;
-  MPI_PROF(ctx, KF_FFT_LINES);
+bool lines_launch_tile(mpi_ctx* ctx, int tile, int L, long blocks, float2* data, int nx, long stride, int n_slabs,
+                       int inner, long outer_stride, long inner_stride, const float2* tw, const uint8_t* rmask,
+                       int mask_nz) {
+#define MPI_LINES_CASE(n)                                                                                     \
+  case n:                                                                                                     \
+    if (tile == 32 && n <= 128)                                                                               \
+      lines_launch<n, INV, (n <= 128 ? 32 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,   \
+                                                inner_stride, tw, rmask, mask_nz);                           \
+    else if (tile == 16 && n <= 256)                                                                          \
+      lines_launch<n, INV, (n <= 256 ? 16 : 8)>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride,   \
+                                                inner_stride, tw, rmask, mask_nz);                           \
+    else if (tile == 8)                                                                                       \
+      lines_launch<n, INV, 8>(ctx, blocks, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw,    \
+                              rmask, mask_nz);                                                               \
+    else                                                                                                      \
+      return false;                                                                                           \
+    return true;
   switch (L) {
     MPI_LINES_CASE(16)
     MPI_LINES_CASE(32)
@@ -437,9 +435,117 @@ mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, i
     MPI_LINES_CASE(320)
     MPI_LINES_CASE(512)
     default:
-      return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+      return false;
   }
 #undef MPI_LINES_CASE
+}
+
+// Autotuner of the line passes' tile width.  A pass shape is tuned once per
+// context: each candidate width (at most 16 elements per thread in the copy
+// phases) is launched once to warm up and then three times between two CUDA
+// events on the context's stream, on the tuning scratch buffer (the pass's
+// timing does not depend on the values it transforms); the fastest is kept.
+// Returns 0 when this call cannot tune (no scratch, capture in progress,
+// tuning off).
+template <bool INV>
+int lines_autotune(mpi_ctx* ctx, const long (&key)[10], int L, float2* data, int nx, long stride, int n_slabs,
+                   int inner, long outer_stride, long inner_stride, const float2* tw, const uint8_t* rmask,
+                   int mask_nz) {
+  if (!ctx->autotune || !ctx->tune_scratch) return 0;
+  // the elements the pass touches, from `data`: every slab base plus a full line set
+  const long last_slab = n_slabs - 1;
+  const size_t extent = (size_t)(last_slab / inner) * outer_stride + (size_t)(last_slab % inner) * inner_stride +
+                        (size_t)(L - 1) * stride + nx;
+  if (extent * sizeof(float2) > ctx->tune_scratch_bytes) return 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return 0;
+  float2* scratch = (float2*)ctx->tune_scratch;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    return 0;
+  }
+  mpi_ctx::TuneRecord rec;
+  for (int i = 0; i < 10; ++i) rec.key[i] = key[i];
+  rec.n = 0;
+  rec.choice = 0;
+  float best = 1e30f;
+  const int cands[3] = {8, 16, 32};
+  for (int tile : cands) {
+    if ((long)L * tile / (kLineWarps * 32) > 16) continue;
+    const long blocks = (long)n_slabs * ((nx + tile - 1) / tile);
+    if (blocks > 0x7fffffffL) continue;
+    if (!lines_launch_tile<INV>(ctx, tile, L, blocks, scratch, nx, stride, n_slabs, inner, outer_stride,
+                                inner_stride, tw, rmask, mask_nz))
+      continue;
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 3; ++r)
+      lines_launch_tile<INV>(ctx, tile, L, blocks, scratch, nx, stride, n_slabs, inner, outer_stride, inner_stride,
+                             tw, rmask, mask_nz);
+    cudaEventRecord(e1, ctx->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const float us = 1e3f * ms / 3.f;
+    rec.cand[rec.n] = tile;
+    rec.us[rec.n] = us;
+    rec.n++;
+    if (us < best) {
+      best = us;
+      rec.choice = tile;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rec.choice || cudaGetLastError() != cudaSuccess) return 0;
+  char buf[256];
+  int len = snprintf(buf, sizeof buf, "FFT line pass L=%d %s stride=%ld lines=%ld%s: tile %d (", L, INV ? "inverse" : "forward",
+                     stride, (long)n_slabs * nx, rmask ? " row-masked" : "", rec.choice);
+  for (int i = 0; i < rec.n && len < (int)sizeof buf; ++i)
+    len += snprintf(buf + len, sizeof buf - len, "%s%d: %.1f us", i ? ", " : "", rec.cand[i], rec.us[i]);
+  if (len < (int)sizeof buf) snprintf(buf + len, sizeof buf - len, ")");
+  rec.what = buf;
+  ctx->tuned.push_back(rec);
+  return rec.choice;
+}
+
+template <bool INV>
+mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, int nx, long stride, int n_slabs,
+                          int inner, long outer_stride, long inner_stride, const uint8_t* rmask = nullptr,
+                          int mask_nz = 1) {
+  const float2* tw = twiddle_table(ctx, L);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  if ((long)n_slabs * nx == 0) return MPI_OK;
+  const long key[10] = {L, INV ? 1 : 0, nx, stride, n_slabs, inner, outer_stride, inner_stride, rmask ? 1 : 0,
+                        mask_nz};
+  int tile = 0;
+  for (const auto& r : ctx->tuned)
+    if (std::equal(r.key, r.key + 10, key)) {
+      tile = r.choice;
+      break;
+    }
+  if (!tile)
+    tile = lines_autotune<INV>(ctx, key, L, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw, rmask,
+                               mask_nz);
+  if (!tile) tile = lines_tile(ctx, L, nx, n_slabs);
+  const int x_tiles = (nx + tile - 1) / tile;
+  const long blocks = (long)n_slabs * x_tiles;
+  if (blocks > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many FFT tiles");
+  MPI_PROF(ctx, KF_FFT_LINES);
+  if (!lines_launch_tile<INV>(ctx, tile, L, blocks, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw,
+                              rmask, mask_nz))
+    return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
   MPI_LAUNCH_CHECK(ctx, name);
   return MPI_OK;
 }

@@ -50,6 +50,22 @@ struct mpi_ctx {
   int pending_family = -1;
   double prof_ms[KF_COUNT] = {0};
   int64_t prof_launches[KF_COUNT] = {0};
+  // Autotuned launch shapes (fft.cu): one record per pass shape, with the
+  // candidates' measured times.  Tuning runs on `tune_scratch` (a workspace
+  // buffer the operator calls are not using at that point), never while the
+  // stream is being captured, and only while `autotune` is set.
+  bool autotune = true;
+  void* tune_scratch = nullptr;
+  size_t tune_scratch_bytes = 0;
+  struct TuneRecord {
+    long key[10];
+    int choice;
+    int n;
+    int cand[4];
+    float us[4];
+    std::string what;
+  };
+  std::vector<TuneRecord> tuned;
 };
 
 struct mpi_plan {

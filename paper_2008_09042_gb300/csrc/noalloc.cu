@@ -77,6 +77,15 @@ extern "C" mpi_status mpi_forward_noalloc(mpi_ctx* ctx, const mpi_plan* plan, co
   a.alpha = (const float2*)alpha;
   a.p = (const float2*)p;
   a.out = v;
+  // No launch-shape tuning here (it times candidates with events on scratch
+  // memory): the passes take a shape tuned by an earlier call, or the default.
+  void* scratch = ctx->tune_scratch;
+  ctx->tune_scratch = nullptr;
+  struct Restore {
+    mpi_ctx* c;
+    void* s;
+    ~Restore() { c->tune_scratch = s; }
+  } restore{ctx, scratch};
   if ((st = expand(ctx, basis, EX_FWD, a, MPI_PREC_FP32))) return st;
   if (plan->ndim == 3 && (st = launch_fft_z(ctx, v, C, plan->nz, plan->ny, plan->nx, false))) return st;
   if ((st = launch_fft_cols(ctx, v, C, plan->nz, plan->ny, plan->nx, false))) return st;

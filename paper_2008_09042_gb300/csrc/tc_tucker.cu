@@ -254,9 +254,14 @@ __device__ __forceinline__ float pos_sign(int z, int b, int nx) {
 
 // ------------------------------------------------------------------- kernel
 
+// Registers per thread: the most that lets one CTA of (6 + 4 N1 / 32) warps fit
+// the SM's 65,536 (a multiple of 8, at most 255).
+constexpr int tx_max_regs(int n1) {
+  return ((65536 / ((kEpi0 + 4 * (n1 / 32)) * 32)) & ~7) > 255 ? 255 : ((65536 / ((kEpi0 + 4 * (n1 / 32)) * 32)) & ~7);
+}
+
 template <int PREC, int MODE, int N1>
-__global__ void __launch_bounds__((kEpi0 + 4 * (N1 / 32)) * 32, 1)
-    k_tucker_x1(const __grid_constant__ CUtensorMap tmap, TxArgs a) {
+__global__ void __maxnreg__(tx_max_regs(N1)) k_tucker_x1(const __grid_constant__ CUtensorMap tmap, TxArgs a) {
   constexpr bool TF = PREC == 0;
   constexpr int NSUB = N1 / 32;          // epilogue warps per lane quarter
   constexpr int NEPI = 4 * NSUB;
@@ -442,6 +447,8 @@ __global__ void __launch_bounds__((kEpi0 + 4 * (N1 / 32)) * 32, 1)
     int b = 0;
     bool failed = false;
     int tc = 0;
+    float2 pnext[MODE == kTxFwd ? R : 1];  // forward: image values of the next sub-DFT
+    bool p_ready = false;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tc) {
       const int buf = tc & 1;
       const bool got = mpi_ptx::mbar_wait(&acc_full[buf], (uint32_t)((tc >> 1) & 1), a.err);
@@ -457,14 +464,25 @@ __global__ void __launch_bounds__((kEpi0 + 4 * (N1 / 32)) * 32, 1)
       const uint32_t tbase = tmem + lane_base + (uint32_t)(buf * NG);
       if (MODE == kTxFwd) {
         const float sb = ((b % a.nx + b / a.nx) & 1) ? -1.f : 1.f;
-        // stage 1: the 8 sub-DFTs of length R over z = j1 + 8 j2, in place
+        // stage 1: the 8 sub-DFTs of length R over z = j1 + 8 j2, in place.  The
+        // image values of the next j1 (or of the next tile's first j1) are
+        // loaded while the current one is transformed.
         constexpr int J1_PER = (8 + NSUB - 1) / NSUB;
-        for (int j1 = sub * J1_PER; j1 < min(8, (sub + 1) * J1_PER); ++j1) {
+        const int j1_lo = sub * J1_PER, j1_hi = min(8, (sub + 1) * J1_PER);
+        if (!p_ready) {
+#pragma unroll
+          for (int j2 = 0; j2 < R; ++j2) pnext[j2] = a.p[(size_t)(j1_lo + 8 * j2) * a.B + b];
+        }
+        for (int j1 = j1_lo; j1 < j1_hi; ++j1) {
           float2 v[R], pv[R];
 #pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) pv[j2] = a.p[(size_t)(j1 + 8 * j2) * a.B + b];
+          for (int j2 = 0; j2 < R; ++j2) pv[j2] = pnext[j2];
 #pragma unroll
           for (int j2 = 0; j2 < R; ++j2) tmem_ld2(tbase + 2u * (j1 + 8 * j2), v[j2]);
+          if (j1 + 1 < j1_hi) {
+#pragma unroll
+            for (int j2 = 0; j2 < R; ++j2) pnext[j2] = a.p[(size_t)(j1 + 1 + 8 * j2) * a.B + b];
+          }
           tmem_wait_ld();
 #pragma unroll
           for (int j2 = 0; j2 < R; ++j2) {
@@ -483,6 +501,13 @@ __global__ void __launch_bounds__((kEpi0 + 4 * (N1 / 32)) * 32, 1)
         fence_before();
         epi_bar_any(0, NT);
         fence_after();
+        p_ready = t + (int)gridDim.x < n_tiles;
+        if (p_ready) {
+          const int nn = (t + (int)gridDim.x) * kTileM + row;
+          const int bn = nn % a.B;
+#pragma unroll
+          for (int j2 = 0; j2 < R; ++j2) pnext[j2] = a.p[(size_t)(j1_lo + 8 * j2) * a.B + bn];
+        }
         // stage 2: the 8-point DFTs over j1 for each k2; output kz = k2 + R k1
         constexpr int K2_PER = (R + NSUB - 1) / NSUB;
         float2* o = a.out + (size_t)c * N1 * a.B + b;
@@ -501,11 +526,18 @@ __global__ void __launch_bounds__((kEpi0 + 4 * (N1 / 32)) * 32, 1)
       } else {
         // adjoint: conj(s_c) w_c for this thread's 32 values of z, summed over coils
         const float2* wp = a.w + (size_t)c * N1 * a.B + (size_t)(32 * sub) * a.B + b;
+        float2 wn[8];  // the next chunk's loads are issued before this chunk's arithmetic
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wn[i] = wp[(size_t)i * a.B];
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
-          float2 wv[8];  // this chunk's loads, issued before the accumulator read
+          float2 wv[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) wv[i] = wp[(size_t)(8 * ch + i) * a.B];
+          for (int i = 0; i < 8; ++i) wv[i] = wn[i];
+          if (ch + 1 < 4) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) wn[i] = wp[(size_t)(8 * (ch + 1) + i) * a.B];
+          }
           uint32_t raw[16];
           tmem_ld16_start(tbase + (uint32_t)(64 * sub + 16 * ch), raw);
           tmem_wait_ld();

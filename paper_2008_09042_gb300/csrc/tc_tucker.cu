@@ -20,8 +20,9 @@
 // warps, hi and lo coefficient rows as two MMAs into one accumulator); BF16:
 // one kind::f16 MMA per K step.  Double-buffered accumulator in tensor memory.
 //
-// Epilogue warps: 4 per 32 values of z (warps 6 .. 6 + 4 N1 / 32 - 1, the warp
-// index mod 4 picking its 32 tensor-memory lanes).
+// Epilogue warps: warps 6 and up, the warp index mod 4 picking its 32
+// tensor-memory lanes; two per lane quarter in the forward, one per 32 values
+// of z and lane quarter in the adjoint.
 //  - forward: the DFT of length N1 = 8 R along z is done per position (one
 //    thread) through tensor memory: for each j1 < 8 the R values
 //    z = j1 + 8 j2 are read, multiplied by the image and the centring sign,
@@ -254,16 +255,21 @@ __device__ __forceinline__ float pos_sign(int z, int b, int nx) {
 
 // ------------------------------------------------------------------- kernel
 
-// Registers per thread: the most that lets one CTA of (6 + 4 N1 / 32) warps fit
-// the SM's 65,536 (a multiple of 8, at most 255).
-constexpr int tx_max_regs(int n1) {
-  return ((65536 / ((kEpi0 + 4 * (n1 / 32)) * 32)) & ~7) > 255 ? 255 : ((65536 / ((kEpi0 + 4 * (n1 / 32)) * 32)) & ~7);
+// Epilogue warps per lane quarter: the adjoint holds 32 values of z per
+// thread (N1 / 32 warps per quarter); the forward splits its DFT work over two.
+// The CTA then has 6 + 4 NSUB warps; __launch_bounds__ lets the compiler size
+// the registers so that the warps of every SM sub-partition fit its register
+// file.
+template <int MODE, int N1>
+constexpr int tx_nsub() {
+  return MODE == kTxFwd ? 2 : N1 / 32;
 }
 
 template <int PREC, int MODE, int N1>
-__global__ void __maxnreg__(tx_max_regs(N1)) k_tucker_x1(const __grid_constant__ CUtensorMap tmap, TxArgs a) {
+__global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
+    k_tucker_x1(const __grid_constant__ CUtensorMap tmap, TxArgs a) {
   constexpr bool TF = PREC == 0;
-  constexpr int NSUB = N1 / 32;          // epilogue warps per lane quarter
+  constexpr int NSUB = tx_nsub<MODE, N1>();  // epilogue warps per lane quarter
   constexpr int NEPI = 4 * NSUB;
   constexpr int NG = 2 * N1;             // accumulator columns
   constexpr int R = N1 / 8;              // the DFT along z is 8 x R
@@ -526,18 +532,11 @@ __global__ void __maxnreg__(tx_max_regs(N1)) k_tucker_x1(const __grid_constant__
       } else {
         // adjoint: conj(s_c) w_c for this thread's 32 values of z, summed over coils
         const float2* wp = a.w + (size_t)c * N1 * a.B + (size_t)(32 * sub) * a.B + b;
-        float2 wn[8];  // the next chunk's loads are issued before this chunk's arithmetic
-#pragma unroll
-        for (int i = 0; i < 8; ++i) wn[i] = wp[(size_t)i * a.B];
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
-          float2 wv[8];
+          float2 wv[8];  // this chunk's loads, issued before the accumulator read
 #pragma unroll
-          for (int i = 0; i < 8; ++i) wv[i] = wn[i];
-          if (ch + 1 < 4) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) wn[i] = wp[(size_t)(8 * (ch + 1) + i) * a.B];
-          }
+          for (int i = 0; i < 8; ++i) wv[i] = wp[(size_t)(8 * ch + i) * a.B];
           uint32_t raw[16];
           tmem_ld16_start(tbase + (uint32_t)(64 * sub + 16 * ch), raw);
           tmem_wait_ld();
@@ -575,7 +574,7 @@ __global__ void __maxnreg__(tx_max_regs(N1)) k_tucker_x1(const __grid_constant__
 
 template <int PREC, int MODE, int N1>
 constexpr int tx_threads() {
-  return (kEpi0 + 4 * (N1 / 32)) * 32;
+  return (kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32;
 }
 
 template <int PREC, int N1>

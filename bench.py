@@ -166,7 +166,7 @@ def kernel_bytes_per_pair(case, prec):
         # adjoint: per-coil data in, image out
         pk = "bf16" if prec == "bf16" else "tf32x3"
         out[f"k_tucker_x1<{pk},fwd+dft_z>"] = ob * C * n2 * n3 * 2 * r1 + P + V
-        out[f"k_tucker_x1<{pk},adj>"] = ob * C * n2 * n3 * 2 * r1 + V + P
+        out[f"k_tucker_x1<{pk},idft_z+adj>"] = ob * C * n2 * n3 * 2 * r1 + V + P
     else:
         per = basis_bytes(case, prec) + 8 * C * q + V + P
         for k in ("k_expand_tf32x3", "k_expand_tc", "k_expand"):

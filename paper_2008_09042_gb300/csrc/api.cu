@@ -774,18 +774,21 @@ extern "C" mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   DeviceGuard g(ctx->device);
   Work w;
   if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
-  if ((st = kspace_to_image(ctx, plan, (const float2*)y, C, w.A, w.grid))) return st;
   ExpandArgs a = base_args(plan, basis, C);
   a.alpha = (const float2*)alpha;
   a.w = w.A;
   a.out = (float2*)p_out;
   if (tucker_x1_fused_supported(basis, plan, C, prec)) {
-    // the maps' x1 product fused with the sum over coils of conj(s_c) w_c
+    // inverse passes along x and y, then one tensor-core pass: the inverse DFT
+    // along z, the maps' x1 product and the sum over coils of conj(s_c) w_c
+    if ((st = launch_rows_scatter_inv(ctx, plan, (const float2*)y, C, w.A))) return st;
+    if ((st = launch_fft_cols(ctx, w.A, C, plan->nz, plan->ny, plan->nx, true, plan->row_has))) return st;
     void* op = nullptr;
     void* map = nullptr;
     if ((st = tucker_x1_operand(ctx, basis, a.alpha, C, w.T, prec, &op, &map))) return st;
-    return tucker_x1_fused_launch(ctx, basis, plan, true, C, map, nullptr, a.w, a.out, a.scale, prec);
+    return tucker_x1_fused_launch(ctx, basis, plan, true, C, map, nullptr, w.A, a.out, a.scale, prec);
   }
+  if ((st = kspace_to_image(ctx, plan, (const float2*)y, C, w.A, w.grid))) return st;
   return run_expand(ctx, basis, EX_ADJ, a, prec, w);
 }
 

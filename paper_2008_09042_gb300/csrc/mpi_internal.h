@@ -249,11 +249,12 @@ mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const f
 mpi_status tucker_x1_operand(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp,
                              mpi_precision prec, void** op_out, void** map_out);
 // The x1 product on the tensor cores fused with the forward's point-wise step
-// and DFT along z (out = vhat [C][n1][n2 n3]), or with the adjoint's sum over
-// coils of conj(s_c) w_c (out = image [N]) (tc_tucker.cu).
+// and DFT along z (out = vhat [C][n1][n2 n3]), or with the inverse DFT along z
+// of `wk` [C][n1][n2 n3] and the adjoint's sum over coils of conj(s_c) w_c
+// (out = image [N]) (tc_tucker.cu).
 bool tucker_x1_fused_supported(const mpi_basis* b, const mpi_plan* plan, int C, mpi_precision prec);
 mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_plan* plan, bool adjoint, int C,
-                                  const void* map, const float2* p, const float2* w, float2* out, float scale,
+                                  const void* map, const float2* p, const float2* wk, float2* out, float scale,
                                   mpi_precision prec);
 
 // Loads the module holding the allocation-free forward's static scratch on the

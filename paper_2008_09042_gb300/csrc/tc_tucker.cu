@@ -4,38 +4,35 @@
 //
 //   forward  (Eq. 5):  v_c[z][b] = sign(z, b) scale p[z][b] sum_a U1[z][a] T_c[a][b],
 //                      then the DFT of v_c along z, written as vhat_c[kz][b];
-//   adjoint:           x[z][b]  = sign(z, b) scale sum_c conj(s_c[z][b]) w_c[z][b],
+//   adjoint:           w_c = the inverse DFT along z of wk_c[kz][b] (the per-coil
+//                      data after the inverse passes along x and y), then
+//                      x[z][b] = sign(z, b) scale sum_c conj(s_c[z][b]) w_c[z][b],
 //                      s_c[z][b] = sum_a U1[z][a] T_c[a][b],
 //
 // with T_c = G alpha_c x3 U3 x2 U2 (the core contraction and the other two mode
-// products, made before this kernel), b = (y, x) the position in a z-plane, and
-// w_c the per-coil image-side data after the inverse FFT passes.  The coil maps
-// are never stored.
+// products, made before this kernel) and b = (y, x) the position in a z-plane.
+// The coil maps are never stored, and neither pass along z is a separate kernel.
 //
 // GEMM: the flattened operand rows are the positions (c, b) (K = [Re T | Im T]
 // over a), the coefficient rows are U1's rows real-ified as in the dense
 // expansion, so accumulator columns 2z, 2z + 1 of row (c, b) hold Re and Im of
-// s_c[z][b].  A 128-row tile is 128 consecutive positions of one coil.  FP32:
-// 3xTF32 (raw tile as hi, lo(T) staged in tensor memory by four converter
-// warps, hi and lo coefficient rows as two MMAs into one accumulator); BF16:
-// one kind::f16 MMA per K step.  Double-buffered accumulator in tensor memory.
+// s_c[z][b].  FP32: 3xTF32 (raw tile as hi, lo(T) staged in tensor memory by
+// four converter warps, hi and lo coefficient rows as two MMAs into one
+// accumulator); BF16: one kind::f16 MMA per K step.
 //
-// Epilogue warps: warps 6 and up, the warp index mod 4 picking its 32
-// tensor-memory lanes; two per lane quarter in the forward, one per 32 values
-// of z and lane quarter in the adjoint.
-//  - forward: the DFT of length N1 = 8 R along z is done per position (one
-//    thread) through tensor memory: for each j1 < 8 the R values
-//    z = j1 + 8 j2 are read, multiplied by the image and the centring sign,
-//    transformed (R-point DFT in registers), twiddled by w_N1^(j1 k2) and
-//    written back to the same columns; after a barrier of the epilogue warps
-//    each k2 < R reads its 8 values (16 consecutive columns), takes the 8-point
-//    DFT and stores vhat[k2 + R k1], k1 < 8.  The j1 and k2 work is split over
-//    the epilogue warps of a lane quarter.
-//  - adjoint: each thread accumulates its 32 values of z over the coils in
-//    registers; the CTA owns one 128-position block and runs through its tiles
-//    coil by coil (grid = positions / 128), writing the image at the end.
-// Every mbarrier wait is bounded; an epilogue decision that depends on a wait
-// is made uniform over the epilogue warps with a reducing barrier.
+// A CTA owns one block of 128 positions and runs through the coils (a 128-row
+// tile per coil), so the data that every coil of the block shares stays in
+// shared memory: the image block (forward) or the coil-sum accumulator
+// (adjoint), [N1][128] complex.  The DFT of length N1 = 8 R along z is done per
+// position (one thread) through tensor memory: for each j1 < 8 the R values
+// z = j1 + 8 j2 are transformed in registers (R-point DFT), twiddled by
+// w_N1^(j1 k2) and written back to the same columns; after a barrier of the
+// epilogue warps each k2 < R reads its 8 values (16 consecutive columns) and
+// takes the 8-point DFT, giving index k2 + R k1.  The inverse is the forward
+// on conjugated data.  The j1 and k2 work is split over the two epilogue warps
+// of each lane quarter.  Every mbarrier wait is bounded; an epilogue decision
+// that depends on a wait is made uniform over the epilogue warps with a
+// reducing barrier.
 #include <cuda.h>
 
 #include <algorithm>
@@ -59,12 +56,14 @@ struct TxArgs {
   int rows;      // C B operand rows
   int B;         // positions per z-plane (n2 n3), a multiple of 128
   int C;         // coils
+  int cgroups;   // forward: coil groups per position block (grid.y); coil c goes to group c % cgroups
   int nx, ny;    // the position b = y nx + x, for the centring sign
   int centre;
   float scale;
   const float2* p;   // image [N1][B]
   const float2* w;   // adjoint input [C][N1][B]
   float2* out;       // forward: vhat [C][N1][B]; adjoint: image [N1][B]
+  const float2* wk;  // adjoint input: per-coil data along kz [C][N1][B]
   const float2* tw;  // exp(-2 pi i m / N1), m < N1
   int* err;
   int tmem_cols;
@@ -255,32 +254,33 @@ __device__ __forceinline__ float pos_sign(int z, int b, int nx) {
 
 // ------------------------------------------------------------------- kernel
 
-// Epilogue warps per lane quarter: the adjoint holds 32 values of z per
-// thread (N1 / 32 warps per quarter); the forward splits its DFT work over two.
-// The CTA then has 6 + 4 NSUB warps; __launch_bounds__ lets the compiler size
-// the registers so that the warps of every SM sub-partition fit its register
-// file.
-template <int MODE, int N1>
-constexpr int tx_nsub() {
-  return MODE == kTxFwd ? 2 : N1 / 32;
-}
+constexpr int kNSub = 2;                  // epilogue warps per lane quarter
+constexpr int kNEpi = 4 * kNSub;          // epilogue warps
+constexpr int kTxThreads = (kEpi0 + kNEpi) * 32;
+
+template <int PREC, int N1>
+struct TxShape {
+  static constexpr bool TF = PREC == 0;
+  static constexpr int NG = 2 * N1;  // accumulator columns
+  static constexpr int STAGE = TF ? 2 * kBox32 : kTileM * 128;
+  static constexpr uint32_t B_BYTES = TF ? 2u * NG * kKp * 4 : (uint32_t)NG * kKp * 2;
+  static constexpr uint32_t B_PAD = (B_BYTES + 1023) & ~1023u;
+  static constexpr uint32_t X_BYTES = (uint32_t)N1 * kTileM * 8;  // [N1][128] complex
+};
 
 template <int PREC, int MODE, int N1>
-__global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
-    k_tucker_x1(const __grid_constant__ CUtensorMap tmap, TxArgs a) {
-  constexpr bool TF = PREC == 0;
-  constexpr int NSUB = tx_nsub<MODE, N1>();  // epilogue warps per lane quarter
-  constexpr int NEPI = 4 * NSUB;
-  constexpr int NG = 2 * N1;             // accumulator columns
-  constexpr int R = N1 / 8;              // the DFT along z is 8 x R
-  constexpr int STAGE = TF ? 2 * kBox32 : kTileM * 128;
+__global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_constant__ CUtensorMap tmap, TxArgs a) {
+  using S = TxShape<PREC, N1>;
+  constexpr bool TF = S::TF;
+  constexpr int NG = S::NG;
+  constexpr int R = N1 / 8;  // the DFT along z is 8 x R
+  constexpr int STAGE = S::STAGE;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int stages = a.stages;
-  constexpr uint32_t b_bytes = TF ? 2u * NG * kKp * 4 : (uint32_t)NG * kKp * 2;
-  constexpr uint32_t b_pad = (b_bytes + 1023) & ~1023u;
   unsigned char* sB = smem;
-  unsigned char* sA = smem + b_pad;
+  float2* sX = reinterpret_cast<float2*>(smem + S::B_PAD);  // image block or coil-sum accumulator
+  unsigned char* sA = smem + S::B_PAD + S::X_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(sA + (size_t)stages * STAGE);
   uint64_t* conv = full + stages;
   uint64_t* empty = conv + stages;
@@ -293,9 +293,12 @@ __global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
   __shared__ int s_failed;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // the operand is written by the previous kernel in the stream
+  // the operand and the per-coil data are written by the previous kernels
   mpi_ptx::pdl_wait();
   mpi_ptx::pdl_trigger();
+  // forward: double-buffered accumulator; adjoint: one accumulator plus a
+  // scratch block for the inverse DFT along z
+  constexpr int NACC = MODE == kTxFwd ? 2 : 1;
   if (tid == 0) {
     s_failed = 0;
     for (int s = 0; s < stages; ++s) {
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mpi_ptx::mbar_init(&acc_full[b], 1);
-      mpi_ptx::mbar_init(&acc_empty[b], NEPI);
+      mpi_ptx::mbar_init(&acc_empty[b], kNEpi);
     }
     mpi_ptx::mbar_init(drain, 1);
     mpi_ptx::mbar_init(bfull, 4);
@@ -322,24 +325,24 @@ __global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tmem_lo = tmem + 2u * NG;  // lo(T) slots: 64 columns per stage (FP32)
-  const int n_tiles = a.rows / kTileM;
-  const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const uint32_t tmem_scr = tmem + (uint32_t)NG;           // adjoint: DFT scratch
+  const uint32_t tmem_lo = tmem + 2u * NG;                 // lo(T) slots: 64 columns per stage (FP32)
+  // this CTA: position block blockIdx.x, coils blockIdx.y, blockIdx.y + gridDim.y, ...
+  const int nb = a.B / kTileM;
+  const int my_tiles = (int)blockIdx.y < a.C ? (a.C - 1 - (int)blockIdx.y) / (int)gridDim.y + 1 : 0;
+  auto tile_row0 = [&](int k) -> int { return ((int)blockIdx.y + k * (int)gridDim.y) * a.B + (int)blockIdx.x * kTileM; };
+  (void)nb;
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer: one stage (the whole K = 64) per tile
     RingPos r;
     int g = 0;
-    for (int t = blockIdx.x; g < my_tiles; ++g, t += gridDim.x) {
+    for (; g < my_tiles; ++g) {
       if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err)) break;
       unsigned char* dst = sA + (size_t)r.s * STAGE;
       mpi_ptx::mbar_arrive_expect_tx(&full[r.s], STAGE);
-      if (TF) {
-        tma_load_2d(dst, &tmap, 0, t * kTileM, &full[r.s]);
-        tma_load_2d(dst + kBox32, &tmap, 32, t * kTileM, &full[r.s]);
-      } else {
-        tma_load_2d(dst, &tmap, 0, t * kTileM, &full[r.s]);
-      }
+      tma_load_2d(dst, &tmap, 0, tile_row0(g), &full[r.s]);
+      if (TF) tma_load_2d(dst + kBox32, &tmap, 32, tile_row0(g), &full[r.s]);
       r.next(stages);
     }
     if (g < my_tiles) {
@@ -385,9 +388,10 @@ __global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
     RingPos r;
     bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err);
     for (int tc = 0; tc < my_tiles && ok; ++tc) {
-      const int buf = tc & 1;
+      const int buf = NACC == 2 ? (tc & 1) : 0;
+      const uint32_t par = NACC == 2 ? (uint32_t)((tc >> 1) & 1) : (uint32_t)(tc & 1);
       const uint32_t tacc = tmem + (uint32_t)(buf * NG);
-      if (!mpi_ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), a.err)) {
+      if (!mpi_ptx::mbar_wait(&acc_empty[buf], par ^ 1u, a.err)) {
         ok = false;
         break;
       }
@@ -436,131 +440,151 @@ __global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
     mpi_ptx::mbar_wait(drain, 0, a.err);
     if (!ok) s_failed = 1;
   } else if (warp >= kEpi0) {
-    // ---------------- epilogue
+    // ---------------- epilogue: 2 warps per lane quarter (sub 0, 1)
     const int e = warp - kEpi0;
     const int qd = warp & 3, sub = e >> 2;
     const int row = qd * 32 + lane;
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-    constexpr int NT = NEPI * 32;
-    if (e < 4) build_coef_smem<TF>(a.coef, sB, kKp, false, e * 32 + lane, bfull);
-    for (int i = e * 32 + lane; i < N1; i += NT) s_tw[i] = a.tw[i];
-    epi_bar_any(0, NT);  // twiddles visible to every epilogue warp
-    float2 pacc[32];
-    if (MODE == kTxAdj) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) pacc[j] = make_float2(0.f, 0.f);
+    constexpr int NT = kNEpi * 32;
+    const int et = e * 32 + lane;  // 0 .. NT - 1
+    const int b = (int)blockIdx.x * kTileM + row;
+    if (e < 4) build_coef_smem<TF>(a.coef, sB, kKp, false, et, bfull);
+    for (int i = et; i < N1; i += NT) s_tw[i] = a.tw[i];
+    // forward: this block's image values; adjoint: a zeroed accumulator ([z][position])
+    for (int i = et; i < N1 * kTileM; i += NT) {
+      const int z = i / kTileM, pos = i - z * kTileM;
+      sX[i] = MODE == kTxFwd ? a.p[(size_t)z * a.B + (size_t)blockIdx.x * kTileM + pos] : make_float2(0.f, 0.f);
     }
-    int b = 0;
+    epi_bar_any(0, NT);
+    constexpr int J1_PER = 8 / kNSub, K2_PER = (R + kNSub - 1) / kNSub;
+    const int j1_lo = sub * J1_PER, k2_lo = sub * K2_PER, k2_hi = min(R, (sub + 1) * K2_PER);
+    const float sb = ((b % a.nx + b / a.nx) & 1) ? -1.f : 1.f;
     bool failed = false;
-    int tc = 0;
-    float2 pnext[MODE == kTxFwd ? R : 1];  // forward: image values of the next sub-DFT
-    bool p_ready = false;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tc) {
-      const int buf = tc & 1;
-      const bool got = mpi_ptx::mbar_wait(&acc_full[buf], (uint32_t)((tc >> 1) & 1), a.err);
-      if (epi_bar_any(!got, NT)) {
-        failed = true;
-        s_failed = 1;
-        break;
-      }
-      fence_after();
-      const int n = t * kTileM + row;
-      const int c = n / a.B;
-      b = n - c * a.B;
-      const uint32_t tbase = tmem + lane_base + (uint32_t)(buf * NG);
+    for (int tc = 0; tc < my_tiles; ++tc) {
+      const int c = (int)blockIdx.y + tc * (int)gridDim.y;
+      const int buf = NACC == 2 ? (tc & 1) : 0;
+      const uint32_t par = NACC == 2 ? (uint32_t)((tc >> 1) & 1) : (uint32_t)(tc & 1);
+      const uint32_t tacc = tmem + lane_base + (uint32_t)(buf * NG);
       if (MODE == kTxFwd) {
-        const float sb = ((b % a.nx + b / a.nx) & 1) ? -1.f : 1.f;
-        // stage 1: the 8 sub-DFTs of length R over z = j1 + 8 j2, in place.  The
-        // image values of the next j1 (or of the next tile's first j1) are
-        // loaded while the current one is transformed.
-        constexpr int J1_PER = (8 + NSUB - 1) / NSUB;
-        const int j1_lo = sub * J1_PER, j1_hi = min(8, (sub + 1) * J1_PER);
-        if (!p_ready) {
-#pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) pnext[j2] = a.p[(size_t)(j1_lo + 8 * j2) * a.B + b];
+        const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err);
+        if (epi_bar_any(!got, NT)) {
+          failed = true;
+          break;
         }
-        for (int j1 = j1_lo; j1 < j1_hi; ++j1) {
-          float2 v[R], pv[R];
+        fence_after();
+        // stage 1: v = s p sign scale over z = j1 + 8 j2, R-point DFT, twiddle, in place
+        for (int j1 = j1_lo; j1 < j1_lo + J1_PER; ++j1) {
+          float2 v[R];
 #pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) pv[j2] = pnext[j2];
-#pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) tmem_ld2(tbase + 2u * (j1 + 8 * j2), v[j2]);
-          if (j1 + 1 < j1_hi) {
-#pragma unroll
-            for (int j2 = 0; j2 < R; ++j2) pnext[j2] = a.p[(size_t)(j1 + 1 + 8 * j2) * a.B + b];
-          }
+          for (int j2 = 0; j2 < R; ++j2) tmem_ld2(tacc + 2u * (j1 + 8 * j2), v[j2]);
           tmem_wait_ld();
 #pragma unroll
           for (int j2 = 0; j2 < R; ++j2) {
             fence_reg2(v[j2]);
             const int z = j1 + 8 * j2;
-            const float sg = (a.centre && (z & 1) ? -sb : (a.centre ? sb : 1.f)) * a.scale;
-            v[j2] = cscale(cmulf(v[j2], pv[j2]), sg);
+            const float sg = (a.centre ? ((z & 1) ? -sb : sb) : 1.f) * a.scale;
+            v[j2] = cscale(cmulf(v[j2], sX[z * kTileM + row]), sg);
           }
           dft_r<R>(v);
 #pragma unroll
           for (int k2 = 1; k2 < R; ++k2) v[k2] = cmulf(v[k2], s_tw[(j1 * k2) % N1]);
 #pragma unroll
-          for (int k2 = 0; k2 < R; ++k2) tmem_st2(tbase + 2u * (j1 + 8 * k2), v[k2]);
+          for (int k2 = 0; k2 < R; ++k2) tmem_st2(tacc + 2u * (j1 + 8 * k2), v[k2]);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
         epi_bar_any(0, NT);
         fence_after();
-        p_ready = t + (int)gridDim.x < n_tiles;
-        if (p_ready) {
-          const int nn = (t + (int)gridDim.x) * kTileM + row;
-          const int bn = nn % a.B;
-#pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) pnext[j2] = a.p[(size_t)(j1_lo + 8 * j2) * a.B + bn];
-        }
-        // stage 2: the 8-point DFTs over j1 for each k2; output kz = k2 + R k1
-        constexpr int K2_PER = (R + NSUB - 1) / NSUB;
+        // stage 2: 8-point DFTs over j1 for each k2; output kz = k2 + R k1
         float2* o = a.out + (size_t)c * N1 * a.B + b;
-        for (int k2 = sub * K2_PER; k2 < min(R, (sub + 1) * K2_PER); ++k2) {
+        for (int k2 = k2_lo; k2 < k2_hi; ++k2) {
           uint32_t raw[16];
-          tmem_ld16_start(tbase + 16u * k2, raw);
+          tmem_ld16_start(tacc + 16u * k2, raw);
           tmem_wait_ld();
           reg_fence16(raw);
           float2 u[8];
 #pragma unroll
-          for (int j1 = 0; j1 < 8; ++j1) u[j1] = make_float2(__uint_as_float(raw[2 * j1]), __uint_as_float(raw[2 * j1 + 1]));
+          for (int j1 = 0; j1 < 8; ++j1)
+            u[j1] = make_float2(__uint_as_float(raw[2 * j1]), __uint_as_float(raw[2 * j1 + 1]));
           dft8(u);
 #pragma unroll
           for (int k1 = 0; k1 < 8; ++k1) o[(size_t)(k2 + R * k1) * a.B] = u[k1];
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mpi_ptx::mbar_arrive(&acc_empty[buf]);
       } else {
-        // adjoint: conj(s_c) w_c for this thread's 32 values of z, summed over coils
-        const float2* wp = a.w + (size_t)c * N1 * a.B + (size_t)(32 * sub) * a.B + b;
+        // stage 1 (no accumulator needed): the inverse DFT along z of wk_c,
+        // first half: conjugated inputs kz = j1 + 8 j2, R-point DFT, twiddle,
+        // into the scratch columns j1 + 8 k2.  The next j1's loads are issued
+        // before the current one is transformed.
+        const float2* wk = a.wk + (size_t)c * N1 * a.B + b;
+        float2 nxt[R];
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          float2 wv[8];  // this chunk's loads, issued before the accumulator read
+        for (int j2 = 0; j2 < R; ++j2) nxt[j2] = wk[(size_t)(j1_lo + 8 * j2) * a.B];
+        for (int j1 = j1_lo; j1 < j1_lo + J1_PER; ++j1) {
+          float2 v[R];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) wv[i] = wp[(size_t)(8 * ch + i) * a.B];
+          for (int j2 = 0; j2 < R; ++j2) v[j2] = make_float2(nxt[j2].x, -nxt[j2].y);
+          if (j1 + 1 < j1_lo + J1_PER) {
+#pragma unroll
+            for (int j2 = 0; j2 < R; ++j2) nxt[j2] = wk[(size_t)(j1 + 1 + 8 * j2) * a.B];
+          }
+          dft_r<R>(v);
+#pragma unroll
+          for (int k2 = 1; k2 < R; ++k2) v[k2] = cmulf(v[k2], s_tw[(j1 * k2) % N1]);
+#pragma unroll
+          for (int k2 = 0; k2 < R; ++k2) tmem_st2(tmem_scr + lane_base + 2u * (j1 + 8 * k2), v[k2]);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_before();
+        const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err);
+        if (epi_bar_any(!got, NT)) {
+          failed = true;
+          break;
+        }
+        fence_after();
+        // stage 2: 8-point DFTs over j1, conjugated back: w_c[z], z = k2 + R k1;
+        // then the accumulator's conj(s_c[z]) times w_c[z] into the coil sum
+        for (int k2 = k2_lo; k2 < k2_hi; ++k2) {
           uint32_t raw[16];
-          tmem_ld16_start(tbase + (uint32_t)(64 * sub + 16 * ch), raw);
+          float2 sv[8];
+          tmem_ld16_start(tmem_scr + lane_base + 16u * k2, raw);
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) tmem_ld2(tacc + 2u * (k2 + R * k1), sv[k1]);
           tmem_wait_ld();
           reg_fence16(raw);
+          float2 u[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float2 s = make_float2(__uint_as_float(raw[2 * i]), __uint_as_float(raw[2 * i + 1]));
-            const float2 wz = wv[i];
-            pacc[8 * ch + i].x += s.x * wz.x + s.y * wz.y;
-            pacc[8 * ch + i].y += s.x * wz.y - s.y * wz.x;
+          for (int j1 = 0; j1 < 8; ++j1)
+            u[j1] = make_float2(__uint_as_float(raw[2 * j1]), __uint_as_float(raw[2 * j1 + 1]));
+          dft8(u);
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) {
+            fence_reg2(sv[k1]);
+            const float2 wz = make_float2(u[k1].x, -u[k1].y);
+            float2& acc = sX[(k2 + R * k1) * kTileM + row];
+            acc.x += sv[k1].x * wz.x + sv[k1].y * wz.y;
+            acc.y += sv[k1].x * wz.y - sv[k1].y * wz.x;
           }
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mpi_ptx::mbar_arrive(&acc_empty[buf]);
+        // the scratch columns are rewritten by the next tile's first stage
+        epi_bar_any(0, NT);
+        fence_after();
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mpi_ptx::mbar_arrive(&acc_empty[buf]);
     }
+    if (failed) s_failed = 1;
     if (MODE == kTxAdj && !failed && my_tiles > 0) {
-      // the CTA's tiles are every coil of one 128-position block: write the image
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int z = 32 * sub + j;
-        const float sg = (a.centre ? pos_sign(z, b, a.nx) : 1.f) * a.scale;
-        a.out[(size_t)z * a.B + b] = cscale(pacc[j], sg);
+      epi_bar_any(0, NT);
+      // the coil sum of this position block: the image, with sign and scale
+      for (int i = et; i < N1 * kTileM; i += NT) {
+        const int z = i / kTileM, pos = i - z * kTileM;
+        const int bb = (int)blockIdx.x * kTileM + pos;
+        const float sg = (a.centre ? pos_sign(z, bb, a.nx) : 1.f) * a.scale;
+        a.out[(size_t)z * a.B + bb] = cscale(sX[i], sg);
       }
     }
   }
@@ -572,44 +596,37 @@ __global__ void __launch_bounds__((kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32, 1)
   }
 }
 
-template <int PREC, int MODE, int N1>
-constexpr int tx_threads() {
-  return (kEpi0 + 4 * tx_nsub<MODE, N1>()) * 32;
-}
-
 template <int PREC, int N1>
 size_t tx_smem(int stages) {
-  constexpr int NG = 2 * N1;
-  const size_t b_bytes = PREC == 0 ? 2 * (size_t)NG * kKp * 4 : (size_t)NG * kKp * 2;
-  const size_t stage = PREC == 0 ? 2 * kBox32 : kTileM * 128;
-  return 1024 + ((b_bytes + 1023) & ~(size_t)1023) + stages * stage + 8 * (3 * stages + 6) + 16;
+  using S = TxShape<PREC, N1>;
+  return 1024 + S::B_PAD + S::X_BYTES + (size_t)stages * S::STAGE + 8 * (3 * stages + 6) + 16;
 }
 
 template <int PREC, int MODE, int N1>
-mpi_status tx_launch(mpi_ctx* ctx, const CUtensorMap* map, TxArgs& a, int grid) {
-  // ring depth: as many stages as fit (at most 4), at least 2
+mpi_status tx_launch(mpi_ctx* ctx, const CUtensorMap* map, TxArgs& a, dim3 grid) {
+  using S = TxShape<PREC, N1>;
   int stages = 4;
-  while (stages > 2 && tx_smem<PREC, N1>(stages) > kSmemCap) --stages;
-  const size_t smem = tx_smem<PREC, N1>(stages);
-  if (smem > kSmemCap) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker x1 kernel: shared memory");
-  constexpr int NG = 2 * N1;
-  int cols = PREC == 0 ? 2 * NG + 64 * stages : 2 * NG;
-  if (PREC == 0 && cols > 512) {
-    stages = 2;
-    cols = 2 * NG + 128;
-  }
-  if (cols > 512) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker x1 kernel: tensor memory");
+  while (stages > 1 && tx_smem<PREC, N1>(stages) > kSmemCap) --stages;
+  if (tx_smem<PREC, N1>(stages) > kSmemCap) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker x1 kernel: shared memory");
+  // tensor memory: accumulators (two forward, one adjoint), the adjoint's DFT
+  // scratch, the lo(T) slots of the FP32 kernel
+  auto cols_for = [&](int st) {
+    return (MODE == kTxFwd ? 2 * S::NG : 2 * S::NG) + (PREC == 0 ? 64 * st : 0);
+  };
+  while (stages > 1 && cols_for(stages) > 512) --stages;
+  if (cols_for(stages) > 512) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker x1 kernel: tensor memory");
   int tcols = 32;
-  while (tcols < cols) tcols <<= 1;
+  while (tcols < cols_for(stages)) tcols <<= 1;
   a.tmem_cols = tcols;
   a.stages = stages;
+  const size_t smem = tx_smem<PREC, N1>(stages);
   auto kern = k_tucker_x1<PREC, MODE, N1>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tx_smem<PREC, N1>(stages));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "Tucker x1 smem attribute");
   MPI_PROF(ctx, KF_EXPAND);
-  launch_pdl(ctx, kern, dim3(grid), dim3(tx_threads<PREC, MODE, N1>()), tx_smem<PREC, N1>(stages), *map, a);
+  launch_pdl(ctx, kern, grid, dim3(kTxThreads), smem, *map, a);
   MPI_LAUNCH_CHECK(ctx, MODE == kTxFwd ? (PREC == 0 ? "k_tucker_x1<tf32x3,fwd+dft_z>" : "k_tucker_x1<bf16,fwd+dft_z>")
-                                       : (PREC == 0 ? "k_tucker_x1<tf32x3,adj>" : "k_tucker_x1<bf16,adj>"));
+                                       : (PREC == 0 ? "k_tucker_x1<tf32x3,idft_z+adj>" : "k_tucker_x1<bf16,idft_z+adj>"));
   return MPI_OK;
 }
 
@@ -622,17 +639,17 @@ bool tucker_x1_fused_supported(const mpi_basis* b, const mpi_plan* plan, int C, 
   if (!(n1 == 64 || n1 == 96 || (n1 == 128 && prec == MPI_PREC_BF16))) return false;
   if (2 * b->r[0] > kKp) return false;
   const long B = (long)b->n[1] * b->n[2];
-  if (B % kTileM || (long)C * B > 0x7fffffffL) return false;
-  // the adjoint's grid is one CTA per 128-position block
-  if (B / kTileM > 65535) return false;
+  if (B % kTileM || (long)C * B > 0x7fffffffL || C > 65535) return false;
+  if (B / kTileM > 0x7fffffffL) return false;
   return plan->nz == b->n[0] && plan->ny == b->n[1] && plan->nx == b->n[2];
 }
 
-// x1 product fused with the forward's point-wise step and the DFT along z (fwd)
-// or with the adjoint's conj(s) w sum over coils (adj).  `op` is the flattened
-// operand [C B][64] (FP32 or BF16, from k_x1_operand) and `map` its tensor map.
+// x1 product fused with the forward's point-wise step and the DFT along z
+// (forward: out = vhat [C][n1][n2 n3]), or with the inverse DFT along z of `wk`
+// and the adjoint's coil sum (adjoint: out = image [N]).  `map` is the tensor
+// map of the flattened operand [C B][64] (FP32 or BF16, from k_x1_operand).
 mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_plan* plan, bool adjoint, int C,
-                                  const void* map, const float2* p, const float2* w, float2* out, float scale,
+                                  const void* map, const float2* p, const float2* wk, float2* out, float scale,
                                   mpi_precision prec) {
   TxArgs a;
   const long B = (long)b->n[1] * b->n[2];
@@ -644,7 +661,8 @@ mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_pl
   a.centre = 1;
   a.scale = scale;
   a.p = p;
-  a.w = w;
+  a.w = nullptr;
+  a.wk = wk;
   a.out = out;
   a.tw = twiddle_table(ctx, b->n[0]);
   a.err = ctx->dev_err;
@@ -656,8 +674,13 @@ mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_pl
   cf.n_gemm = 2 * b->n[0];
   cf.half = cf.n_gemm;
   cf.alpha = b->F[0];
-  const int n_tiles = (int)(C * B / kTileM);
-  const int grid = adjoint ? (int)(B / kTileM) : std::min(n_tiles, std::max(ctx->num_sms, 1));
+  // one CTA per 128-position block; the forward splits the coils into groups
+  // when there are fewer blocks than SMs (the adjoint's coil sum stays in one CTA)
+  const int nb = (int)(B / kTileM);
+  int groups = 1;
+  if (!adjoint) groups = std::max(1, std::min(C, std::max(ctx->num_sms, 1) / nb));
+  a.cgroups = groups;
+  const dim3 grid((unsigned)nb, (unsigned)groups);
   const CUtensorMap* m = (const CUtensorMap*)map;
   const bool bf = prec == MPI_PREC_BF16;
 #define MPI_TX(P, M, N)                                   \

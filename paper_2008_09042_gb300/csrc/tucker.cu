@@ -41,8 +41,8 @@ __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * 
   return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
-constexpr int kIB = 16;  // outputs along i per thread
 constexpr int kPB = 8;   // contracted elements loaded per batch
+constexpr int kIB1 = 16; // outputs along i per thread of the CUDA-core x1 forward
 
 // Y[r][i][b] = sum_p X[r][p][b] M(i, p), with M(i, p) = F[i][p] (forward, F is I x P)
 // or conj(F[p][i]) (adjoint, F is P x I).  Threads run along b (coalesced);
@@ -50,7 +50,7 @@ constexpr int kPB = 8;   // contracted elements loaded per batch
 // memory as [P][kIB] for the CTA's i-block.  The i-block is the fastest grid
 // index, so the CTAs that read the same X tile run together and all but the
 // first find it in L2.
-template <bool ADJ>
+template <bool ADJ, int kIB>
 __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, const float2* __restrict__ F, int R,
                                                 int P, int I, long B, float2* __restrict__ Y) {
   mpi_ptx::pdl_trigger();
@@ -103,38 +103,67 @@ __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, co
 }
 
 // Same contraction with B = 1 (last mode): Y[r][i] = sum_p X[r][p] M(i, p).
-// Threads run along i; the CTA handles 8 rows r, whose X rows sit in shared memory.
+// A CTA of 256 threads takes 64 rows r and every i: M is staged in shared
+// memory as [p][i] (so a warp's lanes read consecutive i), the CTA's X rows as
+// [r][p]; each thread accumulates 8 rows (warp-uniform, shared-memory
+// broadcasts) x 4 values of i (i = lane + 32 k) in registers.
+constexpr int kLastRows = 64;
 template <bool ADJ>
 __global__ void __launch_bounds__(256) k_mode_last(const float2* __restrict__ X, const float2* __restrict__ F, int R,
                                                    int P, int I, float2* __restrict__ Y) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
-  constexpr int kRows = 8;
-  __shared__ float2 sX[kRows * 128];
-  const int r0 = blockIdx.x * kRows;
-  for (int e = threadIdx.x; e < kRows * P; e += blockDim.x) {
-    const int rr = e / P, p = e % P;
-    sX[e] = (r0 + rr < R) ? X[(size_t)(r0 + rr) * P + p] : make_float2(0.f, 0.f);
+  extern __shared__ float2 sh[];
+  float2* sM = sh;                           // [P][I]
+  float2* sX = sh + (size_t)P * I;           // [kLastRows][P]
+  const int r0 = blockIdx.x * kLastRows;
+  for (int e = threadIdx.x; e < P * I; e += blockDim.x) {
+    const int p = e / I, i = e - p * I;
+    float2 m;
+    if (ADJ) {
+      const float2 f = F[(size_t)p * I + i];
+      m = make_float2(f.x, -f.y);
+    } else {
+      m = F[(size_t)i * P + p];
+    }
+    sM[e] = m;
+  }
+  for (int e = threadIdx.x; e < kLastRows * P; e += blockDim.x) {
+    const int rr = e / P;
+    sX[e] = (r0 + rr < R) ? X[(size_t)r0 * P + e] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < I; i += blockDim.x) {
-    float2 acc[kRows];
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;  // rows rg * 8 .. rg * 8 + 7
+  for (int i0 = 0; i0 < I; i0 += 128) {
+    float2 acc[8][4];
 #pragma unroll
-    for (int rr = 0; rr < kRows; ++rr) acc[rr] = make_float2(0.f, 0.f);
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[j][k] = make_float2(0.f, 0.f);
     for (int p = 0; p < P; ++p) {
-      float2 m;
-      if (ADJ) {
-        const float2 f = F[(size_t)p * I + i];
-        m = make_float2(f.x, -f.y);
-      } else {
-        m = F[(size_t)i * P + p];
+      float2 m[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = i0 + lane + 32 * k;
+        m[k] = i < I ? sM[p * I + i] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int rr = 0; rr < kRows; ++rr) cfma(acc[rr], sX[rr * P + p], m);
+      for (int j = 0; j < 8; ++j) {
+        const float2 x = sX[(rg * 8 + j) * P + p];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cfma(acc[j][k], x, m[k]);
+      }
     }
 #pragma unroll
-    for (int rr = 0; rr < kRows; ++rr)
-      if (r0 + rr < R) Y[(size_t)(r0 + rr) * I + i] = acc[rr];
+    for (int j = 0; j < 8; ++j) {
+      const int r = r0 + rg * 8 + j;
+      if (r >= R) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = i0 + lane + 32 * k;
+        if (i < I) Y[(size_t)r * I + i] = acc[j][k];
+      }
+    }
   }
 }
 
@@ -194,12 +223,12 @@ __global__ void __launch_bounds__(256) k_mode1_fwd(const float2* __restrict__ X,
                                                    int I, long B, ExpandArgs a) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
-  __shared__ float2 sM[(128 + kPB) * kIB];  // M(i, p) = F[i][p] of the i-block; rows beyond P are zero
-  const int i0 = blockIdx.x * kIB;
-  for (int e = P * kIB + threadIdx.x; e < ((P + kPB - 1) / kPB) * kPB * kIB; e += blockDim.x)
+  __shared__ float2 sM[(128 + kPB) * kIB1];  // M(i, p) = F[i][p] of the i-block; rows beyond P are zero
+  const int i0 = blockIdx.x * kIB1;
+  for (int e = P * kIB1 + threadIdx.x; e < ((P + kPB - 1) / kPB) * kPB * kIB1; e += blockDim.x)
     sM[e] = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < P * kIB; e += blockDim.x) {
-    const int p = e / kIB, ii = e % kIB;
+  for (int e = threadIdx.x; e < P * kIB1; e += blockDim.x) {
+    const int p = e / kIB1, ii = e % kIB1;
     sM[e] = i0 + ii < I ? F[(size_t)(i0 + ii) * P + p] : make_float2(0.f, 0.f);
   }
   __syncthreads();
@@ -208,12 +237,12 @@ __global__ void __launch_bounds__(256) k_mode1_fwd(const float2* __restrict__ X,
   if (b >= B || c >= a.C) return;
   // the image values this thread multiplies, loaded before the contraction so
   // that their latency overlaps it
-  float2 pv[kIB];
+  float2 pv[kIB1];
 #pragma unroll
-  for (int ii = 0; ii < kIB; ++ii) pv[ii] = i0 + ii < I ? a.p[(size_t)(i0 + ii) * B + b] : make_float2(0.f, 0.f);
-  float2 acc[kIB];
+  for (int ii = 0; ii < kIB1; ++ii) pv[ii] = i0 + ii < I ? a.p[(size_t)(i0 + ii) * B + b] : make_float2(0.f, 0.f);
+  float2 acc[kIB1];
 #pragma unroll
-  for (int ii = 0; ii < kIB; ++ii) acc[ii] = make_float2(0.f, 0.f);
+  for (int ii = 0; ii < kIB1; ++ii) acc[ii] = make_float2(0.f, 0.f);
   const float2* x = X + (size_t)c * P * B + b;
   for (int p0 = 0; p0 < P; p0 += kPB) {
     float2 xv[kPB];
@@ -221,9 +250,9 @@ __global__ void __launch_bounds__(256) k_mode1_fwd(const float2* __restrict__ X,
     for (int u = 0; u < kPB; ++u) xv[u] = p0 + u < P ? x[(size_t)(p0 + u) * B] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < kPB; ++u) {
-      const float4* mp = reinterpret_cast<const float4*>(sM + (p0 + u) * kIB);
+      const float4* mp = reinterpret_cast<const float4*>(sM + (p0 + u) * kIB1);
 #pragma unroll
-      for (int i2 = 0; i2 < kIB / 2; ++i2) {
+      for (int i2 = 0; i2 < kIB1 / 2; ++i2) {
         const float4 m = mp[i2];
         cfma(acc[2 * i2], xv[u], make_float2(m.x, m.y));
         cfma(acc[2 * i2 + 1], xv[u], make_float2(m.z, m.w));
@@ -233,7 +262,7 @@ __global__ void __launch_bounds__(256) k_mode1_fwd(const float2* __restrict__ X,
   // centring sign (-1)^(x + y + z) with z = i and b = y nx + x
   const int sb = (int)((b % a.nx) + (b / a.nx)) & 1;
 #pragma unroll
-  for (int ii = 0; ii < kIB; ++ii) {
+  for (int ii = 0; ii < kIB1; ++ii) {
     const int i = i0 + ii;
     if (i >= I) continue;
     const size_t n = (size_t)i * B + b;
@@ -273,22 +302,33 @@ __global__ void __launch_bounds__(256) k_x1_operand(const float2* __restrict__ t
 mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, long B, float2* Y) {
   if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
   const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);  // no idle lanes when B = 128
-  const dim3 grid((unsigned)((I + kIB - 1) / kIB), (unsigned)((B + block - 1) / block), (unsigned)R);
+  // 32 outputs along i per thread for long output axes (half the re-reads of X),
+  // 16 otherwise (fewer idle outputs)
+  const int ib = I >= 96 ? 32 : 16;
+  const dim3 grid((unsigned)((I + ib - 1) / ib), (unsigned)((B + block - 1) / block), (unsigned)R);
   if (R > 65535 || grid.y > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
   MPI_PROF(ctx, KF_EXPAND);
-  if (adj) launch_pdl(ctx, k_mode_b<true>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
-  else launch_pdl(ctx, k_mode_b<false>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+  if (ib == 32) {
+    if (adj) launch_pdl(ctx, k_mode_b<true, 32>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+    else launch_pdl(ctx, k_mode_b<false, 32>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+  } else {
+    if (adj) launch_pdl(ctx, k_mode_b<true, 16>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+    else launch_pdl(ctx, k_mode_b<false, 16>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+  }
   MPI_LAUNCH_CHECK(ctx, "k_mode_b");
   return MPI_OK;
 }
 
 mpi_status mode_last(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, float2* Y) {
-  if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
-  const unsigned grid = (unsigned)((R + 7) / 8);
-  const int block = std::min(256, (I + 31) / 32 * 32);  // threads run along i
+  if (P > 128 || I > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: length > 128");
+  const unsigned grid = (unsigned)((R + kLastRows - 1) / kLastRows);
+  const size_t smem = ((size_t)P * I + (size_t)kLastRows * P) * sizeof(float2);
+  cudaError_t e = adj ? cudaFuncSetAttribute(k_mode_last<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaFuncSetAttribute(k_mode_last<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "k_mode_last smem attribute");
   MPI_PROF(ctx, KF_EXPAND);
-  if (adj) launch_pdl(ctx, k_mode_last<true>, dim3(grid), dim3(block), 0, X, F, R, P, I, Y);
-  else launch_pdl(ctx, k_mode_last<false>, dim3(grid), dim3(block), 0, X, F, R, P, I, Y);
+  if (adj) launch_pdl(ctx, k_mode_last<true>, dim3(grid), dim3(256), smem, X, F, R, P, I, Y);
+  else launch_pdl(ctx, k_mode_last<false>, dim3(grid), dim3(256), smem, X, F, R, P, I, Y);
   MPI_LAUNCH_CHECK(ctx, "k_mode_last");
   return MPI_OK;
 }
@@ -472,7 +512,7 @@ mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const Expand
   const long B = (long)b->n[1] * b->n[2];
   if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
   const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);
-  const dim3 grid((unsigned)((I + kIB - 1) / kIB), (unsigned)((B + block - 1) / block), (unsigned)a.C);
+  const dim3 grid((unsigned)((I + kIB1 - 1) / kIB1), (unsigned)((B + block - 1) / block), (unsigned)a.C);
   if (grid.y > 65535 || a.C > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
   MPI_PROF(ctx, KF_EXPAND);
   launch_pdl(ctx, k_mode1_fwd, grid, dim3(block), 0, t2, b->F[0], P, I, B, a);

@@ -146,18 +146,9 @@ mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandAr
   if (prec == MPI_PREC_FP32) {
     const int g = tf32_group(basis, mode, a.C);
     if (g == a.C) return launch_expand_tf32(ctx, basis, mode, a);
-    if (g > 0) {  // coil groups: each launch takes its slice of alpha (dalpha) and of the per-coil output
-      for (int c0 = 0; c0 < a.C; c0 += g) {
-        ExpandArgs ag = a;
-        ag.C = std::min(g, a.C - c0);
-        ag.alpha = a.alpha + (size_t)c0 * a.q;
-        if (a.dalpha) ag.dalpha = a.dalpha + (size_t)c0 * a.q;
-        ag.out = a.out + (a.tuck_B ? (size_t)c0 * a.tuck_B : (size_t)c0 * a.N);
-        mpi_status st = launch_expand_tf32(ctx, basis, mode, ag);
-        if (st) return st;
-      }
-      return MPI_OK;
-    }
+    // coil groups in one launch: each grid row takes its slice of alpha (dalpha)
+    // and of the per-coil output
+    if (g > 0) return launch_expand_tf32(ctx, basis, mode, a, g);
   }
   return launch_expand(ctx, mode, a);
 }

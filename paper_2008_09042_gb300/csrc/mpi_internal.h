@@ -215,7 +215,9 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
 mpi_status tc_basis_prepare(mpi_ctx* ctx, mpi_basis* b);
 void tc_basis_release(mpi_basis* b);
 // FP32-accurate tensor-core expansion (3xTF32); same modes and arguments.
-mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a);
+// With group_coils > 0 (< C), one launch runs the coils in groups of that size
+// (grid rows), each row streaming the same basis tiles in step.
+mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a, int group_coils = 0);
 bool tf32_supported(const mpi_basis* b, int mode, int C);
 // Coils per launch of the 3xTF32 kernel: C when the whole call fits, else the
 // largest group that fits (forward-type modes only), or 0.

@@ -29,6 +29,10 @@ struct TcArgs {
   int* err;
   int tuck_B;         // maps mode: output remap for a flattened Tucker operand (0: none)
   long tuck_stride;
+  // Coil groups in one launch (3xTF32 kernel): CTA row blockIdx.y takes coils
+  // [blockIdx.y group_coils, + group_coils) of C_total; 0 = one group.
+  int group_coils;
+  int C_total;
 };
 
 // Position in a ring of `n` shared-memory stages: slot and the parity of the

@@ -273,6 +273,8 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.vout = x.vout;
   a.err = ctx->dev_err;
   a.tuck_B = x.tuck_B;
+  a.group_coils = 0;
+  a.C_total = x.C;
   a.tuck_stride = x.tuck_stride;
   const size_t b_bytes = round_up(a.n_gemm * b->Kp * 2, 1024);
   // Two CTAs per SM (one's epilogue overlaps the other's loads) when each can

@@ -85,8 +85,19 @@ __device__ __forceinline__ void mma_tf32_tmem_a(uint32_t tmem_d, uint32_t tmem_a
 // elements).  TMEM columns: [0, 2 half_cols) accumulators, then 64 columns of
 // lo(U) per stage.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_constant__ CUtensorMap tmap, TcArgs a,
+__global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_constant__ CUtensorMap tmap, TcArgs a_in,
                                                                 int stages) {
+  // Coil groups: the CTAs of row blockIdx.y expand their group's coils.  The
+  // rows of a launch stream the same basis tiles in the same order, so all but
+  // one of them mostly find each tile in L2.
+  TcArgs a = a_in;
+  if (a.group_coils) {
+    const int c0 = (int)blockIdx.y * a.group_coils;
+    a.C = min(a.group_coils, a.C_total - c0);
+    a.alpha += (size_t)c0 * a.q;
+    if (a.dalpha) a.dalpha += (size_t)c0 * a.q;
+    a.out += a.tuck_B ? (size_t)c0 * a.tuck_B : (size_t)c0 * a.N;
+  }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int Kp = a.KC * kKChunk32;
@@ -394,9 +405,11 @@ int tf32_group(const mpi_basis* b, int mode, int C) {
   return 0;
 }
 
-mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& x) {
+mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& x, int group_coils) {
   TfPlan pl;
-  if (!b->Uf32 || !b->tmap32 || !plan_tf32(b, mode, x.C, &pl))
+  const int Cg = group_coils > 0 ? std::min(group_coils, x.C) : x.C;  // coils per launch row
+  const int groups = (x.C + Cg - 1) / Cg;
+  if (!b->Uf32 || !b->tmap32 || !plan_tf32(b, mode, Cg, &pl))
     return set_err(ctx, MPI_ERR_UNSUPPORTED, "3xTF32 expansion unavailable for this shape");
   if (x.N <= 0 || x.C <= 0) return MPI_OK;
   TcArgs a;
@@ -423,8 +436,12 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.err = ctx->dev_err;
   a.tuck_B = x.tuck_B;
   a.tuck_stride = x.tuck_stride;
+  a.group_coils = groups > 1 ? Cg : 0;
+  a.C_total = x.C;
+  if (groups > 1) a.C = Cg;
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
-  const int grid = std::min(n_tiles, std::max(ctx->num_sms, 1));
+  // one CTA per SM over all groups
+  const dim3 grid((unsigned)std::min(n_tiles, std::max(std::max(ctx->num_sms, 1) / groups, 1)), (unsigned)groups);
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap32;
   cudaError_t e = cudaSuccess;
 #define MPI_TF_CASE(m)                                                                                        \
@@ -432,7 +449,7 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
     e = cudaFuncSetAttribute(k_expand_tf32x3<m>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);  \
     if (e != cudaSuccess) return cuda_check(ctx, e, "tf32 smem attribute");                                  \
     MPI_PROF(ctx, KF_EXPAND);                                                                                \
-    launch_pdl(ctx, k_expand_tf32x3<m>, dim3(grid), dim3(kThreads32), pl.smem, map, a, pl.stages);                      \
+    launch_pdl(ctx, k_expand_tf32x3<m>, grid, dim3(kThreads32), pl.smem, map, a, pl.stages);                          \
     break;
   switch (mode) {
     MPI_TF_CASE(EX_MAPS)

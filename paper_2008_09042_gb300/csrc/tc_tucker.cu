@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
   uint64_t* drain = acc_empty + 2;
   uint64_t* bfull = drain + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bfull + 1);
-  __shared__ float2 s_tw[N1];
+  __shared__ float2 s_tw[N1];  // w_N1^(j1 k2) at [j1 R + k2]
   __shared__ int s_failed;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -449,16 +449,22 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
     const int et = e * 32 + lane;  // 0 .. NT - 1
     const int b = (int)blockIdx.x * kTileM + row;
     if (e < 4) build_coef_smem<TF>(a.coef, sB, kKp, false, et, bfull);
-    for (int i = et; i < N1; i += NT) s_tw[i] = a.tw[i];
-    // forward: this block's image values; adjoint: a zeroed accumulator ([z][position])
+    for (int i = et; i < N1; i += NT) s_tw[i] = a.tw[((i / R) * (i % R)) % N1];
+    // forward: this block's image values with the centring sign and the scale;
+    // adjoint: a zeroed accumulator ([z][position])
     for (int i = et; i < N1 * kTileM; i += NT) {
       const int z = i / kTileM, pos = i - z * kTileM;
-      sX[i] = MODE == kTxFwd ? a.p[(size_t)z * a.B + (size_t)blockIdx.x * kTileM + pos] : make_float2(0.f, 0.f);
+      const int bb = (int)blockIdx.x * kTileM + pos;
+      if (MODE == kTxFwd) {
+        const float sg = (a.centre ? pos_sign(z, bb, a.nx) : 1.f) * a.scale;
+        sX[i] = cscale(a.p[(size_t)z * a.B + bb], sg);
+      } else {
+        sX[i] = make_float2(0.f, 0.f);
+      }
     }
     epi_bar_any(0, NT);
     constexpr int J1_PER = 8 / kNSub, K2_PER = (R + kNSub - 1) / kNSub;
     const int j1_lo = sub * J1_PER, k2_lo = sub * K2_PER, k2_hi = min(R, (sub + 1) * K2_PER);
-    const float sb = ((b % a.nx + b / a.nx) & 1) ? -1.f : 1.f;
     bool failed = false;
     for (int tc = 0; tc < my_tiles; ++tc) {
       const int c = (int)blockIdx.y + tc * (int)gridDim.y;
@@ -472,24 +478,28 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
           break;
         }
         fence_after();
-        // stage 1: v = s p sign scale over z = j1 + 8 j2, R-point DFT, twiddle, in place
-        for (int j1 = j1_lo; j1 < j1_lo + J1_PER; ++j1) {
-          float2 v[R];
+        // stage 1: v = s p (sign and scale folded into the staged image) over
+        // z = j1 + 8 j2, R-point DFT, twiddle, in place; two j1 per round
+        for (int j1 = j1_lo; j1 < j1_lo + J1_PER; j1 += 2) {
+          float2 v[2][R];
 #pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) tmem_ld2(tacc + 2u * (j1 + 8 * j2), v[j2]);
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j2 = 0; j2 < R; ++j2) tmem_ld2(tacc + 2u * (j1 + h + 8 * j2), v[h][j2]);
           tmem_wait_ld();
 #pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) {
-            fence_reg2(v[j2]);
-            const int z = j1 + 8 * j2;
-            const float sg = (a.centre ? ((z & 1) ? -sb : sb) : 1.f) * a.scale;
-            v[j2] = cscale(cmulf(v[j2], sX[z * kTileM + row]), sg);
+          for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int j2 = 0; j2 < R; ++j2) {
+              fence_reg2(v[h][j2]);
+              v[h][j2] = cmulf(v[h][j2], sX[(j1 + h + 8 * j2) * kTileM + row]);
+            }
+            dft_r<R>(v[h]);
+#pragma unroll
+            for (int k2 = 1; k2 < R; ++k2) v[h][k2] = cmulf(v[h][k2], s_tw[(j1 + h) * R + k2]);
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) tmem_st2(tacc + 2u * (j1 + h + 8 * k2), v[h][k2]);
           }
-          dft_r<R>(v);
-#pragma unroll
-          for (int k2 = 1; k2 < R; ++k2) v[k2] = cmulf(v[k2], s_tw[(j1 * k2) % N1]);
-#pragma unroll
-          for (int k2 = 0; k2 < R; ++k2) tmem_st2(tacc + 2u * (j1 + 8 * k2), v[k2]);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
@@ -532,7 +542,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
           }
           dft_r<R>(v);
 #pragma unroll
-          for (int k2 = 1; k2 < R; ++k2) v[k2] = cmulf(v[k2], s_tw[(j1 * k2) % N1]);
+          for (int k2 = 1; k2 < R; ++k2) v[k2] = cmulf(v[k2], s_tw[j1 * R + k2]);
 #pragma unroll
           for (int k2 = 0; k2 < R; ++k2) tmem_st2(tmem_scr + lane_base + 2u * (j1 + 8 * k2), v[k2]);
         }

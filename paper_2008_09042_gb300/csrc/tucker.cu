@@ -117,16 +117,15 @@ __global__ void __launch_bounds__(256) k_mode_last(const float2* __restrict__ X,
   float2* sM = sh;                           // [P][I]
   float2* sX = sh + (size_t)P * I;           // [kLastRows][P]
   const int r0 = blockIdx.x * kLastRows;
+  // F is read in its own memory order (coalesced); forward F is [I][P], adjoint [P][I]
   for (int e = threadIdx.x; e < P * I; e += blockDim.x) {
-    const int p = e / I, i = e - p * I;
-    float2 m;
+    const float2 f = F[e];
     if (ADJ) {
-      const float2 f = F[(size_t)p * I + i];
-      m = make_float2(f.x, -f.y);
+      sM[e] = make_float2(f.x, -f.y);  // e = p I + i
     } else {
-      m = F[(size_t)i * P + p];
+      const int i = e / P, p = e - i * P;
+      sM[p * I + i] = f;
     }
-    sM[e] = m;
   }
   for (int e = threadIdx.x; e < kLastRows * P; e += blockDim.x) {
     const int rr = e / P;
@@ -302,9 +301,8 @@ __global__ void __launch_bounds__(256) k_x1_operand(const float2* __restrict__ t
 mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, long B, float2* Y) {
   if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
   const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);  // no idle lanes when B = 128
-  // 32 outputs along i per thread for long output axes (half the re-reads of X),
-  // 16 otherwise (fewer idle outputs)
-  const int ib = I >= 96 ? 32 : 16;
+  // 16 outputs along i per thread (32 measured slower: fewer resident warps)
+  const int ib = 16;
   const dim3 grid((unsigned)((I + ib - 1) / ib), (unsigned)((B + block - 1) / block), (unsigned)R);
   if (R > 65535 || grid.y > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
   MPI_PROF(ctx, KF_EXPAND);

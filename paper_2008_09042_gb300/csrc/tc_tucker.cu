@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
     }
     for (int b = 0; b < 2; ++b) {
       mpi_ptx::mbar_init(&acc_full[b], 1);
-      mpi_ptx::mbar_init(&acc_empty[b], kNEpi);
+      // forward: the 4 warps of the buffer's parity release it; adjoint: all
+      mpi_ptx::mbar_init(&acc_empty[b], MODE == kTxFwd ? 4 : kNEpi);
     }
     mpi_ptx::mbar_init(drain, 1);
     mpi_ptx::mbar_init(bfull, 4);
@@ -472,15 +473,18 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
       const uint32_t par = NACC == 2 ? (uint32_t)((tc >> 1) & 1) : (uint32_t)(tc & 1);
       const uint32_t tacc = tmem + lane_base + (uint32_t)(buf * NG);
       if (MODE == kTxFwd) {
+        // the two warps of a lane quarter take alternate tiles (sub = buffer =
+        // tile parity) and each runs the whole DFT of its 32 positions
+        if ((tc & 1) != sub) continue;
         const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err);
-        if (epi_bar_any(!got, NT)) {
+        if (!__all_sync(0xffffffffu, got)) {
           failed = true;
           break;
         }
         fence_after();
         // stage 1: v = s p (sign and scale folded into the staged image) over
         // z = j1 + 8 j2, R-point DFT, twiddle, in place; two j1 per round
-        for (int j1 = j1_lo; j1 < j1_lo + J1_PER; j1 += 2) {
+        for (int j1 = 0; j1 < 8; j1 += 2) {
           float2 v[2][R];
 #pragma unroll
           for (int h = 0; h < 2; ++h)
@@ -502,12 +506,9 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
           }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        fence_before();
-        epi_bar_any(0, NT);
-        fence_after();
         // stage 2: 8-point DFTs over j1 for each k2; output kz = k2 + R k1
         float2* o = a.out + (size_t)c * N1 * a.B + b;
-        for (int k2 = k2_lo; k2 < k2_hi; ++k2) {
+        for (int k2 = 0; k2 < R; ++k2) {
           uint32_t raw[16];
           tmem_ld16_start(tacc + 16u * k2, raw);
           tmem_wait_ld();

@@ -82,7 +82,7 @@ def test_tf32_coil_groups_for_wide_coefficients(ctx, mp):
     assert mp.expand_path(ctx, B, C, "fp32") == "tf32x3"
     l0 = ctx.launches()
     s = f64(mp.basis_expand(ctx, B, c64(a), prec="fp32"))
-    assert ctx.launches() - l0 >= 2  # more than one group
+    assert ctx.launches() - l0 == 1  # the groups are grid rows of one launch
     ctx.synchronize()
     assert rel(s, op.expand(U, a)) < TOL
 

@@ -698,6 +698,7 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
     if (b->F[k]) cudaFree(b->F[k]);
   if (b->core) mpi_basis_destroy(b->core);
   delete (CUtensorMap*)b->op_map;
+  tucker_chain_release(b);
   delete b;
   return MPI_OK;
 }

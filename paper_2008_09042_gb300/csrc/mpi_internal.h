@@ -131,6 +131,7 @@ struct mpi_basis {
   void* op_map = nullptr;
   const void* op_map_ptr = nullptr;
   int op_map_C = -1, op_map_prec = -1;
+  void* chain_maps = nullptr;  // tensor maps of the FP32 tensor-core mode-product chain (tucker.cu)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -180,7 +181,18 @@ inline cudaError_t launch_pdl(mpi_ctx* ctx, void (*kern)(KArgs...), dim3 grid, d
 
 // ------------------------------------------------------- expansion kernels
 
-enum ExpandMode { EX_MAPS = 0, EX_FWD = 1, EX_JFWD = 2, EX_ADJ = 3, EX_JADJ = 4 };
+enum ExpandMode { EX_MAPS = 0, EX_FWD = 1, EX_JFWD = 2, EX_ADJ = 3, EX_JADJ = 4, EX_SCATTER = 5 };
+
+// EX_SCATTER (3xTF32 kernel): the real and imaginary parts of output (row n,
+// column pair j) go to the FP32 array `out` at
+//   (n / (L0 L1)) s_hi + ((n / L0) % L1) s_mid + n % L0 + j s_col   and  + im,
+// which writes a product straight into the real-ified K-major operand layout
+// the next contraction streams (the Tucker mode-product chain).
+struct ScatterMap {
+  int L0 = 1, L1 = 1;
+  long s_hi = 0, s_mid = 0, s_col = 0;
+  int im = 0;
+};
 
 struct ExpandArgs {
   const float2* U = nullptr;  // [q][N]
@@ -202,6 +214,7 @@ struct ExpandArgs {
   int tuck_B = 0;
   long tuck_stride = 0;
   const char* kname = nullptr;  // name of the launch in the per-kernel timing (default: the kernel's)
+  ScatterMap sc;                // EX_SCATTER output map
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
@@ -228,6 +241,9 @@ void tf32_basis_release(mpi_basis* b);
 // tensor-core kernels read their basis copies; `map` is a CUtensorMap.
 bool tc_encode_operand_map(void* map, void* ptr, long rows, int Kp);
 bool tf32_encode_operand_map(void* map, void* ptr, long rows, int Kp);
+// FP32 operand of `rows` rows of K (a multiple of 4) values, read by the 3xTF32
+// kernel as Kp = round_up(K, 64) columns (the rest zero-filled by the copy engine).
+bool tf32_encode_operand_map_k(void* map, void* ptr, long rows, int K);
 // dalpha[c][j] = sum_n conj(U[j][n]) V[c][n]; partials in `work_partials`.
 mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
                        float2* dalpha, float2* work_partials, size_t partial_cap_elems);
@@ -247,6 +263,8 @@ mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const Expand
 mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,
                           float2* partials, size_t partial_cap);
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS);
+void tucker_chain_release(mpi_basis* b);
+bool tucker_chain_on_tensor_cores(const mpi_basis* b, int C);
 // The flattened x1 operand of alpha's maps and its tensor map (see tucker.cu).
 mpi_status tucker_x1_operand(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp,
                              mpi_precision prec, void** op_out, void** map_out);

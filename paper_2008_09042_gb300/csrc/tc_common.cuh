@@ -33,6 +33,9 @@ struct TcArgs {
   // [blockIdx.y group_coils, + group_coils) of C_total; 0 = one group.
   int group_coils;
   int C_total;
+  // EX_SCATTER output map (see ScatterMap); sc_col0 = the launch row's first column pair
+  int sc_L0, sc_L1, sc_im, sc_col0;
+  long sc_hi, sc_mid, sc_col;
 };
 
 // Position in a ring of `n` shared-memory stages: slot and the parity of the
@@ -261,6 +264,13 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
         maps_cstride = (size_t)a.tuck_B;
       }
       const float2 dpi = (MODE == EX_JFWD) ? a.dp[nn] : make_float2(0.f, 0.f);
+      // scatter mode: this row's part of the output address
+      size_t sc_base = 0;
+      if (MODE == EX_SCATTER) {
+        const int lo = nn % a.sc_L0, q1 = nn / a.sc_L0;
+        sc_base = (size_t)(q1 / a.sc_L1) * a.sc_hi + (size_t)(q1 % a.sc_L1) * a.sc_mid + lo +
+                  (size_t)a.sc_col0 * a.sc_col;
+      }
       float2 pacc = make_float2(0.f, 0.f);
       const int n_chunks = (2 * a.C + 15) / 16;
       for (int ch = 0; ch < n_chunks; ++ch) {
@@ -302,6 +312,12 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
           const float2 s = make_float2(r[2 * i], r[2 * i + 1]);
           if (MODE == EX_MAPS) {
             if (cv) a.out[maps_base + (size_t)c * maps_cstride] = s;
+          } else if (MODE == EX_SCATTER) {
+            if (cv) {
+              float* o = reinterpret_cast<float*>(a.out) + sc_base + (size_t)c * a.sc_col;
+              o[0] = s.x;
+              o[a.sc_im] = s.y;
+            }
           } else if (MODE == EX_FWD) {
             const float2 v = cmul(s, pimg);
             if (cv) a.out[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);

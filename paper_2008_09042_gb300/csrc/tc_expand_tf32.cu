@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     a.C = min(a.group_coils, a.C_total - c0);
     a.alpha += (size_t)c0 * a.q;
     if (a.dalpha) a.dalpha += (size_t)c0 * a.q;
-    a.out += a.tuck_B ? (size_t)c0 * a.tuck_B : (size_t)c0 * a.N;
+    if (MODE == EX_SCATTER) a.sc_col0 = c0;
+    else a.out += a.tuck_B ? (size_t)c0 * a.tuck_B : (size_t)c0 * a.N;
   }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -385,6 +386,24 @@ bool tf32_encode_operand_map(void* map, void* ptr, long rows, int Kp) {
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tf32_encode_operand_map_k(void* map, void* ptr, long rows, int K) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+  if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  // K columns stored; boxes past K (up to the kernel's Kp) read as zeros
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kKChunk32, (cuuint32_t)kTileM};
+  const cuuint32_t estr[2] = {1, 1};
+  return ((EncodeTiledFn)fn)((CUtensorMap*)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void tf32_basis_release(mpi_basis* b) {
   delete (CUtensorMap*)b->tmap32;
   b->tmap32 = nullptr;
@@ -399,7 +418,7 @@ int tf32_group(const mpi_basis* b, int mode, int C) {
   if (tf32_supported(b, mode, C)) return C;
   // coils are independent in these modes, so they can run in groups whose
   // coefficient operand and accumulators fit; the adjoint modes sum over coils
-  if (mode != EX_MAPS && mode != EX_FWD && mode != EX_JFWD) return 0;
+  if (mode != EX_MAPS && mode != EX_FWD && mode != EX_JFWD && mode != EX_SCATTER) return 0;
   for (int g = C - 1; g >= 1; --g)
     if (tf32_supported(b, mode, g)) return g;
   return 0;
@@ -436,6 +455,13 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.err = ctx->dev_err;
   a.tuck_B = x.tuck_B;
   a.tuck_stride = x.tuck_stride;
+  a.sc_L0 = x.sc.L0;
+  a.sc_L1 = x.sc.L1;
+  a.sc_hi = x.sc.s_hi;
+  a.sc_mid = x.sc.s_mid;
+  a.sc_col = x.sc.s_col;
+  a.sc_im = x.sc.im;
+  a.sc_col0 = 0;
   a.group_coils = groups > 1 ? Cg : 0;
   a.C_total = x.C;
   if (groups > 1) a.C = Cg;
@@ -457,6 +483,7 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
     MPI_TF_CASE(EX_JFWD)
     MPI_TF_CASE(EX_ADJ)
     MPI_TF_CASE(EX_JADJ)
+    MPI_TF_CASE(EX_SCATTER)
     default:
       return set_err(ctx, MPI_ERR_ARG, "unknown expansion mode");
   }

@@ -414,13 +414,172 @@ bool tucker_x1_on_tensor_cores(const mpi_basis* b, int C, mpi_precision prec) {
   return ok;
 }
 
+namespace {
+
+template <typename T>
+T* align256(void* p) {
+  return (T*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+}
+
+// A 3xTF32 "basis" over an FP32 operand of `rows` rows of K = 2 q values
+// (real parts, then imaginary parts), read as round_up(K, 64) columns.
+void operand_view(const mpi_basis* b, void* ptr, void* map, long rows, int q, mpi_basis* v) {
+  v->ctx = b->ctx;
+  v->device = b->device;
+  v->N = (int)rows;
+  v->q = q;
+  v->Uf32 = (float*)ptr;
+  v->Kp32 = (2 * q + 63) / 64 * 64;
+  v->tmap32 = map;
+}
+
+// Tensor map cache of the chain's operands (re-encoded when the address or
+// the row count changes).
+struct ChainMaps {
+  CUtensorMap m[3];
+  const void* ptr[3] = {nullptr, nullptr, nullptr};
+  long rows[3] = {0, 0, 0};
+};
+
+bool chain_map(mpi_basis* b, int i, void* ptr, long rows, int K, void** out) {
+  if (!b->chain_maps) b->chain_maps = new ChainMaps;
+  ChainMaps* cm = (ChainMaps*)b->chain_maps;
+  if (cm->ptr[i] != ptr || cm->rows[i] != rows) {
+    if (!tf32_encode_operand_map_k(&cm->m[i], ptr, rows, K)) {
+      cm->ptr[i] = nullptr;
+      return false;
+    }
+    cm->ptr[i] = ptr;
+    cm->rows[i] = rows;
+  }
+  *out = &cm->m[i];
+  return true;
+}
+
+}  // namespace
+
+void tucker_chain_release(mpi_basis* b) {
+  delete (ChainMaps*)b->chain_maps;
+  b->chain_maps = nullptr;
+}
+
+// Whether the FP32 mode-product chain runs on the tensor cores: even ranks (the
+// operands' rows are whole 16-byte units), 2 r_k <= 128, and factor lengths
+// the 3xTF32 kernel takes in coil groups.
+bool tucker_chain_on_tensor_cores(const mpi_basis* b, int C) {
+  for (int k = 0; k < 3; ++k)
+    if (b->r[k] % 2 || 2 * b->r[k] > 128) return false;
+  const long rows3 = (long)C * b->r[0] * b->r[1], rows2 = (long)C * b->n[2] * b->r[0];
+  if (rows2 > 0x7fffffffL - 128 || (long)C * b->n[1] * b->n[2] > 0x7fffffffL - 128) return false;
+  mpi_basis v3, v2;  // shape-only views
+  operand_view(b, (void*)256, (void*)256, rows3, b->r[2], &v3);
+  operand_view(b, (void*)256, (void*)256, rows2, b->r[1], &v2);
+  const bool ok = tf32_group(&v3, EX_SCATTER, b->n[2]) > 0 && tf32_group(&v2, EX_SCATTER, b->n[1]) > 0 &&
+                  tf32_group(b->core, EX_SCATTER, C) > 0;
+  v3.Uf32 = v2.Uf32 = nullptr;
+  v3.tmap32 = v2.tmap32 = nullptr;
+  return ok;
+}
+
+namespace {
+
+// The FP32 chain on the tensor cores, every product written by the 3xTF32
+// kernel's scatter epilogue straight into the real-ified K-major rows the next
+// one streams:
+//   g  = G alpha_c            rows (c, a, b) x [Re g(d) | Im g(d)]       (K = 2 r3)
+//   t1 = g x3 U3              rows (c, x, a) x [Re t1(b) | Im t1(b)]     (K = 2 r2)
+//   op = t1 x2 U2             rows (c, y, x) x [Re t2(a) | Im t2(a)]     (K = 2 r1)
+// (a, b, d index the ranks r1, r2, r3; z, y, x the grid n1, n2, n3).  Each
+// factor's rows are the coefficient rows of its product.
+mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp, void** op_out,
+                           void** map_out) {
+  const int n2 = b->n[1], n3 = b->n[2];
+  const int r1 = b->r[0], r2 = b->r[1], r3 = b->r[2];
+  const long R = (long)r1 * r2 * r3;
+  mpi_basis* mb = const_cast<mpi_basis*>(b);
+  float* g = align256<float>(tmp);
+  float* t1 = align256<float>(g + (size_t)C * R * 2);
+  float* op = align256<float>(tmp + x1_op_offset(b, C));
+  const long rows3 = (long)C * r1 * r2, rows2 = (long)C * n3 * r1, rows1 = (long)C * n2 * n3;
+  void *m3 = nullptr, *m2 = nullptr, *m1 = nullptr;
+  if (!chain_map(mb, 0, g, rows3, 2 * r3, &m3) || !chain_map(mb, 1, t1, rows2, 2 * r2, &m2) ||
+      !chain_map(mb, 2, op, rows1, 2 * r1, &m1))
+    return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker chain tensor maps");
+  // the core contraction: rows (a, b, d) of the core, column pairs = coils
+  ExpandArgs a;
+  a.U = b->core->U;
+  a.N = b->core->N;
+  a.q = b->q;
+  a.C = C;
+  a.alpha = alpha;
+  a.out = (float2*)g;
+  a.sc.L0 = r3;
+  a.sc.L1 = 1 << 30;
+  a.sc.s_mid = 2L * r3;
+  a.sc.s_col = R / r3 * 2L * r3;
+  a.sc.im = r3;
+  a.kname = "k_expand_tf32x3<tucker core>";
+  mpi_status st = expand(ctx, b->core, EX_SCATTER, a, MPI_PREC_FP32);
+  if (st) return st;
+  // x3: rows (c, a, b) with K = d, column pairs = x; out rows (c, x, a)
+  // (these kernels stream operands written by the kernel before: plain stream order)
+  const bool pdl = ctx->pdl;
+  ctx->pdl = false;
+  mpi_basis v;
+  operand_view(b, g, m3, rows3, r3, &v);
+  ExpandArgs a3;
+  a3.N = (int)rows3;
+  a3.q = r3;
+  a3.C = n3;
+  a3.alpha = b->F[2];
+  a3.out = (float2*)t1;
+  a3.sc.L0 = r2;
+  a3.sc.L1 = r1;
+  a3.sc.s_hi = (long)n3 * r1 * 2 * r2;
+  a3.sc.s_mid = 2L * r2;
+  a3.sc.s_col = (long)r1 * 2 * r2;
+  a3.sc.im = r2;
+  a3.kname = "k_expand_tf32x3<tucker x3>";
+  st = expand(ctx, &v, EX_SCATTER, a3, MPI_PREC_FP32);
+  // x2: rows (c, x, a) with K = b, column pairs = y; out rows (c, y, x)
+  if (!st) {
+    operand_view(b, t1, m2, rows2, r2, &v);
+    ExpandArgs a2;
+    a2.N = (int)rows2;
+    a2.q = r2;
+    a2.C = n2;
+    a2.alpha = b->F[1];
+    a2.out = (float2*)op;
+    a2.sc.L0 = r1;
+    a2.sc.L1 = n3;
+    a2.sc.s_hi = (long)n2 * n3 * 2 * r1;
+    a2.sc.s_mid = 2L * r1;
+    a2.sc.s_col = (long)n3 * 2 * r1;
+    a2.sc.im = r1;
+    a2.kname = "k_expand_tf32x3<tucker x2>";
+    st = expand(ctx, &v, EX_SCATTER, a2, MPI_PREC_FP32);
+  }
+  ctx->pdl = pdl;
+  v.Uf32 = nullptr;
+  v.tmap32 = nullptr;
+  if (st) return st;
+  *op_out = op;
+  *map_out = m1;
+  return MPI_OK;
+}
+
+}  // namespace
+
 // The flattened x1 operand of alpha's coil maps: the core contraction, the x3
 // and x2 mode products and the rewrite of T2 [C][r1][n2 n3] as K-major rows
 // [(c, b)][Kp] (FP32 or BF16) at a 256-byte aligned place in `tmp`; returns the
 // operand and its tensor map (re-encoded only when the workspace, C or the
-// precision change).
+// precision change).  FP32 with even ranks: the whole chain on the tensor cores
+// (tucker_chain_tc), rows of 2 r1 values.
 mpi_status tucker_x1_operand(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp,
                              mpi_precision prec, void** op_out, void** map_out) {
+  if (prec == MPI_PREC_FP32 && tucker_chain_on_tensor_cores(b, C))
+    return tucker_chain_tc(ctx, b, alpha, C, tmp, op_out, map_out);
   float2* t2 = nullptr;
   mpi_status st = tucker_t2(ctx, b, alpha, C, tmp, prec, &t2);
   if (st) return st;

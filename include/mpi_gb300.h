@@ -96,6 +96,11 @@ int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx);
  * the context's lifetime), MPI_ERR_ARG past the last.  Library machinery, no
  * paper passage. */
 mpi_status mpi_ctx_set_autotune(mpi_ctx* ctx, int enable);
+/* Fixes the FFT line passes' kernel instead of tuning it: 8, 16 or 32 lines per
+ * CTA (shared-memory Stockham passes), -1 the register two-step pass along y
+ * (lengths 64, 96, 128, 192, 256), 0 back to tuning.  A pass the choice does
+ * not cover keeps its tuned or default kernel.  MPI_ERR_ARG for other values. */
+mpi_status mpi_ctx_set_line_kernel(mpi_ctx* ctx, int choice);
 mpi_status mpi_ctx_tuning_record(const mpi_ctx* ctx, int index, const char** text_out);
 /* Per-launch device timing: while enabled, every kernel the context launches is
  * bracketed by two CUDA events on the context's stream (16384 launches at most

@@ -55,6 +55,11 @@ class Context:
     def set_autotune(self, enable=True):
         check(self.h, self.lib.mpi_ctx_set_autotune(self.h, 1 if enable else 0))
 
+    def set_line_kernel(self, choice=0):
+        """Fix the FFT line passes' kernel: 8, 16, 32 (lines per CTA), -1 (register
+        two-step pass along y) or 0 (tuned)."""
+        check(self.h, self.lib.mpi_ctx_set_line_kernel(self.h, int(choice)))
+
     def tuning_records(self):
         """Text of every launch-shape decision the autotuner made on this context."""
         out = []

@@ -437,6 +437,14 @@ extern "C" mpi_status mpi_ctx_set_autotune(mpi_ctx* ctx, int enable) {
   return MPI_OK;
 }
 
+extern "C" mpi_status mpi_ctx_set_line_kernel(mpi_ctx* ctx, int choice) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (choice != 0 && choice != 8 && choice != 16 && choice != 32 && choice != -1)
+    return set_err(ctx, MPI_ERR_ARG, "line kernel choice must be 0, 8, 16, 32 or -1");
+  ctx->line_kernel = choice;
+  return MPI_OK;
+}
+
 extern "C" mpi_status mpi_ctx_tuning_record(const mpi_ctx* ctx, int index, const char** text_out) {
   if (!ctx || !text_out) return MPI_ERR_ARG;
   if (index < 0 || index >= (int)ctx->tuned.size()) return MPI_ERR_ARG;

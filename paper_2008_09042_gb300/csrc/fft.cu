@@ -19,6 +19,7 @@
 
 #include <algorithm>
 
+#include "dft_reg.cuh"
 #include "mpi_internal.h"
 #include "ptx.cuh"
 
@@ -403,12 +404,103 @@ int lines_tile(const mpi_ctx* ctx, int L, int nx, int n_slabs) {
   return 8;
 }
 
-// Launch of one line pass with tile width `tile` (8, 16 or 32 lines); false
-// when the length / tile pair is not compiled.
+// The pass along y as a two-step FFT in registers: L = R1 R2 points per
+// column, y = r + R2 m.  A CTA takes 32 adjacent columns (one per lane) of one
+// (coil, z) plane.  Step 1: for each r, the R1 values y = r + R2 m are loaded
+// (rows of 32 columns: coalesced), transformed (R1-point DFT in registers) and
+// twiddled by w_L^(r k1) into shared memory [k1][r][column].  Step 2: for each
+// k1, the R2 values are read back, transformed (R2-point DFT) and stored to
+// rows k = k1 + R1 k2.  One shared-memory write and read per element (the
+// Stockham passes take one per radix stage plus two transposes).  The inverse
+// is the forward of the conjugated data, conjugated back.  Row mask as in
+// k_fft_lines: inverse, rows without samples are read as zeros; forward, only
+// rows with samples are stored.
+template <int R1, int R2, bool INV>
+__global__ void __launch_bounds__(256, 2) k_fft_cols_reg(float2* __restrict__ data, int nx, int n_slabs, long plane,
+                                                      const float2* __restrict__ tw_g,
+                                                      const uint8_t* __restrict__ rmask, int mask_nz) {
+  constexpr int L = R1 * R2;
+  __shared__ float2 sY[L * 32];  // [k1][r][column]
+  __shared__ float2 tw[L];
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int i = tid; i < L; i += 256) tw[i] = tw_g[i];
+  const int x_tiles = (nx + 31) / 32;
+  const int slab = (int)blockIdx.x / x_tiles, x0 = ((int)blockIdx.x - slab * x_tiles) * 32;
+  const bool ok = x0 + lane < nx;
+  float2* col = data + (size_t)slab * plane + x0 + lane;
+  const uint8_t* rm = rmask ? rmask + (size_t)(slab % mask_nz) * L : nullptr;
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < (R2 + 7) / 8; ++it) {
+    const int r = w + 8 * it;
+    if (r >= R2) break;
+    float2 v[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+      const int y = r + R2 * m;
+      float2 t = make_float2(0.f, 0.f);
+      if (ok && !(INV && rm && !rm[y])) t = col[(size_t)y * nx];
+      v[m] = INV ? make_float2(t.x, -t.y) : t;
+    }
+    mpi_dft::dft_r<R1>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) v[k1] = mpi_dft::cmulf(v[k1], tw[r * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) sY[(k1 * R2 + r) * 32 + lane] = v[k1];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < (R1 + 7) / 8; ++it) {
+    const int k1 = w + 8 * it;
+    if (k1 >= R1) break;
+    float2 u[R2];
+#pragma unroll
+    for (int r = 0; r < R2; ++r) u[r] = sY[(k1 * R2 + r) * 32 + lane];
+    mpi_dft::dft_r<R2>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int k = k1 + R1 * k2;
+      if (ok && (INV || !rm || rm[k])) col[(size_t)k * nx] = INV ? make_float2(u[k2].x, -u[k2].y) : u[k2];
+    }
+  }
+}
+
+// Launch of the register pass along y for length L; false where L has no
+// (R1, R2) split or the geometry is not a y pass (lines of stride nx in
+// planes of `outer_stride`).
+template <bool INV>
+bool cols_reg_launch(mpi_ctx* ctx, int L, float2* data, int nx, long stride, int n_slabs, int inner,
+                     long outer_stride, const float2* tw, const uint8_t* rmask, int mask_nz) {
+  if (stride != nx || inner != 1) return false;
+  const long blocks = (long)n_slabs * ((nx + 31) / 32);
+  if (blocks == 0 || blocks > 0x7fffffffL) return false;
+#define MPI_CREG(n, r1, r2)                                                                                   \
+  case n:                                                                                                    \
+    launch_pdl(ctx, k_fft_cols_reg<r1, r2, INV>, dim3((unsigned)blocks), dim3(256), 0, data, nx, n_slabs,       \
+               outer_stride, tw, rmask, mask_nz);                                                            \
+    return true;
+  switch (L) {
+    MPI_CREG(64, 8, 8)
+    MPI_CREG(96, 8, 12)
+    MPI_CREG(128, 8, 16)
+    MPI_CREG(192, 16, 12)
+    MPI_CREG(256, 16, 16)
+    default:
+      return false;
+  }
+#undef MPI_CREG
+}
+
+// Launch of one line pass with tile width `tile` (8, 16 or 32 lines, or -1
+// for the register pass along y); false when the length / tile pair is not
+// compiled.
 template <bool INV>
 bool lines_launch_tile(mpi_ctx* ctx, int tile, int L, long blocks, float2* data, int nx, long stride, int n_slabs,
                        int inner, long outer_stride, long inner_stride, const float2* tw, const uint8_t* rmask,
                        int mask_nz) {
+  if (tile == -1) return cols_reg_launch<INV>(ctx, L, data, nx, stride, n_slabs, inner, outer_stride, tw, rmask, mask_nz);
 #define MPI_LINES_CASE(n)                                                                                     \
   case n:                                                                                                     \
     if (tile == 32 && n <= 128)                                                                               \
@@ -479,10 +571,11 @@ int lines_autotune(mpi_ctx* ctx, const long (&key)[10], int L, float2* data, int
   rec.n = 0;
   rec.choice = 0;
   float best = 1e30f;
-  const int cands[3] = {8, 16, 32};
+  const int cands[4] = {8, 16, 32, -1};
   for (int tile : cands) {
-    if ((long)L * tile / (kLineWarps * 32) > 16) continue;
-    const long blocks = (long)n_slabs * ((nx + tile - 1) / tile);
+    if (tile > 0 && (long)L * tile / (kLineWarps * 32) > 16) continue;
+    const int cols = tile < 0 ? 32 : tile;  // columns per CTA
+    const long blocks = (long)n_slabs * ((nx + cols - 1) / cols);
     if (blocks > 0x7fffffffL) continue;
     if (!lines_launch_tile<INV>(ctx, tile, L, blocks, scratch, nx, stride, n_slabs, inner, outer_stride,
                                 inner_stride, tw, rmask, mask_nz))
@@ -510,10 +603,18 @@ int lines_autotune(mpi_ctx* ctx, const long (&key)[10], int L, float2* data, int
   cudaEventDestroy(e1);
   if (!rec.choice || cudaGetLastError() != cudaSuccess) return 0;
   char buf[256];
-  int len = snprintf(buf, sizeof buf, "FFT line pass L=%d %s stride=%ld lines=%ld%s: tile %d (", L, INV ? "inverse" : "forward",
-                     stride, (long)n_slabs * nx, rmask ? " row-masked" : "", rec.choice);
-  for (int i = 0; i < rec.n && len < (int)sizeof buf; ++i)
-    len += snprintf(buf + len, sizeof buf - len, "%s%d: %.1f us", i ? ", " : "", rec.cand[i], rec.us[i]);
+  auto tname = [](int t, char* b, size_t n) {
+    if (t < 0) snprintf(b, n, "register two-step");
+    else snprintf(b, n, "%d lines", t);
+  };
+  char tn[32];
+  tname(rec.choice, tn, sizeof tn);
+  int len = snprintf(buf, sizeof buf, "FFT line pass L=%d %s stride=%ld lines=%ld%s: %s (", L, INV ? "inverse" : "forward",
+                     stride, (long)n_slabs * nx, rmask ? " row-masked" : "", tn);
+  for (int i = 0; i < rec.n && len < (int)sizeof buf; ++i) {
+    tname(rec.cand[i], tn, sizeof tn);
+    len += snprintf(buf + len, sizeof buf - len, "%s%s: %.1f us", i ? ", " : "", tn, rec.us[i]);
+  }
   if (len < (int)sizeof buf) snprintf(buf + len, sizeof buf - len, ")");
   rec.what = buf;
   ctx->tuned.push_back(rec);
@@ -530,16 +631,23 @@ mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, i
   const long key[10] = {L, INV ? 1 : 0, nx, stride, n_slabs, inner, outer_stride, inner_stride, rmask ? 1 : 0,
                         mask_nz};
   int tile = 0;
-  for (const auto& r : ctx->tuned)
-    if (std::equal(r.key, r.key + 10, key)) {
-      tile = r.choice;
-      break;
-    }
+  // a caller's fixed choice (mpi_ctx_set_line_kernel), where this pass has it
+  if (ctx->line_kernel) {
+    const int t = ctx->line_kernel;
+    const bool ok = t == -1 ? (L == 64 || L == 96 || L == 128 || L == 192 || L == 256) && stride == nx && inner == 1
+                            : (t == 8 || (t == 16 && L <= 256) || (t == 32 && L <= 128));
+    if (ok) tile = t;
+  }
+  for (const auto& r : ctx->tuned) {
+    if (tile) break;
+    if (std::equal(r.key, r.key + 10, key)) tile = r.choice;
+  }
   if (!tile)
     tile = lines_autotune<INV>(ctx, key, L, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw, rmask,
                                mask_nz);
   if (!tile) tile = lines_tile(ctx, L, nx, n_slabs);
-  const int x_tiles = (nx + tile - 1) / tile;
+  const int tw_cols = tile < 0 ? 32 : tile;
+  const int x_tiles = (nx + tw_cols - 1) / tw_cols;
   const long blocks = (long)n_slabs * x_tiles;
   if (blocks > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "too many FFT tiles");
   MPI_PROF(ctx, KF_FFT_LINES);

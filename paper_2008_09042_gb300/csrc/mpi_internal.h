@@ -55,6 +55,7 @@ struct mpi_ctx {
   // buffer the operator calls are not using at that point), never while the
   // stream is being captured, and only while `autotune` is set.
   bool autotune = true;
+  int line_kernel = 0;  // fixed line-pass choice (8, 16, 32 lines, -1 register two-step), 0 = tuned
   void* tune_scratch = nullptr;
   size_t tune_scratch_bytes = 0;
   struct TuneRecord {

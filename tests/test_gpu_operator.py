@@ -372,3 +372,47 @@ def test_destroy_context_before_children(mp):
     bt.close()
     B.close()
     plan.close()
+
+
+@pytest.mark.parametrize("choice", [8, 16, 32, -1])
+@pytest.mark.parametrize("dims,C,q,R", [((256, 256), 6, 24, 6), ((128, 192), 5, 16, 4), ((96, 64), 4, 12, 3)])
+def test_line_pass_kernels_match_oracle(mp, choice, dims, C, q, R):
+    # every FFT line-pass kernel the autotuner chooses between, fixed in turn:
+    # forward and adjoint against the oracle (row-masked passes along y included)
+    ctx = mp.Context(0)
+    ctx.set_line_kernel(choice)
+    mask = w.poisson_disc_mask(dims[0], dims[1], R, calib=(8, 8), seed=17)
+    cs = _case(ctx, mp, dims, C, q, mask, seed=18)
+    ag, pg = c64(cs["a"]), c64(cs["p"])
+    y = mp.forward(ctx, cs["plan"], cs["B"], ag, pg)
+    assert rel(f64(y), op.forward(cs["Fs"], cs["U"], cs["a"], cs["p"])) < TOL
+    r = w.random_coefficients(C, cs["M"], seed=19, decay=False).astype(np.complex64).astype(np.complex128)
+    x = mp.adjoint(ctx, cs["plan"], cs["B"], ag, c64(r))
+    assert rel(f64(x), op.adjoint(cs["Fs"], cs["U"], cs["a"], r)) < TOL
+    ctx.synchronize()
+
+
+@pytest.mark.parametrize("choice", [16, -1])
+def test_line_pass_kernels_3d_volume(mp, choice):
+    # the 3D path's row-masked passes along y (96 x 128 x 128 planes are the
+    # bench's shape; a 48 x 64 x 128 volume keeps the oracle quick)
+    from oracle import tucker
+
+    ctx = mp.Context(0)
+    ctx.set_line_kernel(choice)
+    dims, ranks, q, C = (64, 64, 128), (16, 16, 16), 24, 3
+    core, fac = w.smooth_tucker_basis(dims, ranks, q, seed=27)
+    core = core.astype(np.complex64).astype(np.complex128)
+    fac = [f.astype(np.complex64).astype(np.complex128) for f in fac]
+    tb = tucker.TuckerBasis(core, fac)
+    idx = w.mask_to_indices(w.poisson_disc_mask_3d(*dims, R=8, calib=(12, 12), seed=28))
+    Fs = fourier.CartesianSampling(dims, idx)
+    N = int(np.prod(dims))
+    a = w.random_coefficients(C, q, seed=29).astype(np.complex64).astype(np.complex128)
+    p = w.random_image(N, seed=30).astype(np.complex64).astype(np.complex128)
+    r = w.random_coefficients(C, idx.size, seed=31, decay=False).astype(np.complex64).astype(np.complex128)
+    plan = mp.Plan(ctx, dims, sample_idx=idx)
+    B = mp.TuckerBasis(ctx, core, fac)
+    assert rel(f64(mp.forward(ctx, plan, B, c64(a), c64(p))), op.forward(Fs, tb, a, p)) < TOL
+    assert rel(f64(mp.adjoint(ctx, plan, B, c64(a), c64(r))), op.adjoint(Fs, tb, a, r)) < TOL
+    ctx.synchronize()

@@ -86,6 +86,18 @@ int64_t mpi_ctx_launch_count(const mpi_ctx* ctx);
  * and host-call staging buffer (0 until an operator call or mpi_ctx_reserve
  * grows them); -1 for a null context.  Library bookkeeping, no paper passage. */
 int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx);
+/* Bounded waits.  Every mbarrier wait of the tensor-core kernels gives up after
+ * `cycles` SM clock cycles (default 2^32, about 2 s at 2 GHz; at least 1000):
+ * the kernel then records MPI_ERR_TIMEOUT in the context's device error word,
+ * waits (bounded) for the copies it issued, frees its tensor memory and
+ * returns; mpi_ctx_synchronize reports the timeout and clears the word, and the
+ * context stays usable.  mpi_ctx_inject_stall(ctx, k) is a fault-injection
+ * hook for testing that path: with k >= 0 the FP32 tensor-core expansion's
+ * copy producer stops after k ring stages, so the waits on the stages it never
+ * loads run out (the failure is made by withholding work; nothing faults);
+ * k < 0 switches it off.  Library machinery, no paper passage. */
+mpi_status mpi_ctx_set_wait_limit(mpi_ctx* ctx, int64_t cycles);
+mpi_status mpi_ctx_inject_stall(mpi_ctx* ctx, int stages);
 /* Launch-shape autotuning (on by default).  The first operator call that runs an
  * FFT line pass of a new shape (length, stride, line count, row mask) times each
  * candidate tile width of that pass with CUDA events on a free workspace buffer

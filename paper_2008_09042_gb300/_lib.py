@@ -21,7 +21,7 @@ PREC = {"fp32": 0, "bf16": 1, "fp32_simt": 2}
 # Every symbol include/mpi_gb300.h declares.
 EXPORTS = [
     "mpi_ctx_create", "mpi_ctx_destroy", "mpi_ctx_set_stream", "mpi_ctx_synchronize", "mpi_ctx_reserve",
-    "mpi_last_error", "mpi_ctx_launch_count", "mpi_ctx_workspace_bytes", "mpi_ctx_set_autotune", "mpi_ctx_set_line_kernel", "mpi_ctx_tuning_record", "mpi_ctx_profile", "mpi_ctx_profile_read", "mpi_ctx_profile_kernel", "mpi_plan_create", "mpi_plan_destroy", "mpi_plan_grid_index",
+    "mpi_last_error", "mpi_ctx_launch_count", "mpi_ctx_workspace_bytes", "mpi_ctx_set_autotune", "mpi_ctx_set_line_kernel", "mpi_ctx_set_wait_limit", "mpi_ctx_inject_stall", "mpi_ctx_tuning_record", "mpi_ctx_profile", "mpi_ctx_profile_read", "mpi_ctx_profile_kernel", "mpi_plan_create", "mpi_plan_destroy", "mpi_plan_grid_index",
     "mpi_basis_load_dense", "mpi_basis_load_tucker", "mpi_basis_destroy", "mpi_basis_expand", "mpi_forward", "mpi_adjoint",
     "mpi_jacobian", "mpi_jacobian_adjoint", "mpi_basis_project", "mpi_sm_estimate", "mpi_image_solve",
     "mpi_tv_prox", "mpi_forward_noalloc", "mpi_batch_create", "mpi_batch_run", "mpi_batch_kernel_count",
@@ -91,6 +91,8 @@ def load(path=LIB_PATH):
         "mpi_ctx_reserve": [vp, vp, vp, i],
         "mpi_ctx_set_autotune": [vp, i],
         "mpi_ctx_set_line_kernel": [vp, i],
+        "mpi_ctx_set_wait_limit": [vp, i64],
+        "mpi_ctx_inject_stall": [vp, i],
         "mpi_ctx_tuning_record": [vp, i, ctypes.POINTER(ctypes.c_char_p)],
         "mpi_ctx_profile": [vp, i],
         "mpi_ctx_profile_read": [vp, i, ctypes.POINTER(d), ctypes.POINTER(i64), i],

@@ -55,6 +55,15 @@ class Context:
     def set_autotune(self, enable=True):
         check(self.h, self.lib.mpi_ctx_set_autotune(self.h, 1 if enable else 0))
 
+    def set_wait_limit(self, cycles):
+        """Bounded-wait limit of the tensor-core kernels, in SM clock cycles."""
+        check(self.h, self.lib.mpi_ctx_set_wait_limit(self.h, int(cycles)))
+
+    def inject_stall(self, stages=-1):
+        """Fault injection for tests of the timeout path: the FP32 tensor-core
+        expansion's copy producer stops after `stages` ring stages (-1: off)."""
+        check(self.h, self.lib.mpi_ctx_inject_stall(self.h, int(stages)))
+
     def set_line_kernel(self, choice=0):
         """Fix the FFT line passes' kernel: 8, 16, 32 (lines per CTA), -1 (register
         two-step pass along y) or 0 (tuned)."""

@@ -437,6 +437,19 @@ extern "C" mpi_status mpi_ctx_set_autotune(mpi_ctx* ctx, int enable) {
   return MPI_OK;
 }
 
+extern "C" mpi_status mpi_ctx_set_wait_limit(mpi_ctx* ctx, int64_t cycles) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (cycles < 1000) return set_err(ctx, MPI_ERR_ARG, "wait limit below 1000 cycles");
+  ctx->wait_cycles = cycles;
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_ctx_inject_stall(mpi_ctx* ctx, int stages) {
+  if (!ctx) return MPI_ERR_ARG;
+  ctx->stall_after = stages < 0 ? -1 : stages;
+  return MPI_OK;
+}
+
 extern "C" mpi_status mpi_ctx_set_line_kernel(mpi_ctx* ctx, int choice) {
   if (!ctx) return MPI_ERR_ARG;
   if (choice != 0 && choice != 8 && choice != 16 && choice != 32 && choice != -1)

@@ -55,7 +55,9 @@ struct mpi_ctx {
   // buffer the operator calls are not using at that point), never while the
   // stream is being captured, and only while `autotune` is set.
   bool autotune = true;
-  int line_kernel = 0;  // fixed line-pass choice (8, 16, 32 lines, -1 register two-step), 0 = tuned
+  int line_kernel = 0;
+  long long wait_cycles = 4LL << 30;  // bounded-wait limit of the tensor-core kernels (SM clock cycles)
+  int stall_after = -1;               // fault injection in the 3xTF32 expansion's producer (-1: off)  // fixed line-pass choice (8, 16, 32 lines, -1 register two-step), 0 = tuned
   void* tune_scratch = nullptr;
   size_t tune_scratch_bytes = 0;
   struct TuneRecord {

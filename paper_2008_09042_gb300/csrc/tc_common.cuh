@@ -36,6 +36,8 @@ struct TcArgs {
   // EX_SCATTER output map (see ScatterMap); sc_col0 = the launch row's first column pair
   int sc_L0, sc_L1, sc_im, sc_col0;
   long sc_hi, sc_mid, sc_col;
+  long long wait_cycles;  // bounded-wait limit (SM clock cycles)
+  int stall_after;        // fault injection: the producer stops after this many stages (-1: off)
 };
 
 // Position in a ring of `n` shared-memory stages: slot and the parity of the
@@ -244,7 +246,7 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
     int tc = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tc) {
       const int buf = tc & 1;
-      const bool got = mpi_ptx::mbar_wait(&acc_full[buf], (uint32_t)((tc >> 1) & 1), a.err);
+      const bool got = mpi_ptx::mbar_wait(&acc_full[buf], (uint32_t)((tc >> 1) & 1), a.err, a.wait_cycles);
       if (!__all_sync(0xffffffffu, got)) {  // warp-uniform decision before the .sync.aligned loads
         *s_failed = 1;
         break;

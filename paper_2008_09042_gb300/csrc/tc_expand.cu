@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       for (int kc = 0; kc < a.KC; ++kc, ++it) {
-        if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err)) {
+        if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err, a.wait_cycles)) {
           ok = false;
           break;
         }
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
       s_failed = 1;
       // bounded wait for the fills still in flight
       for (int g = (it > stages ? it - stages : 0); g < it; ++g)
-        mpi_ptx::mbar_wait(&full[g % stages], (uint32_t)((g / stages) & 1), nullptr);
+        mpi_ptx::mbar_wait(&full[g % stages], (uint32_t)((g / stages) & 1), nullptr, a.wait_cycles);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -120,18 +120,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
     const uint32_t b_chunk = (uint32_t)(a.n_gemm * 128) >> 4;  // descriptor step per K chunk
     RingPos r;
     int tc = 0;
-    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err);
+    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err, a.wait_cycles);
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tc) {
       const int buf = tc & 1;
       const uint32_t tacc = tmem + (uint32_t)(buf * a.half_cols);
-      if (!mpi_ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), a.err)) {
+      if (!mpi_ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), a.err, a.wait_cycles)) {
         ok = false;
         break;
       }
       fence_after();
       for (int kc = 0; kc < a.KC; ++kc) {
         const int s = r.s;
-        if (!mpi_ptx::mbar_wait(&full[s], r.ph, a.err)) {
+        if (!mpi_ptx::mbar_wait(&full[s], r.ph, a.err, a.wait_cycles)) {
           ok = false;
           break;
         }
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
     }
     // all MMAs issued by this thread have completed once `drain` fires
     mma_commit(drain);
-    mpi_ptx::mbar_wait(drain, 0, a.err);
+    mpi_ptx::mbar_wait(drain, 0, a.err, a.wait_cycles);
     if (!ok) s_failed = 1;
   } else if (warp >= 2) {
     mpi_ptx::pdl_wait();  // alpha, p and w may come from the previous kernel
@@ -272,6 +272,8 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.out = x.out;
   a.vout = x.vout;
   a.err = ctx->dev_err;
+  a.wait_cycles = ctx->wait_cycles;
+  a.stall_after = -1;
   a.tuck_B = x.tuck_B;
   a.group_coils = 0;
   a.C_total = x.C;

@@ -159,7 +159,10 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     RingPos r;
     int g = 0, kc = 0, t = (int)blockIdx.x;  // kc: first box of the stage
     for (; g < G; ++g) {
-      if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err)) break;
+      // fault injection (a test of the timeout path): stop issuing copies, so
+      // that every consumer's wait on the stages not loaded runs out
+      if (a.stall_after >= 0 && g >= a.stall_after) break;
+      if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err, a.wait_cycles)) break;
       unsigned char* dst = sA + (size_t)r.s * kStageBytes32;
       mpi_ptx::mbar_arrive_expect_tx(&full[r.s], kStageBytes32);
       tma_load_2d(dst, &tmap, kc * kKChunk32, t * kTileM, &full[r.s]);
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     if (g < G) {
       s_failed = 1;
       for (int h = (g > stages ? g - stages : 0); h < g; ++h)  // fills still in flight (bounded)
-        mpi_ptx::mbar_wait(&full[h % stages], (uint32_t)((h / stages) & 1), nullptr);
+        mpi_ptx::mbar_wait(&full[h % stages], (uint32_t)((h / stages) & 1), nullptr, a.wait_cycles);
     }
   } else if (warp >= 6) {
     // ---------------- converters: lo(x) of tile row 32 (warp % 4) + lane into TMEM.
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     RingPos r;
     for (int g = 0; g < G; ++g) {
-      const bool got = mpi_ptx::mbar_wait(&full[r.s], r.ph, a.err);
+      const bool got = mpi_ptx::mbar_wait(&full[r.s], r.ph, a.err, a.wait_cycles);
       if (!__all_sync(0xffffffffu, got)) {
         s_failed = 1;
         break;
@@ -222,18 +225,18 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     const uint32_t b_chunk = (uint32_t)(2 * a.n_gemm * 128) >> 4;  // descriptor step per K chunk
     RingPos r;
     int tc = 0;
-    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err);
+    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err, a.wait_cycles);
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tc) {
       const int buf = tc & 1;
       const uint32_t tacc = tmem + (uint32_t)(buf * a.half_cols);
-      if (!mpi_ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), a.err)) {
+      if (!mpi_ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), a.err, a.wait_cycles)) {
         ok = false;
         break;
       }
       fence_after();
       for (int kc = 0; kc < a.KC; kc += kBoxesPerStage) {
         const int s = r.s;
-        if (!mpi_ptx::mbar_wait(&full[s], r.ph, a.err)) {
+        if (!mpi_ptx::mbar_wait(&full[s], r.ph, a.err, a.wait_cycles)) {
           ok = false;
           break;
         }
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
         mma_tf32_acc(tacc, ad + kBoxDesc + 2, bd + b_chunk + 2, idesc_hi);
         mma_tf32_acc(tacc, ad + kBoxDesc + 4, bd + b_chunk + 4, idesc_hi);
         mma_tf32_acc(tacc, ad + kBoxDesc + 6, bd + b_chunk + 6, idesc_hi);
-        if (!mpi_ptx::mbar_wait(&conv[s], r.ph, a.err)) {
+        if (!mpi_ptx::mbar_wait(&conv[s], r.ph, a.err, a.wait_cycles)) {
           ok = false;
           break;
         }
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
       if (ok) mma_commit(&acc_full[buf]);
     }
     mma_commit(drain);
-    mpi_ptx::mbar_wait(drain, 0, a.err);
+    mpi_ptx::mbar_wait(drain, 0, a.err, a.wait_cycles);
     if (!ok) s_failed = 1;
   } else if (warp >= 2 && warp <= 5) {
     mpi_ptx::pdl_wait();  // alpha, p and w may come from the previous kernel
@@ -453,6 +456,8 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.out = x.out;
   a.vout = x.vout;
   a.err = ctx->dev_err;
+  a.wait_cycles = ctx->wait_cycles;
+  a.stall_after = ctx->stall_after;
   a.tuck_B = x.tuck_B;
   a.tuck_stride = x.tuck_stride;
   a.sc_L0 = x.sc.L0;

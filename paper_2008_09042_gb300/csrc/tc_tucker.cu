@@ -68,6 +68,7 @@ struct TxArgs {
   const float2* wk;  // adjoint input: per-coil data along kz [C][N1][B]
   const float2* tw;  // exp(-2 pi i m / N1), m < N1
   int* err;
+  long long wait_cycles;  // bounded-wait limit (SM clock cycles)
   int tmem_cols;
   int stages;
   TcArgs coef;       // coefficient builder: C = N1 rows of U1, q = r1, alpha = U1
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
     RingPos r;
     int g = 0;
     for (; g < my_tiles; ++g) {
-      if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err)) break;
+      if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err, a.wait_cycles)) break;
       unsigned char* dst = sA + (size_t)r.s * STAGE;
       mpi_ptx::mbar_arrive_expect_tx(&full[r.s], STAGE);
       tma_load_2d(dst, &tmap, 0, tile_row0(g), &full[r.s]);
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
     if (g < my_tiles) {
       s_failed = 1;
       for (int h = (g > stages ? g - stages : 0); h < g; ++h)  // fills still in flight (bounded)
-        mpi_ptx::mbar_wait(&full[h % stages], (uint32_t)((h / stages) & 1), nullptr);
+        mpi_ptx::mbar_wait(&full[h % stages], (uint32_t)((h / stages) & 1), nullptr, a.wait_cycles);
     }
   } else if (TF && warp >= 2 && warp <= 5) {
     // ---------------- converters: lo(x) of tile row 32 (warp % 4) + lane into TMEM
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     RingPos r;
     for (int g = 0; g < my_tiles; ++g) {
-      const bool got = mpi_ptx::mbar_wait(&full[r.s], r.ph, a.err);
+      const bool got = mpi_ptx::mbar_wait(&full[r.s], r.ph, a.err, a.wait_cycles);
       if (!__all_sync(0xffffffffu, got)) {
         s_failed = 1;
         break;
@@ -264,18 +265,18 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
     const uint64_t a0 = sdesc_sw128(mpi_ptx::smem_addr(sA));
     const uint64_t b0 = sdesc_sw128(mpi_ptx::smem_addr(sB));
     RingPos r;
-    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err);
+    bool ok = mpi_ptx::mbar_wait(bfull, 0, a.err, a.wait_cycles);
     for (int tc = 0; tc < my_tiles && ok; ++tc) {
       const int buf = NACC == 2 ? (tc & 1) : 0;
       const uint32_t par = NACC == 2 ? (uint32_t)((tc >> 1) & 1) : (uint32_t)(tc & 1);
       const uint32_t tacc = tmem + (uint32_t)(buf * NG);
-      if (!mpi_ptx::mbar_wait(&acc_empty[buf], par ^ 1u, a.err)) {
+      if (!mpi_ptx::mbar_wait(&acc_empty[buf], par ^ 1u, a.err, a.wait_cycles)) {
         ok = false;
         break;
       }
       fence_after();
       const int s = r.s;
-      if (!mpi_ptx::mbar_wait(&full[s], r.ph, a.err)) {
+      if (!mpi_ptx::mbar_wait(&full[s], r.ph, a.err, a.wait_cycles)) {
         ok = false;
         break;
       }
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
             mma_tf32(tacc, adk, bdk, idesc, (h | ks) != 0);
             mma_tf32(tacc, adk, bdk + lo_off, idesc, 1);
           }
-        if (!mpi_ptx::mbar_wait(&conv[s], r.ph, a.err)) {
+        if (!mpi_ptx::mbar_wait(&conv[s], r.ph, a.err, a.wait_cycles)) {
           ok = false;
           break;
         }
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
       r.next(stages);
     }
     mma_commit(drain);
-    mpi_ptx::mbar_wait(drain, 0, a.err);
+    mpi_ptx::mbar_wait(drain, 0, a.err, a.wait_cycles);
     if (!ok) s_failed = 1;
   } else if (warp >= kEpi0) {
     // ---------------- epilogue: 2 warps per lane quarter (sub 0, 1)
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
         // the two warps of a lane quarter take alternate tiles (sub = buffer =
         // tile parity) and each runs the whole DFT of its 32 positions
         if ((tc & 1) != sub) continue;
-        const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err);
+        const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err, a.wait_cycles);
         if (!__all_sync(0xffffffffu, got)) {
           failed = true;
           break;
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
-        const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err);
+        const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err, a.wait_cycles);
         if (epi_bar_any(!got, NT)) {
           failed = true;
           break;
@@ -554,6 +555,7 @@ mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_pl
   a.out = out;
   a.tw = twiddle_table(ctx, b->n[0]);
   a.err = ctx->dev_err;
+  a.wait_cycles = ctx->wait_cycles;
   if (!a.tw) return set_err(ctx, MPI_ERR_SHAPE, "Tucker x1: no twiddle table for n1");
   TcArgs& cf = a.coef;
   cf = TcArgs{};

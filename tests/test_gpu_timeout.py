@@ -2,8 +2,8 @@
 GPU without faulting it.
 
 With a short wait limit and the fault-injection hook that makes the FP32
-expansion's copy producer stop after one ring stage, the consumers' waits on
-the stages never loaded run out: the kernel records MPI_ERR_TIMEOUT in the
+expansion's copy producer issue no copy at all, the consumers' waits on the
+stages never loaded run out: the kernel records MPI_ERR_TIMEOUT in the
 context's device error word, drains the copies it issued, frees its tensor
 memory and returns.  The host learns of it at mpi_ctx_synchronize, and the
 next call on the same context must be correct.
@@ -41,7 +41,7 @@ def test_wait_timeout_reported_and_context_recovers():
     ctx.synchronize()
 
     ctx.set_wait_limit(2_000_000)  # about 1 ms at 2 GHz
-    ctx.inject_stall(1)
+    ctx.inject_stall(0)  # no ring stage is loaded (at this size a CTA has one per tile)
     mp.forward(ctx, plan, B, ag, pg)
     with pytest.raises(MpiError) as e:
         ctx.synchronize()

@@ -49,6 +49,12 @@ extern "C" mpi_status mpi_batch_create(mpi_ctx* ctx, const mpi_batch_slice* slic
     mpi_status st = mpi_ctx_reserve(ctx, s.plan, s.basis, s.C);
     if (st) return st;
   }
+  // tune the slices' FFT line passes now: no tuning happens inside the capture
+  for (int i = 0; i < n; ++i) {
+    mpi_status st = mpi_ctx_reserve(ctx, slices[i].plan, slices[i].basis, slices[i].C);
+    if (st == MPI_OK) st = tune_line_passes(ctx, slices[i].plan, slices[i].C);
+    if (st) return st;
+  }
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),

@@ -621,13 +621,11 @@ int lines_autotune(mpi_ctx* ctx, const long (&key)[10], int L, float2* data, int
   return rec.choice;
 }
 
+// The tile width of a line pass: the caller's fixed choice where it applies,
+// else the tuned one (tuning it now if this call can), else 0.
 template <bool INV>
-mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, int nx, long stride, int n_slabs,
-                          int inner, long outer_stride, long inner_stride, const uint8_t* rmask = nullptr,
-                          int mask_nz = 1) {
-  const float2* tw = twiddle_table(ctx, L);
-  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
-  if ((long)n_slabs * nx == 0) return MPI_OK;
+int lines_choose(mpi_ctx* ctx, float2* data, int L, int nx, long stride, int n_slabs, int inner, long outer_stride,
+                 long inner_stride, const float2* tw, const uint8_t* rmask, int mask_nz) {
   const long key[10] = {L, INV ? 1 : 0, nx, stride, n_slabs, inner, outer_stride, inner_stride, rmask ? 1 : 0,
                         mask_nz};
   int tile = 0;
@@ -644,6 +642,18 @@ mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, i
   }
   if (!tile)
     tile = lines_autotune<INV>(ctx, key, L, data, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw, rmask,
+                               mask_nz);
+  return tile;
+}
+
+template <bool INV>
+mpi_status lines_dispatch(mpi_ctx* ctx, const char* name, float2* data, int L, int nx, long stride, int n_slabs,
+                          int inner, long outer_stride, long inner_stride, const uint8_t* rmask = nullptr,
+                          int mask_nz = 1) {
+  const float2* tw = twiddle_table(ctx, L);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "unsupported FFT length");
+  if ((long)n_slabs * nx == 0) return MPI_OK;
+  int tile = lines_choose<INV>(ctx, data, L, nx, stride, n_slabs, inner, outer_stride, inner_stride, tw, rmask,
                                mask_nz);
   if (!tile) tile = lines_tile(ctx, L, nx, n_slabs);
   const int tw_cols = tile < 0 ? 32 : tile;
@@ -795,6 +805,33 @@ mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int n
   const long vol = plane * nz;
   if (inverse) return lines_dispatch<true>(ctx, "k_fft_lines<z,inv>", data, nz, nx, plane, C * ny, ny, vol, nx);
   return lines_dispatch<false>(ctx, "k_fft_lines<z,fwd>", data, nz, nx, plane, C * ny, ny, vol, nx);
+}
+
+mpi_status tune_line_passes(mpi_ctx* ctx, const mpi_plan* plan, int C) {
+  if (!ctx->autotune || plan->kind != MPI_TRAJ_CARTESIAN || C < 1) return MPI_OK;
+  const size_t cn = (size_t)C * plan->N;
+  if (!ctx->work || ctx->work_bytes < 2 * cn * sizeof(float2)) return MPI_OK;
+  // the workspace's second [C][N] buffer, as in the operator calls
+  void* saved = ctx->tune_scratch;
+  const size_t saved_bytes = ctx->tune_scratch_bytes;
+  float2* base = (float2*)ctx->work;
+  ctx->tune_scratch = base + cn;
+  ctx->tune_scratch_bytes = cn * sizeof(float2);
+  const int nz = plan->nz, ny = plan->ny, nx = plan->nx;
+  const long plane = (long)ny * nx, vol = plane * nz;
+  const float2* twy = twiddle_table(ctx, ny);
+  if (twy) {
+    lines_choose<false>(ctx, base, ny, nx, nx, C * nz, 1, plane, 0, twy, plan->row_has, nz);
+    lines_choose<true>(ctx, base, ny, nx, nx, C * nz, 1, plane, 0, twy, plan->row_has, nz);
+  }
+  const float2* twz = plan->ndim == 3 ? twiddle_table(ctx, nz) : nullptr;
+  if (twz) {
+    lines_choose<false>(ctx, base, nz, nx, plane, C * ny, ny, vol, nx, twz, nullptr, 1);
+    lines_choose<true>(ctx, base, nz, nx, plane, C * ny, ny, vol, nx, twz, nullptr, 1);
+  }
+  ctx->tune_scratch = saved;
+  ctx->tune_scratch_bytes = saved_bytes;
+  return cuda_check(ctx, cudaGetLastError(), "line-pass tuning");
 }
 
 mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const float2* data, int C,

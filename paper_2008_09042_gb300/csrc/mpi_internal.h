@@ -302,6 +302,10 @@ mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, in
 // deapodisation and sign on the fly); inverse writes only the window into dst.
 mpi_status launch_fft_cols_window(mpi_ctx* ctx, float2* grid, int C, int G, const float2* src, float2* dst,
                                   const float* deap, int n, bool inverse);
+// Tunes the line passes the operators run on this plan with C coils (in the
+// workspace, which must already hold them) so that a stream capture that
+// follows records the tuned kernels.
+mpi_status tune_line_passes(mpi_ctx* ctx, const mpi_plan* plan, int C);
 // In-place FFT along z of [C][nz][ny][nx].
 mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);
 // Forward: FFT along x of every row, centring sign on k, gather of the sampled points.

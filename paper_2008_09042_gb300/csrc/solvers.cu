@@ -788,6 +788,10 @@ extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const 
     g->out_p = g->out_alpha + Cq;
     g->hist = g->dbase;
     g->work = ctx->work;
+    if ((st = tune_line_passes(ctx, plan, C))) {
+      delete g;
+      return st;
+    }
     st = capture(ctx, g, [&]() {
       return irgn_body(ctx, plan, basis, C, prm, prec, g->sv, g->base, g->in_y, g->out_alpha, g->out_p, g->hist);
     });
@@ -957,6 +961,10 @@ extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const 
     g->hist = scratch + 2 * (size_t)C + (size_t)C * kRedBlocks;  // [n_outer][3]
     g->in_eps = g->hist + 3 * (size_t)prm->n_outer;
     g->work = ctx->work;
+    if ((st = tune_line_passes(ctx, plan, C))) {
+      delete g;
+      return st;
+    }
     st = capture(ctx, g, [&]() {
       return admm_body(ctx, plan, basis, C, prm, prec, g->sv, g->base, scratch, (const mpi_c32*)g->in_alpha,
                        g->in_y, g->in_eps, g->out_p, g->hist);

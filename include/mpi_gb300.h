@@ -55,8 +55,11 @@ typedef enum { MPI_TRAJ_CARTESIAN = 0, MPI_TRAJ_RADIAL = 1 } mpi_traj_kind;
  * budget (2 C <= 256, or 4 C <= 256 for the Jacobian, and 2 q <= 256 or so),
  * else on the CUDA cores.  BF16: tensor cores, BF16 basis and coefficients,
  * FP32 accumulation.  FP32_SIMT: always the CUDA-core FFMA kernel.  FFT,
- * gridding and reductions are FP32 in all three. */
-typedef enum { MPI_PREC_FP32 = 0, MPI_PREC_BF16 = 1, MPI_PREC_FP32_SIMT = 2 } mpi_precision;
+ * gridding and reductions are FP32 in all three.
+ * MIXED (the solvers only): BF16 operators inside the CG iterations, FP32 for
+ * the outer residuals, the right-hand sides and a refinement of each inner
+ * solve (see mpi_sm_estimate, mpi_image_solve); operator calls reject it. */
+typedef enum { MPI_PREC_FP32 = 0, MPI_PREC_BF16 = 1, MPI_PREC_FP32_SIMT = 2, MPI_PREC_MIXED = 3 } mpi_precision;
 
 typedef struct mpi_ctx mpi_ctx;
 typedef struct mpi_plan mpi_plan;

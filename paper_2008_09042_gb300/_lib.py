@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "MPI_OK", 1: "MPI_ERR_ARG", 2: "MPI_ERR_SHAPE", 3: "MPI_ERR_C
 
 TRAJ_CARTESIAN = 0
 TRAJ_RADIAL = 1
-PREC = {"fp32": 0, "bf16": 1, "fp32_simt": 2}
+PREC = {"fp32": 0, "bf16": 1, "fp32_simt": 2, "mixed": 3}
 
 # Every symbol include/mpi_gb300.h declares.
 EXPORTS = [

@@ -701,8 +701,16 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
                      float2* p_out, double* hist) {
   const long N = plan->N, Cq = (long)C * basis->q, CM = (long)C * plan->M, X = N + Cq;
   float2 *x = base, *dx = x + X, *res = dx + X, *d = res + X, *Ad = d + X, *h = Ad + X;
-  float2 *ys = h + X, *yt = ys + std::max(CM, 1L), *r = yt + std::max(CM, 1L);
+  float2 *bn = h + X, *del = bn + X;  // right-hand side, refinement correction
+  float2 *ys = del + X, *yt = ys + std::max(CM, 1L), *r = yt + std::max(CM, 1L);
   float2 *p = x, *al = x + N;
+  // MIXED: the CG iterations apply BF16 operators; the residual r, the
+  // right-hand side and one refinement of each Gauss-Newton step are FP32:
+  // e = b - (J^H J + 2L) dx in FP32, then the correction from a second CG
+  // solve (BF16 operators, n_cg / 2 iterations) is added to dx.
+  const mpi_precision pin = prec == MPI_PREC_MIXED ? MPI_PREC_BF16 : prec;
+  const mpi_precision pout = prec == MPI_PREC_MIXED ? MPI_PREC_FP32 : prec;
+  const int n_refine = prec == MPI_PREC_MIXED ? 1 : 0;
   // data scale: ys = y * target / ||y||
   if (CM > 0) {
     TRY(sv.dot(yc, nullptr, CM, FIN_SCALE, 0, prm->scale_target));
@@ -712,40 +720,59 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
   }
   TRY(sv.fill(p, make_float2(1.f, 0.f), N));
   TRY(sv.fill(al, make_float2(0.f, 0.f), Cq));
-  for (int n = 0; n <= prm->n_outer; ++n) {
-    // r = ys - G(x)
-    TRY(mpi_forward(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (mpi_c32*)yt, prec));
-    if (CM > 0) TRY(sv.lincomb(r, ys, 1.f, yt, -1.f, CM));
-    if (CM > 0) TRY(sv.dot(r, nullptr, CM, FIN_SQRT_TO_HIST, 0, 0, hist, n));
-    if (n == prm->n_outer) break;
-    const double an = std::max(prm->a0 * pow(prm->decay, n), prm->floor_);
-    const double bn = std::max(prm->b0 * pow(prm->decay, n), prm->floor_);
-    const float l1 = (float)(2.0 * an), l2 = (float)(2.0 * bn);
-    // rhs = J^H r - 2 L x
-    TRY(mpi_jacobian_adjoint(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)r,
-                             (mpi_c32*)h, (mpi_c32*)(h + N), prec));
-    TRY(sv.lincomb(res, h, 1.f, x, -l1, N));
-    TRY(sv.lincomb(res + N, h + N, 1.f, x + N, -l2, Cq));
-    TRY(sv.fill(dx, make_float2(0.f, 0.f), X));
+  float l1 = 0.f, l2 = 0.f;
+  // (J^H J + 2L) v into Ad, v in `v`, operators at precision pr
+  auto normal = [&](const float2* v, mpi_precision pr) -> mpi_status {
+    TRY(mpi_jacobian(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)v,
+                     (const mpi_c32*)(v + N), (mpi_c32*)yt, pr));
+    TRY(mpi_jacobian_adjoint(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)yt,
+                             (mpi_c32*)h, (mpi_c32*)(h + N), pr));
+    MPI_PROF(ctx, KF_SOLVER);
+    k_normal_finish<<<kRedBlocks, kVecThreads, 0, ctx->stream>>>(h, v, X, N, l1, l2, Ad, sv.partials);
+    MPI_LAUNCH_CHECK(ctx, "k_normal_finish");
+    return MPI_OK;
+  };
+  // `iters` CG iterations for (J^H J + 2L) sol = rhs from sol = 0
+  auto cg = [&](float2* sol, const float2* rhs, int iters, mpi_precision pr) -> mpi_status {
+    TRY(sv.fill(sol, make_float2(0.f, 0.f), X));
+    TRY(sv.lincomb(res, rhs, 1.f, nullptr, 0.f, X));
     TRY(sv.lincomb(d, res, 1.f, nullptr, 0.f, X));
     TRY(sv.dot(res, nullptr, X, FIN_STORE, S_RR));
-    for (int it = 0; it < prm->n_cg; ++it) {
-      // Ad = J^H J d + 2 L d
-      TRY(mpi_jacobian(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)d,
-                       (const mpi_c32*)(d + N), (mpi_c32*)yt, prec));
-      TRY(mpi_jacobian_adjoint(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)yt,
-                               (mpi_c32*)h, (mpi_c32*)(h + N), prec));
-      MPI_PROF(ctx, KF_SOLVER);
-      k_normal_finish<<<kRedBlocks, kVecThreads, 0, ctx->stream>>>(h, d, X, N, l1, l2, Ad, sv.partials);
-      MPI_LAUNCH_CHECK(ctx, "k_normal_finish");
+    for (int it = 0; it < iters; ++it) {
+      TRY(normal(d, pr));
       TRY(sv.fin(FIN_CG_ALPHA));
       MPI_PROF(ctx, KF_SOLVER);
-      k_cg_update<<<kRedBlocks, kVecThreads, 0, ctx->stream>>>(dx, res, d, Ad, X, sv.S, sv.partials);
+      k_cg_update<<<kRedBlocks, kVecThreads, 0, ctx->stream>>>(sol, res, d, Ad, X, sv.S, sv.partials);
       MPI_LAUNCH_CHECK(ctx, "k_cg_update");
       TRY(sv.fin(FIN_CG_BETA));
       MPI_PROF(ctx, KF_SOLVER);
       k_cg_dir<<<grid_for(X), kVecThreads, 0, ctx->stream>>>(d, res, X, sv.S);
       MPI_LAUNCH_CHECK(ctx, "k_cg_dir");
+    }
+    return MPI_OK;
+  };
+  for (int n = 0; n <= prm->n_outer; ++n) {
+    // r = ys - G(x)
+    TRY(mpi_forward(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (mpi_c32*)yt, pout));
+    if (CM > 0) TRY(sv.lincomb(r, ys, 1.f, yt, -1.f, CM));
+    if (CM > 0) TRY(sv.dot(r, nullptr, CM, FIN_SQRT_TO_HIST, 0, 0, hist, n));
+    if (n == prm->n_outer) break;
+    const double an = std::max(prm->a0 * pow(prm->decay, n), prm->floor_);
+    const double bnn = std::max(prm->b0 * pow(prm->decay, n), prm->floor_);
+    l1 = (float)(2.0 * an);
+    l2 = (float)(2.0 * bnn);
+    // b = J^H r - 2 L x
+    TRY(mpi_jacobian_adjoint(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)r,
+                             (mpi_c32*)h, (mpi_c32*)(h + N), pout));
+    TRY(sv.lincomb(bn, h, 1.f, x, -l1, N));
+    TRY(sv.lincomb(bn + N, h + N, 1.f, x + N, -l2, Cq));
+    TRY(cg(dx, bn, prm->n_cg, pin));
+    for (int k = 0; k < n_refine; ++k) {
+      // e = b - (J^H J + 2L) dx in FP32 (into bn's slot after use: b is not needed again)
+      TRY(normal(dx, pout));
+      TRY(sv.lincomb(bn, bn, 1.f, Ad, -1.f, X));
+      TRY(cg(del, bn, std::max(1, prm->n_cg / 2), pin));
+      TRY(sv.lincomb(dx, dx, 1.f, del, 1.f, X));
     }
     TRY(sv.lincomb(x, x, 1.f, dx, (float)prm->gamma, X));
   }
@@ -777,13 +804,13 @@ extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const 
     g->C = C;
     g->prec = prec;
     g->key.assign((const unsigned char*)prm, (const unsigned char*)prm + sizeof(*prm));
-    // x, dx, res, d, Ad, h (X each); ys, yt, r (CM each); in_y, out_alpha, out_p
-    mpi_status st = alloc_solver(ctx, g->mem, 6 * X + 4 * CMs + Cq + N, prm->n_outer + 1, g->sv, &g->base, &g->dbase);
+    // x, dx, res, d, Ad, h, b, del (X each); ys, yt, r (CM each); in_y, out_alpha, out_p
+    mpi_status st = alloc_solver(ctx, g->mem, 8 * X + 4 * CMs + Cq + N, prm->n_outer + 1, g->sv, &g->base, &g->dbase);
     if (st) {
       delete g;
       return st;
     }
-    g->in_y = g->base + 6 * X + 3 * CMs;
+    g->in_y = g->base + 8 * X + 3 * CMs;
     g->out_alpha = g->in_y + CMs;
     g->out_p = g->out_alpha + Cq;
     g->hist = g->dbase;
@@ -845,10 +872,16 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
   TRY(sv.set(S_RHO, prm->rho0));
   const unsigned ball_blocks = (unsigned)std::max(1L, std::min((M + kVecThreads - 1) / kVecThreads, (long)kRedBlocks));
 
-  auto normal = [&](const float2* v, float2* out) -> mpi_status {
+  // MIXED: BF16 operators in the CG iterations; FP32 for the constraint-side
+  // products (A p for the projections and the dual update), the right-hand
+  // side and the CG's starting residual (each p-update warm-starts from the
+  // previous p, so every outer step refines it against an FP32 residual).
+  const mpi_precision pin = prec == MPI_PREC_MIXED ? MPI_PREC_BF16 : prec;
+  const mpi_precision pout = prec == MPI_PREC_MIXED ? MPI_PREC_FP32 : prec;
+  auto normal = [&](const float2* v, float2* out, mpi_precision pr) -> mpi_status {
     // out = v + S^H F^H F S v
-    TRY(mpi_forward(ctx, plan, basis, A, C, (const mpi_c32*)v, (mpi_c32*)wk, prec));
-    TRY(mpi_adjoint(ctx, plan, basis, A, C, (const mpi_c32*)wk, (mpi_c32*)out, prec));
+    TRY(mpi_forward(ctx, plan, basis, A, C, (const mpi_c32*)v, (mpi_c32*)wk, pr));
+    TRY(mpi_adjoint(ctx, plan, basis, A, C, (const mpi_c32*)wk, (mpi_c32*)out, pr));
     return sv.lincomb(out, out, 1.f, v, 1.f, N);
   };
 
@@ -868,7 +901,7 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
       k_ball_apply<<<grid_for(CM), kVecThreads, 0, ctx->stream>>>(Apk, uk, yc, C, (int)M, fball, zk);
       MPI_LAUNCH_CHECK(ctx, "k_ball_apply");
       TRY(sv.lincomb(wk, zk, 1.f, uk, -1.f, CM));
-      TRY(mpi_adjoint(ctx, plan, basis, A, C, (const mpi_c32*)wk, (mpi_c32*)rhs, prec));
+      TRY(mpi_adjoint(ctx, plan, basis, A, C, (const mpi_c32*)wk, (mpi_c32*)rhs, pout));
       TRY(sv.lincomb(rhs, rhs, 1.f, z0, 1.f, N));
       TRY(sv.lincomb(rhs, rhs, 1.f, u0, -1.f, N));
     } else {
@@ -877,12 +910,12 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
     // p = (I + S^H F^H F S)^{-1} rhs by CG from the previous p
     TRY(sv.lincomb(p_prev, p, 1.f, nullptr, 0.f, N));
     if (CM > 0) TRY(sv.lincomb(Apk_prev, Apk, 1.f, nullptr, 0.f, CM));
-    TRY(normal(p, Ad));
+    TRY(normal(p, Ad, pout));
     TRY(sv.lincomb(r, rhs, 1.f, Ad, -1.f, N));
     TRY(sv.lincomb(d, r, 1.f, nullptr, 0.f, N));
     TRY(sv.dot(r, nullptr, N, FIN_STORE, S_RR));
     for (int k = 0; k < prm->n_cg; ++k) {
-      TRY(normal(d, t));
+      TRY(normal(d, t, pin));
       MPI_PROF(ctx, KF_SOLVER);
       k_normal_finish<<<kRedBlocks, kVecThreads, 0, ctx->stream>>>(t, d, N, N, 0.f, 0.f, Ad, sv.partials);
       MPI_LAUNCH_CHECK(ctx, "k_normal_finish");
@@ -900,7 +933,7 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
     k_dual_update<<<grid_for(N), kVecThreads, 0, ctx->stream>>>(u0, p, z0, N);
     MPI_LAUNCH_CHECK(ctx, "k_dual_update");
     if (CM > 0) {
-      TRY(mpi_forward(ctx, plan, basis, A, C, (const mpi_c32*)p, (mpi_c32*)Apk, prec));
+      TRY(mpi_forward(ctx, plan, basis, A, C, (const mpi_c32*)p, (mpi_c32*)Apk, pout));
       MPI_PROF(ctx, KF_SOLVER);
       k_dual_update<<<grid_for(CM), kVecThreads, 0, ctx->stream>>>(uk, Apk, zk, CM);
       MPI_LAUNCH_CHECK(ctx, "k_dual_update");

@@ -146,3 +146,24 @@ def test_bf16_solvers_against_oracle(ctx, mp, prob):
     x_ref, _ = solvers.admm_tv(prob["Fs"], op.expand(prob["U"], at), prob["y"], prob["eps"],
                                (prob["ny"], prob["nx"]), n_outer=50, n_cg=5, n_tv=10)
     assert nrmse(f64(x), x_ref) < 1e-2
+
+
+def test_mixed_precision_solvers_against_oracle(ctx, mp, prob):
+    # MIXED: BF16 operators inside the CG iterations, FP32 residuals and
+    # right-hand sides with a refinement of each Gauss-Newton step; against the
+    # FP64 oracle it must be at least as close as plain BF16 (NRMSE <= 1e-2)
+    plan = mp.Plan(ctx, (prob["ny"], prob["nx"]), sample_idx=prob["idx"])
+    B = mp.Basis(ctx, prob["U"].T)
+    p_ref, a_ref, _ = solvers.irgn(prob["Fs"], prob["U"], prob["y"], prob["C"], prob["q"], n_outer=20, n_cg=10)
+    ci_ref = op.expand(prob["U"], a_ref) * p_ref[None]
+    errs = {}
+    for prec in ("bf16", "mixed"):
+        a, p, _ = mp.sm_estimate(ctx, plan, B, c64(prob["y"]), prob["C"], n_outer=20, n_cg=10, prec=prec)
+        errs[prec] = nrmse(op.expand(prob["U"], f64(a)) * f64(p)[None], ci_ref)
+    assert errs["mixed"] < 1e-2
+    at = prob["a_true"].astype(np.complex64).astype(np.complex128)
+    x, _ = mp.image_solve(ctx, plan, B, c64(at), c64(prob["y"]), prob["eps"], n_outer=50, n_cg=5, n_tv=10,
+                          prec="mixed")
+    x_ref, _ = solvers.admm_tv(prob["Fs"], op.expand(prob["U"], at), prob["y"], prob["eps"],
+                               (prob["ny"], prob["nx"]), n_outer=50, n_cg=5, n_tv=10)
+    assert nrmse(f64(x), x_ref) < 1e-2

@@ -491,44 +491,50 @@ def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
     return out
 
 
-def recon_per_slice(mp, ctx, dev, prec_list=("fp32", "bf16"), reps=2):
-    """MPI-BL (20 IRGN x 10 CG) + MPI-L (50 ADMM x 5 CG x 10 TV) wall time per slice
-    on the 64 x 64, 4-coil, q = 32 workload; NRMSE of each precision's image
-    against the FP32 result."""
+def recon_per_slice(mp, ctx, dev, names=("cart2d_64_c4_q32", "cart2d_256_c16_q128", "cart2d_320_c16_q100"),
+                    precs=("fp32", "bf16", "mixed"), reps=2):
+    """MPI-BL (20 IRGN x 10 CG) + MPI-L (50 ADMM x 5 CG x 10 TV) wall time per
+    slice for each precision, on data and against reconstructions the FP64
+    oracle made (tests/golden/recon_<workload>.npz, written by
+    tests/golden/make_recon_golden.py): NRMSE of the coil images s_k (.) p
+    (MPI-BL) and of the image (MPI-L) against the oracle's."""
     import torch
 
-    cfg = w.workload("cart2d_64_c4_q32")
-    ny, nx = cfg["dims"]
-    C, q = cfg["C"], cfg["q"]
-    base = w.BASE_SEED
-    U = w.smooth_orthonormal_basis(ny, nx, q, seed=base)
-    mask = w.vd_lines_mask(ny, nx, cfg["R"], cfg["acs"], seed=base + 1)
-    idx = w.mask_to_indices(mask)
-    plan = mp.Plan(ctx, (ny, nx), sample_idx=idx)
-    B = mp.Basis(ctx, U.T)
-    a_true = torch.from_numpy(w.random_coefficients(C, q, seed=base + 2).astype(np.complex64)).to(dev)
-    p_true = torch.from_numpy(w.random_ellipses(ny, nx, seed=base + 3).ravel().astype(np.complex64)).to(dev)
-    y0 = mp.forward(ctx, plan, B, a_true, p_true).cpu().numpy()
-    sig = w.noise_sigma_for_snr(y0, cfg["snr_db"])
-    y = torch.from_numpy((y0 + w.complex_noise(y0.shape, sig, seed=base + 4)).astype(np.complex64)).to(dev)
-    eps = np.full(C, sig * np.sqrt(idx.size))
-    res = {}
-    images = {}
-    for prec in prec_list:
-        times = []
-        for _ in range(reps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            a, _, _ = mp.sm_estimate(ctx, plan, B, y, C, n_outer=cfg["n_irgn"], n_cg=10, prec=prec)
-            img, _ = mp.image_solve(ctx, plan, B, a, y, eps, n_outer=cfg["n_admm"], n_cg=5, n_tv=10, prec=prec)
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-        images[prec] = img.cpu().numpy().astype(np.complex128)
-        res[prec] = {"ms_per_slice": 1000.0 * min(times)}
-    ref = images["fp32"]
-    for prec in prec_list:
-        res[prec]["nrmse_vs_fp32"] = float(np.linalg.norm(images[prec] - ref) / np.linalg.norm(ref))
-    return {"workload": cfg["name"], "iterations": "20 IRGN x 10 CG + 50 ADMM x 5 CG x 10 TV", **res}
+    out = {"iterations": "20 IRGN x 10 CG + 50 ADMM x 5 CG x 10 TV",
+           "reference": "FP64 oracle reconstruction of the same data (stored fixture)"}
+    for name in names:
+        path = os.path.join(ROOT, "tests", "golden", f"recon_{name}.npz")
+        if not os.path.exists(path):
+            out[name] = {"unavailable": f"{os.path.relpath(path, ROOT)} missing"}
+            continue
+        g = np.load(path)
+        cfg, U, idx, _, _ = w.recon_case(name)
+        ny, nx = cfg["dims"]
+        C = cfg["C"]
+        plan = mp.Plan(ctx, (ny, nx), sample_idx=idx)
+        B = mp.Basis(ctx, U.T)
+        y = torch.from_numpy(np.ascontiguousarray(g["y"])).to(dev)
+        eps = g["eps"]
+        ref_ci = (g["alpha_bl"].astype(np.complex128) @ U.T) * g["p_bl"].astype(np.complex128)[None]
+        ref_p = g["p_l"].astype(np.complex128)
+        res = {}
+        for prec in precs:
+            times = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                a, p, _ = mp.sm_estimate(ctx, plan, B, y, C, n_outer=cfg["n_irgn"], n_cg=10, prec=prec)
+                img, _ = mp.image_solve(ctx, plan, B, a, y, eps, n_outer=cfg["n_admm"], n_cg=5, n_tv=10, prec=prec)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            ci = (a.cpu().numpy().astype(np.complex128) @ U.T) * p.cpu().numpy().astype(np.complex128)[None]
+            x = img.cpu().numpy().astype(np.complex128)
+            res[prec] = {"ms_per_slice": 1000.0 * min(times),
+                         "nrmse_coil_images_vs_oracle": float(np.linalg.norm(ci - ref_ci) / np.linalg.norm(ref_ci)),
+                         "nrmse_image_vs_oracle": float(np.linalg.norm(x - ref_p) / np.linalg.norm(ref_p))}
+        out[name] = {"dims": list(cfg["dims"]), "C": C, "q": cfg["q"], "M": int(idx.size), **res}
+        del plan, B
+    return out
 
 
 # --------------------------------------------------------------------- arms

@@ -452,9 +452,11 @@ extern "C" mpi_status mpi_ctx_inject_stall(mpi_ctx* ctx, int stages) {
 
 extern "C" mpi_status mpi_ctx_set_line_kernel(mpi_ctx* ctx, int choice) {
   if (!ctx) return MPI_ERR_ARG;
-  if (choice != 0 && choice != 8 && choice != 16 && choice != 32 && choice != -1)
-    return set_err(ctx, MPI_ERR_ARG, "line kernel choice must be 0, 8, 16, 32 or -1");
-  ctx->line_kernel = choice;
+  if (choice != 0 && choice != 8 && choice != 16 && choice != 32 && choice != -1 && choice != -2)
+    return set_err(ctx, MPI_ERR_ARG, "line kernel choice must be 0, 8, 16, 32, -1 or -2");
+  // -2: separate passes along y and x in 3D (no plane kernel), tuned line passes
+  ctx->plane_pass = choice != -2;
+  ctx->line_kernel = choice == -2 ? 0 : choice;
   return MPI_OK;
 }
 
@@ -771,6 +773,7 @@ extern "C" mpi_status mpi_forward(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
     void* map = nullptr;
     if ((st = tucker_x1_operand(ctx, basis, a.alpha, C, w.T, prec, &op, &map))) return st;
     if ((st = tucker_x1_fused_launch(ctx, basis, plan, false, C, map, a.p, nullptr, w.A, a.scale, prec))) return st;
+    if (ctx->plane_pass && plane_pass_supported(plan)) return launch_plane_yx(ctx, plan, w.A, C, (float2*)y, false);
     if ((st = launch_fft_cols(ctx, w.A, C, plan->nz, plan->ny, plan->nx, false, plan->row_has))) return st;
     return launch_rows_fwd_gather(ctx, plan, w.A, C, (float2*)y);
   }
@@ -794,8 +797,12 @@ extern "C" mpi_status mpi_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_
   if (tucker_x1_fused_supported(basis, plan, C, prec)) {
     // inverse passes along x and y, then one tensor-core pass: the inverse DFT
     // along z, the maps' x1 product and the sum over coils of conj(s_c) w_c
-    if ((st = launch_rows_scatter_inv(ctx, plan, (const float2*)y, C, w.A))) return st;
-    if ((st = launch_fft_cols(ctx, w.A, C, plan->nz, plan->ny, plan->nx, true, plan->row_has))) return st;
+    if (ctx->plane_pass && plane_pass_supported(plan)) {
+      if ((st = launch_plane_yx(ctx, plan, w.A, C, (float2*)y, true))) return st;
+    } else {
+      if ((st = launch_rows_scatter_inv(ctx, plan, (const float2*)y, C, w.A))) return st;
+      if ((st = launch_fft_cols(ctx, w.A, C, plan->nz, plan->ny, plan->nx, true, plan->row_has))) return st;
+    }
     void* op = nullptr;
     void* map = nullptr;
     if ((st = tucker_x1_operand(ctx, basis, a.alpha, C, w.T, prec, &op, &map))) return st;

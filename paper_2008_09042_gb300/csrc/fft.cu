@@ -754,6 +754,151 @@ __global__ void __launch_bounds__(kLineWarps * 32, (L * 8 <= 2048) ? 4 : (L * 8 
 
 float axis_sign(int n) { return ((n / 2) & 1) ? -1.f : 1.f; }
 
+// The passes along y and x of one (coil, kz) plane of a 3D volume in one CTA,
+// the plane held in shared memory S [NY][NX] (NY x NX x 8 bytes, at most 128 KB).
+// NX / 8 warps: four per 32-column group.
+//  forward: the DFT along y as a register two-step (NY = 8 R2; y = r + R2 m):
+//    DFT8 over m straight from the coalesced rows of global memory, twiddle
+//    w_NY^(r k1), into S rows r + R2 k1; then for each k1 the R2 rows R2 k1 + r
+//    are read back, transformed (R2-point DFT) and written in place, so that
+//    row R2 (ky % 8) + ky / 8 holds k-space row ky.  Then each k-space row with
+//    samples takes its DFT along x (Stockham, one warp per row) and the gather
+//    of its samples with the k-side centring sign.
+//  inverse: the rows with samples are zero-filled from theirs, signed and
+//    transformed along x into S row ky (the others zeroed), then the inverse
+//    two-step along y (the forward one on conjugated data) writes the plane's
+//    rows y straight to global memory.
+// Rows along x: one per sample row of the plan (row_ptr over (kz, ky)).
+template <int NY, int NX, bool INV>
+__global__ void __launch_bounds__(NX * 4, 1) k_plane_yx(float2* __restrict__ data, float2* __restrict__ y, int nz,
+                                                        const int32_t* __restrict__ idx,
+                                                        const int32_t* __restrict__ row_ptr, int M, float ksign,
+                                                        const float2* __restrict__ twy_g,
+                                                        const float2* __restrict__ twx_g) {
+  constexpr int R2 = NY / 8;
+  constexpr int NW = NX / 8;
+  constexpr int NT = NW * 32;
+  constexpr int GROUPS = NX / 32;
+  extern __shared__ float2 sh[];
+  float2* S = sh;                               // [NY][NX]
+  float2* rbuf = S + NY * NX;                   // [NW][padded_len(NX)]
+  float2* twy = rbuf + NW * padded_len(NX);     // [NY]
+  float2* twx = twy + NY;                       // [NX]
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cg = warp % GROUPS, sub = warp / GROUPS;  // sub < 4
+  const int col = cg * 32 + lane;
+  const int plane = (int)blockIdx.x;
+  const int c = plane / nz, kz = plane - c * nz;
+  float2* P = data + (size_t)plane * NY * NX;
+  for (int i = tid; i < NY; i += NT) twy[i] = twy_g[i];
+  for (int i = tid; i < NX; i += NT) twx[i] = twx_g[i];
+  float2* b = rbuf + warp * padded_len(NX);
+  const int rbase = kz * NY;  // k-space row (kz, ky) = kz NY + ky
+  if (!INV) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < R2 / 4; ++i) {
+      const int r = sub + 4 * i;
+      float2 v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = P[(size_t)(r + R2 * m) * NX + col];
+      mpi_dft::dft8(v);
+#pragma unroll
+      for (int k1 = 1; k1 < 8; ++k1) v[k1] = mpi_dft::cmulf(v[k1], twy[r * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) S[(r + R2 * k1) * NX + col] = v[k1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k1 = sub; k1 < 8; k1 += 4) {
+      float2 u[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) u[r] = S[(R2 * k1 + r) * NX + col];
+      mpi_dft::dft_r<R2>(u);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) S[(R2 * k1 + k2) * NX + col] = u[k2];
+    }
+    __syncthreads();
+    for (int ky = warp; ky < NY; ky += NW) {
+      const int row = rbase + ky;
+      const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
+      if (m1 <= m0) continue;  // warp-uniform
+      const float2* src = S + (R2 * (ky % 8) + ky / 8) * NX;
+      for (int i = lane; i < NX; i += 32) b[pad8(i)] = src[i];
+      __syncwarp();
+      Fft<NX, false>::go(b, twx, lane);
+      const int rpar = (kz + ky) & 1;
+      const size_t rb = (size_t)row * NX;
+      for (int m = m0 + lane; m < m1; m += 32) {
+        const int kx = (int)(idx[m] - rb);
+        const float sg = ((kx + rpar) & 1) ? -ksign : ksign;
+        const float2 t = b[pad8(kx)];
+        y[(size_t)c * M + m] = make_float2(t.x * sg, t.y * sg);
+      }
+      __syncwarp();
+    }
+  } else {
+    __syncthreads();
+    for (int ky = warp; ky < NY; ky += NW) {
+      const int row = rbase + ky;
+      const int m0 = row_ptr[row], m1 = row_ptr[row + 1];
+      float2* dst = S + ky * NX;
+      if (m1 <= m0) {  // warp-uniform
+        for (int i = lane; i < NX; i += 32) dst[i] = make_float2(0.f, 0.f);
+        continue;
+      }
+      for (int i = lane; i < padded_len(NX); i += 32) b[i] = make_float2(0.f, 0.f);
+      __syncwarp();
+      const int rpar = (kz + ky) & 1;
+      const size_t rb = (size_t)row * NX;
+      for (int m = m0 + lane; m < m1; m += 32) {
+        const int kx = (int)(idx[m] - rb);
+        const float sg = ((kx + rpar) & 1) ? -ksign : ksign;
+        const float2 t = y[(size_t)c * M + m];
+        b[pad8(kx)] = make_float2(t.x * sg, t.y * sg);
+      }
+      __syncwarp();
+      Fft<NX, true>::go(b, twx, lane);
+      for (int i = lane; i < NX; i += 32) dst[i] = b[pad8(i)];
+      __syncwarp();
+    }
+    __syncthreads();
+    // inverse along y: the forward two-step on conjugated values, conjugated back
+#pragma unroll
+    for (int i = 0; i < R2 / 4; ++i) {
+      const int r = sub + 4 * i;
+      float2 v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const float2 t = S[(r + R2 * m) * NX + col];
+        v[m] = make_float2(t.x, -t.y);
+      }
+      mpi_dft::dft8(v);
+#pragma unroll
+      for (int k1 = 1; k1 < 8; ++k1) v[k1] = mpi_dft::cmulf(v[k1], twy[r * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) S[(r + R2 * k1) * NX + col] = v[k1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k1 = sub; k1 < 8; k1 += 4) {
+      float2 u[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) u[r] = S[(R2 * k1 + r) * NX + col];
+      mpi_dft::dft_r<R2>(u);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) P[(size_t)(k1 + 8 * k2) * NX + col] = make_float2(u[k2].x, -u[k2].y);
+    }
+  }
+}
+
+template <int NY, int NX>
+size_t plane_smem() {
+  return ((size_t)NY * NX + (size_t)(NX / 8) * padded_len(NX) + NY + NX) * sizeof(float2);
+}
+
 }  // namespace
 
 mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse,
@@ -832,6 +977,41 @@ mpi_status tune_line_passes(mpi_ctx* ctx, const mpi_plan* plan, int C) {
   ctx->tune_scratch = saved;
   ctx->tune_scratch_bytes = saved_bytes;
   return cuda_check(ctx, cudaGetLastError(), "line-pass tuning");
+}
+
+bool plane_pass_supported(const mpi_plan* plan) {
+  if (plan->kind != MPI_TRAJ_CARTESIAN || plan->ndim != 3) return false;
+  const int ny = plan->ny, nx = plan->nx;
+  return (ny == 64 || ny == 96 || ny == 128) && (nx == 64 || nx == 96 || nx == 128);
+}
+
+mpi_status launch_plane_yx(mpi_ctx* ctx, const mpi_plan* plan, float2* data, int C, float2* y, bool inverse) {
+  if (!plane_pass_supported(plan)) return set_err(ctx, MPI_ERR_UNSUPPORTED, "plane pass: shape");
+  const long planes = (long)C * plan->nz;
+  if (planes == 0) return MPI_OK;
+  if (planes > 0x7fffffffL) return set_err(ctx, MPI_ERR_SHAPE, "plane pass: too many planes");
+  const float ks = axis_sign(plan->nx) * axis_sign(plan->ny) * axis_sign(plan->nz);
+  const float2* twy = twiddle_table(ctx, plan->ny);
+  const float2* twx = twiddle_table(ctx, plan->nx);
+  if (!twy || !twx) return set_err(ctx, MPI_ERR_SHAPE, "plane pass: no twiddle table");
+  cudaError_t e = cudaSuccess;
+#define MPI_PLANE(NY_, NX_)                                                                                    \
+  if (plan->ny == NY_ && plan->nx == NX_) {                                                                    \
+    const size_t smem = plane_smem<NY_, NX_>();                                                                \
+    auto kern = inverse ? k_plane_yx<NY_, NX_, true> : k_plane_yx<NY_, NX_, false>;                            \
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                    \
+    if (e != cudaSuccess) return cuda_check(ctx, e, "plane pass smem attribute");                              \
+    MPI_PROF(ctx, KF_FFT_ROWS);                                                                                \
+    launch_pdl(ctx, kern, dim3((unsigned)planes), dim3(NX_ * 4), smem, data, y, plan->nz, plan->idx,           \
+               plan->row_ptr, plan->M, ks, twy, twx);                                                          \
+    MPI_LAUNCH_CHECK(ctx, inverse ? "k_plane_yx<inv>" : "k_plane_yx<fwd>");                                    \
+    return MPI_OK;                                                                                             \
+  }
+  MPI_PLANE(64, 64) MPI_PLANE(64, 96) MPI_PLANE(64, 128)
+  MPI_PLANE(96, 64) MPI_PLANE(96, 96) MPI_PLANE(96, 128)
+  MPI_PLANE(128, 64) MPI_PLANE(128, 96) MPI_PLANE(128, 128)
+#undef MPI_PLANE
+  return set_err(ctx, MPI_ERR_UNSUPPORTED, "plane pass: shape");
 }
 
 mpi_status launch_rows_fwd_gather(mpi_ctx* ctx, const mpi_plan* plan, const float2* data, int C,

@@ -56,6 +56,7 @@ struct mpi_ctx {
   // stream is being captured, and only while `autotune` is set.
   bool autotune = true;
   int line_kernel = 0;
+  bool plane_pass = true;  // 3D: the passes along y and x in one kernel per plane where it applies
   long long wait_cycles = 4LL << 30;  // bounded-wait limit of the tensor-core kernels (SM clock cycles)
   int stall_after = -1;               // fault injection in the 3xTF32 expansion's producer (-1: off)  // fixed line-pass choice (8, 16, 32 lines, -1 register two-step), 0 = tuned
   void* tune_scratch = nullptr;
@@ -306,6 +307,12 @@ mpi_status launch_fft_cols_window(mpi_ctx* ctx, float2* grid, int C, int G, cons
 // workspace, which must already hold them) so that a stream capture that
 // follows records the tuned kernels.
 mpi_status tune_line_passes(mpi_ctx* ctx, const mpi_plan* plan, int C);
+// The passes along y and x of every (coil, kz) plane of a 3D volume in one
+// kernel (plane in shared memory): forward, data [C][nz][ny][nx] (already
+// transformed along z) -> samples y; inverse, samples -> data (to be
+// transformed along z).  Planes of 64 / 96 / 128 squared.
+bool plane_pass_supported(const mpi_plan* plan);
+mpi_status launch_plane_yx(mpi_ctx* ctx, const mpi_plan* plan, float2* data, int C, float2* y, bool inverse);
 // In-place FFT along z of [C][nz][ny][nx].
 mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);
 // Forward: FFT along x of every row, centring sign on k, gather of the sampled points.

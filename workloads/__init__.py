@@ -23,5 +23,6 @@ from .noise import complex_noise, noise_sigma_for_snr  # noqa: F401
 from .coefs import random_coefficients, random_image  # noqa: F401
 from .standin import smooth_orthonormal_basis, smooth_tucker_basis  # noqa: F401
 from .configs import WORKLOADS, workload  # noqa: F401
+from .recon import RECON_SEED, recon_case  # noqa: F401
 
 BASE_SEED = 20200820

@@ -14,6 +14,12 @@ WORKLOADS = {
         kind="cartesian", dims=(256, 256), C=16, q=128, mask="poisson", R=6, calib=(24, 24),
         snr_db=30.0, n_irgn=20, n_admm=50,
     ),
+    # the paper's 2D Cartesian timing shape (320 x 320, 16 coils, R = 2 with 16
+    # ACS lines, q = 100), used for reconstruction times
+    "cart2d_320_c16_q100": dict(
+        kind="cartesian", dims=(320, 320), C=16, q=100, mask="vd_lines", R=2, acs=16,
+        snr_db=30.0, n_irgn=20, n_admm=50,
+    ),
     "radial2d_256_c12_q96": dict(
         kind="radial", dims=(256, 256), C=12, q=96, spokes=64, readout=512, W=6, sigma=2.0,
         snr_db=30.0,

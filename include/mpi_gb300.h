@@ -57,8 +57,10 @@ typedef enum { MPI_TRAJ_CARTESIAN = 0, MPI_TRAJ_RADIAL = 1 } mpi_traj_kind;
  * FP32 accumulation.  FP32_SIMT: always the CUDA-core FFMA kernel.  FFT,
  * gridding and reductions are FP32 in all three.
  * MIXED (the solvers only): BF16 operators inside the CG iterations, FP32 for
- * the outer residuals, the right-hand sides and a refinement of each inner
- * solve (see mpi_sm_estimate, mpi_image_solve); operator calls reject it. */
+ * the outer residuals and the right-hand sides (IRGN: r = y - G(x) and
+ * J^H r - 2 L x of every Gauss-Newton step; ADMM: A p, the right-hand side and
+ * each p-update's starting residual), so the outer iterations refine the
+ * solution against FP32 residuals; operator calls reject it. */
 typedef enum { MPI_PREC_FP32 = 0, MPI_PREC_BF16 = 1, MPI_PREC_FP32_SIMT = 2, MPI_PREC_MIXED = 3 } mpi_precision;
 
 typedef struct mpi_ctx mpi_ctx;

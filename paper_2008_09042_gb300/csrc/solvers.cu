@@ -701,16 +701,15 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
                      float2* p_out, double* hist) {
   const long N = plan->N, Cq = (long)C * basis->q, CM = (long)C * plan->M, X = N + Cq;
   float2 *x = base, *dx = x + X, *res = dx + X, *d = res + X, *Ad = d + X, *h = Ad + X;
-  float2 *bn = h + X, *del = bn + X;  // right-hand side, refinement correction
-  float2 *ys = del + X, *yt = ys + std::max(CM, 1L), *r = yt + std::max(CM, 1L);
+  float2 *bn = h + X;  // right-hand side
+  float2 *ys = bn + 2 * X, *yt = ys + std::max(CM, 1L), *r = yt + std::max(CM, 1L);
   float2 *p = x, *al = x + N;
-  // MIXED: the CG iterations apply BF16 operators; the residual r, the
-  // right-hand side and one refinement of each Gauss-Newton step are FP32:
-  // e = b - (J^H J + 2L) dx in FP32, then the correction from a second CG
-  // solve (BF16 operators, n_cg / 2 iterations) is added to dx.
+  // MIXED: the CG iterations apply BF16 operators; the data residual
+  // r = y - G(x) and the right-hand side J^H r - 2 L x of every Gauss-Newton
+  // step are FP32, so the outer iteration refines x against FP32 residuals
+  // (the inner solve stays the same fixed number of CG iterations).
   const mpi_precision pin = prec == MPI_PREC_MIXED ? MPI_PREC_BF16 : prec;
   const mpi_precision pout = prec == MPI_PREC_MIXED ? MPI_PREC_FP32 : prec;
-  const int n_refine = prec == MPI_PREC_MIXED ? 1 : 0;
   // data scale: ys = y * target / ||y||
   if (CM > 0) {
     TRY(sv.dot(yc, nullptr, CM, FIN_SCALE, 0, prm->scale_target));
@@ -767,13 +766,6 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
     TRY(sv.lincomb(bn, h, 1.f, x, -l1, N));
     TRY(sv.lincomb(bn + N, h + N, 1.f, x + N, -l2, Cq));
     TRY(cg(dx, bn, prm->n_cg, pin));
-    for (int k = 0; k < n_refine; ++k) {
-      // e = b - (J^H J + 2L) dx in FP32 (into bn's slot after use: b is not needed again)
-      TRY(normal(dx, pout));
-      TRY(sv.lincomb(bn, bn, 1.f, Ad, -1.f, X));
-      TRY(cg(del, bn, std::max(1, prm->n_cg / 2), pin));
-      TRY(sv.lincomb(dx, dx, 1.f, del, 1.f, X));
-    }
     TRY(sv.lincomb(x, x, 1.f, dx, (float)prm->gamma, X));
   }
   // outputs: alpha, p / scale
@@ -804,7 +796,7 @@ extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const 
     g->C = C;
     g->prec = prec;
     g->key.assign((const unsigned char*)prm, (const unsigned char*)prm + sizeof(*prm));
-    // x, dx, res, d, Ad, h, b, del (X each); ys, yt, r (CM each); in_y, out_alpha, out_p
+    // x, dx, res, d, Ad, h, b, spare (X each); ys, yt, r (CM each); in_y, out_alpha, out_p
     mpi_status st = alloc_solver(ctx, g->mem, 8 * X + 4 * CMs + Cq + N, prm->n_outer + 1, g->sv, &g->base, &g->dbase);
     if (st) {
       delete g;

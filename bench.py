@@ -149,6 +149,9 @@ def kernel_bytes_per_pair(case, prec):
         "k_fft_lines<y,fwd>": V * (1 + f), "k_fft_lines<y,inv>": V * (1 + f),
         "k_rows_fwd_gather": f * V + Y, "k_rows_scatter_inv": Y + f * V,
         "k_pointwise<fwd>": 2 * V + P, "k_pointwise<adj>": 2 * V + P,
+        # the per-plane kernel: passes along y and x with the gather (forward)
+        # or the scatter (adjoint), one read and one write
+        "k_plane_yx<fwd>": V + Y, "k_plane_yx<inv>": Y + V,
     }
     if case["tucker"]:
         n1, n2, n3 = case["dims"]
@@ -162,6 +165,10 @@ def kernel_bytes_per_pair(case, prec):
         out["k_mode_b"] = 2 * (8 * C * r1 * r2 * n3 + 8 * C * r1 * n2 * n3)
         out["k_x1_operand"] = 2 * (8 * C * r1 * n2 * n3 + ob * C * n2 * n3 * 2 * r1)
         out[f"{tc}<tucker x1>"] = 2 * (ob * C * n2 * n3 * 2 * r1 + V)
+        # the FP32 tensor-core chain (core -> x3 -> x2), each product written
+        # in the next one's operand layout; twice per pair
+        out["k_expand_tf32x3<tucker x3>"] = 2 * (8 * C * R + 8 * C * r1 * r2 * n3)
+        out["k_expand_tf32x3<tucker x2>"] = 2 * (8 * C * r1 * r2 * n3 + 8 * C * r1 * n2 * n3)
         # the fused x1 kernels: operand in; forward: image in, DFT'd volume out;
         # adjoint: per-coil data in, image out
         pk = "bf16" if prec == "bf16" else "tf32x3"

@@ -415,6 +415,67 @@ def slice_line(mp, ctx, dev, flush, stream, name, prec_list=("fp32", "bf16"), st
     return out
 
 
+def jacobian_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", steps=10, warmup=3):
+    """Jacobian + Jacobian-adjoint pairs (the operator of every IRGN CG
+    iteration) per precision, with the roofline of the adjoint's coefficient
+    block dalpha = U^H v (k_uh_tc on the tensor cores; k_uh_v, the CUDA-core
+    form, under fp32_simt)."""
+    import torch
+
+    case = make_case(name)
+    plan, basis, a_d, p_d = gpu_objects(mp, ctx, dev, case)
+    C, N, q = case["C"], case["N"], case["q"]
+    hbm, _, src = load_peaks()
+    g = torch.Generator().manual_seed(w.BASE_SEED + 77)
+    dp = torch.randn(N, dtype=torch.complex64, generator=g).to(dev)
+    da = torch.randn((C, q), dtype=torch.complex64, generator=g).to(dev)
+    r = torch.empty((C, plan.M), dtype=torch.complex64, device=dev)
+    gp = torch.empty((N,), dtype=torch.complex64, device=dev)
+    ga = torch.empty((C, q), dtype=torch.complex64, device=dev)
+
+    def run(prec):
+        mp.jacobian(ctx, plan, basis, a_d, p_d, dp, da, prec, out=r)
+        mp.jacobian_adjoint(ctx, plan, basis, a_d, p_d, r, prec, out_p=gp, out_alpha=ga)
+
+    out = {}
+    for prec in ("fp32", "bf16", "fp32_simt"):
+        for _ in range(warmup):
+            run(prec)
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            run(prec)
+            e.record(stream)
+            e.synchronize()
+            total += s.elapsed_time(e)
+        ms = total / steps
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        for _ in range(steps):
+            flush.zero_()
+            run(prec)
+        _, kern = ctx.profile_read(reset=True, kernels=True)
+        ctx.profile(False)
+        per = {k: (v[0] / steps, v[1] / steps) for k, v in kern.items() if v[1]}
+        uh = {"fp32": "k_uh_tc<tf32x3>", "bf16": "k_uh_tc<bf16>", "fp32_simt": "k_uh_v"}[prec]
+        entry = {"value": 1000.0 / ms, "unit": "Jacobian + adjoint pairs/s", "ms_per_pair": ms,
+                 "kernels": {k: round(v[0] * 1e3, 2) for k, v in per.items()}}
+        if uh in per:
+            # algorithmic bytes: the basis (FP32 view 8 N q, BF16 view 4 N q) and v (8 C N) once
+            ub = (4 if prec == "bf16" else 8) * N * q
+            b = ub + 8 * C * N
+            t = per[uh][0] * 1e-3 / per[uh][1]
+            entry["uh_roofline"] = {"bound": "hbm", "kernel": uh, "achieved": b / t / 1e9, "peak": hbm,
+                                    "unit": "GB/s", "frac": b / t / 1e9 / hbm, "algorithmic_bytes_per_launch": b,
+                                    "avg_launch_us": t * 1e6, "launches_per_pair": per[uh][1],
+                                    "peak_source": f"{src} HBM copy bandwidth"}
+        out[prec] = entry
+    return out
+
+
 def radial_line(mp, ctx, dev, flush, stream, steps=10, warmup=3):
     """radial 256^2, 12 coils, q = 96, 64 golden-angle spokes x 512 samples, KB W = 6, sigma = 2."""
     import torch
@@ -711,6 +772,7 @@ def run_ours(args):
                 wl[f"{case['name']}/{prec}"] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms}
         wl = {k: v for k, v in wl.items() if v is not None}
         wl["radial2d_256_c12_q96"] = radial_line(mp, ctx, dev, flush, stream)
+        wl["cart2d_256_c16_q128/jacobian"] = jacobian_line(mp, ctx, dev, flush, stream)
         wl["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
         line["workloads"] = wl
         line["recon"] = recon_per_slice(mp, ctx, dev)

@@ -93,7 +93,7 @@ bool bad_ptr(const void* p) { return p == nullptr; }
 size_t partial_elems(const mpi_ctx* ctx, const mpi_basis* basis, int C) {
   if (!basis) return 0;
   const mpi_basis* b = basis->tucker ? basis->core : basis;
-  return uh_v_partial_elems(ctx, b->N, b->q, C);
+  return std::max(uh_v_partial_elems(ctx, b->N, b->q, C), uh_tc_partial_elems(ctx, b->N, b->q, C));
 }
 
 size_t op_work_bytes(const mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C) {
@@ -151,6 +151,13 @@ mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandAr
     if (g > 0) return launch_expand_tf32(ctx, basis, mode, a, g);
   }
   return launch_expand(ctx, mode, a);
+}
+
+mpi_status uh_v(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* partials,
+                size_t partial_cap, mpi_precision prec) {
+  if (prec != MPI_PREC_FP32_SIMT && uh_tc_supported(b, prec))
+    return launch_uh_tc(ctx, b, V, C, dalpha, partials, partial_cap, prec);
+  return launch_uh_v(ctx, b->U, b->N, b->q, V, C, dalpha, partials, partial_cap);
 }
 
 namespace {
@@ -648,6 +655,8 @@ extern "C" mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N
     b->Uf32 = nullptr;
     tf32_basis_release(b);
   }
+  // views of U for the tensor-core U^H V; without them it runs on the CUDA cores
+  if (uh_tc_prepare(ctx, b) != MPI_OK) uh_tc_release(b);
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     mpi_status st = cuda_check(ctx, e, "basis conversion");
@@ -717,6 +726,7 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   tc_basis_release(b);
   if (b->Uf32) cudaFree(b->Uf32);
   tf32_basis_release(b);
+  uh_tc_release(b);
   for (int k = 0; k < 3; ++k)
     if (b->F[k]) cudaFree(b->F[k]);
   if (b->core) mpi_basis_destroy(b->core);
@@ -950,6 +960,7 @@ extern "C" mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, c
   a.out = (float2*)dp;
   a.vout = w.B;
   if ((st = run_expand(ctx, basis, EX_JADJ, a, prec, w))) return st;
-  if (basis->tucker) return tucker_adjoint(ctx, basis, w.B, C, (float2*)dalpha, w.T, w.partials, w.partial_cap);
-  return launch_uh_v(ctx, basis->U, basis->N, basis->q, w.B, C, (float2*)dalpha, w.partials, w.partial_cap);
+  if (basis->tucker)
+    return tucker_adjoint(ctx, basis, w.B, C, (float2*)dalpha, w.T, w.partials, w.partial_cap, prec);
+  return uh_v(ctx, basis, w.B, C, (float2*)dalpha, w.partials, w.partial_cap, prec);
 }

@@ -123,6 +123,11 @@ struct mpi_basis {
   float* Uf32 = nullptr;         // FP32 operand copy [N][Kp32] (3xTF32 tensor-core path)
   int Kp32 = 0;                  // round_up(2 q, 32)
   void* tmap32 = nullptr;        // CUtensorMap of Uf32 (owned)
+  // U^H V on the tensor cores (tc_uh.cu): tensor maps of the interleaved view
+  // [q][2N] of U (FP32, in place) and of its BF16 copy Uview_bf
+  void* umap32 = nullptr;
+  void* umap_bf = nullptr;
+  void* Uview_bf = nullptr;
   std::string bf16_err;          // why the BF16 copy is missing, if it is
   // Tucker-factored basis (3D): N = n1 n2 n3; the core (r1 r2 r3 x q) is held
   // as an internal dense basis `core`; factors F[k] = U_k [n_k][r_k].
@@ -252,6 +257,17 @@ bool tf32_encode_operand_map_k(void* map, void* ptr, long rows, int K);
 mpi_status launch_uh_v(mpi_ctx* ctx, const float2* U, int N, int q, const float2* V, int C,
                        float2* dalpha, float2* work_partials, size_t partial_cap_elems);
 size_t uh_v_partial_elems(const mpi_ctx* ctx, int N, int q, int C);
+// dalpha_c = U^H V_c on the tensor cores (3xTF32 for FP32, BF16 for BF16);
+// V is [C][N] complex.  Prepared at basis load (tensor maps, the BF16 view).
+mpi_status uh_tc_prepare(mpi_ctx* ctx, mpi_basis* b);
+void uh_tc_release(mpi_basis* b);
+bool uh_tc_supported(const mpi_basis* b, mpi_precision prec);
+size_t uh_tc_partial_elems(const mpi_ctx* ctx, int N, int q, int C);
+mpi_status launch_uh_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha,
+                        float2* partials, size_t partial_cap, mpi_precision prec);
+// U^H V on the tensor cores where the basis and precision allow, else on the CUDA cores.
+mpi_status uh_v(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* partials,
+                size_t partial_cap, mpi_precision prec);
 
 // Tucker basis: per-coil maps, the adjoint contraction, point-wise epilogues.
 size_t tucker_work_elems(const mpi_basis* b, int C);
@@ -265,7 +281,7 @@ bool tucker_x1_on_tensor_cores(const mpi_basis* b, int C, mpi_precision prec);
 mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a, float2* tmp,
                         mpi_precision prec);
 mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,
-                          float2* partials, size_t partial_cap);
+                          float2* partials, size_t partial_cap, mpi_precision prec);
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS);
 void tucker_chain_release(mpi_basis* b);
 bool tucker_chain_on_tensor_cores(const mpi_basis* b, int C);

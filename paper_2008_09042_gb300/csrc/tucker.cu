@@ -679,7 +679,7 @@ mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const Expand
 
 // dalpha[c] = U^H v_c (C x q): conjugate-transposed mode products, then the core's U^H V.
 mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* tmp,
-                          float2* partials, size_t partial_cap) {
+                          float2* partials, size_t partial_cap, mpi_precision prec) {
   const int n1 = b->n[0], n2 = b->n[1], n3 = b->n[2];
   const int r1 = b->r[0], r2 = b->r[1], r3 = b->r[2];
   const long R = (long)r1 * r2 * r3;
@@ -690,7 +690,7 @@ mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int
   if ((st = mode_b(ctx, true, V, b->F[0], C, n1, r1, (long)n2 * n3, t2))) return st;
   if ((st = mode_b(ctx, true, t2, b->F[1], C * r1, n2, r2, n3, t1))) return st;
   if ((st = mode_last(ctx, true, t1, b->F[2], C * r1 * r2, n3, r3, g))) return st;
-  return launch_uh_v(ctx, b->core->U, b->core->N, b->q, g, C, dalpha, partials, partial_cap);
+  return uh_v(ctx, b->core, g, C, dalpha, partials, partial_cap, prec);
 }
 
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS) {

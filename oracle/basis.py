@@ -103,16 +103,24 @@ class MaxwellBasis2D:
 
 
 def build_maxwell_basis_2d(ny, nx, q, fov_m=(0.22, 0.22), f_hz=128e6, n_sites=64,
-                           n_exc=500, radius_factor=1.5, seed=0):
-    """Maxwell basis for a 2D slice (steps 1-4 of the module docstring)."""
+                           n_exc=500, radius_factor=1.5, seed=0, omega=None):
+    """Maxwell basis for a 2D slice (steps 1-4 of the module docstring).
+
+    ``omega`` (6 D x L complex), when given, is the excitation matrix itself
+    (rows in the column order of ``dipole_b_fields``); otherwise it is drawn
+    from ``seed``."""
     k = wavenumber(f_hz)
     half_diag = 0.5 * np.hypot(fov_m[0], fov_m[1])
     src = circle_sources(n_sites, radius_factor * half_diag)
     pts = pixel_centroids(ny, nx, fov_m)
     B = dipole_b_fields(pts, src, k)  # (N, 6D)
-    rng = np.random.default_rng(seed)
-    L = n_exc
-    Omega = (rng.normal(size=(B.shape[1], L)) + 1j * rng.normal(size=(B.shape[1], L))) / np.sqrt(2.0)
+    if omega is not None:
+        Omega = np.asarray(omega, dtype=np.complex128)
+        L = Omega.shape[1]
+    else:
+        rng = np.random.default_rng(seed)
+        L = n_exc
+        Omega = (rng.normal(size=(B.shape[1], L)) + 1j * rng.normal(size=(B.shape[1], L))) / np.sqrt(2.0)
     Y = B @ Omega
     Uy, sv, Vh = np.linalg.svd(Y, full_matrices=False)
     U = Uy[:, :q]

@@ -20,7 +20,7 @@ from .masks import (  # noqa: F401
 )
 from .trajectory import golden_angle_radial  # noqa: F401
 from .noise import complex_noise, noise_sigma_for_snr  # noqa: F401
-from .coefs import random_coefficients, random_image  # noqa: F401
+from .coefs import random_coefficients, random_excitations, random_image  # noqa: F401
 from .standin import smooth_orthonormal_basis, smooth_tucker_basis  # noqa: F401
 from .configs import WORKLOADS, workload  # noqa: F401
 from .recon import RECON_SEED, recon_case  # noqa: F401

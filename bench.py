@@ -476,6 +476,36 @@ def jacobian_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", steps
     return out
 
 
+def maxwell_basis_line(mp, ctx, n=256, q=128, n_sites=64, L=500, reps=3):
+    """The Maxwell basis of an n x n slice built on the GPU (64 dipole sites x 6
+    dipoles, Fig. 1's 500 excitations): wall time per build (it synchronises),
+    its agreement with the FP64 oracle (singular values; subspace of the q
+    leading vectors), and the oracle's own time on this host."""
+    import torch
+    from oracle import basis as ob
+
+    src = ob.circle_sources(n_sites, 1.5 * 0.5 * np.hypot(0.22, 0.22))
+    om = w.random_excitations(6 * n_sites, L, seed=w.BASE_SEED)
+    mp.maxwell_basis_2d(ctx, (n, n), q, src, om)  # warm-up (module load, first allocations)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        U, sv = mp.maxwell_basis_2d(ctx, (n, n), q, src, om)
+        times.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    ref = ob.build_maxwell_basis_2d(n, n, q, n_sites=n_sites, omega=om)
+    t_cpu = time.perf_counter() - t0
+    Uo = np.linalg.qr(U.cpu().numpy().astype(np.complex128).T)[0]
+    sin_theta = float(np.linalg.norm(Uo - ref.U @ (ref.U.conj().T @ Uo), 2))
+    nsv = sv.size
+    return {"shape": [n, n], "q": q, "dipoles": 6 * n_sites, "excitations": L,
+            "value": float(np.median(times)), "unit": "s per basis build (GPU, FP64)",
+            "cpu_baseline": {"kind": "oracle", "value": t_cpu, "unit": "s per basis build", "cores": host_threads(),
+                             "sample": "one whole build: complex128 numpy, LAPACK SVD of B Omega"},
+            "vs_oracle": {"sv_max_abs_err_over_sigma1": float(np.max(np.abs(sv - ref.sv[:nsv])) / ref.sv[0]),
+                          "subspace_sin_theta": sin_theta, "sigma_q_over_sigma1": float(ref.sv[q - 1] / ref.sv[0])}}
+
+
 def radial_line(mp, ctx, dev, flush, stream, steps=10, warmup=3):
     """radial 256^2, 12 coils, q = 96, 64 golden-angle spokes x 512 samples, KB W = 6, sigma = 2."""
     import torch
@@ -773,6 +803,7 @@ def run_ours(args):
         wl = {k: v for k, v in wl.items() if v is not None}
         wl["radial2d_256_c12_q96"] = radial_line(mp, ctx, dev, flush, stream)
         wl["cart2d_256_c16_q128/jacobian"] = jacobian_line(mp, ctx, dev, flush, stream)
+        wl["maxwell_basis_2d_256_q128"] = maxwell_basis_line(mp, ctx)
         wl["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
         line["workloads"] = wl
         line["recon"] = recon_per_slice(mp, ctx, dev)

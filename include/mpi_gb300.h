@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef struct { float x, y; } mpi_c32;
+typedef struct { double x, y; } mpi_c64;
 
 typedef enum {
   MPI_OK = 0,
@@ -193,6 +194,38 @@ mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, const mpi_c3
                                  const mpi_c32* U3, const int n[3], const int r[3], int q, int on_device,
                                  mpi_basis** out);
 mpi_status mpi_basis_destroy(mpi_basis* basis);
+
+/* Maxwell basis of a 2D slice built on the GPU (Maxwell Regularization
+ * section: the dyadic Green's functions of Eqs. 17-18, the field operator of
+ * Eq. 15 sampled by random boundary excitations as in Fig. 1, truncation by
+ * singular value as in Eq. 16).
+ *   Pixels: ny x nx centroids of a field of view fov_y x fov_x metres centred
+ *   on the origin in the z = 0 plane, raster order (x fastest).
+ *   Sources: n_sites points (host, double [n_sites][3], metres), each with three
+ *   electric and three magnetic point dipoles (x, y, z); column 6 s + t of the
+ *   field matrix B (N x 6 n_sites) is the circularly polarised field
+ *   (H_x - i H_y) / sqrt(2) of dipole t of site s, with k = 2 pi f_hz / c0 and
+ *   the magnetic dipoles scaled by the free-space impedance.
+ *   omega: host, complex128 [6 n_sites][L] row-major, the random excitation
+ *   amplitudes (row order = the column order of B).
+ * Result: the q leading left singular vectors of Y = B omega, ordered by
+ * singular value, as a device array U_out [q][N] complex64 (the layout
+ * mpi_basis_load_dense takes; each vector's phase is arbitrary), and all
+ * min(6 n_sites, L) singular values of Y in descending order into sv_out
+ * (host, double).  Computed in FP64 (Householder QR of B, X = R omega, one-sided
+ * Jacobi SVD of X, Q applied to the leading vectors), so subspaces with singular
+ * values down to about 1e-15 sigma_1 are resolved where the gaps allow.
+ * Allocates its FP64 workspace (about 16 N (6 n_sites + q) bytes) and
+ * synchronises the context's stream; do not call it during stream capture.
+ * Fields that are identically zero (three of the six per site when the sites
+ * lie in the slice plane) are dropped with their rows of omega; they add only
+ * zero singular values.
+ * Errors: MPI_ERR_SHAPE unless 6 n_sites <= N and q <= min(number of nonzero
+ * fields, L); MPI_ERR_OOM; MPI_ERR_CUDA if the Jacobi sweeps do not converge
+ * (60 sweeps). */
+mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double fov_y, double fov_x, double f_hz,
+                                const double* sources, int n_sites, const mpi_c64* omega, int L, int q,
+                                mpi_c32* U_out, double* sv_out);
 
 /* Which kernel carries the dense contraction U alpha (for a Tucker basis, the
  * core contraction) for C coils at precision `prec`; `jacobian` != 0 asks

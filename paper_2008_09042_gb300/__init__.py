@@ -17,6 +17,7 @@ from .api import (  # noqa: F401
     adjoint,
     basis_expand,
     basis_project,
+    maxwell_basis_2d,
     expand_path,
     forward,
     forward_host,

@@ -25,7 +25,7 @@ EXPORTS = [
     "mpi_basis_load_dense", "mpi_basis_load_tucker", "mpi_basis_destroy", "mpi_basis_expand", "mpi_forward", "mpi_adjoint",
     "mpi_jacobian", "mpi_jacobian_adjoint", "mpi_basis_project", "mpi_sm_estimate", "mpi_image_solve",
     "mpi_tv_prox", "mpi_forward_noalloc", "mpi_batch_create", "mpi_batch_run", "mpi_batch_kernel_count",
-    "mpi_batch_destroy", "mpi_expand_path", "mpi_forward_host", "mpi_adjoint_host",
+    "mpi_batch_destroy", "mpi_expand_path", "mpi_forward_host", "mpi_adjoint_host", "mpi_maxwell_basis_2d",
 ]
 
 
@@ -104,6 +104,7 @@ def load(path=LIB_PATH):
         "mpi_basis_load_tucker": [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   i, i, pp],
         "mpi_basis_destroy": [vp],
+        "mpi_maxwell_basis_2d": [vp, i, i, d, d, d, vp, i, vp, i, i, vp, vp],
         "mpi_expand_path": [vp, i, i, i],
         "mpi_basis_expand": [vp, vp, vp, i, vp, i],
         "mpi_forward": [vp, vp, vp, vp, i, vp, vp, i],

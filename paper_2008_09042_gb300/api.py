@@ -334,6 +334,28 @@ def expand_path(ctx, basis, C, prec="fp32", jacobian=False):
     return EXPAND_PATHS[r]
 
 
+def maxwell_basis_2d(ctx, shape, q, sources, omega, fov=(0.22, 0.22), f_hz=128e6):
+    """Maxwell basis of an ny x nx slice built on the GPU (mpi_maxwell_basis_2d).
+
+    sources: (D, 3) dipole sites in metres; omega: (6 D, L) complex excitation
+    amplitudes.  Returns (U, sv): U the (q, N) complex64 device tensor of the q
+    leading left singular vectors of B omega (load it with Basis(ctx, U)), sv
+    the min(6 D, L) singular values (numpy, descending)."""
+    ny, nx = shape
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.float64))
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.complex128))
+    D = src.shape[0]
+    if src.shape != (D, 3) or om.ndim != 2 or om.shape[0] != 6 * D:
+        raise ValueError("sources must be (D, 3) and omega (6 D, L)")
+    L = om.shape[1]
+    U = torch.empty((q, ny * nx), dtype=torch.complex64, device=f"cuda:{ctx.device}")
+    sv = np.zeros(min(6 * D, L), dtype=np.float64)
+    check(ctx.h, ctx.lib.mpi_maxwell_basis_2d(ctx.h, ny, nx, float(fov[0]), float(fov[1]), float(f_hz),
+                                             src.ctypes.data, D, om.ctypes.data, L, q, _ptr(U),
+                                             sv.ctypes.data))
+    return U, sv
+
+
 def basis_project(ctx, basis, maps):
     C = maps.shape[0]
     _need(maps, (C, basis.N), "maps")

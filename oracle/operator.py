@@ -68,3 +68,38 @@ def jacobian_adjoint(Fs, U, alpha, p, r):
     v = np.asarray(p).conj()[None, :] * w
     dalpha = expand_adjoint(U, v)
     return dp, dalpha
+
+
+# --- several sets of maps (Discussion, "Forward Model Extensions") ----------
+#
+# The signal equation with M sets of maps adds bilinear terms:
+#   y_k = F_s( sum_m (U alpha_{m,k}) (.) p_m ),
+# alphas (M, C, q), ps (M, N).  M = 1 is the model above.
+
+
+def forward_multi(Fs, U, alphas, ps):
+    """y_k = F_s(sum_m U alpha_{m,k} (.) p_m); returns (C, M_samples)."""
+    v = sum(expand(U, a) * np.asarray(p)[None, :] for a, p in zip(alphas, ps))
+    return Fs.fwd(v)
+
+
+def adjoint_multi(Fs, U, alphas, y):
+    """The adjoint in the images: [sum_k conj(U alpha_{m,k}) (.) F_s^H y_k]_m; returns (M, N)."""
+    w = Fs.adj(y)
+    return np.stack([np.sum(expand(U, a).conj() * w, axis=0) for a in alphas])
+
+
+def jacobian_multi(Fs, U, alphas, ps, dps, dalphas):
+    """J[dp; dalpha] = [F_s(sum_m U alpha_{m,k} (.) dp_m + p_m (.) U dalpha_{m,k})]_k."""
+    v = sum(expand(U, a) * np.asarray(dp)[None, :] + np.asarray(p)[None, :] * expand(U, da)
+            for a, p, dp, da in zip(alphas, ps, dps, dalphas))
+    return Fs.fwd(v)
+
+
+def jacobian_adjoint_multi(Fs, U, alphas, ps, r):
+    """J^H r for M sets of maps: dp_m = sum_k conj(U alpha_{m,k}) (.) F_s^H r_k,
+    dalpha_{m,k} = U^H (conj(p_m) (.) F_s^H r_k); returns ((M, N), (M, C, q))."""
+    w = Fs.adj(r)
+    dps = np.stack([np.sum(expand(U, a).conj() * w, axis=0) for a in alphas])
+    dalphas = np.stack([expand_adjoint(U, np.asarray(p).conj()[None, :] * w) for p in ps])
+    return dps, dalphas

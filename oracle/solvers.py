@@ -101,6 +101,52 @@ def irgn(Fs, U, y, C, q, n_outer=20, n_cg=10, a0=1.0, b0=1.0, decay=0.5,
     return p / scale, alpha, np.array(hist)
 
 
+def irgn_multi(Fs, U, y, C, q, M, n_outer=20, n_cg=10, a0=1.0, b0=1.0, decay=0.5,
+               floor=1e-6, gamma=1.0, scale_target=100.0, p0=None, alpha0=None):
+    """MPI-BL with M sets of maps (the forward model with extra bilinear terms,
+    "Forward Model Extensions"): the unknowns are x = (p_1..p_M, alpha_1..alpha_M),
+    Eq. 6's penalties apply alpha_n to every image and beta_n to every set of
+    coefficients, and each step solves the same regularised normal equations.
+
+    Start (the paper is silent): p_m = 1 for every set, alpha_1 = 0, and for
+    m >= 2 the first basis coefficient of every coil 0.1.  Sets that start
+    proportional, (p_m, alpha_m) = c (p_1, alpha_1), stay proportional (their
+    Jacobian columns are parallel), so the extra sets must start off that line;
+    p_m = 0 with alpha_m = 0 is a stationary point of the block.  M = 1 is
+    ``irgn``.  Returns ((M, N) images, (M, C, q) coefficients, residual
+    history), images in the units of y."""
+    y = np.asarray(y, dtype=np.complex128)
+    N = Fs.N
+    ny = np.linalg.norm(y)
+    scale = scale_target / ny if ny > 0 else 1.0
+    ys = y * scale
+    P = np.ones((M, N), dtype=np.complex128) if p0 is None else np.array(p0, dtype=np.complex128)
+    if alpha0 is None:
+        A = np.zeros((M, C, q), dtype=np.complex128)
+        A[1:, :, 0] = 0.1
+    else:
+        A = np.array(alpha0, dtype=np.complex128)
+    hist = []
+    for n in range(n_outer):
+        an = max(a0 * decay ** n, floor)
+        bn = max(b0 * decay ** n, floor)
+        r = ys - op.forward_multi(Fs, U, A, P)
+        hist.append(np.linalg.norm(r))
+        gp, ga = op.jacobian_adjoint_multi(Fs, U, A, P, r)
+        rhs = (gp - 2.0 * an * P, ga - 2.0 * bn * A)
+
+        def normal(d, P=P, A=A, an=an, bn=bn):
+            jd = op.jacobian_multi(Fs, U, A, P, d[0], d[1])
+            hp, ha = op.jacobian_adjoint_multi(Fs, U, A, P, jd)
+            return [hp + 2.0 * an * d[0], ha + 2.0 * bn * d[1]]
+
+        dP, dA = cg(normal, rhs, (np.zeros((M, N)), np.zeros((M, C, q))), n_cg)
+        P = P + gamma * dP
+        A = A + gamma * dA
+    hist.append(np.linalg.norm(ys - op.forward_multi(Fs, U, A, P)))
+    return P / scale, A, np.array(hist)
+
+
 # --- TV prox (FGP) -----------------------------------------------------------
 
 def grad_fd(x):

@@ -476,6 +476,43 @@ def jacobian_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", steps
     return out
 
 
+def multimap_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", M=2, steps=10, warmup=3):
+    """The forward model with M sets of maps (extra bilinear terms) on a 2D
+    workload: forward + adjoint (in the M images) pairs per second."""
+    import torch
+
+    case = make_case(name)
+    plan, basis, a_d, p_d = gpu_objects(mp, ctx, dev, case)
+    C, N, q = case["C"], case["N"], case["q"]
+    g = torch.Generator().manual_seed(w.BASE_SEED + 91)
+    A = torch.stack([a_d] + [0.3 * torch.randn((C, q), dtype=torch.complex64, generator=g).to(dev)
+                             for _ in range(M - 1)]).contiguous()
+    P = torch.stack([p_d] + [torch.randn(N, dtype=torch.complex64, generator=g).to(dev) for _ in range(M - 1)])
+    P = P.contiguous()
+    y = torch.empty((C, plan.M), dtype=torch.complex64, device=dev)
+    x = torch.empty((M, N), dtype=torch.complex64, device=dev)
+    out = {"sets": M}
+    for prec in ("fp32", "bf16"):
+        def run():
+            mp.forward_maps(ctx, plan, basis, A, P, prec, out=y)
+            mp.adjoint_maps(ctx, plan, basis, A, y, prec, out=x)
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            run()
+            e.record(stream)
+            e.synchronize()
+            total += s.elapsed_time(e)
+        ms = total / steps
+        out[prec] = {"value": 1000.0 / ms, "unit": "pairs/s", "ms_per_pair": ms}
+    return out
+
+
 def maxwell_basis_line(mp, ctx, n=256, q=128, n_sites=64, L=500, reps=3):
     """The Maxwell basis of an n x n slice built on the GPU (64 dipole sites x 6
     dipoles, Fig. 1's 500 excitations): wall time per build (it synchronises),
@@ -804,6 +841,7 @@ def run_ours(args):
         wl["radial2d_256_c12_q96"] = radial_line(mp, ctx, dev, flush, stream)
         wl["cart2d_256_c16_q128/jacobian"] = jacobian_line(mp, ctx, dev, flush, stream)
         wl["maxwell_basis_2d_256_q128"] = maxwell_basis_line(mp, ctx)
+        wl["cart2d_256_c16_q128/two_sets_of_maps"] = multimap_line(mp, ctx, dev, flush, stream)
         wl["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
         line["workloads"] = wl
         line["recon"] = recon_per_slice(mp, ctx, dev)

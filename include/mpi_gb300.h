@@ -313,6 +313,29 @@ mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, const mpi_ba
                                 const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* r,
                                 mpi_c32* dp, mpi_c32* dalpha, mpi_precision prec);
 
+/* Several sets of maps (Discussion, "Forward Model Extensions": extra bilinear
+ * terms in the signal equation), M >= 1 sets on a dense basis:
+ *   y_k = F_s( sum_m (U alpha_{m,k}) (.) p_m )
+ * alpha [M][C][q] (set m's coefficients contiguous), p [M][N], all device
+ * pointers; M = 1 is the single-set call.  The products are summed image-side
+ * in the expansion epilogues, so F_s runs once per coil whatever M.
+ * MPI_ERR_UNSUPPORTED for Tucker bases with M > 1. */
+mpi_status mpi_forward_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                            const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y, mpi_precision prec);
+/* The adjoint in the images: p_out[m] = sum_k conj(U alpha_{m,k}) (.) F_s^H y_k, [M][N]. */
+mpi_status mpi_adjoint_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                            const mpi_c32* alpha, int C, const mpi_c32* y, mpi_c32* p_out, mpi_precision prec);
+/* J[dp; dalpha] = [F_s(sum_m U alpha_{m,k} (.) dp_m + p_m (.) U dalpha_{m,k})]_k
+ * (Eq. 7 summed over the sets); dp [M][N], dalpha [M][C][q], dy [C][M_samples]. */
+mpi_status mpi_jacobian_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                             const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* dp,
+                             const mpi_c32* dalpha, mpi_c32* dy, mpi_precision prec);
+/* J^H r per set: dp[m] = sum_k conj(U alpha_{m,k}) (.) F_s^H r_k,
+ * dalpha[m][k] = U^H (conj(p_m) (.) F_s^H r_k); F_s^H runs once. */
+mpi_status mpi_jacobian_adjoint_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                                     const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* r,
+                                     mpi_c32* dp, mpi_c32* dalpha, mpi_precision prec);
+
 /* alpha_k = (U^H U)^{-1} U^H maps_k: projection of given maps onto the basis
  * (Fig. 2 caption).  Gram matrix, Cholesky factor and triangular solves in FP64.
  * maps [C][N] -> alpha [C][q]. */
@@ -367,6 +390,15 @@ mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* 
                            const mpi_c32* y, int C, const mpi_irgn_params* prm,
                            mpi_c32* alpha_out, mpi_c32* p_out, double* resid_out,
                            mpi_precision prec);
+/* MPI-BL with M sets of maps (the model of mpi_forward_maps): the same IRGN with
+ * the unknowns x = [p_1 .. p_M ; alpha_1 .. alpha_M], Eq. 6's penalties on every
+ * image (alpha_n) and every coefficient set (beta_n).  Start: p_m = 1, alpha_1 = 0
+ * and, for m >= 2, the first basis coefficient of every coil 0.1 (sets that start
+ * proportional to the first stay proportional).  Outputs alpha_out [M][C][q],
+ * p_out [M][N] (device); resid_out as mpi_sm_estimate.  M = 1 is mpi_sm_estimate. */
+mpi_status mpi_sm_estimate_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                                const mpi_c32* y, int C, const mpi_irgn_params* prm, mpi_c32* alpha_out,
+                                mpi_c32* p_out, double* resid_out, mpi_precision prec);
 
 /* MPI-L: constrained TV reconstruction (Eq. 8) by scaled ADMM (Eq. 11):
  *   z0 = prox_{TV/rho}(p + u0)        (n_tv FGP iterations from zero)

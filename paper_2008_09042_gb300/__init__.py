@@ -18,6 +18,11 @@ from .api import (  # noqa: F401
     basis_expand,
     basis_project,
     maxwell_basis_2d,
+    forward_maps,
+    adjoint_maps,
+    jacobian_maps,
+    jacobian_adjoint_maps,
+    sm_estimate_maps,
     expand_path,
     forward,
     forward_host,

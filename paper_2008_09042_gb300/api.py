@@ -402,6 +402,63 @@ def sm_estimate(ctx, plan, basis, y, C, n_outer=20, n_cg=10, a0=1.0, b0=1.0, dec
     return alpha, p, hist
 
 
+def forward_maps(ctx, plan, basis, alpha, p, prec="fp32", out=None):
+    """y_k = F_s(sum_m U alpha[m, k] (.) p[m]) for M sets of maps: alpha (M, C, q), p (M, N)."""
+    M, C = alpha.shape[0], alpha.shape[1]
+    _need(alpha, (M, C, basis.q), "alpha")
+    _need(p, (M, plan.N), "p")
+    out = out if out is not None else torch.empty((C, plan.M), dtype=torch.complex64, device=p.device)
+    check(ctx.h, ctx.lib.mpi_forward_maps(ctx.h, plan.h, basis.h, M, _ptr(alpha), C, _ptr(p), _ptr(out), PREC[prec]))
+    return out
+
+
+def adjoint_maps(ctx, plan, basis, alpha, y, prec="fp32", out=None):
+    """The adjoint in the M images: (M, N)."""
+    M, C = alpha.shape[0], alpha.shape[1]
+    _need(alpha, (M, C, basis.q), "alpha")
+    _need(y, (C, plan.M), "y")
+    out = out if out is not None else torch.empty((M, plan.N), dtype=torch.complex64, device=y.device)
+    check(ctx.h, ctx.lib.mpi_adjoint_maps(ctx.h, plan.h, basis.h, M, _ptr(alpha), C, _ptr(y), _ptr(out), PREC[prec]))
+    return out
+
+
+def jacobian_maps(ctx, plan, basis, alpha, p, dp, dalpha, prec="fp32", out=None):
+    M, C = alpha.shape[0], alpha.shape[1]
+    for t, sh, n in ((alpha, (M, C, basis.q), "alpha"), (dalpha, (M, C, basis.q), "dalpha"),
+                     (p, (M, plan.N), "p"), (dp, (M, plan.N), "dp")):
+        _need(t, sh, n)
+    out = out if out is not None else torch.empty((C, plan.M), dtype=torch.complex64, device=p.device)
+    check(ctx.h, ctx.lib.mpi_jacobian_maps(ctx.h, plan.h, basis.h, M, _ptr(alpha), C, _ptr(p), _ptr(dp),
+                                           _ptr(dalpha), _ptr(out), PREC[prec]))
+    return out
+
+
+def jacobian_adjoint_maps(ctx, plan, basis, alpha, p, r, prec="fp32"):
+    """J^H r per set of maps: ((M, N), (M, C, q))."""
+    M, C = alpha.shape[0], alpha.shape[1]
+    _need(alpha, (M, C, basis.q), "alpha")
+    _need(p, (M, plan.N), "p")
+    _need(r, (C, plan.M), "r")
+    gp = torch.empty((M, plan.N), dtype=torch.complex64, device=p.device)
+    ga = torch.empty((M, C, basis.q), dtype=torch.complex64, device=p.device)
+    check(ctx.h, ctx.lib.mpi_jacobian_adjoint_maps(ctx.h, plan.h, basis.h, M, _ptr(alpha), C, _ptr(p), _ptr(r),
+                                                   _ptr(gp), _ptr(ga), PREC[prec]))
+    return gp, ga
+
+
+def sm_estimate_maps(ctx, plan, basis, y, C, M, n_outer=20, n_cg=10, a0=1.0, b0=1.0, decay=0.5, floor=1e-6,
+                     gamma=1.0, scale_target=100.0, prec="fp32"):
+    """MPI-BL with M sets of maps.  Returns (alpha (M, C, q), p (M, N), residual history)."""
+    _need(y, (C, plan.M), "y")
+    prm = _lib.IrgnParams(n_outer, n_cg, a0, b0, decay, floor, gamma, scale_target)
+    alpha = torch.empty((M, C, basis.q), dtype=torch.complex64, device=y.device)
+    p = torch.empty((M, plan.N), dtype=torch.complex64, device=y.device)
+    hist = np.zeros(n_outer + 1, dtype=np.float64)
+    check(ctx.h, ctx.lib.mpi_sm_estimate_maps(ctx.h, plan.h, basis.h, M, _ptr(y), C, ctypes.byref(prm), _ptr(alpha),
+                                              _ptr(p), hist.ctypes.data_as(ctypes.c_void_p), PREC[prec]))
+    return alpha, p, hist
+
+
 def image_solve(ctx, plan, basis, alpha, y, eps, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0, tau=2.0,
                 prec="fp32"):
     """MPI-L (ADMM-TV, Eqs. 8-11).  Returns (p [N], history (n_outer, 3) of primal, dual, rho)."""

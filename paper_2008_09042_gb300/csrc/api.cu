@@ -964,3 +964,127 @@ extern "C" mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, c
     return tucker_adjoint(ctx, basis, w.B, C, (float2*)dalpha, w.T, w.partials, w.partial_cap, prec);
   return uh_v(ctx, basis, w.B, C, (float2*)dalpha, w.partials, w.partial_cap, prec);
 }
+
+// ----------------------------------------------------- several sets of maps
+//
+// y_k = F_s(sum_m (U alpha_{m,k}) (.) p_m) (the forward model with extra
+// bilinear terms, Discussion: "Forward Model Extensions").  Dense bases.  The
+// image-side sum is formed by the expansion epilogues: two sets per launch
+// through the Jacobian's two-product epilogue (s (.) dp + ds (.) p with
+// (alpha, dp, dalpha, p) = (alpha_m, p_m, alpha_{m+1}, p_{m+1})), further
+// launches adding into the same buffer.
+
+namespace {
+
+mpi_status check_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M, int C, mpi_precision prec) {
+  mpi_status st = check_op(ctx, plan, basis, C, prec);
+  if (st) return st;
+  if (M < 1) return set_err(ctx, MPI_ERR_ARG, "M must be >= 1");
+  if (basis->tucker && M > 1) return set_err(ctx, MPI_ERR_UNSUPPORTED, "several sets of maps: dense bases only");
+  return MPI_OK;
+}
+
+}  // namespace
+
+extern "C" mpi_status mpi_forward_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                                       const mpi_c32* alpha, int C, const mpi_c32* p, mpi_c32* y,
+                                       mpi_precision prec) {
+  mpi_status st = check_maps(ctx, plan, basis, M, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p) || (plan->M > 0 && bad_ptr(y))) return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  if (M == 1) return mpi_forward(ctx, plan, basis, alpha, C, p, y, prec);
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  const size_t Cq = (size_t)C * basis->q, N = (size_t)plan->N;
+  for (int m = 0; m < M; m += 2) {
+    ExpandArgs a = base_args(plan, basis, C);
+    a.out = w.A;
+    a.accumulate = m > 0;
+    a.alpha = (const float2*)alpha + m * Cq;
+    if (m + 1 < M) {
+      a.dp = (const float2*)p + m * N;
+      a.dalpha = (const float2*)alpha + (m + 1) * Cq;
+      a.p = (const float2*)p + (m + 1) * N;
+      if ((st = expand(ctx, basis, EX_JFWD, a, prec))) return st;
+    } else {
+      a.p = (const float2*)p + m * N;
+      if ((st = expand(ctx, basis, EX_FWD, a, prec))) return st;
+    }
+  }
+  return image_to_kspace(ctx, plan, w.A, C, (float2*)y, w.grid);
+}
+
+extern "C" mpi_status mpi_adjoint_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                                       const mpi_c32* alpha, int C, const mpi_c32* y, mpi_c32* p_out,
+                                       mpi_precision prec) {
+  mpi_status st = check_maps(ctx, plan, basis, M, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p_out) || (plan->M > 0 && bad_ptr(y)))
+    return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  if (M == 1) return mpi_adjoint(ctx, plan, basis, alpha, C, y, p_out, prec);
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  if ((st = kspace_to_image(ctx, plan, (const float2*)y, C, w.A, w.grid))) return st;
+  const size_t Cq = (size_t)C * basis->q, N = (size_t)plan->N;
+  for (int m = 0; m < M; ++m) {
+    ExpandArgs a = base_args(plan, basis, C);
+    a.alpha = (const float2*)alpha + m * Cq;
+    a.w = w.A;
+    a.out = (float2*)p_out + m * N;
+    if ((st = expand(ctx, basis, EX_ADJ, a, prec))) return st;
+  }
+  return MPI_OK;
+}
+
+extern "C" mpi_status mpi_jacobian_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                                        const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* dp,
+                                        const mpi_c32* dalpha, mpi_c32* dy, mpi_precision prec) {
+  mpi_status st = check_maps(ctx, plan, basis, M, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p) || bad_ptr(dp) || bad_ptr(dalpha) || (plan->M > 0 && bad_ptr(dy)))
+    return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  if (M == 1) return mpi_jacobian(ctx, plan, basis, alpha, C, p, dp, dalpha, dy, prec);
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  const size_t Cq = (size_t)C * basis->q, N = (size_t)plan->N;
+  for (int m = 0; m < M; ++m) {
+    ExpandArgs a = base_args(plan, basis, C);
+    a.out = w.A;
+    a.accumulate = m > 0;
+    a.alpha = (const float2*)alpha + m * Cq;
+    a.dalpha = (const float2*)dalpha + m * Cq;
+    a.p = (const float2*)p + m * N;
+    a.dp = (const float2*)dp + m * N;
+    if ((st = expand(ctx, basis, EX_JFWD, a, prec))) return st;
+  }
+  return image_to_kspace(ctx, plan, w.A, C, (float2*)dy, w.grid);
+}
+
+extern "C" mpi_status mpi_jacobian_adjoint_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                                                const mpi_c32* alpha, int C, const mpi_c32* p, const mpi_c32* r,
+                                                mpi_c32* dp, mpi_c32* dalpha, mpi_precision prec) {
+  mpi_status st = check_maps(ctx, plan, basis, M, C, prec);
+  if (st) return st;
+  if (bad_ptr(alpha) || bad_ptr(p) || bad_ptr(dp) || bad_ptr(dalpha) || (plan->M > 0 && bad_ptr(r)))
+    return set_err(ctx, MPI_ERR_ARG, "null pointer");
+  if (M == 1) return mpi_jacobian_adjoint(ctx, plan, basis, alpha, C, p, r, dp, dalpha, prec);
+  DeviceGuard g(ctx->device);
+  Work w;
+  if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  if ((st = kspace_to_image(ctx, plan, (const float2*)r, C, w.A, w.grid))) return st;
+  const size_t Cq = (size_t)C * basis->q, N = (size_t)plan->N;
+  for (int m = 0; m < M; ++m) {
+    ExpandArgs a = base_args(plan, basis, C);
+    a.alpha = (const float2*)alpha + m * Cq;
+    a.p = (const float2*)p + m * N;
+    a.w = w.A;
+    a.out = (float2*)dp + m * N;
+    a.vout = w.B;
+    if ((st = expand(ctx, basis, EX_JADJ, a, prec))) return st;
+    if ((st = uh_v(ctx, basis, w.B, C, (float2*)dalpha + m * Cq, w.partials, w.partial_cap, prec))) return st;
+  }
+  return MPI_OK;
+}

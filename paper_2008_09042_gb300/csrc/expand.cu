@@ -128,7 +128,15 @@ __global__ void __launch_bounds__(kExpandMaxThreads) k_expand(ExpandArgs a, int 
       } else if (MODE == EX_FWD) {
 #pragma unroll
         for (int c = 0; c < CB; ++c)
-          if (c0 + c < a.C) a.out[(size_t)(c0 + c) * a.N + n] = cscale(cmul(acc[c], pimg), sg);
+          if (c0 + c < a.C) {
+            float2* o = a.out + (size_t)(c0 + c) * a.N + n;
+            float2 v = cscale(cmul(acc[c], pimg), sg);
+            if (a.accumulate) {
+              v.x += o->x;
+              v.y += o->y;
+            }
+            *o = v;
+          }
       } else if (MODE == EX_JFWD) {
         const float2 dpi = a.dp[n];
 #pragma unroll
@@ -138,7 +146,13 @@ __global__ void __launch_bounds__(kExpandMaxThreads) k_expand(ExpandArgs a, int 
             const float2 t = cmul(dacc[c], pimg);
             v.x += t.x;
             v.y += t.y;
-            a.out[(size_t)(c0 + c) * a.N + n] = cscale(v, sg);
+            float2* o = a.out + (size_t)(c0 + c) * a.N + n;
+            v = cscale(v, sg);
+            if (a.accumulate) {
+              v.x += o->x;
+              v.y += o->y;
+            }
+            *o = v;
           }
         }
       } else {  // ADJ / JADJ

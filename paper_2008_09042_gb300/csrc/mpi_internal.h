@@ -224,6 +224,7 @@ struct ExpandArgs {
   long tuck_stride = 0;
   const char* kname = nullptr;  // name of the launch in the per-kernel timing (default: the kernel's)
   ScatterMap sc;                // EX_SCATTER output map
+  int accumulate = 0;           // EX_FWD / EX_JFWD: add into out instead of storing (several sets of maps)
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);

@@ -695,11 +695,22 @@ mpi_status launch_graph(mpi_ctx* ctx, SolverGraph* g) {
 
 // ------------------------------------------------------------------ MPI-BL
 
-// Enqueue the IRGN solve.  Inputs: y (C x M).  Outputs: alpha_out, p_out, hist.
-mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C, const mpi_irgn_params* prm,
-                     mpi_precision prec, Solver& sv, float2* base, const float2* yc, float2* alpha_out,
-                     float2* p_out, double* hist) {
-  const long N = plan->N, Cq = (long)C * basis->q, CM = (long)C * plan->M, X = N + Cq;
+// Start of the extra sets of maps (m >= 1): the first basis coefficient of
+// every coil is 0.1 (sets that start proportional to the first stay so).
+__global__ void k_first_coef(float2* __restrict__ al, int rows, int q, float v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) al[(size_t)i * q] = make_float2(v, 0.f);
+}
+
+// Enqueue the IRGN solve with `nm` sets of maps (1: the model of Eq. 5; more:
+// the extra bilinear terms of the Forward Model Extensions discussion).  The
+// unknowns are x = [p_1 .. p_nm ; alpha_1 .. alpha_nm]; Eq. 6's penalties
+// weigh every image by alpha_n and every coefficient set by beta_n.  Inputs:
+// y (C x M).  Outputs: alpha_out (nm C q), p_out (nm N), hist.
+mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int nm, int C,
+                     const mpi_irgn_params* prm, mpi_precision prec, Solver& sv, float2* base, const float2* yc,
+                     float2* alpha_out, float2* p_out, double* hist) {
+  const long N = (long)nm * plan->N, Cq = (long)nm * C * basis->q, CM = (long)C * plan->M, X = N + Cq;
   float2 *x = base, *dx = x + X, *res = dx + X, *d = res + X, *Ad = d + X, *h = Ad + X;
   float2 *bn = h + X;  // right-hand side
   float2 *ys = bn + 2 * X, *yt = ys + std::max(CM, 1L), *r = yt + std::max(CM, 1L);
@@ -719,13 +730,19 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
   }
   TRY(sv.fill(p, make_float2(1.f, 0.f), N));
   TRY(sv.fill(al, make_float2(0.f, 0.f), Cq));
+  if (nm > 1) {
+    const int rows = (nm - 1) * C;
+    MPI_PROF(ctx, KF_SOLVER);
+    k_first_coef<<<(rows + 255) / 256, 256, 0, ctx->stream>>>(al + (long)C * basis->q, rows, basis->q, 0.1f);
+    MPI_LAUNCH_CHECK(ctx, "k_first_coef");
+  }
   float l1 = 0.f, l2 = 0.f;
   // (J^H J + 2L) v into Ad, v in `v`, operators at precision pr
   auto normal = [&](const float2* v, mpi_precision pr) -> mpi_status {
-    TRY(mpi_jacobian(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)v,
-                     (const mpi_c32*)(v + N), (mpi_c32*)yt, pr));
-    TRY(mpi_jacobian_adjoint(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)yt,
-                             (mpi_c32*)h, (mpi_c32*)(h + N), pr));
+    TRY(mpi_jacobian_maps(ctx, plan, basis, nm, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)v,
+                          (const mpi_c32*)(v + N), (mpi_c32*)yt, pr));
+    TRY(mpi_jacobian_adjoint_maps(ctx, plan, basis, nm, (const mpi_c32*)al, C, (const mpi_c32*)p,
+                                  (const mpi_c32*)yt, (mpi_c32*)h, (mpi_c32*)(h + N), pr));
     MPI_PROF(ctx, KF_SOLVER);
     k_normal_finish<<<kRedBlocks, kVecThreads, 0, ctx->stream>>>(h, v, X, N, l1, l2, Ad, sv.partials);
     MPI_LAUNCH_CHECK(ctx, "k_normal_finish");
@@ -752,7 +769,7 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
   };
   for (int n = 0; n <= prm->n_outer; ++n) {
     // r = ys - G(x)
-    TRY(mpi_forward(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (mpi_c32*)yt, pout));
+    TRY(mpi_forward_maps(ctx, plan, basis, nm, (const mpi_c32*)al, C, (const mpi_c32*)p, (mpi_c32*)yt, pout));
     if (CM > 0) TRY(sv.lincomb(r, ys, 1.f, yt, -1.f, CM));
     if (CM > 0) TRY(sv.dot(r, nullptr, CM, FIN_SQRT_TO_HIST, 0, 0, hist, n));
     if (n == prm->n_outer) break;
@@ -761,8 +778,8 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
     l1 = (float)(2.0 * an);
     l2 = (float)(2.0 * bnn);
     // b = J^H r - 2 L x
-    TRY(mpi_jacobian_adjoint(ctx, plan, basis, (const mpi_c32*)al, C, (const mpi_c32*)p, (const mpi_c32*)r,
-                             (mpi_c32*)h, (mpi_c32*)(h + N), pout));
+    TRY(mpi_jacobian_adjoint_maps(ctx, plan, basis, nm, (const mpi_c32*)al, C, (const mpi_c32*)p,
+                                  (const mpi_c32*)r, (mpi_c32*)h, (mpi_c32*)(h + N), pout));
     TRY(sv.lincomb(bn, h, 1.f, x, -l1, N));
     TRY(sv.lincomb(bn + N, h + N, 1.f, x + N, -l2, Cq));
     TRY(cg(dx, bn, prm->n_cg, pin));
@@ -776,21 +793,24 @@ mpi_status irgn_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
 
 }  // namespace
 
-extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, const mpi_c32* y,
-                                      int C, const mpi_irgn_params* prm, mpi_c32* alpha_out, mpi_c32* p_out,
-                                      double* resid_out, mpi_precision prec) {
+namespace {
+
+mpi_status sm_estimate_impl(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int nm, const mpi_c32* y,
+                            int C, const mpi_irgn_params* prm, mpi_c32* alpha_out, mpi_c32* p_out,
+                            double* resid_out, mpi_precision prec) {
   if (!ctx) return MPI_ERR_ARG;
-  if (!plan || !basis || !prm || !alpha_out || !p_out || C < 1 || (plan->M > 0 && !y))
+  if (!plan || !basis || !prm || !alpha_out || !p_out || C < 1 || nm < 1 || (plan->M > 0 && !y))
     return set_err(ctx, MPI_ERR_ARG, "sm_estimate: bad argument");
   if (prm->n_outer < 0 || prm->n_cg < 0) return set_err(ctx, MPI_ERR_ARG, "negative iteration count");
+  if (nm > 1 && basis->tucker) return set_err(ctx, MPI_ERR_UNSUPPORTED, "several sets of maps: dense bases only");
   cudaSetDevice(ctx->device);
   TRY(mpi_ctx_reserve(ctx, plan, basis, C));
-  const long N = plan->N, Cq = (long)C * basis->q, CM = (long)C * plan->M, X = N + Cq;
+  const long N = (long)nm * plan->N, Cq = (long)nm * C * basis->q, CM = (long)C * plan->M, X = N + Cq;
   const long CMs = std::max(CM, 1L);
-  SolverGraph* g = cache_find(ctx, 0, plan, basis, C, prec, prm, sizeof(*prm));
+  SolverGraph* g = cache_find(ctx, nm == 1 ? 0 : 100 + nm, plan, basis, C, prec, prm, sizeof(*prm));
   if (!g) {
     g = new SolverGraph();
-    g->kind = 0;
+    g->kind = nm == 1 ? 0 : 100 + nm;
     g->plan = plan;
     g->basis = basis;
     g->C = C;
@@ -812,7 +832,8 @@ extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const 
       return st;
     }
     st = capture(ctx, g, [&]() {
-      return irgn_body(ctx, plan, basis, C, prm, prec, g->sv, g->base, g->in_y, g->out_alpha, g->out_p, g->hist);
+      return irgn_body(ctx, plan, basis, nm, C, prm, prec, g->sv, g->base, g->in_y, g->out_alpha, g->out_p,
+                       g->hist);
     });
     if (st) {
       delete g;
@@ -836,6 +857,20 @@ extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const 
       for (int i = 0; i <= prm->n_outer; ++i) resid_out[i] = 0.0;
   }
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sm_estimate");
+}
+
+}  // namespace
+
+extern "C" mpi_status mpi_sm_estimate(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, const mpi_c32* y,
+                                      int C, const mpi_irgn_params* prm, mpi_c32* alpha_out, mpi_c32* p_out,
+                                      double* resid_out, mpi_precision prec) {
+  return sm_estimate_impl(ctx, plan, basis, 1, y, C, prm, alpha_out, p_out, resid_out, prec);
+}
+
+extern "C" mpi_status mpi_sm_estimate_maps(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int M,
+                                           const mpi_c32* y, int C, const mpi_irgn_params* prm, mpi_c32* alpha_out,
+                                           mpi_c32* p_out, double* resid_out, mpi_precision prec) {
+  return sm_estimate_impl(ctx, plan, basis, M, y, C, prm, alpha_out, p_out, resid_out, prec);
 }
 
 // ------------------------------------------------------------------- MPI-L

@@ -36,6 +36,7 @@ struct TcArgs {
   // EX_SCATTER output map (see ScatterMap); sc_col0 = the launch row's first column pair
   int sc_L0, sc_L1, sc_im, sc_col0;
   long sc_hi, sc_mid, sc_col;
+  int accumulate;         // EX_FWD / EX_JFWD: add into out instead of storing
   long long wait_cycles;  // bounded-wait limit (SM clock cycles)
   int stall_after;        // fault injection: the producer stops after this many stages (-1: off)
 };
@@ -322,12 +323,28 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
             }
           } else if (MODE == EX_FWD) {
             const float2 v = cmul(s, pimg);
-            if (cv) a.out[(size_t)c * a.N + n] = make_float2(v.x * sg, v.y * sg);
+            if (cv) {
+              float2* o = a.out + (size_t)c * a.N + n;
+              float2 r2 = make_float2(v.x * sg, v.y * sg);
+              if (a.accumulate) {
+                r2.x += o->x;
+                r2.y += o->y;
+              }
+              *o = r2;
+            }
           } else if (MODE == EX_JFWD) {
             const float2 ds = make_float2(rd[2 * i], rd[2 * i + 1]);
             const float2 v1 = cmul(s, dpi);
             const float2 v2 = cmul(ds, pimg);
-            if (cv) a.out[(size_t)c * a.N + n] = make_float2((v1.x + v2.x) * sg, (v1.y + v2.y) * sg);
+            if (cv) {
+              float2* o = a.out + (size_t)c * a.N + n;
+              float2 r2 = make_float2((v1.x + v2.x) * sg, (v1.y + v2.y) * sg);
+              if (a.accumulate) {
+                r2.x += o->x;
+                r2.y += o->y;
+              }
+              *o = r2;
+            }
           } else {
             if (cv) {
               const float2 t2 = cmul_conj(s, wv[i]);

@@ -273,6 +273,7 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.vout = x.vout;
   a.err = ctx->dev_err;
   a.wait_cycles = ctx->wait_cycles;
+  a.accumulate = x.accumulate;
   a.stall_after = -1;
   a.tuck_B = x.tuck_B;
   a.group_coils = 0;

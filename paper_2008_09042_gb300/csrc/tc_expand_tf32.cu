@@ -457,6 +457,7 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.vout = x.vout;
   a.err = ctx->dev_err;
   a.wait_cycles = ctx->wait_cycles;
+  a.accumulate = x.accumulate;
   a.stall_after = ctx->stall_after;
   a.tuck_B = x.tuck_B;
   a.tuck_stride = x.tuck_stride;

@@ -48,6 +48,26 @@ def pixel_centroids(ny, nx, fov_m):
     return np.stack([X.ravel(), Y.ravel(), np.zeros(ny * nx)], axis=1)
 
 
+def voxel_centroids(nz, ny, nx, fov_m):
+    """(N, 3) centroids of an nz x ny x nx grid centred on the origin, raster
+    order (x fastest, z slowest); fov_m = (fov_z, fov_y, fov_x)."""
+    dz, dy, dx = fov_m[0] / nz, fov_m[1] / ny, fov_m[2] / nx
+    z = (np.arange(nz) - nz / 2 + 0.5) * dz
+    y = (np.arange(ny) - ny / 2 + 0.5) * dy
+    x = (np.arange(nx) - nx / 2 + 0.5) * dx
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def sphere_sources(n_sites, radius):
+    """n_sites points spread over a sphere (the Fibonacci lattice)."""
+    i = np.arange(n_sites) + 0.5
+    zc = 1.0 - 2.0 * i / n_sites
+    rho = np.sqrt(1.0 - zc ** 2)
+    th = np.pi * (3.0 - np.sqrt(5.0)) * i
+    return radius * np.stack([rho * np.cos(th), rho * np.sin(th), zc], axis=1)
+
+
 def circle_sources(n_sites, radius, z=0.0):
     th = 2.0 * np.pi * np.arange(n_sites) / n_sites
     return np.stack([radius * np.cos(th), radius * np.sin(th), np.full(n_sites, z)], axis=1)
@@ -126,6 +146,23 @@ def build_maxwell_basis_2d(ny, nx, q, fov_m=(0.22, 0.22), f_hz=128e6, n_sites=64
     U = Uy[:, :q]
     comb = Omega @ (Vh[:q].conj().T / sv[:q][None, :])
     return MaxwellBasis2D(U, sv, comb, src, k, (ny, nx), fov_m)
+
+
+def build_maxwell_basis_3d(nz, ny, nx, q, fov_m=(0.22, 0.22, 0.22), f_hz=128e6, n_sites=64, omega=None,
+                           radius_factor=1.5, sources=None, seed=0, n_exc=500):
+    """Maxwell basis of a 3D volume: the 2D steps with voxel centroids and, by
+    default, dipole sites on a sphere of radius radius_factor x the FOV
+    half-diagonal.  Returns (U (N, q), singular values, sources)."""
+    k = wavenumber(f_hz)
+    if sources is None:
+        sources = sphere_sources(n_sites, radius_factor * 0.5 * np.sqrt(np.sum(np.square(fov_m))))
+    pts = voxel_centroids(nz, ny, nx, fov_m)
+    B = dipole_b_fields(pts, sources, k)
+    if omega is None:
+        rng = np.random.default_rng(seed)
+        omega = (rng.normal(size=(B.shape[1], n_exc)) + 1j * rng.normal(size=(B.shape[1], n_exc))) / np.sqrt(2.0)
+    Uy, sv, _ = np.linalg.svd(B @ np.asarray(omega, dtype=np.complex128), full_matrices=False)
+    return Uy[:, :q], sv, np.asarray(sources)
 
 
 def coil_maps_2d(ny, nx, C, fov_m=(0.22, 0.22), f_hz=128e6, radius_factor=1.2):

@@ -132,3 +132,24 @@ def test_table_s1_dense_ram_column():
     N = 6266880
     for q, mb in fix:
         assert round(N * q * 16 / 2 ** 20) == mb
+
+
+def test_voxel_centroids_and_3d_builder_reduce_to_2d():
+    # one slice of voxels is the 2D pixel grid, and the 3D builder with the 2D
+    # sources and excitations gives the 2D basis (subspace) and singular values
+    pts3 = basis.voxel_centroids(1, 6, 8, (0.01, 0.22, 0.22))
+    np.testing.assert_allclose(pts3, basis.pixel_centroids(6, 8, (0.22, 0.22)), atol=0)
+    src = basis.circle_sources(8, 1.5 * 0.5 * np.hypot(0.22, 0.22))
+    om = (np.random.default_rng(4).normal(size=(48, 40)) + 1j * np.random.default_rng(5).normal(size=(48, 40)))
+    b2 = basis.build_maxwell_basis_2d(12, 12, 6, n_sites=8, omega=om)
+    U3, sv3, _ = basis.build_maxwell_basis_3d(1, 12, 12, 6, fov_m=(0.01, 0.22, 0.22), omega=om, sources=src)
+    np.testing.assert_allclose(sv3, b2.sv, rtol=1e-12)
+    assert np.linalg.norm(U3 - b2.U @ (b2.U.conj().T @ U3)) < 1e-10
+
+
+def test_sphere_sources_on_the_sphere_and_spread():
+    s = basis.sphere_sources(50, 0.3)
+    np.testing.assert_allclose(np.linalg.norm(s, axis=1), 0.3, rtol=1e-12)
+    assert abs(s.mean(axis=0)).max() < 0.02  # no hemisphere favoured
+    d = np.linalg.norm(s[:, None] - s[None], axis=2) + np.eye(50)
+    assert d.min() > 0.5 * 0.3 * np.sqrt(4 * np.pi / 50)  # no two sites much closer than the mean spacing

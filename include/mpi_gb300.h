@@ -187,7 +187,8 @@ mpi_status mpi_basis_load_dense(mpi_ctx* ctx, const mpi_c32* U, int N, int q, in
  * is G_j x1 U1 x2 U2 x3 U3, with the core G given as [q][r1][r2][r3] (the core
  * slice of column j contiguous) and factors U_k as [n_k][r_k] (row-major), all
  * complex64; host pointers when on_device = 0, else device pointers.  Limits:
- * 1 <= r_k <= n_k <= 128, r1 r2 r3 and n1 n2 n3 multiples of 4, q <= 256.  The
+ * 1 <= r_k <= min(n_k, 128), n_k <= 256, r1 r2 r3 and n1 n2 n3 multiples of 4,
+ * q <= 256.  The
  * operators expand maps as (G x4 alpha_c^T) x1 U1 x2 U2 x3 U3 (the core
  * contraction in FP32 or on BF16 tensor cores, the mode products in FP32). */
 mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, const mpi_c32* U1, const mpi_c32* U2,
@@ -226,6 +227,29 @@ mpi_status mpi_basis_destroy(mpi_basis* basis);
 mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double fov_y, double fov_x, double f_hz,
                                 const double* sources, int n_sites, const mpi_c64* omega, int L, int q,
                                 mpi_c32* U_out, double* sv_out);
+/* The same for a 3D volume of nz x ny x nx voxels (fov_z x fov_y x fov_x metres,
+ * centred on the origin, raster order x fastest, z slowest): U_out [q][N] with
+ * N = nz ny nx is the dense basis tensor [q][nz][ny][nx] that
+ * mpi_tucker_compress takes. */
+mpi_status mpi_maxwell_basis_3d(mpi_ctx* ctx, int nz, int ny, int nx, double fov_z, double fov_y, double fov_x,
+                                double f_hz, const double* sources, int n_sites, const mpi_c64* omega, int L, int q,
+                                mpi_c32* U_out, double* sv_out);
+
+/* Tucker compression of a dense basis on the GPU ("A Compression Scheme for
+ * Maxwell Basis", Eqs. 19-21): T (device, complex64 [q][n1][n2][n3], i.e. a
+ * dense basis [q][N] on an n1 x n2 x n3 grid, n1 slowest) -> a Tucker basis
+ * (*out, owned by the caller, as from mpi_basis_load_tucker).  HOSVD: U_k = the
+ * leading eigenvectors of the mode-k Gram matrix T_(k) T_(k)^H (formed in FP64
+ * with a fixed summation order), r_k = the fewest with discarded eigenvalues
+ * summing to at most eps^2 ||T||^2 / 3, core = T x1 U1^H x2 U2^H x3 U3^H (FP32).
+ * Then ||T - T~|| <= bound ||T|| with bound = sqrt(sum_k tail_k) / ||T|| <= eps
+ * (Eq. 21).  r3 is raised where needed to make r1 r2 r3 a multiple of 4 (the
+ * Tucker basis layout); ranks_out receives the ranks used, bound_out the bound
+ * for them.  Limits: n_k <= 256, q <= 256, n1 n2 n3 a multiple of 4; a rank above
+ * 128 is MPI_ERR_UNSUPPORTED.  Allocates its workspace (about 16 q r1 n2 n3
+ * bytes for the mode products) and synchronises the context's stream. */
+mpi_status mpi_tucker_compress(mpi_ctx* ctx, const mpi_c32* T, const int n[3], int q, double eps,
+                               mpi_basis** out, int ranks_out[3], double* bound_out);
 
 /* Which kernel carries the dense contraction U alpha (for a Tucker basis, the
  * core contraction) for C coils at precision `prec`; `jacobian` != 0 asks

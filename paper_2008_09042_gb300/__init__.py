@@ -18,6 +18,8 @@ from .api import (  # noqa: F401
     basis_expand,
     basis_project,
     maxwell_basis_2d,
+    maxwell_basis_3d,
+    tucker_compress,
     forward_maps,
     adjoint_maps,
     jacobian_maps,

@@ -27,6 +27,7 @@ EXPORTS = [
     "mpi_tv_prox", "mpi_forward_noalloc", "mpi_batch_create", "mpi_batch_run", "mpi_batch_kernel_count",
     "mpi_batch_destroy", "mpi_expand_path", "mpi_forward_host", "mpi_adjoint_host", "mpi_maxwell_basis_2d",
     "mpi_forward_maps", "mpi_adjoint_maps", "mpi_jacobian_maps", "mpi_jacobian_adjoint_maps", "mpi_sm_estimate_maps",
+    "mpi_maxwell_basis_3d", "mpi_tucker_compress",
 ]
 
 
@@ -106,6 +107,9 @@ def load(path=LIB_PATH):
                                   i, i, pp],
         "mpi_basis_destroy": [vp],
         "mpi_maxwell_basis_2d": [vp, i, i, d, d, d, vp, i, vp, i, i, vp, vp],
+        "mpi_maxwell_basis_3d": [vp, i, i, i, d, d, d, d, vp, i, vp, i, i, vp, vp],
+        "mpi_tucker_compress": [vp, vp, ctypes.POINTER(ctypes.c_int), i, d, pp, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(d)],
         "mpi_expand_path": [vp, i, i, i],
         "mpi_basis_expand": [vp, vp, vp, i, vp, i],
         "mpi_forward": [vp, vp, vp, vp, i, vp, vp, i],

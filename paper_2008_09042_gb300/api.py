@@ -356,6 +356,49 @@ def maxwell_basis_2d(ctx, shape, q, sources, omega, fov=(0.22, 0.22), f_hz=128e6
     return U, sv
 
 
+def maxwell_basis_3d(ctx, shape, q, sources, omega, fov=(0.22, 0.22, 0.22), f_hz=128e6):
+    """Maxwell basis of an nz x ny x nx volume built on the GPU (mpi_maxwell_basis_3d).
+    Returns (U (q, N) complex64 device tensor, singular values)."""
+    nz, ny, nx = shape
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.float64))
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.complex128))
+    D = src.shape[0]
+    if src.shape != (D, 3) or om.ndim != 2 or om.shape[0] != 6 * D:
+        raise ValueError("sources must be (D, 3) and omega (6 D, L)")
+    L = om.shape[1]
+    U = torch.empty((q, nz * ny * nx), dtype=torch.complex64, device=f"cuda:{ctx.device}")
+    sv = np.zeros(min(6 * D, L), dtype=np.float64)
+    check(ctx.h, ctx.lib.mpi_maxwell_basis_3d(ctx.h, nz, ny, nx, float(fov[0]), float(fov[1]), float(fov[2]),
+                                             float(f_hz), src.ctypes.data, D, om.ctypes.data, L, q, _ptr(U),
+                                             sv.ctypes.data))
+    return U, sv
+
+
+class CompressedBasis(Basis):
+    """A Tucker basis made by mpi_tucker_compress (held by the library)."""
+
+    def __init__(self, ctx, handle, shape, q, ranks, bound):
+        self.ctx, self.h = ctx, handle
+        self.n, self.q, self.N = tuple(shape), int(q), int(np.prod(shape))
+        self.ranks, self.bound = tuple(ranks), float(bound)
+
+
+def tucker_compress(ctx, T, shape, eps=1e-4):
+    """HOSVD compression of a dense basis T (q, n1 n2 n3) on the GPU to accuracy
+    eps (Eq. 21).  Returns a CompressedBasis with .ranks and .bound."""
+    q = int(T.shape[0])
+    t = T.to(device=f"cuda:{ctx.device}", dtype=torch.complex64).contiguous()
+    if t.shape[1] != int(np.prod(shape)):
+        raise ValueError("T must be (q, n1 n2 n3)")
+    n_arr = (ctypes.c_int * 3)(*[int(x) for x in shape])
+    r_arr = (ctypes.c_int * 3)()
+    bound = ctypes.c_double()
+    h = ctypes.c_void_p()
+    check(ctx.h, ctx.lib.mpi_tucker_compress(ctx.h, _ptr(t), n_arr, q, float(eps), ctypes.byref(h), r_arr,
+                                             ctypes.byref(bound)))
+    return CompressedBasis(ctx, h, shape, q, tuple(r_arr), bound.value)
+
+
 def basis_project(ctx, basis, maps):
     C = maps.shape[0]
     _need(maps, (C, basis.N), "maps")

@@ -675,10 +675,10 @@ extern "C" mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, c
   if (!core || !U1 || !U2 || !U3 || !n || !r || !out) return set_err(ctx, MPI_ERR_ARG, "null Tucker argument");
   *out = nullptr;
   for (int k = 0; k < 3; ++k)
-    if (n[k] < 1 || r[k] < 1 || r[k] > n[k] || r[k] > 128 || n[k] > 128 * 4096)
+    if (n[k] < 1 || r[k] < 1 || r[k] > n[k] || r[k] > 128)
       return set_err(ctx, MPI_ERR_SHAPE, "Tucker ranks must satisfy 1 <= r_k <= min(n_k, 128)");
-  if (n[1] > 128 || n[2] > 128 || n[0] > 128)
-    return set_err(ctx, MPI_ERR_SHAPE, "Tucker factor lengths above 128 are not supported");
+  if (n[1] > 256 || n[2] > 256 || n[0] > 256)
+    return set_err(ctx, MPI_ERR_SHAPE, "Tucker factor lengths above 256 are not supported");
   const long long R = (long long)r[0] * r[1] * r[2];
   const long long N = (long long)n[0] * n[1] * n[2];
   if (R % 4 || N % 4 || N > (1LL << 31) - 1) return set_err(ctx, MPI_ERR_SHAPE, "Tucker sizes (R, N must be multiples of 4)");

@@ -66,16 +66,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Without B: |b|^2 summed per dipole into norm2 (per-CTA sums, then one
 // atomic add per CTA and dipole; only used to find the identically zero fields).
 __global__ void k_dipole_fields(double2* __restrict__ B, const int* __restrict__ pos, double* __restrict__ norm2,
-                                int N, int ny, int nx, double dy, double dx, const double* __restrict__ src,
-                                double k) {
+                                int N, int nz, int ny, int nx, double dz, double dy, double dx,
+                                const double* __restrict__ src, double k) {
   __shared__ double s_n2[6][8];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
   double2 b[6];
   if (n < N) {
-    const int iy = n / nx, ix = n - iy * nx;
-    const double px = (ix - 0.5 * nx + 0.5) * dx, py = (iy - 0.5 * ny + 0.5) * dy;
-    const double rx = px - src[3 * s + 0], ry = py - src[3 * s + 1], rz = -src[3 * s + 2];
+    const int ix = n % nx, t = n / nx, iy = t % ny, iz = t / ny;  // raster order, x fastest, z slowest
+    const double px = (ix - 0.5 * nx + 0.5) * dx, py = (iy - 0.5 * ny + 0.5) * dy, pz = (iz - 0.5 * nz + 0.5) * dz;
+    const double rx = px - src[3 * s + 0], ry = py - src[3 * s + 1], rz = pz - src[3 * s + 2];
     const double R = sqrt(rx * rx + ry * ry + rz * rz);
     const double ux = rx / R, uy = ry / R, uz = rz / R;
     double sn, cs;
@@ -405,12 +405,73 @@ mpi_status apply_reflector(mpi_ctx* ctx, const double2* A, double2* T, int N, in
 
 }  // namespace
 
-extern "C" mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double fov_y, double fov_x, double f_hz,
-                                           const double* sources, int n_sites, const mpi_c64* omega, int L, int q,
-                                           mpi_c32* U_out, double* sv_out) {
+// One-sided Jacobi on the nj (even) columns of M (L x nj, column-major, FP64),
+// accumulating the rotations into V (nj x nj, set to I here), until no pair
+// rotates (at most 60 sweeps).  A pair counts as orthogonal once
+// |m_a^H m_b| <= L eps |m_a| |m_b| (the rounding bound of the L-term dot
+// product itself: a tighter test keeps rotating on rounding noise); columns with
+// |m|^2 below eps^2 ||M||_F^2 (invariant under the rotations) are at M's
+// rounding floor.  One sweep is a CUDA graph of nj - 1 steps.  On return
+// sig_host holds the final column norms (the singular values of M, in column
+// order).  sig_dev: nj doubles; flag: one int (device scratch).
+mpi_status jacobi_columns(mpi_ctx* ctx, double2* M, int L, int nj, double2* V, double* sig_dev, int* flag,
+                          std::vector<double>& sig_host, const char* what) {
+  cudaStream_t st = ctx->stream;
+  MPI_PROF(ctx, KF_OTHER);
+  k_identity<<<(nj * nj + 255) / 256, 256, 0, st>>>(V, nj);
+  MPI_LAUNCH_CHECK(ctx, "k_identity");
+  constexpr double kEps = 2.220446049250313e-16;
+  const double tol = (double)L * kEps;
+  MPI_PROF(ctx, KF_OTHER);
+  k_col_norms<<<nj, 128, 0, st>>>(M, L, sig_dev);
+  MPI_LAUNCH_CHECK(ctx, "k_col_norms");
+  sig_host.assign(nj, 0.0);
+  cudaError_t e = cudaMemcpyAsync(sig_host.data(), sig_dev, nj * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_check(ctx, e, what);
+  double fro2 = 0.0;
+  for (double v : sig_host) fro2 += v * v;
+  const double floor2 = kEps * kEps * fro2;
+  SweepGraph sg;
+  e = cudaStreamCreateWithFlags(&sg.cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(sg.cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int s = 0; s < nj - 1; ++s) k_jacobi_step<<<nj / 2, 128, 0, sg.cap>>>(M, L, V, nj, s, tol, floor2, flag);
+    cudaError_t e2 = cudaStreamEndCapture(sg.cap, &sg.graph);
+    e = e2 != cudaSuccess ? e2 : cudaGraphInstantiate(&sg.exec, sg.graph, 0);
+  }
+  if (e != cudaSuccess) return cuda_check(ctx, e, what);
+  int rot = 1;
+  for (int sweeps = 0; sweeps < 60 && rot; ++sweeps) {
+    e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, what);
+    MPI_PROF(ctx, KF_OTHER);
+    e = cudaGraphLaunch(sg.exec, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, what);
+    ctx->launches += nj - 2;  // the sweep's kernels (MPI_LAUNCH_CHECK counts one)
+    MPI_LAUNCH_CHECK(ctx, "k_jacobi_step (sweep)");
+    e = cudaMemcpyAsync(&rot, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, what);
+  }
+  if (rot) return set_err(ctx, MPI_ERR_CUDA, std::string(what) + ": Jacobi SVD did not converge");
+  MPI_PROF(ctx, KF_OTHER);
+  k_col_norms<<<nj, 128, 0, st>>>(M, L, sig_dev);
+  MPI_LAUNCH_CHECK(ctx, "k_col_norms");
+  e = cudaMemcpyAsync(sig_host.data(), sig_dev, nj * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? MPI_OK : cuda_check(ctx, e, what);
+}
+
+namespace {
+
+mpi_status maxwell_basis(mpi_ctx* ctx, int nz, int ny, int nx, double fov_z, double fov_y, double fov_x,
+                         double f_hz, const double* sources, int n_sites, const mpi_c64* omega, int L, int q,
+                         mpi_c32* U_out, double* sv_out) {
   if (!ctx) return MPI_ERR_ARG;
   if (!sources || !omega || !U_out || !sv_out) return set_err(ctx, MPI_ERR_ARG, "null argument");
-  const long Nl = (long)ny * nx;
+  if (nz < 1 || !(fov_z > 0)) return set_err(ctx, MPI_ERR_SHAPE, "Maxwell basis: bad sizes");
+  const long Nl = (long)nz * ny * nx;
   const int n = 6 * n_sites;
   if (ny < 1 || nx < 1 || n_sites < 1 || L < 1 || q < 1 || n_sites > 4096 || L > 65536)
     return set_err(ctx, MPI_ERR_SHAPE, "Maxwell basis: bad sizes");
@@ -437,8 +498,8 @@ extern "C" mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double 
     return set_err(ctx, MPI_ERR_OOM, "Maxwell basis sources");
   }
   MPI_PROF(ctx, KF_OTHER);
-  k_dipole_fields<<<fgrid, 256, 0, st>>>(nullptr, nullptr, (double*)bN2.p, N, ny, nx, fov_y / ny, fov_x / nx,
-                                         (const double*)bSrc.p, k);
+  k_dipole_fields<<<fgrid, 256, 0, st>>>(nullptr, nullptr, (double*)bN2.p, N, nz, ny, nx, fov_z / nz, fov_y / ny,
+                                         fov_x / nx, (const double*)bSrc.p, k);
   MPI_LAUNCH_CHECK(ctx, "k_dipole_fields (norms)");
   std::vector<double> n2(n);
   e = cudaMemcpyAsync(n2.data(), bN2.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -498,8 +559,8 @@ extern "C" mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double 
   if (e == cudaSuccess) e = cudaMemsetAsync(M, 0, (size_t)L * nj * sizeof(double2), st);
   if (e != cudaSuccess) return cuda_check(ctx, e, "Maxwell basis inputs");
   MPI_PROF(ctx, KF_OTHER);
-  k_dipole_fields<<<fgrid, 256, 0, st>>>(A, (const int*)bPos.p, nullptr, N, ny, nx, fov_y / ny, fov_x / nx,
-                                         (const double*)bSrc.p, k);
+  k_dipole_fields<<<fgrid, 256, 0, st>>>(A, (const int*)bPos.p, nullptr, N, nz, ny, nx, fov_z / nz, fov_y / ny,
+                                         fov_x / nx, (const double*)bSrc.p, k);
   MPI_LAUNCH_CHECK(ctx, "k_dipole_fields");
   // 2a. Householder QR
   for (int j = 0; j < ne; ++j) {
@@ -519,55 +580,12 @@ extern "C" mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double 
   MPI_PROF(ctx, KF_OTHER);
   k_small_x<<<dim3((unsigned)((L + 127) / 128), (unsigned)ne), 128, 0, st>>>(A, N, ne, Om, L, M);
   MPI_LAUNCH_CHECK(ctx, "k_small_x");
-  MPI_PROF(ctx, KF_OTHER);
-  k_identity<<<(nj * nj + 255) / 256, 256, 0, st>>>(V, nj);
-  MPI_LAUNCH_CHECK(ctx, "k_identity");
-  // 2c. one-sided Jacobi sweeps until no pair rotates.  A pair counts as
-  // orthogonal once |m_a^H m_b| <= L eps |m_a| |m_b| (the rounding bound of the
-  // L-term dot product itself: a tighter test keeps rotating on rounding noise);
-  // columns with |m|^2 below eps^2 ||M||_F^2 (invariant under the rotations)
-  // are at M's rounding floor.  One sweep is a CUDA graph of n - 1 steps.
-  constexpr double kEps = 2.220446049250313e-16;
-  const double tol = (double)L * kEps;
-  MPI_PROF(ctx, KF_OTHER);
-  k_col_norms<<<nj, 128, 0, st>>>(M, L, (double*)bSig.p);
-  MPI_LAUNCH_CHECK(ctx, "k_col_norms");
-  std::vector<double> sig(nj);
-  e = cudaMemcpyAsync(sig.data(), bSig.p, nj * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_check(ctx, e, "Maxwell basis column norms");
-  double fro2 = 0.0;
-  for (double v : sig) fro2 += v * v;
-  const double floor2 = kEps * kEps * fro2;
-  SweepGraph sg;
-  e = cudaStreamCreateWithFlags(&sg.cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamBeginCapture(sg.cap, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    for (int s = 0; s < nj - 1; ++s) k_jacobi_step<<<nj / 2, 128, 0, sg.cap>>>(M, L, V, nj, s, tol, floor2, flag);
-    cudaError_t e2 = cudaStreamEndCapture(sg.cap, &sg.graph);
-    e = e2 != cudaSuccess ? e2 : cudaGraphInstantiate(&sg.exec, sg.graph, 0);
+  // 2c. one-sided Jacobi on the columns of M = X^H
+  std::vector<double> sig;
+  {
+    mpi_status s2 = jacobi_columns(ctx, M, L, nj, V, (double*)bSig.p, flag, sig, "Maxwell basis");
+    if (s2) return s2;
   }
-  if (e != cudaSuccess) return cuda_check(ctx, e, "Maxwell basis Jacobi sweep graph");
-  int sweeps = 0, rot = 1;
-  for (; sweeps < 60 && rot; ++sweeps) {
-    e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "Maxwell basis Jacobi flag");
-    MPI_PROF(ctx, KF_OTHER);
-    e = cudaGraphLaunch(sg.exec, st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "Maxwell basis Jacobi sweep");
-    ctx->launches += nj - 2;  // the sweep's kernels (MPI_LAUNCH_CHECK counts one)
-    MPI_LAUNCH_CHECK(ctx, "k_jacobi_step (sweep)");
-    e = cudaMemcpyAsync(&rot, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "Maxwell basis Jacobi sweep");
-  }
-  if (rot) return set_err(ctx, MPI_ERR_CUDA, "Maxwell basis: Jacobi SVD did not converge");
-  MPI_PROF(ctx, KF_OTHER);
-  k_col_norms<<<nj, 128, 0, st>>>(M, L, (double*)bSig.p);
-  MPI_LAUNCH_CHECK(ctx, "k_col_norms");
-  e = cudaMemcpyAsync(sig.data(), bSig.p, nj * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_check(ctx, e, "Maxwell basis singular values");
   std::vector<int> order(nj);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sig[x] > sig[y]; });
@@ -590,4 +608,18 @@ extern "C" mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double 
   MPI_LAUNCH_CHECK(ctx, "k_z_to_c64");
   e = cudaStreamSynchronize(st);  // the workspace is freed on return
   return e == cudaSuccess ? MPI_OK : cuda_check(ctx, e, "Maxwell basis");
+}
+
+}  // namespace
+
+extern "C" mpi_status mpi_maxwell_basis_2d(mpi_ctx* ctx, int ny, int nx, double fov_y, double fov_x, double f_hz,
+                                           const double* sources, int n_sites, const mpi_c64* omega, int L, int q,
+                                           mpi_c32* U_out, double* sv_out) {
+  return maxwell_basis(ctx, 1, ny, nx, 1.0, fov_y, fov_x, f_hz, sources, n_sites, omega, L, q, U_out, sv_out);
+}
+
+extern "C" mpi_status mpi_maxwell_basis_3d(mpi_ctx* ctx, int nz, int ny, int nx, double fov_z, double fov_y,
+                                           double fov_x, double f_hz, const double* sources, int n_sites,
+                                           const mpi_c64* omega, int L, int q, mpi_c32* U_out, double* sv_out) {
+  return maxwell_basis(ctx, nz, ny, nx, fov_z, fov_y, fov_x, f_hz, sources, n_sites, omega, L, q, U_out, sv_out);
 }

@@ -266,6 +266,16 @@ bool uh_tc_supported(const mpi_basis* b, mpi_precision prec);
 size_t uh_tc_partial_elems(const mpi_ctx* ctx, int N, int q, int C);
 mpi_status launch_uh_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha,
                         float2* partials, size_t partial_cap, mpi_precision prec);
+// One-sided Jacobi SVD of the nj (even) columns of an FP64 L x nj column-major
+// matrix M (maxwell.cu): rotations accumulated into V (nj x nj), final column
+// norms (the singular values, column order) into sig_host.
+mpi_status jacobi_columns(mpi_ctx* ctx, double2* M, int L, int nj, double2* V, double* sig_dev, int* flag,
+                          std::vector<double>& sig_host, const char* what);
+// core [q][r1][r2][r3] = T x1 U1^H x2 U2^H x3 U3^H for a dense tensor T
+// [q][n1][n2][n3] and factors F_k [n_k][r_k] (tucker.cu, FP32 mode products);
+// tmp holds q r1 (n2 n3 + r2 n3) complex values.
+mpi_status tucker_project(mpi_ctx* ctx, const float2* T, int q, const int n[3], const int r[3], const float2* F0,
+                          const float2* F1, const float2* F2, float2* core, float2* tmp);
 // U^H V on the tensor cores where the basis and precision allow, else on the CUDA cores.
 mpi_status uh_v(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* partials,
                 size_t partial_cap, mpi_precision prec);

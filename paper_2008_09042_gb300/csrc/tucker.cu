@@ -42,6 +42,7 @@ __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * 
 }
 
 constexpr int kPB = 8;   // contracted elements loaded per batch
+constexpr int kMaxP = 256;  // longest contracted length of the CUDA-core mode products (factor length or rank)
 constexpr int kIB1 = 16; // outputs along i per thread of the CUDA-core x1 forward
 
 // Y[r][i][b] = sum_p X[r][p][b] M(i, p), with M(i, p) = F[i][p] (forward, F is I x P)
@@ -50,12 +51,12 @@ constexpr int kIB1 = 16; // outputs along i per thread of the CUDA-core x1 forwa
 // memory as [P][kIB] for the CTA's i-block.  The i-block is the fastest grid
 // index, so the CTAs that read the same X tile run together and all but the
 // first find it in L2.
-template <bool ADJ, int kIB>
+template <bool ADJ, int kIB, int MAXP>
 __global__ void __launch_bounds__(256) k_mode_b(const float2* __restrict__ X, const float2* __restrict__ F, int R,
                                                 int P, int I, long B, float2* __restrict__ Y) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
-  __shared__ float2 sM[(128 + kPB) * kIB];  // rows beyond P are zero (the last load batch)
+  __shared__ float2 sM[(MAXP + kPB) * kIB];  // rows beyond P are zero (the last load batch)
   const int i0 = blockIdx.x * kIB;
   for (int e = P * kIB + threadIdx.x; e < ((P + kPB - 1) / kPB) * kPB * kIB; e += blockDim.x)
     sM[e] = make_float2(0.f, 0.f);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(256) k_mode1_fwd(const float2* __restrict__ X,
                                                    int I, long B, ExpandArgs a) {
   mpi_ptx::pdl_trigger();
   mpi_ptx::pdl_wait();
-  __shared__ float2 sM[(128 + kPB) * kIB1];  // M(i, p) = F[i][p] of the i-block; rows beyond P are zero
+  __shared__ float2 sM[(128 + kPB) * kIB1];  // M(i, p) = F[i][p] of the i-block (P = r1 <= 128); rows beyond P are zero
   const int i0 = blockIdx.x * kIB1;
   for (int e = P * kIB1 + threadIdx.x; e < ((P + kPB - 1) / kPB) * kPB * kIB1; e += blockDim.x)
     sM[e] = make_float2(0.f, 0.f);
@@ -299,28 +300,30 @@ __global__ void __launch_bounds__(256) k_x1_operand(const float2* __restrict__ t
 }
 
 mpi_status mode_b(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, long B, float2* Y) {
-  if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
+  if (P > kMaxP) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 256");
   const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);  // no idle lanes when B = 128
   // 16 outputs along i per thread (32 measured slower: fewer resident warps)
   const int ib = 16;
   const dim3 grid((unsigned)((I + ib - 1) / ib), (unsigned)((B + block - 1) / block), (unsigned)R);
   if (R > 65535 || grid.y > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
   MPI_PROF(ctx, KF_EXPAND);
-  if (ib == 32) {
-    if (adj) launch_pdl(ctx, k_mode_b<true, 32>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
-    else launch_pdl(ctx, k_mode_b<false, 32>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+  // contracted lengths above 128 (the adjoint products of factors longer than
+  // 128) take a kernel with a larger staging buffer
+  if (P > 128) {
+    if (adj) launch_pdl(ctx, k_mode_b<true, 16, kMaxP>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+    else launch_pdl(ctx, k_mode_b<false, 16, kMaxP>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
   } else {
-    if (adj) launch_pdl(ctx, k_mode_b<true, 16>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
-    else launch_pdl(ctx, k_mode_b<false, 16>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+    if (adj) launch_pdl(ctx, k_mode_b<true, 16, 128>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
+    else launch_pdl(ctx, k_mode_b<false, 16, 128>, grid, dim3(block), 0, X, F, R, P, I, B, Y);
   }
   MPI_LAUNCH_CHECK(ctx, "k_mode_b");
   return MPI_OK;
 }
 
 mpi_status mode_last(mpi_ctx* ctx, bool adj, const float2* X, const float2* F, int R, int P, int I, float2* Y) {
-  if (P > 128 || I > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: length > 128");
   const unsigned grid = (unsigned)((R + kLastRows - 1) / kLastRows);
   const size_t smem = ((size_t)P * I + (size_t)kLastRows * P) * sizeof(float2);
+  if (smem > 232448 - 1024) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker last-mode product: factor too large");
   cudaError_t e = adj ? cudaFuncSetAttribute(k_mode_last<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                       : cudaFuncSetAttribute(k_mode_last<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "k_mode_last smem attribute");
@@ -667,7 +670,7 @@ mpi_status tucker_fused(mpi_ctx* ctx, const mpi_basis* b, int mode, const Expand
   if (st) return st;
   const int P = b->r[0], I = b->n[0];
   const long B = (long)b->n[1] * b->n[2];
-  if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: contracted length > 128");
+  if (P > 128) return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker mode product: rank > 128");
   const int block = (int)std::min<long>(256, (B + 31) / 32 * 32);
   const dim3 grid((unsigned)((I + kIB1 - 1) / kIB1), (unsigned)((B + block - 1) / block), (unsigned)a.C);
   if (grid.y > 65535 || a.C > 65535) return set_err(ctx, MPI_ERR_SHAPE, "Tucker mode product grid");
@@ -718,4 +721,16 @@ mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const f
   }
   MPI_LAUNCH_CHECK(ctx, name);
   return MPI_OK;
+}
+
+// The HOSVD core of a dense tensor: conjugate-transposed mode products, mode 1
+// first (the same products as the adjoint chain above).
+mpi_status tucker_project(mpi_ctx* ctx, const float2* T, int q, const int n[3], const int r[3], const float2* F0,
+                          const float2* F1, const float2* F2, float2* core, float2* tmp) {
+  float2* t2 = tmp;                                           // [q][r1][n2][n3]
+  float2* t1 = t2 + (size_t)q * r[0] * n[1] * n[2];           // [q][r1][r2][n3]
+  mpi_status st;
+  if ((st = mode_b(ctx, true, T, F0, q, n[0], r[0], (long)n[1] * n[2], t2))) return st;
+  if ((st = mode_b(ctx, true, t2, F1, q * r[0], n[1], r[1], n[2], t1))) return st;
+  return mode_last(ctx, true, t1, F2, q * r[0] * r[1], n[2], r[2], core);
 }

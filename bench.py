@@ -519,9 +519,8 @@ def maxwell_basis_line(mp, ctx, n=256, q=128, n_sites=64, L=500, reps=3):
     its agreement with the FP64 oracle (singular values; subspace of the q
     leading vectors), and the oracle's own time on this host."""
     import torch
-    from oracle import basis as ob
 
-    src = ob.circle_sources(n_sites, 1.5 * 0.5 * np.hypot(0.22, 0.22))
+    src = w.circle_sites(n_sites, 1.5 * 0.5 * np.hypot(0.22, 0.22))
     om = w.random_excitations(6 * n_sites, L, seed=w.BASE_SEED)
     mp.maxwell_basis_2d(ctx, (n, n), q, src, om)  # warm-up (module load, first allocations)
     times = []
@@ -529,6 +528,8 @@ def maxwell_basis_line(mp, ctx, n=256, q=128, n_sites=64, L=500, reps=3):
         t0 = time.perf_counter()
         U, sv = mp.maxwell_basis_2d(ctx, (n, n), q, src, om)
         times.append(time.perf_counter() - t0)
+    from oracle import basis as ob  # the CPU baseline of this line
+
     t0 = time.perf_counter()
     ref = ob.build_maxwell_basis_2d(n, n, q, n_sites=n_sites, omega=om)
     t_cpu = time.perf_counter() - t0
@@ -541,6 +542,62 @@ def maxwell_basis_line(mp, ctx, n=256, q=128, n_sites=64, L=500, reps=3):
                              "sample": "one whole build: complex128 numpy, LAPACK SVD of B Omega"},
             "vs_oracle": {"sv_max_abs_err_over_sigma1": float(np.max(np.abs(sv - ref.sv[:nsv])) / ref.sv[0]),
                           "subspace_sin_theta": sin_theta, "sigma_q_over_sigma1": float(ref.sv[q - 1] / ref.sv[0])}}
+
+
+def table_s1_line(mp, ctx, shape=(192, 192, 170), cases=((75, 16, 96), (200, 40, 256)), eps=1e-4, reps=10):
+    """Supporting Table S1's setting: a 192 x 192 x 170 volume, a Maxwell basis of q
+    columns built on the GPU (dipole sites on a sphere; 6 D dipoles, L
+    excitations), compressed on the GPU to eps = 1e-4; its ranks, memory, the
+    error of the compressed basis, and the matrix-vector product U alpha (one
+    coil) with the Tucker and the dense basis.  The paper's numbers (V100,
+    MARIE basis) are context: the source model differs."""
+    import torch
+
+    out = {"shape": list(shape), "eps": eps}
+    fov = (0.22, 0.22, 0.22 * shape[2] / shape[0])
+    for q, D, L in cases:
+        src = w.sphere_sites(D, 1.5 * 0.5 * np.sqrt(np.sum(np.square(fov))))
+        om = w.random_excitations(6 * D, L, seed=w.BASE_SEED + q)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U, sv = mp.maxwell_basis_3d(ctx, shape, q, src, om, fov=fov)
+        torch.cuda.synchronize()
+        t_basis = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        B = mp.tucker_compress(ctx, U, shape, eps)
+        torch.cuda.synchronize()
+        t_comp = time.perf_counter() - t0
+        r = B.ranks
+        ram = (q * r[0] * r[1] * r[2] + sum(n * rk for n, rk in zip(shape, r))) * 8 / 1e6
+        err2 = tot2 = 0.0
+        for c0 in range(0, q, 25):
+            c1 = min(q, c0 + 25)
+            eye = torch.zeros((c1 - c0, q), dtype=torch.complex64, device=U.device)
+            eye[torch.arange(c1 - c0), torch.arange(c0, c1)] = 1
+            S = mp.basis_expand(ctx, B, eye)
+            err2 += float(torch.sum(torch.abs(S - U[c0:c1]) ** 2))
+            tot2 += float(torch.sum(torch.abs(U[c0:c1]) ** 2))
+        Bd = mp.Basis(ctx, U)
+        a = torch.randn((1, q), dtype=torch.complex64, device=U.device)
+        mvp = {}
+        for name, basis in (("tucker", B), ("dense", Bd)):
+            for prec in ("fp32", "bf16"):
+                for _ in range(3):
+                    mp.basis_expand(ctx, basis, a, prec=prec)
+                torch.cuda.synchronize()
+                s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s_.record()
+                for _ in range(reps):
+                    mp.basis_expand(ctx, basis, a, prec=prec)
+                e_.record()
+                e_.synchronize()
+                mvp[f"{name}_{prec}_ms"] = s_.elapsed_time(e_) / reps
+        out[f"q{q}"] = {"dipoles": 6 * D, "excitations": L, "basis_build_s": t_basis, "compress_s": t_comp,
+                        "ranks": list(r), "tucker_MB": ram, "dense_MB": 8 * q * int(np.prod(shape)) / 1e6,
+                        "bound": B.bound, "error": float(np.sqrt(err2 / tot2)), "mvp": mvp}
+        del Bd, B, U
+        torch.cuda.empty_cache()
+    return out
 
 
 def radial_line(mp, ctx, dev, flush, stream, steps=10, warmup=3):
@@ -842,6 +899,10 @@ def run_ours(args):
         wl["cart2d_256_c16_q128/jacobian"] = jacobian_line(mp, ctx, dev, flush, stream)
         wl["maxwell_basis_2d_256_q128"] = maxwell_basis_line(mp, ctx)
         wl["cart2d_256_c16_q128/two_sets_of_maps"] = multimap_line(mp, ctx, dev, flush, stream)
+        try:
+            wl["table_s1_192x192x170"] = table_s1_line(mp, ctx)
+        except Exception as exc:  # reported, not fatal to the headline
+            wl["table_s1_192x192x170"] = {"error": str(exc)}
         wl["batched2d_64slices"] = batched_slices(mp, ctx, dev, flush, stream)
         line["workloads"] = wl
         line["recon"] = recon_per_slice(mp, ctx, dev)

@@ -263,6 +263,68 @@ def admm_tv(Fs, s, y, eps, shape, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0
     return p, np.array(hist)
 
 
+def admm_tv_dynamic(Fs_t, s, y, eps, shape, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0, tau=2.0,
+                    trace=None):
+    """Dynamic MPI-L (the constrained problem with a spatiotemporal regulariser
+    that closes the "Regularized Density Reconstruction" section): T frames
+    p_t share the coil maps s, frame t is sampled by its own Fs_t[t], and
+        min_p R(p)  s.t.  ||y_{k,t} - F_s^t S_k p_t|| <= eps_{k,t}  for all k, t,
+    with R the isotropic TV over the (t, y, x) grid of the T frames (the
+    frame axis weighted like the spatial ones; (y, x) alone when T = 1).  The
+    ADMM steps of Eq. 11 with A = [I; (F_s^t S_k)_{k,t}], residual-balancing
+    rho as in ``admm_tv``.  y (T, C, M), eps (T, C); returns ((T, N) frames,
+    history of (primal, dual, rho)).  T = 1 is ``admm_tv``."""
+    s = np.asarray(s, dtype=np.complex128)
+    y = np.asarray(y, dtype=np.complex128)
+    eps = np.asarray(eps, dtype=np.float64)
+    T, C, M = y.shape
+    N = Fs_t[0].N
+    grid = tuple(shape) if T == 1 else (T,) + tuple(shape)
+    p = np.zeros((T, N), dtype=np.complex128)
+    u0 = np.zeros((T, N), dtype=np.complex128)
+    uk = np.zeros((T, C, M), dtype=np.complex128)
+    rho = rho0
+
+    def fwd(v):
+        return np.stack([Fs_t[t].fwd(s * v[t][None, :]) for t in range(T)])
+
+    def adj(w):
+        return np.stack([np.sum(s.conj() * Fs_t[t].adj(w[t]), axis=0) for t in range(T)])
+
+    def normal(v):
+        return [v[0] + adj(fwd(v[0]))]
+
+    hist = []
+    Apk = np.zeros((T, C, M), dtype=np.complex128)
+    for _ in range(n_outer):
+        z0n = tv_prox(p + u0, 1.0 / rho, grid, n_tv).reshape(T, N)
+        zkn = project_ball((Apk + uk).reshape(T * C, M), y.reshape(T * C, M), eps.reshape(T * C)).reshape(T, C, M)
+        rhs = (z0n - u0) + adj(zkn - uk)
+        p_prev, Apk_prev = p, Apk
+        (p,) = cg(normal, (rhs,), (p,), n_cg)
+        Apk = fwd(p)
+        u0 = u0 + p - z0n
+        uk = uk + Apk - zkn
+        if trace is not None:
+            trace("dual", rho, u0.copy(), uk.copy())
+        r_norm = np.sqrt(np.linalg.norm(p - z0n) ** 2 + np.linalg.norm(Apk - zkn) ** 2)
+        s_norm = rho * np.sqrt(np.linalg.norm(p - p_prev) ** 2 + np.linalg.norm(Apk - Apk_prev) ** 2)
+        hist.append((r_norm, s_norm, rho))
+        if r_norm > mu * s_norm:
+            rho *= tau
+            u0 = u0 / tau
+            uk = uk / tau
+            if trace is not None:
+                trace("rho", rho, u0.copy(), uk.copy())
+        elif s_norm > mu * r_norm:
+            rho /= tau
+            u0 = u0 * tau
+            uk = uk * tau
+            if trace is not None:
+                trace("rho", rho, u0.copy(), uk.copy())
+    return p, np.array(hist)
+
+
 def project_onto_basis(U, S):
     """alpha_k = (U^H U)^{-1} U^H s_k via a Cholesky factor of the Gram matrix
     (the projection in the Fig. 2 caption).  S is (C, N); returns (C, q)."""

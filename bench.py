@@ -544,6 +544,34 @@ def maxwell_basis_line(mp, ctx, n=256, q=128, n_sites=64, L=500, reps=3):
                           "subspace_sin_theta": sin_theta, "sigma_q_over_sigma1": float(ref.sv[q - 1] / ref.sv[0])}}
 
 
+def dynamic_line(mp, ctx, dev, n=256, C=16, q=128, T=8, R=4, n_outer=50, n_cg=5, n_tv=10, reps=3):
+    """Dynamic MPI-L on a movie of T frames of an n x n slice (each frame its own
+    variable-density line pattern, shared maps, TV over (t, y, x)): time per
+    movie through mpi_image_solve_dynamic (solver graph replayed)."""
+    import torch
+
+    base = w.BASE_SEED + 300
+    B = mp.Basis(ctx, w.smooth_orthonormal_basis(n, n, q, seed=base).T)
+    a = torch.from_numpy(w.random_coefficients(C, q, seed=base + 1).astype(np.complex64)).to(dev)
+    plans = [mp.Plan(ctx, (n, n), sample_idx=w.mask_to_indices(w.vd_lines_mask(n, n, R, 16, seed=base + 10 + t)))
+             for t in range(T)]
+    M = plans[0].M
+    g = torch.Generator().manual_seed(base + 2)
+    y = (torch.randn((T, C, M), dtype=torch.complex64, generator=g) * 0.01).to(dev)
+    eps = np.full((T, C), 0.01 * np.sqrt(M))
+    out = {"frames": T, "shape": [n, n], "C": C, "q": q, "iterations": f"{n_outer} ADMM x {n_cg} CG x {n_tv} TV"}
+    for prec in ("fp32", "bf16"):
+        mp.image_solve_dynamic(ctx, plans, B, a, y, eps, n_outer=n_outer, n_cg=n_cg, n_tv=n_tv, prec=prec)  # records
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mp.image_solve_dynamic(ctx, plans, B, a, y, eps, n_outer=n_outer, n_cg=n_cg, n_tv=n_tv, prec=prec)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        out[prec] = {"ms_per_movie": ms, "ms_per_frame": ms / T}
+    return out
+
+
 def table_s1_line(mp, ctx, shape=(192, 192, 170), cases=((75, 16, 96), (200, 40, 256)), eps=1e-4, reps=10):
     """Supporting Table S1's setting: a 192 x 192 x 170 volume, a Maxwell basis of q
     columns built on the GPU (dipole sites on a sphere; 6 D dipoles, L
@@ -899,6 +927,7 @@ def run_ours(args):
         wl["cart2d_256_c16_q128/jacobian"] = jacobian_line(mp, ctx, dev, flush, stream)
         wl["maxwell_basis_2d_256_q128"] = maxwell_basis_line(mp, ctx)
         wl["cart2d_256_c16_q128/two_sets_of_maps"] = multimap_line(mp, ctx, dev, flush, stream)
+        wl["dynamic_mpi_l_256_c16_q128_t8"] = dynamic_line(mp, ctx, dev)
         try:
             wl["table_s1_192x192x170"] = table_s1_line(mp, ctx)
         except Exception as exc:  # reported, not fatal to the headline

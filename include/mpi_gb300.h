@@ -441,6 +441,20 @@ mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* 
                            const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
                            const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out,
                            mpi_precision prec);
+/* Dynamic MPI-L (the constrained problem with a spatiotemporal regulariser
+ * that closes the "Regularized Density Reconstruction" section): T frames p_t
+ * of one 2D grid share the coil maps (alpha), frame t is sampled by plans[t]
+ * (equal sample counts M), and
+ *   min R(p)  s.t.  ||y_{k,t} - F_s^t S_k p_t|| <= eps_{k,t}  for all k, t,
+ * with R the isotropic TV over the (t, y, x) grid of the frames (the frame
+ * axis weighted like the spatial ones).  The steps of mpi_image_solve with
+ * the data blocks of all frames.  y: device [T][C][M]; eps: host [T][C];
+ * p_out: device [T][N]; hist_out as mpi_image_solve.  T = 1 is mpi_image_solve.
+ * MPI_ERR_SHAPE unless every plan is 2D with the first plan's grid and M. */
+mpi_status mpi_image_solve_dynamic(mpi_ctx* ctx, const mpi_plan* const* plans, int T, const mpi_basis* basis,
+                                   const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
+                                   const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out,
+                                   mpi_precision prec);
 
 /* TV prox alone: x = argmin (1/2)||x - v||^2 + lam TV(x) by n_iter FGP
  * iterations (the z0 update of Eq. 11).  v, x device [N] on the plan's grid. */

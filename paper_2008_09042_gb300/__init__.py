@@ -32,6 +32,7 @@ from .api import (  # noqa: F401
     jacobian,
     jacobian_adjoint,
     image_solve,
+    image_solve_dynamic,
     mpi_operator,
     sm_estimate,
     tv_prox,

@@ -27,7 +27,7 @@ EXPORTS = [
     "mpi_tv_prox", "mpi_forward_noalloc", "mpi_batch_create", "mpi_batch_run", "mpi_batch_kernel_count",
     "mpi_batch_destroy", "mpi_expand_path", "mpi_forward_host", "mpi_adjoint_host", "mpi_maxwell_basis_2d",
     "mpi_forward_maps", "mpi_adjoint_maps", "mpi_jacobian_maps", "mpi_jacobian_adjoint_maps", "mpi_sm_estimate_maps",
-    "mpi_maxwell_basis_3d", "mpi_tucker_compress",
+    "mpi_maxwell_basis_3d", "mpi_tucker_compress", "mpi_image_solve_dynamic",
 ]
 
 
@@ -126,6 +126,8 @@ def load(path=LIB_PATH):
         "mpi_jacobian_adjoint_maps": [vp, vp, vp, i, vp, i, vp, vp, vp, vp, i],
         "mpi_sm_estimate_maps": [vp, vp, vp, i, vp, i, ctypes.POINTER(IrgnParams), vp, vp, vp, i],
         "mpi_image_solve": [vp, vp, vp, vp, i, vp, vp, ctypes.POINTER(AdmmParams), vp, vp, i],
+        "mpi_image_solve_dynamic": [vp, ctypes.POINTER(ctypes.c_void_p), i, vp, vp, i, vp, vp,
+                                    ctypes.POINTER(AdmmParams), vp, vp, i],
         "mpi_tv_prox": [vp, vp, vp, d, i, vp],
         "mpi_forward_noalloc": [vp, vp, vp, vp, i, vp, vp],
         "mpi_batch_create": [vp, ctypes.POINTER(BatchSlice), i, i, i, pp],

@@ -518,6 +518,25 @@ def image_solve(ctx, plan, basis, alpha, y, eps, n_outer=50, n_cg=5, n_tv=10, rh
     return p, hist[:n_outer]
 
 
+def image_solve_dynamic(ctx, plans, basis, alpha, y, eps, n_outer=50, n_cg=5, n_tv=10, rho0=1.0, mu=10.0, tau=2.0,
+                        prec="fp32"):
+    """Dynamic MPI-L: frames sampled by plans[t], shared maps, spatiotemporal TV.
+    y (T, C, M), eps (T, C).  Returns (p (T, N), history (n_outer, 3))."""
+    T = len(plans)
+    C = alpha.shape[0]
+    _need(alpha, (C, basis.q), "alpha")
+    _need(y, (T, C, plans[0].M), "y")
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(T, C))
+    prm = _lib.AdmmParams(n_outer, n_cg, n_tv, rho0, mu, tau)
+    hs = (ctypes.c_void_p * T)(*[pl.h.value if isinstance(pl.h, ctypes.c_void_p) else pl.h for pl in plans])
+    p = torch.empty((T, plans[0].N), dtype=torch.complex64, device=y.device)
+    hist = np.zeros((max(n_outer, 1), 3), dtype=np.float64)
+    check(ctx.h, ctx.lib.mpi_image_solve_dynamic(ctx.h, hs, T, basis.h, _ptr(alpha), C, _ptr(y),
+                                                 eps.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _ptr(p),
+                                                 hist.ctypes.data_as(ctypes.c_void_p), PREC[prec]))
+    return p, hist[:n_outer]
+
+
 def tv_prox(ctx, plan, v, lam, n_iter):
     """argmin (1/2)||x - v||^2 + lam TV(x) by n_iter FGP iterations."""
     _need(v, (plan.N,), "v")

@@ -601,6 +601,7 @@ struct SolverGraph {
   int C = 0;
   int prec = 0;
   std::vector<unsigned char> key;
+  std::vector<const mpi_plan*> others;  // every plan the graph reads (the frames of a dynamic solve)
   void* work = nullptr;  // ctx->work at capture time
   SolverMem mem;
   Solver sv;
@@ -877,19 +878,27 @@ extern "C" mpi_status mpi_sm_estimate_maps(mpi_ctx* ctx, const mpi_plan* plan, c
 
 namespace {
 
-// Enqueue the ADMM solve.  Inputs: alpha (C x q), y (C x M), eps_d (C, device).
-// Outputs: p_out, hist (n_outer x 3).
-mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis, int C, const mpi_admm_params* prm,
-                     mpi_precision prec, Solver& sv, float2* base, double* dx, const mpi_c32* A, const float2* yc,
-                     const double* eps_d, float2* p_out, double* hist) {
-  const Grid3 g = grid_of(plan);
-  const long N = plan->N, M = plan->M, CM = (long)C * M, CMs = std::max(CM, 1L);
+// Enqueue the ADMM solve over T frames (T = 1: MPI-L, Eqs. 8-11; T > 1: the
+// dynamic problem with a spatiotemporal regulariser, frame t sampled by
+// plans[t], the maps shared, TV over the (t, y, x) grid of 2D frames).
+// Inputs: alpha (C x q), y (T x C x M), eps_d (T C, device).  Outputs: p_out
+// (T x N), hist (n_outer x 3).
+mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* const* plans, int T, const mpi_basis* basis, int C,
+                     const mpi_admm_params* prm, mpi_precision prec, Solver& sv, float2* base, double* dx,
+                     const mpi_c32* A, const float2* yc, const double* eps_d, float2* p_out, double* hist) {
+  Grid3 g = grid_of(plans[0]);
+  if (T > 1) {
+    g.nz = T;
+    g.nd = 3;
+  }
+  const long N1 = plans[0]->N, M = plans[0]->M, CM1 = (long)C * M;
+  const long N = (long)T * N1, TC = (long)T * C, CM = TC * M, CMs = std::max(CM, 1L);
   float2 *p = base, *p_prev = p + N, *u0 = p_prev + N, *z0 = u0 + N, *rhs = z0 + N, *t = rhs + N;
   float2 *r = t + N, *d = r + N, *Ad = d + N, *tvx = Ad + N, *P = tvx + N, *R = P + (size_t)g.nd * N;
   float2 *uk = R + (size_t)g.nd * N, *zk = uk + CMs, *Apk = zk + CMs, *Apk_prev = Apk + CMs, *wk = Apk_prev + CMs;
   (void)tvx;
   double* fball = dx;
-  double* bpart = fball + C;
+  double* bpart = fball + TC;
   TRY(sv.fill(p, make_float2(0.f, 0.f), N));
   TRY(sv.fill(u0, make_float2(0.f, 0.f), N));
   if (CM > 0) {
@@ -906,9 +915,11 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
   const mpi_precision pin = prec == MPI_PREC_MIXED ? MPI_PREC_BF16 : prec;
   const mpi_precision pout = prec == MPI_PREC_MIXED ? MPI_PREC_FP32 : prec;
   auto normal = [&](const float2* v, float2* out, mpi_precision pr) -> mpi_status {
-    // out = v + S^H F^H F S v
-    TRY(mpi_forward(ctx, plan, basis, A, C, (const mpi_c32*)v, (mpi_c32*)wk, pr));
-    TRY(mpi_adjoint(ctx, plan, basis, A, C, (const mpi_c32*)wk, (mpi_c32*)out, pr));
+    // out = v + S^H F^H F S v, frame by frame
+    for (int t = 0; t < T; ++t) {
+      TRY(mpi_forward(ctx, plans[t], basis, A, C, (const mpi_c32*)(v + t * N1), (mpi_c32*)(wk + t * CM1), pr));
+      TRY(mpi_adjoint(ctx, plans[t], basis, A, C, (const mpi_c32*)(wk + t * CM1), (mpi_c32*)(out + t * N1), pr));
+    }
     return sv.lincomb(out, out, 1.f, v, 1.f, N);
   };
 
@@ -919,16 +930,18 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
     // zk = Pi(F S p + uk)
     if (CM > 0) {
       MPI_PROF(ctx, KF_SOLVER);
-      k_ball_norm_partial<<<dim3(ball_blocks, C), kVecThreads, 0, ctx->stream>>>(Apk, uk, yc, (int)M, bpart);
+      k_ball_norm_partial<<<dim3(ball_blocks, (unsigned)TC), kVecThreads, 0, ctx->stream>>>(Apk, uk, yc, (int)M,
+                                                                                            bpart);
       MPI_LAUNCH_CHECK(ctx, "k_ball_norm_partial");
       MPI_PROF(ctx, KF_SOLVER);
-      k_ball_factor<<<1, kVecThreads, 0, ctx->stream>>>(bpart, ball_blocks, C, eps_d, fball);
+      k_ball_factor<<<1, kVecThreads, 0, ctx->stream>>>(bpart, ball_blocks, (int)TC, eps_d, fball);
       MPI_LAUNCH_CHECK(ctx, "k_ball_factor");
       MPI_PROF(ctx, KF_SOLVER);
-      k_ball_apply<<<grid_for(CM), kVecThreads, 0, ctx->stream>>>(Apk, uk, yc, C, (int)M, fball, zk);
+      k_ball_apply<<<grid_for(CM), kVecThreads, 0, ctx->stream>>>(Apk, uk, yc, (int)TC, (int)M, fball, zk);
       MPI_LAUNCH_CHECK(ctx, "k_ball_apply");
       TRY(sv.lincomb(wk, zk, 1.f, uk, -1.f, CM));
-      TRY(mpi_adjoint(ctx, plan, basis, A, C, (const mpi_c32*)wk, (mpi_c32*)rhs, pout));
+      for (int t = 0; t < T; ++t)
+        TRY(mpi_adjoint(ctx, plans[t], basis, A, C, (const mpi_c32*)(wk + t * CM1), (mpi_c32*)(rhs + t * N1), pout));
       TRY(sv.lincomb(rhs, rhs, 1.f, z0, 1.f, N));
       TRY(sv.lincomb(rhs, rhs, 1.f, u0, -1.f, N));
     } else {
@@ -960,7 +973,8 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
     k_dual_update<<<grid_for(N), kVecThreads, 0, ctx->stream>>>(u0, p, z0, N);
     MPI_LAUNCH_CHECK(ctx, "k_dual_update");
     if (CM > 0) {
-      TRY(mpi_forward(ctx, plan, basis, A, C, (const mpi_c32*)p, (mpi_c32*)Apk, pout));
+      for (int t = 0; t < T; ++t)
+        TRY(mpi_forward(ctx, plans[t], basis, A, C, (const mpi_c32*)(p + t * N1), (mpi_c32*)(Apk + t * CM1), pout));
       MPI_PROF(ctx, KF_SOLVER);
       k_dual_update<<<grid_for(CM), kVecThreads, 0, ctx->stream>>>(uk, Apk, zk, CM);
       MPI_LAUNCH_CHECK(ctx, "k_dual_update");
@@ -981,33 +995,49 @@ mpi_status admm_body(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
 
 }  // namespace
 
-extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
-                                      const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
-                                      const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out,
-                                      mpi_precision prec) {
+namespace {
+
+mpi_status image_solve_impl(mpi_ctx* ctx, const mpi_plan* const* plans, int T, const mpi_basis* basis,
+                            const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
+                            const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out, mpi_precision prec) {
   if (!ctx) return MPI_ERR_ARG;
-  if (!plan || !basis || !alpha || !eps || !prm || !p_out || C < 1 || (plan->M > 0 && !y))
+  if (!plans || T < 1 || !plans[0] || !basis || !alpha || !eps || !prm || !p_out || C < 1 ||
+      (plans[0]->M > 0 && !y))
     return set_err(ctx, MPI_ERR_ARG, "image_solve: bad argument");
+  for (int t = 1; t < T; ++t) {
+    const mpi_plan* a = plans[0];
+    const mpi_plan* b = plans[t];
+    if (!b) return set_err(ctx, MPI_ERR_ARG, "image_solve: null plan");
+    if (b->ndim != 2 || a->ndim != 2 || b->ny != a->ny || b->nx != a->nx || b->M != a->M || b->ctx != a->ctx)
+      return set_err(ctx, MPI_ERR_SHAPE, "dynamic image_solve: frames need 2D plans of one grid and sample count");
+  }
   if (prm->n_outer < 0 || prm->n_cg < 0 || prm->n_tv < 0 || !(prm->rho0 > 0) || !(prm->tau > 0))
     return set_err(ctx, MPI_ERR_ARG, "image_solve: bad parameters");
-  for (int c = 0; c < C; ++c)
+  const long TC = (long)T * C;
+  for (long c = 0; c < TC; ++c)
     if (!(eps[c] >= 0)) return set_err(ctx, MPI_ERR_ARG, "eps must be >= 0");
   cudaSetDevice(ctx->device);
-  TRY(mpi_ctx_reserve(ctx, plan, basis, C));
-  const Grid3 gr = grid_of(plan);
-  const long N = plan->N, M = plan->M, CM = (long)C * M, CMs = std::max(CM, 1L), Cq = (long)C * basis->q;
-  SolverGraph* g = cache_find(ctx, 1, plan, basis, C, prec, prm, sizeof(*prm));
+  for (int t = 0; t < T; ++t) TRY(mpi_ctx_reserve(ctx, plans[t], basis, C));
+  Grid3 gr = grid_of(plans[0]);
+  if (T > 1) gr.nd = 3;
+  const long N = (long)T * plans[0]->N, CM = TC * plans[0]->M, CMs = std::max(CM, 1L), Cq = (long)C * basis->q;
+  // the cache key: the parameters, then the frame count and every frame's plan
+  std::vector<unsigned char> key((const unsigned char*)prm, (const unsigned char*)prm + sizeof(*prm));
+  key.insert(key.end(), (const unsigned char*)&T, (const unsigned char*)&T + sizeof(T));
+  key.insert(key.end(), (const unsigned char*)plans, (const unsigned char*)(plans + T));
+  SolverGraph* g = cache_find(ctx, 1, plans[0], basis, C, prec, key.data(), key.size());
   if (!g) {
     g = new SolverGraph();
     g->kind = 1;
-    g->plan = plan;
+    g->plan = plans[0];
+    g->others.assign(plans, plans + T);
     g->basis = basis;
     g->C = C;
     g->prec = prec;
-    g->key.assign((const unsigned char*)prm, (const unsigned char*)prm + sizeof(*prm));
+    g->key = key;
     // image side: 10 N + 2 nd N; k-space: 5 CM; inputs y (CM), alpha (Cq); output p (N)
     const size_t elems = 10 * N + 2 * (size_t)gr.nd * N + 5 * CMs + CMs + Cq + N;
-    const size_t extra = 2 * (size_t)C + (size_t)C * kRedBlocks + 3 * (size_t)prm->n_outer + C + 8;
+    const size_t extra = 2 * (size_t)TC + (size_t)TC * kRedBlocks + 3 * (size_t)prm->n_outer + TC + 8;
     mpi_status st = alloc_solver(ctx, g->mem, elems, extra, g->sv, &g->base, &g->dbase);
     if (st) {
       delete g;
@@ -1017,16 +1047,17 @@ extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const 
     g->in_y = io;
     g->in_alpha = io + CMs;
     g->out_p = g->in_alpha + Cq;
-    double* scratch = g->dbase;                                   // fball, bpart
-    g->hist = scratch + 2 * (size_t)C + (size_t)C * kRedBlocks;  // [n_outer][3]
+    double* scratch = g->dbase;                                     // fball, bpart
+    g->hist = scratch + 2 * (size_t)TC + (size_t)TC * kRedBlocks;  // [n_outer][3]
     g->in_eps = g->hist + 3 * (size_t)prm->n_outer;
     g->work = ctx->work;
-    if ((st = tune_line_passes(ctx, plan, C))) {
+    for (int t = 0; t < T && st == MPI_OK; ++t) st = tune_line_passes(ctx, plans[t], C);
+    if (st) {
       delete g;
       return st;
     }
     st = capture(ctx, g, [&]() {
-      return admm_body(ctx, plan, basis, C, prm, prec, g->sv, g->base, scratch, (const mpi_c32*)g->in_alpha,
+      return admm_body(ctx, plans, T, basis, C, prm, prec, g->sv, g->base, scratch, (const mpi_c32*)g->in_alpha,
                        g->in_y, g->in_eps, g->out_p, g->hist);
     });
     if (st) {
@@ -1040,7 +1071,7 @@ extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const 
   if (CM > 0)
     TRY(cuda_check(ctx, cudaMemcpyAsync(g->in_y, y, CM * sizeof(float2), cudaMemcpyDeviceToDevice, ctx->stream),
                    "input copy"));
-  TRY(cuda_check(ctx, cudaMemcpyAsync(g->in_eps, eps, C * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+  TRY(cuda_check(ctx, cudaMemcpyAsync(g->in_eps, eps, TC * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
                  "eps copy"));
   TRY(launch_graph(ctx, g));
   TRY(cuda_check(ctx, cudaMemcpyAsync(p_out, g->out_p, N * sizeof(float2), cudaMemcpyDeviceToDevice, ctx->stream),
@@ -1051,11 +1082,29 @@ extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const 
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "image_solve");
 }
 
+}  // namespace
+
+extern "C" mpi_status mpi_image_solve(mpi_ctx* ctx, const mpi_plan* plan, const mpi_basis* basis,
+                                      const mpi_c32* alpha, int C, const mpi_c32* y, const double* eps,
+                                      const mpi_admm_params* prm, mpi_c32* p_out, double* hist_out,
+                                      mpi_precision prec) {
+  return image_solve_impl(ctx, &plan, 1, basis, alpha, C, y, eps, prm, p_out, hist_out, prec);
+}
+
+extern "C" mpi_status mpi_image_solve_dynamic(mpi_ctx* ctx, const mpi_plan* const* plans, int T,
+                                              const mpi_basis* basis, const mpi_c32* alpha, int C, const mpi_c32* y,
+                                              const double* eps, const mpi_admm_params* prm, mpi_c32* p_out,
+                                              double* hist_out, mpi_precision prec) {
+  return image_solve_impl(ctx, plans, T, basis, alpha, C, y, eps, prm, p_out, hist_out, prec);
+}
+
 void solver_cache_forget(mpi_ctx* ctx, const void* object) {
   if (!ctx || !ctx->solver_cache) return;
   SolverCache* c = (SolverCache*)ctx->solver_cache;
   for (size_t i = 0; i < c->entries.size();) {
-    if (c->entries[i]->plan == object || c->entries[i]->basis == object) {
+    const std::vector<const mpi_plan*>& o = c->entries[i]->others;
+    if (c->entries[i]->plan == object || c->entries[i]->basis == object ||
+        std::find(o.begin(), o.end(), (const mpi_plan*)object) != o.end()) {
       delete c->entries[i];
       c->entries.erase(c->entries.begin() + i);
     } else {

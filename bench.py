@@ -26,6 +26,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -684,8 +685,26 @@ def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
     hbm, _, src = load_peaks()
     out = {"slices": cfg["slices"], "coils_total": int(coils.sum()),
            "grid_counts": {int(k): int((sizes == k).sum()) for k in cfg["sizes"]}}
+    _, bf16_peak, _ = load_peaks()
     for prec in ("fp32", "bf16"):
+        n_rec = len(ctx.tuning_records())
         batch = mp.Batch(ctx, slices, kind="pair", prec=prec)
+        # the grouped expansions' timings from the batch's tuning records
+        grouped = []
+        for rec in ctx.tuning_records()[n_rec:]:
+            m = re.match(r"grouped expansion \((\d+) slices, N=(\d+), q=(\d+), sumC=(\d+), (\w+)\):.* chose (\d+) "
+                         r"\(([\d.]+) us\)", rec)
+            if not m:
+                continue
+            ns, N, q, sumC, pr, ctas, us = m.groups()
+            N, q, sumC, us = int(N), int(q), int(sumC), float(us)
+            flops = 2.0 * N * (2 * q) * (2 * sumC)  # the real-ified GEMM, counted once
+            ub = (2 if prec == "bf16" else 4) * N * 2 * q
+            byts = ub + 8 * sumC * N + 8 * sumC * q + 8 * int(ns) * N  # basis, per-coil images out, alpha, images in
+            grouped.append({"slices": int(ns), "N": N, "q": q, "coils": sumC, "ctas_per_row": int(ctas),
+                            "us_per_launch": us, "tflops": flops / (us * 1e-6) / 1e12,
+                            "frac_of_bf16_tensor_peak": flops / (us * 1e-6) / 1e12 / bf16_peak,
+                            "hbm_gbs": byts / (us * 1e-6) / 1e9, "frac_of_hbm_peak": byts / (us * 1e-6) / 1e9 / hbm})
         for _ in range(warmup):
             batch.run()
         torch.cuda.synchronize()
@@ -702,7 +721,8 @@ def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
         ms = total / steps
         achieved = exam_bytes[prec] / (ms * 1e-3) / 1e9
         out[prec] = {"value": cfg["slices"] * 1000.0 / ms, "unit": "slice pairs/s", "ms_per_exam": ms,
-                     "graph_kernels": batch.kernels(),
+                     "graph_kernels": batch.kernels(), "grouped_launches_per_direction": batch.groups(),
+                     "grouped_expansion": grouped,
                      "roofline": {"bound": "hbm", "kernel": "whole exam (every kernel of the replayed graph)",
                                   "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                                   "algorithmic_bytes_per_exam": exam_bytes[prec], "traffic": None,

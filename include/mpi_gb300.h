@@ -395,6 +395,10 @@ mpi_status mpi_batch_create(mpi_ctx* ctx, const mpi_batch_slice* slices, int n, 
 mpi_status mpi_batch_run(mpi_ctx* ctx, mpi_batch* batch);
 /* Kernels one replay launches (-1 for a NULL batch). */
 int64_t mpi_batch_kernel_count(const mpi_batch* batch);
+/* Grouped expansion launches per direction in the batch (slices on Cartesian
+ * plans sharing a dense basis, FP32 or BF16, are expanded by one launch per
+ * group whose grid rows are the slices), or -1 for a null handle. */
+int mpi_batch_group_count(const mpi_batch* batch);
 mpi_status mpi_batch_destroy(mpi_batch* batch);
 
 /* ----------------------------------------------------------------- solvers */

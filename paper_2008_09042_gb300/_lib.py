@@ -28,6 +28,7 @@ EXPORTS = [
     "mpi_batch_destroy", "mpi_expand_path", "mpi_forward_host", "mpi_adjoint_host", "mpi_maxwell_basis_2d",
     "mpi_forward_maps", "mpi_adjoint_maps", "mpi_jacobian_maps", "mpi_jacobian_adjoint_maps", "mpi_sm_estimate_maps",
     "mpi_maxwell_basis_3d", "mpi_tucker_compress", "mpi_image_solve_dynamic",
+    "mpi_batch_group_count",
 ]
 
 
@@ -146,6 +147,8 @@ def load(path=LIB_PATH):
     lib.mpi_ctx_workspace_bytes.restype = i64
     lib.mpi_batch_kernel_count.argtypes = [vp]
     lib.mpi_batch_kernel_count.restype = i64
+    lib.mpi_batch_group_count.argtypes = [vp]
+    lib.mpi_batch_group_count.restype = i
     _lib = lib
     return lib
 

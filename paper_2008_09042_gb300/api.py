@@ -577,6 +577,10 @@ class Batch:
     def kernels(self):
         return int(self.ctx.lib.mpi_batch_kernel_count(self.h))
 
+    def groups(self):
+        """Grouped expansion launches per direction (slices sharing a basis)."""
+        return int(self.ctx.lib.mpi_batch_group_count(self.h))
+
     def close(self):
         if getattr(self, "h", None):
             self.ctx.lib.mpi_batch_destroy(self.h)

@@ -1088,3 +1088,35 @@ extern "C" mpi_status mpi_jacobian_adjoint_maps(mpi_ctx* ctx, const mpi_plan* pl
   }
   return MPI_OK;
 }
+
+// ----------------------------------------------------------- grouped batches
+
+bool rows_supported(const mpi_basis* basis, int Cmax, mpi_precision prec) {
+  if (basis->tucker || Cmax < 1) return false;
+  if (prec == MPI_PREC_BF16) return basis->Ubf && 2 * ((2 * Cmax + 15) / 16 * 8) <= 256;
+  if (prec == MPI_PREC_FP32) return tf32_supported(basis, EX_FWD, Cmax) && tf32_supported(basis, EX_ADJ, Cmax);
+  return false;
+}
+
+mpi_status expand_rows(mpi_ctx* ctx, const mpi_plan* plan0, const mpi_basis* basis, int mode, const ExpandRow* rows,
+                       int nrows, int Cmax, mpi_precision prec, int row_ctas) {
+  if (!rows_supported(basis, Cmax, prec)) return set_err(ctx, MPI_ERR_UNSUPPORTED, "grouped expansion: shape");
+  if (nrows < 1 || nrows > 65535) return set_err(ctx, MPI_ERR_SHAPE, "grouped expansion: row count");
+  ExpandArgs a = base_args(plan0, basis, Cmax);
+  a.rows = rows;
+  a.nrows = nrows;
+  a.row_ctas = row_ctas;
+  a.kname = mode == EX_FWD ? "k_expand<grouped fwd>" : "k_expand<grouped adj>";
+  if (prec == MPI_PREC_BF16) return launch_expand_tc(ctx, basis, mode, a);
+  return launch_expand_tf32(ctx, basis, mode, a);
+}
+
+mpi_status plan_image_to_kspace(mpi_ctx* ctx, const mpi_plan* plan, float2* v, int C, float2* y) {
+  if (plan->kind != MPI_TRAJ_CARTESIAN) return set_err(ctx, MPI_ERR_UNSUPPORTED, "grouped batch: Cartesian plans");
+  return image_to_kspace(ctx, plan, v, C, y, nullptr);
+}
+
+mpi_status plan_kspace_to_image(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C, float2* w) {
+  if (plan->kind != MPI_TRAJ_CARTESIAN) return set_err(ctx, MPI_ERR_UNSUPPORTED, "grouped batch: Cartesian plans");
+  return kspace_to_image(ctx, plan, y, C, w, nullptr);
+}

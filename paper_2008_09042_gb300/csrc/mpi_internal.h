@@ -203,6 +203,17 @@ struct ScatterMap {
   int im = 0;
 };
 
+// One row of a grouped expansion launch (grid row blockIdx.y): a slice that
+// shares the basis, with its own coefficients, image, per-coil data and output.
+struct ExpandRow {
+  const float2* alpha;
+  const float2* p;
+  const float2* w;
+  float2* out;
+  int C;
+  int pad;
+};
+
 struct ExpandArgs {
   const float2* U = nullptr;  // [q][N]
   int N = 0, q = 0;
@@ -225,6 +236,11 @@ struct ExpandArgs {
   const char* kname = nullptr;  // name of the launch in the per-kernel timing (default: the kernel's)
   ScatterMap sc;                // EX_SCATTER output map
   int accumulate = 0;           // EX_FWD / EX_JFWD: add into out instead of storing (several sets of maps)
+  // Grouped launch (tensor-core kernels): device table of nrows rows, C = the
+  // largest row's coil count; row_ctas CTAs per row (0: the SMs shared out).
+  const ExpandRow* rows = nullptr;
+  int nrows = 0;
+  int row_ctas = 0;
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
@@ -276,6 +292,14 @@ mpi_status jacobi_columns(mpi_ctx* ctx, double2* M, int L, int nj, double2* V, d
 // tmp holds q r1 (n2 n3 + r2 n3) complex values.
 mpi_status tucker_project(mpi_ctx* ctx, const float2* T, int q, const int n[3], const int r[3], const float2* F0,
                           const float2* F1, const float2* F2, float2* core, float2* tmp);
+// Grouped batch pieces (api.cu): one expansion launch over the rows of slices
+// that share `basis` (grid geometry from plan0), and a Cartesian plan's
+// image -> k-space / k-space -> image passes on a caller buffer.
+mpi_status expand_rows(mpi_ctx* ctx, const mpi_plan* plan0, const mpi_basis* basis, int mode, const ExpandRow* rows,
+                       int nrows, int Cmax, mpi_precision prec, int row_ctas);
+bool rows_supported(const mpi_basis* basis, int Cmax, mpi_precision prec);
+mpi_status plan_image_to_kspace(mpi_ctx* ctx, const mpi_plan* plan, float2* v, int C, float2* y);
+mpi_status plan_kspace_to_image(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C, float2* w);
 // U^H V on the tensor cores where the basis and precision allow, else on the CUDA cores.
 mpi_status uh_v(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int C, float2* dalpha, float2* partials,
                 size_t partial_cap, mpi_precision prec);

@@ -37,6 +37,7 @@ struct TcArgs {
   int sc_L0, sc_L1, sc_im, sc_col0;
   long sc_hi, sc_mid, sc_col;
   int accumulate;         // EX_FWD / EX_JFWD: add into out instead of storing
+  const ExpandRow* rows;  // grouped launch: row blockIdx.y's pointers and coil count (nullptr: none)
   long long wait_cycles;  // bounded-wait limit (SM clock cycles)
   int stall_after;        // fault injection: the producer stops after this many stages (-1: off)
 };

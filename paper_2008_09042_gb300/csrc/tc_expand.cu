@@ -38,8 +38,17 @@ constexpr int kMaxStages = 12;
 constexpr int kThreads = 192;
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a,
+__global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a_in,
                                                             int stages) {
+  TcArgs a = a_in;
+  if (a.rows) {  // grouped launch: this row's slice
+    const ExpandRow r = a.rows[blockIdx.y];
+    a.alpha = r.alpha;
+    a.p = r.p;
+    a.w = r.w;
+    a.out = r.out;
+    a.C = r.C;
+  }
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int Kp = a.KC * kKChunk;
@@ -274,6 +283,7 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.err = ctx->dev_err;
   a.wait_cycles = ctx->wait_cycles;
   a.accumulate = x.accumulate;
+  a.rows = x.rows;
   a.stall_after = -1;
   a.tuck_B = x.tuck_B;
   a.group_coils = 0;
@@ -295,7 +305,9 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   if (stages < 2) return set_err(ctx, MPI_ERR_UNSUPPORTED, "BF16 expansion: shared memory");
   const size_t smem = fixed + (size_t)stages * kStageBytes;
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
-  const int grid = std::min(n_tiles, per_sm * std::max(ctx->num_sms, 1));
+  const int nrows = x.rows ? x.nrows : 1;
+  const int per_row = x.rows && x.row_ctas > 0 ? x.row_ctas : std::max(per_sm * std::max(ctx->num_sms, 1) / nrows, 1);
+  const dim3 grid((unsigned)std::min(n_tiles, per_row), (unsigned)nrows);
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap;
   cudaError_t e = cudaSuccess;
 #define MPI_TC_CASE(m)                                                                                        \

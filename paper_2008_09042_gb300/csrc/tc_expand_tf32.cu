@@ -91,6 +91,14 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
   // rows of a launch stream the same basis tiles in the same order, so all but
   // one of them mostly find each tile in L2.
   TcArgs a = a_in;
+  if (a.rows) {  // grouped launch: this row's slice
+    const ExpandRow r = a.rows[blockIdx.y];
+    a.alpha = r.alpha;
+    a.p = r.p;
+    a.w = r.w;
+    a.out = r.out;
+    a.C = r.C;
+  }
   if (a.group_coils) {
     const int c0 = (int)blockIdx.y * a.group_coils;
     a.C = min(a.group_coils, a.C_total - c0);
@@ -458,6 +466,7 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.err = ctx->dev_err;
   a.wait_cycles = ctx->wait_cycles;
   a.accumulate = x.accumulate;
+  a.rows = x.rows;
   a.stall_after = ctx->stall_after;
   a.tuck_B = x.tuck_B;
   a.tuck_stride = x.tuck_stride;
@@ -472,8 +481,11 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.C_total = x.C;
   if (groups > 1) a.C = Cg;
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
-  // one CTA per SM over all groups
-  const dim3 grid((unsigned)std::min(n_tiles, std::max(std::max(ctx->num_sms, 1) / groups, 1)), (unsigned)groups);
+  // one CTA per SM over all groups (or rows of a grouped launch)
+  const int nrows = x.rows ? x.nrows : groups;
+  if (x.rows) a.group_coils = 0;
+  const int per_row = x.rows && x.row_ctas > 0 ? x.row_ctas : std::max(std::max(ctx->num_sms, 1) / nrows, 1);
+  const dim3 grid((unsigned)std::min(n_tiles, per_row), (unsigned)nrows);
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap32;
   cudaError_t e = cudaSuccess;
 #define MPI_TF_CASE(m)                                                                                        \

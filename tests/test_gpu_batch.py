@@ -40,7 +40,10 @@ def test_batch_pair_matches_single_calls(prec):
         slices.append(dict(plan=plan, basis=B, alpha=a, p=p, y=y, x=x))
         refs.append((U, idx, n))
     batch = mp.Batch(ctx, slices, kind="pair", prec=prec)
-    assert batch.kernels() >= 6 * len(slices)
+    # the slices of each grid share a basis: one grouped expansion per grid and
+    # direction, and every slice's four FFT / gather passes
+    assert batch.groups() == 3
+    assert batch.kernels() == 4 * len(slices) + 2 * 3
     for rep in range(2):
         for s in slices:
             s["y"].zero_()

@@ -93,13 +93,15 @@ def test_tucker_operator_full_size(ctx, mp, c5, prec):
 def test_batched_exam_slice_shapes(ctx, mp, prec):
     cfg = w.workload("batched2d_64slices")
     shapes = [(192, 16), (256, 32), (320, 16), (320, 32)]
-    slices, refs = [], []
+    slices, refs, bases = [], [], {}
     for i, (n, C) in enumerate(shapes):
         q = cfg["q_by_size"][n]
         U = q32(w.smooth_orthonormal_basis(n, n, q, seed=w.BASE_SEED + n))
         idx = w.mask_to_indices(w.poisson_disc_mask(n, n, 4 + i, calib=(24, 24), seed=w.BASE_SEED + 10 * n + i))
         plan = mp.Plan(ctx, (n, n), sample_idx=idx)
-        B = mp.Basis(ctx, U.T)
+        if n not in bases:  # the two 320^2 slices share one basis: a grouped expansion
+            bases[n] = mp.Basis(ctx, U.T)
+        B = bases[n]
         a = q32(w.random_coefficients(C, q, seed=40 + i))
         p = q32(w.random_ellipses(n, n, seed=50 + i).ravel())
         slices.append(dict(plan=plan, basis=B, alpha=c64(a), p=c64(p),
@@ -107,6 +109,7 @@ def test_batched_exam_slice_shapes(ctx, mp, prec):
                            x=torch.empty((n * n,), dtype=torch.complex64, device="cuda")))
         refs.append((fourier.CartesianSampling((n, n), idx), U, a, p))
     batch = mp.Batch(ctx, slices, kind="pair", prec=prec)
+    assert batch.groups() == 1
     batch.run()
     ctx.synchronize()
     for s, (Fs, U, a, p) in zip(slices, refs):

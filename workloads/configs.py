@@ -22,7 +22,7 @@ WORKLOADS = {
     ),
     "radial2d_256_c12_q96": dict(
         kind="radial", dims=(256, 256), C=12, q=96, spokes=64, readout=512, W=6, sigma=2.0,
-        snr_db=30.0,
+        snr_db=30.0, n_irgn=20, n_admm=50,
     ),
     "batched2d_64slices": dict(
         kind="batched", slices=64, sizes=(128, 192, 256, 320), coils=(8, 16, 32),

@@ -11,17 +11,25 @@ from .configs import workload
 from .masks import mask_to_indices, poisson_disc_mask, vd_lines_mask
 from .phantom import random_ellipses
 from .standin import smooth_orthonormal_basis
+from .trajectory import golden_angle_radial
 
 RECON_SEED = 20200820 + 500
 
 
 def recon_case(name):
-    """(cfg, U [N][q] complex128 of complex64 values, sample indices, alpha_true, p_true)."""
+    """(cfg, U [N][q] complex128 of complex64 values, sampling, alpha_true, p_true):
+    the sampling is the sorted sample indices of a Cartesian workload or the
+    (M, 2) float32 k-space trajectory (rad/pixel) of a radial one."""
     cfg = workload(name)
     ny, nx = cfg["dims"]
     C, q = cfg["C"], cfg["q"]
     base = RECON_SEED
     U = smooth_orthonormal_basis(ny, nx, q, seed=base).astype(np.complex64).astype(np.complex128)
+    if cfg["kind"] == "radial":
+        k = golden_angle_radial(cfg["spokes"], cfg["readout"]).astype(np.float32)
+        a_true = random_coefficients(C, q, seed=base + 2)
+        p_true = random_ellipses(ny, nx, seed=base + 3).ravel().astype(np.complex128)
+        return cfg, U, k, a_true, p_true
     if cfg["mask"] == "poisson":
         mask = poisson_disc_mask(ny, nx, cfg["R"], calib=cfg["calib"], seed=base + 1)
     else:

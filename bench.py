@@ -153,6 +153,8 @@ def kernel_bytes_per_pair(case, prec):
         # the per-plane kernel: passes along y and x with the gather (forward)
         # or the scatter (adjoint), one read and one write
         "k_plane_yx<fwd>": V + Y, "k_plane_yx<inv>": Y + V,
+        # the same passes as the pipelined persistent kernel (TMA tiles)
+        "k_plane_pipe<fwd>": V + Y, "k_plane_pipe<inv>": Y + V,
     }
     if case["tucker"]:
         n1, n2, n3 = case["dims"]
@@ -416,7 +418,8 @@ def slice_line(mp, ctx, dev, flush, stream, name, prec_list=("fp32", "bf16"), st
     return out
 
 
-def jacobian_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", steps=10, warmup=3):
+def jacobian_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", steps=10, warmup=3,
+                  precs=("fp32", "bf16", "fp32_simt")):
     """Jacobian + Jacobian-adjoint pairs (the operator of every IRGN CG
     iteration) per precision, with the roofline of the adjoint's coefficient
     block dalpha = U^H v (k_uh_tc on the tensor cores; k_uh_v, the CUDA-core
@@ -439,7 +442,7 @@ def jacobian_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", steps
         mp.jacobian_adjoint(ctx, plan, basis, a_d, p_d, r, prec, out_p=gp, out_alpha=ga)
 
     out = {}
-    for prec in ("fp32", "bf16", "fp32_simt"):
+    for prec in precs:
         for _ in range(warmup):
             run(prec)
         torch.cuda.synchronize()
@@ -464,7 +467,7 @@ def jacobian_line(mp, ctx, dev, flush, stream, name="cart2d_256_c16_q128", steps
         uh = {"fp32": "k_uh_tc<tf32x3>", "bf16": "k_uh_tc<bf16>", "fp32_simt": "k_uh_v"}[prec]
         entry = {"value": 1000.0 / ms, "unit": "Jacobian + adjoint pairs/s", "ms_per_pair": ms,
                  "kernels": {k: round(v[0] * 1e3, 2) for k, v in per.items()}}
-        if uh in per:
+        if uh in per and not case["tucker"]:
             # algorithmic bytes: the basis (FP32 view 8 N q, BF16 view 4 N q) and v (8 C N) once
             ub = (4 if prec == "bf16" else 8) * N * q
             b = ub + 8 * C * N
@@ -731,7 +734,8 @@ def batched_slices(mp, ctx, dev, flush, stream, steps=5, warmup=2):
     return out
 
 
-def recon_per_slice(mp, ctx, dev, names=("cart2d_64_c4_q32", "cart2d_256_c16_q128", "cart2d_320_c16_q100"),
+def recon_per_slice(mp, ctx, dev, names=("cart2d_64_c4_q32", "cart2d_256_c16_q128", "cart2d_320_c16_q100",
+                                         "radial2d_256_c12_q96"),
                     precs=("fp32", "bf16", "mixed"), reps=2):
     """MPI-BL (20 IRGN x 10 CG) + MPI-L (50 ADMM x 5 CG x 10 TV) wall time per
     slice for each precision, on data and against reconstructions the FP64
@@ -748,10 +752,13 @@ def recon_per_slice(mp, ctx, dev, names=("cart2d_64_c4_q32", "cart2d_256_c16_q12
             out[name] = {"unavailable": f"{os.path.relpath(path, ROOT)} missing"}
             continue
         g = np.load(path)
-        cfg, U, idx, _, _ = w.recon_case(name)
+        cfg, U, samp, _, _ = w.recon_case(name)
         ny, nx = cfg["dims"]
         C = cfg["C"]
-        plan = mp.Plan(ctx, (ny, nx), sample_idx=idx)
+        if cfg["kind"] == "radial":
+            plan = mp.Plan(ctx, (ny, nx), traj=samp, kb_width=cfg["W"], oversamp=cfg["sigma"])
+        else:
+            plan = mp.Plan(ctx, (ny, nx), sample_idx=samp)
         B = mp.Basis(ctx, U.T)
         y = torch.from_numpy(np.ascontiguousarray(g["y"])).to(dev)
         eps = g["eps"]
@@ -772,7 +779,7 @@ def recon_per_slice(mp, ctx, dev, names=("cart2d_64_c4_q32", "cart2d_256_c16_q12
             res[prec] = {"ms_per_slice": 1000.0 * min(times),
                          "nrmse_coil_images_vs_oracle": float(np.linalg.norm(ci - ref_ci) / np.linalg.norm(ref_ci)),
                          "nrmse_image_vs_oracle": float(np.linalg.norm(x - ref_p) / np.linalg.norm(ref_p))}
-        out[name] = {"dims": list(cfg["dims"]), "C": C, "q": cfg["q"], "M": int(idx.size), **res}
+        out[name] = {"dims": list(cfg["dims"]), "C": C, "q": cfg["q"], "M": int(plan.M), **res}
         del plan, B
     return out
 
@@ -945,6 +952,8 @@ def run_ours(args):
         wl = {k: v for k, v in wl.items() if v is not None}
         wl["radial2d_256_c12_q96"] = radial_line(mp, ctx, dev, flush, stream)
         wl["cart2d_256_c16_q128/jacobian"] = jacobian_line(mp, ctx, dev, flush, stream)
+        wl[f"{HEADLINE}/jacobian"] = jacobian_line(mp, ctx, dev, flush, stream, name=HEADLINE,
+                                                   precs=("fp32", "bf16"), steps=5)
         wl["maxwell_basis_2d_256_q128"] = maxwell_basis_line(mp, ctx)
         wl["cart2d_256_c16_q128/two_sets_of_maps"] = multimap_line(mp, ctx, dev, flush, stream)
         wl["dynamic_mpi_l_256_c16_q128_t8"] = dynamic_line(mp, ctx, dev)

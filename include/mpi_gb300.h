@@ -118,9 +118,12 @@ mpi_status mpi_ctx_set_autotune(mpi_ctx* ctx, int enable);
  * CTA (shared-memory Stockham passes), -1 the register two-step pass along y
  * (lengths 64, 96, 128, 192, 256), 0 back to tuning.  A pass the choice does
  * not cover keeps its tuned or default kernel.  3D Tucker volumes with planes
- * of 64, 96 or 128 squared run the passes along y and x as one kernel per
- * (coil, kz) plane unless the choice is -2 (separate, tuned passes).
- * MPI_ERR_ARG for other values. */
+ * of 64, 96 or 128 squared run the passes along y and x as one kernel over
+ * the (coil, kz) planes unless the choice is -2 (separate, tuned passes): a
+ * persistent kernel that streams the planes through shared memory in TMA
+ * tiles where each plane's rows with samples fit beside the tiles, else, and
+ * always with the choice -3, one CTA per plane.  MPI_ERR_ARG for other
+ * values. */
 mpi_status mpi_ctx_set_line_kernel(mpi_ctx* ctx, int choice);
 mpi_status mpi_ctx_tuning_record(const mpi_ctx* ctx, int index, const char** text_out);
 /* Per-launch device timing: while enabled, every kernel the context launches is

@@ -459,10 +459,12 @@ extern "C" mpi_status mpi_ctx_inject_stall(mpi_ctx* ctx, int stages) {
 
 extern "C" mpi_status mpi_ctx_set_line_kernel(mpi_ctx* ctx, int choice) {
   if (!ctx) return MPI_ERR_ARG;
-  if (choice != 0 && choice != 8 && choice != 16 && choice != 32 && choice != -1 && choice != -2)
-    return set_err(ctx, MPI_ERR_ARG, "line kernel choice must be 0, 8, 16, 32, -1 or -2");
-  // -2: separate passes along y and x in 3D (no plane kernel), tuned line passes
+  if (choice != 0 && choice != 8 && choice != 16 && choice != 32 && choice != -1 && choice != -2 && choice != -3)
+    return set_err(ctx, MPI_ERR_ARG, "line kernel choice must be 0, 8, 16, 32, -1, -2 or -3");
+  // -2: separate passes along y and x in 3D (no plane kernel), tuned line passes;
+  // -3: the plane kernel with one CTA per plane instead of the pipelined one
   ctx->plane_pass = choice != -2;
+  ctx->plane_pipe = choice != -3;
   ctx->line_kernel = choice == -2 ? 0 : choice;
   return MPI_OK;
 }
@@ -541,6 +543,33 @@ extern "C" mpi_status mpi_plan_create(mpi_ctx* ctx, const mpi_plan_desc* d, mpi_
     if (e == cudaSuccess && any_empty) e = cudaMalloc(&plan->row_has, row_has.size());
     if (e == cudaSuccess && any_empty)
       e = cudaMemcpy(plan->row_has, row_has.data(), row_has.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && d->ndim == 3) {
+      // per kz plane, the rows with samples (the pipelined plane passes keep
+      // only those rows of a plane in shared memory)
+      std::vector<int32_t> cnt(nz, 0);
+      std::vector<int16_t> slot((size_t)nz * ny, (int16_t)-1);
+      for (int kz = 0; kz < nz; ++kz)
+        for (int ky = 0; ky < ny; ++ky)
+          if (row_has[(size_t)kz * ny + ky]) slot[(size_t)kz * ny + ky] = (int16_t)cnt[kz]++;
+      plan->plane_kmax = nz > 0 ? *std::max_element(cnt.begin(), cnt.end()) : 0;
+      const int kcap = std::max(plan->plane_kmax, 1);
+      std::vector<int4> rows((size_t)nz * kcap, make_int4(-1, 0, 0, 0));
+      for (int kz = 0; kz < nz; ++kz)
+        for (int ky = 0; ky < ny; ++ky) {
+          const int s = slot[(size_t)kz * ny + ky];
+          const int r = kz * ny + ky;
+          if (s >= 0) rows[(size_t)kz * kcap + s] = make_int4(ky, row_ptr[r], row_ptr[r + 1], 0);
+        }
+      e = cudaMalloc(&plan->plane_rows, rows.size() * sizeof(int4));
+      if (e == cudaSuccess) e = cudaMalloc(&plan->plane_nrows, cnt.size() * sizeof(int32_t));
+      if (e == cudaSuccess) e = cudaMalloc(&plan->plane_slot, slot.size() * sizeof(int16_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(plan->plane_rows, rows.data(), rows.size() * sizeof(int4), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(plan->plane_nrows, cnt.data(), cnt.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(plan->plane_slot, slot.data(), slot.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && d->M > 0) {
       e = cudaMalloc(&plan->idx, (size_t)d->M * sizeof(int32_t));
       if (e == cudaSuccess)
@@ -595,8 +624,9 @@ extern "C" mpi_status mpi_plan_destroy(mpi_plan* plan) {
     solver_cache_forget(plan->ctx, plan);
     ctx_release(&plan->ctx);
   }
-  void* ptrs[] = {plan->idx, plan->row_ptr, plan->row_has, plan->traj, plan->gstart, plan->gw, plan->deap, plan->cell_ptr,
-                  plan->cell_rank, plan->cell_sx, plan->cell_w, plan->cell_dense,
+  void* ptrs[] = {plan->idx,        plan->row_ptr,     plan->row_has,    plan->plane_rows, plan->plane_nrows,
+                  plan->plane_slot, plan->traj,        plan->gstart,     plan->gw,         plan->deap,
+                  plan->cell_ptr,   plan->cell_rank,   plan->cell_sx,    plan->cell_w,     plan->cell_dense,
                   plan->tile_items, plan->tile_samples};
   for (void* p : ptrs)
     if (p) cudaFree(p);

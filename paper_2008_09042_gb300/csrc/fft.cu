@@ -17,6 +17,8 @@
 // registers across a __syncwarp, so the stage runs in place.
 #include <stdio.h>
 
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "dft_reg.cuh"
@@ -899,6 +901,292 @@ size_t plane_smem() {
   return ((size_t)NY * NX + (size_t)(NX / 8) * padded_len(NX) + NY + NX) * sizeof(float2);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined plane passes.  k_plane_yx holds a whole plane per CTA, so at one
+// CTA per SM each plane's global traffic waits for its passes.  Here one
+// persistent CTA per SM (more where shared memory allows) walks its (coil, kz)
+// planes in tiles of TC columns [NY][TC] (pipe_cols):
+//  forward: TMA loads the tiles into a ring of buffers, ahead of
+//    use; each tile takes the two-step DFT along y in place (as k_plane_yx),
+//    and the outputs of the k-space rows with samples go straight to a compact
+//    row store R [plane_kmax][padded NX].  When a plane's tiles are done, each
+//    warp takes rows of R through the DFT along x and the gather, under the
+//    loads of the next plane's tiles.
+//  inverse: the rows with samples are scattered into R and transformed along
+//    x; each tile then takes the inverse two-step along y with its first step
+//    reading R (rows without samples are zero), and the result leaves by TMA
+//    stores (8 strided boxes, one per output class ky mod 8), which run under
+//    the next tile's work.
+// Per plane the CTA keeps its row list (ky, sample range) and each row's slot
+// in R in a double-buffered table, the next plane's loaded into registers
+// while the current one runs.
+constexpr int kPipeThreads = 512;
+
+// Tile width and ring depth: 64 columns in 2 buffers where NX allows (the
+// second step along y then has one item per thread), else 32 in 4.
+__host__ __device__ constexpr int pipe_cols(int nx) { return nx % 64 == 0 ? 64 : 32; }
+__host__ __device__ constexpr int pipe_bufs(int nx) { return pipe_cols(nx) == 64 ? 2 : 4; }
+
+struct PlaneMeta {
+  int4 row;  // thread t < kmax: the plane's t-th row with samples
+  int slot;  // thread t < NY: position of row ky = t in the list, -1 without samples
+  int n;     // number of rows with samples
+};
+
+template <int NY>
+__device__ __forceinline__ PlaneMeta load_plane_meta(int kz, int kmax, const int4* __restrict__ prow,
+                                                     const int32_t* __restrict__ pn,
+                                                     const int16_t* __restrict__ pslot) {
+  PlaneMeta m;
+  const int t = threadIdx.x;
+  m.row = t < kmax ? prow[(size_t)kz * kmax + t] : make_int4(-1, 0, 0, 0);
+  m.slot = t < NY ? (int)pslot[(size_t)kz * NY + t] : -1;
+  m.n = t == 0 ? pn[kz] : 0;
+  return m;
+}
+
+template <int NY>
+__device__ __forceinline__ void store_plane_meta(const PlaneMeta& m, int kmax, int4* rows, int* slot, int* n) {
+  const int t = threadIdx.x;
+  if (t < kmax) rows[t] = m.row;
+  if (t < NY) slot[t] = m.slot;
+  if (t == 0) *n = m.n;
+}
+
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Shared-memory carve-up of k_plane_pipe (byte offsets from a 1024-aligned base).
+template <int NY, int NX>
+struct PipeLayout {
+  static constexpr int TC = pipe_cols(NX), NB = pipe_bufs(NX);
+  static constexpr size_t kTile = (size_t)NY * TC * sizeof(float2);
+  static __host__ __device__ size_t R(int) { return NB * kTile; }
+  static __host__ __device__ size_t tw(int kmax) { return R(kmax) + (size_t)kmax * padded_len(NX) * sizeof(float2); }
+  static __host__ __device__ size_t rows(int kmax) { return align_up(tw(kmax) + (NY + NX) * sizeof(float2), 16); }
+  static __host__ __device__ size_t slot(int kmax) { return rows(kmax) + 2 * (size_t)kmax * sizeof(int4); }
+  static __host__ __device__ size_t n(int kmax) { return slot(kmax) + 2 * (size_t)NY * sizeof(int); }
+  static __host__ __device__ size_t bars(int kmax) { return align_up(n(kmax) + 2 * sizeof(int), 8); }
+  static __host__ __device__ size_t total(int kmax) { return bars(kmax) + NB * sizeof(uint64_t) + 1024; }
+};
+
+template <int NY, int NX, bool INV>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    k_plane_pipe(const __grid_constant__ CUtensorMap tmap, float2* __restrict__ y, int nz, int planes, int kmax,
+                 const int32_t* __restrict__ idx, const int4* __restrict__ prow, const int32_t* __restrict__ pn,
+                 const int16_t* __restrict__ pslot, int M, float ksign, const float2* __restrict__ twy_g,
+                 const float2* __restrict__ twx_g, int* err, long long wait_cycles) {
+  constexpr int R2 = NY / 8;
+  constexpr int TC = pipe_cols(NX), NB = pipe_bufs(NX);
+  constexpr int TP = NX / TC;
+  constexpr int PL = padded_len(NX);
+  constexpr int NT = kPipeThreads;
+  constexpr int NW = NT / 32;
+  using L = PipeLayout<NY, NX>;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* base = (unsigned char*)align_up((size_t)smraw, 1024);
+  float2* bufs = (float2*)base;
+  float2* R = (float2*)(base + L::R(kmax));
+  float2* twy = (float2*)(base + L::tw(kmax));
+  float2* twx = twy + NY;
+  int4* mrows = (int4*)(base + L::rows(kmax));
+  int* mslot = (int*)(base + L::slot(kmax));
+  int* mn = (int*)(base + L::n(kmax));
+  uint64_t* full = (uint64_t*)(base + L::bars(kmax));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  const int first = (int)blockIdx.x, stride = (int)gridDim.x;
+  const int nmine = planes > first ? (planes - 1 - first) / stride + 1 : 0;
+  if (nmine == 0) return;  // CTA-uniform
+  const int total = nmine * TP;
+  for (int i = tid; i < NY; i += NT) twy[i] = twy_g[i];
+  for (int i = tid; i < NX; i += NT) twx[i] = twx_g[i];
+  if (!INV && tid == 0) {
+    for (int b = 0; b < NB; ++b) mpi_ptx::mbar_init(&full[b], 1);
+    mpi_ptx::fence_mbar_init();
+  }
+  {
+    const PlaneMeta m0 = load_plane_meta<NY>(first % nz, kmax, prow, pn, pslot);
+    store_plane_meta<NY>(m0, kmax, mrows, mslot, mn);
+  }
+  __syncthreads();
+  // tile g of this CTA: plane first + (g / TP) stride, columns (g % TP) TC +
+  // [0, TC), ring buffer g % NB
+  auto issue_load = [&](int g) {
+    const int b = g % NB;
+    mpi_ptx::mbar_arrive_expect_tx(&full[b], (uint32_t)L::kTile);
+    mpi_ptx::tma_load_3d(bufs + (size_t)b * NY * TC, &tmap, (g % TP) * 2 * TC, 0,
+                         first + (g / TP) * stride, &full[b]);
+  };
+  if (!INV && tid == 0)
+    for (int g = 0; g < NB && g < total; ++g) issue_load(g);
+  int g = 0;
+  for (int j = 0; j < nmine; ++j) {
+    const int pl = first + j * stride, c = pl / nz, kz = pl - c * nz;
+    const int cur = j & 1;
+    PlaneMeta nxt;
+    if (j + 1 < nmine) nxt = load_plane_meta<NY>((pl + stride) % nz, kmax, prow, pn, pslot);
+    const int4* rows = mrows + cur * kmax;
+    const int* slot = mslot + cur * NY;
+    const int nS = mn[cur];
+    if (!INV) {
+      for (int t = 0; t < TP; ++t, ++g) {
+        const int b = g % NB;
+        float2* B = bufs + (size_t)b * NY * TC;
+        const bool ok = mpi_ptx::mbar_wait(&full[b], (uint32_t)((g / NB) & 1), err, wait_cycles);
+        // first step along y, in place: DFT8 over m of rows r + R2 m, twiddle
+        for (int it = tid; it < TC * R2; it += NT) {
+          const int col = it % TC, r = it / TC;
+          float2 v[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) v[m] = B[(r + R2 * m) * TC + col];
+          mpi_dft::dft8(v);
+#pragma unroll
+          for (int k1 = 1; k1 < 8; ++k1) v[k1] = mpi_dft::cmulf(v[k1], twy[r * k1]);
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) B[(r + R2 * k1) * TC + col] = v[k1];
+        }
+        if (__syncthreads_or(!ok)) return;  // a load timed out (recorded in err)
+        // second step: R2-point DFT over r; output ky = k1 + 8 k2 kept where it has samples
+        for (int it = tid; it < TC * 8; it += NT) {
+          const int col = it % TC, k1 = it / TC;
+          float2 u[R2];
+#pragma unroll
+          for (int r = 0; r < R2; ++r) u[r] = B[(R2 * k1 + r) * TC + col];
+          mpi_dft::dft_r<R2>(u);
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const int s = slot[k1 + 8 * k2];
+            if (s >= 0) R[s * PL + pad8(t * TC + col)] = u[k2];
+          }
+        }
+        mpi_ptx::fence_proxy_async();  // the buffer's generic accesses before the next TMA load into it
+        __syncthreads();
+        if (tid == 0 && g + NB < total) issue_load(g + NB);
+      }
+      // rows along x and the gather (the next plane's tiles load meanwhile)
+      for (int k = warp; k < nS; k += NW) {
+        float2* rr = R + k * PL;
+        Fft<NX, false>::go(rr, twx, lane);
+        const int4 rw = rows[k];  // ky, first sample, end
+        const int rpar = (kz + rw.x) & 1;
+        const size_t rb = ((size_t)kz * NY + rw.x) * NX;
+        const bool whole = rw.z - rw.y == NX;
+        for (int m = rw.y + lane; m < rw.z; m += 32) {
+          const int kx = whole ? m - rw.y : (int)(idx[m] - rb);
+          const float sg = ((kx + rpar) & 1) ? -ksign : ksign;
+          const float2 v = rr[pad8(kx)];
+          y[(size_t)c * M + m] = make_float2(v.x * sg, v.y * sg);
+        }
+      }
+      if (j + 1 < nmine) store_plane_meta<NY>(nxt, kmax, mrows + (cur ^ 1) * kmax, mslot + (cur ^ 1) * NY, mn + (cur ^ 1));
+      __syncthreads();
+    } else {
+      // rows with samples: zero-fill (partial rows), scatter with the k-side sign, inverse DFT along x
+      for (int k = warp; k < nS; k += NW) {
+        float2* rr = R + k * PL;
+        const int4 rw = rows[k];
+        const bool whole = rw.z - rw.y == NX;
+        if (!whole) {
+          for (int i = lane; i < PL; i += 32) rr[i] = make_float2(0.f, 0.f);
+          __syncwarp();
+        }
+        const int rpar = (kz + rw.x) & 1;
+        if (whole) {  // a whole readout: all loads first
+          float2 v[NX / 32];
+#pragma unroll
+          for (int u = 0; u < NX / 32; ++u) v[u] = y[(size_t)c * M + rw.y + lane + 32 * u];
+#pragma unroll
+          for (int u = 0; u < NX / 32; ++u) {
+            const int kx = lane + 32 * u;
+            const float sg = ((kx + rpar) & 1) ? -ksign : ksign;
+            rr[pad8(kx)] = make_float2(v[u].x * sg, v[u].y * sg);
+          }
+        } else {
+          const size_t rb = ((size_t)kz * NY + rw.x) * NX;
+          for (int m = rw.y + lane; m < rw.z; m += 32) {
+            const int kx = (int)(idx[m] - rb);
+            const float sg = ((kx + rpar) & 1) ? -ksign : ksign;
+            const float2 v = y[(size_t)c * M + m];
+            rr[pad8(kx)] = make_float2(v.x * sg, v.y * sg);
+          }
+        }
+        __syncwarp();
+        Fft<NX, true>::go(rr, twx, lane);
+      }
+      __syncthreads();
+      for (int t = 0; t < TP; ++t, ++g) {
+        const int b = g % NB;
+        float2* B = bufs + (size_t)b * NY * TC;
+        // inverse along y: the forward two-step on conjugated values, conjugated back
+        for (int it = tid; it < TC * R2; it += NT) {
+          const int col = it % TC, r = it / TC;
+          float2 v[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const int s = slot[r + R2 * m];
+            const float2 u = s >= 0 ? R[s * PL + pad8(t * TC + col)] : make_float2(0.f, 0.f);
+            v[m] = make_float2(u.x, -u.y);
+          }
+          mpi_dft::dft8(v);
+#pragma unroll
+          for (int k1 = 1; k1 < 8; ++k1) v[k1] = mpi_dft::cmulf(v[k1], twy[r * k1]);
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) B[(r + R2 * k1) * TC + col] = v[k1];
+        }
+        if (t == TP - 1 && j + 1 < nmine)
+          store_plane_meta<NY>(nxt, kmax, mrows + (cur ^ 1) * kmax, mslot + (cur ^ 1) * NY, mn + (cur ^ 1));
+        __syncthreads();
+        // rows R2 k1 + k2 of the buffer take output row y = k1 + 8 k2
+        for (int it = tid; it < TC * 8; it += NT) {
+          const int col = it % TC, k1 = it / TC;
+          float2 u[R2];
+#pragma unroll
+          for (int r = 0; r < R2; ++r) u[r] = B[(R2 * k1 + r) * TC + col];
+          mpi_dft::dft_r<R2>(u);
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) B[(R2 * k1 + k2) * TC + col] = make_float2(u[k2].x, -u[k2].y);
+        }
+        mpi_ptx::fence_proxy_async();  // the buffer's writes before the TMA store reads them
+        // the buffer the next tile writes was last stored NB tiles ago
+        if (tid == 0) mpi_ptx::bulk_wait_read<NB - 2>();
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1)
+            mpi_ptx::tma_store_4d(&tmap, B + (size_t)R2 * k1 * TC, t * 2 * TC, k1, 0, pl);
+          mpi_ptx::bulk_commit();
+        }
+      }
+    }
+  }
+  if (INV && tid == 0) mpi_ptx::bulk_wait_all();
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map over FP32 data (no swizzle, no out-of-range fill needed: every
+// box lies inside the volume).  strides: bytes, one per dimension above the first.
+bool encode_f32_map(CUtensorMap* map, void* ptr, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                    const cuuint32_t* box) {
+  static void* fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult qr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+    if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      fn = nullptr;
+      return false;
+    }
+  }
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return ((EncodeTiledFn)fn)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, ptr, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 mpi_status launch_fft_cols(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse,
@@ -985,6 +1273,56 @@ bool plane_pass_supported(const mpi_plan* plan) {
   return (ny == 64 || ny == 96 || ny == 128) && (nx == 64 || nx == 96 || nx == 128);
 }
 
+namespace {
+
+// The pipelined plane passes: false (nothing launched) where they do not
+// apply (shared memory for the plane's rows with samples, alignment).
+template <int NY, int NX>
+bool try_plane_pipe(mpi_ctx* ctx, const mpi_plan* plan, float2* data, int C, float2* y, bool inverse,
+                    const float2* twy, const float2* twx, float ks, mpi_status* st) {
+  const int kmax = plan->plane_kmax;
+  const size_t smem = PipeLayout<NY, NX>::total(kmax);
+  if (!plan->plane_rows || smem > 227 * 1024 || ((uintptr_t)data & 15)) return false;
+  const long planes = (long)C * plan->nz;
+  CUtensorMap map;
+  bool ok;
+  if (!inverse) {
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * NX, (cuuint64_t)NY, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)NX * sizeof(float2), (cuuint64_t)NY * NX * sizeof(float2)};
+    const cuuint32_t box[3] = {2 * pipe_cols(NX), NY, 1};
+    ok = encode_f32_map(&map, data, 3, dims, strides, box);
+  } else {
+    // rows y = k1 + 8 k2 as dimensions (k1, k2): one box per k1 holds rows k2 = 0 .. NY/8 - 1
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * NX, 8, (cuuint64_t)NY / 8, (cuuint64_t)planes};
+    const cuuint64_t strides[3] = {(cuuint64_t)NX * sizeof(float2), (cuuint64_t)8 * NX * sizeof(float2),
+                                   (cuuint64_t)NY * NX * sizeof(float2)};
+    const cuuint32_t box[4] = {2 * pipe_cols(NX), 1, NY / 8, 1};
+    ok = encode_f32_map(&map, data, 4, dims, strides, box);
+  }
+  if (!ok) return false;
+  auto kern = inverse ? k_plane_pipe<NY, NX, true> : k_plane_pipe<NY, NX, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPipeThreads, smem);
+  if (e != cudaSuccess) {
+    *st = cuda_check(ctx, e, "plane pipe attributes");
+    return true;
+  }
+  const long grid = std::min(planes, (long)ctx->num_sms * std::max(per_sm, 1));
+  MPI_PROF(ctx, KF_FFT_ROWS);
+  e = launch_pdl(ctx, kern, dim3((unsigned)grid), dim3(kPipeThreads), smem, map, y, plan->nz, (int)planes, kmax,
+                 (const int32_t*)plan->idx, (const int4*)plan->plane_rows, (const int32_t*)plan->plane_nrows,
+                 (const int16_t*)plan->plane_slot, plan->M, ks, twy, twx, ctx->dev_err, ctx->wait_cycles);
+  const char* name = inverse ? "k_plane_pipe<inv>" : "k_plane_pipe<fwd>";
+  ctx->launches++;
+  prof_end(ctx, name);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  *st = e == cudaSuccess ? MPI_OK : cuda_check(ctx, e, name);
+  return true;
+}
+
+}  // namespace
+
 mpi_status launch_plane_yx(mpi_ctx* ctx, const mpi_plan* plan, float2* data, int C, float2* y, bool inverse) {
   if (!plane_pass_supported(plan)) return set_err(ctx, MPI_ERR_UNSUPPORTED, "plane pass: shape");
   const long planes = (long)C * plan->nz;
@@ -995,6 +1333,16 @@ mpi_status launch_plane_yx(mpi_ctx* ctx, const mpi_plan* plan, float2* data, int
   const float2* twx = twiddle_table(ctx, plan->nx);
   if (!twy || !twx) return set_err(ctx, MPI_ERR_SHAPE, "plane pass: no twiddle table");
   cudaError_t e = cudaSuccess;
+  if (ctx->plane_pipe) {
+    mpi_status st = MPI_OK;
+#define MPI_PIPE(NY_, NX_) \
+  if (plan->ny == NY_ && plan->nx == NX_ && try_plane_pipe<NY_, NX_>(ctx, plan, data, C, y, inverse, twy, twx, ks, &st)) \
+    return st;
+    MPI_PIPE(64, 64) MPI_PIPE(64, 96) MPI_PIPE(64, 128)
+    MPI_PIPE(96, 64) MPI_PIPE(96, 96) MPI_PIPE(96, 128)
+    MPI_PIPE(128, 64) MPI_PIPE(128, 96) MPI_PIPE(128, 128)
+#undef MPI_PIPE
+  }
 #define MPI_PLANE(NY_, NX_)                                                                                    \
   if (plan->ny == NY_ && plan->nx == NX_) {                                                                    \
     const size_t smem = plane_smem<NY_, NX_>();                                                                \

@@ -55,10 +55,11 @@ struct mpi_ctx {
   // buffer the operator calls are not using at that point), never while the
   // stream is being captured, and only while `autotune` is set.
   bool autotune = true;
-  int line_kernel = 0;
+  int line_kernel = 0;  // fixed line-pass choice (8, 16, 32 lines, -1 register two-step), 0 = tuned
   bool plane_pass = true;  // 3D: the passes along y and x in one kernel per plane where it applies
+  bool plane_pipe = true;  // ... as the pipelined persistent kernel (TMA tiles) where it applies
   long long wait_cycles = 4LL << 30;  // bounded-wait limit of the tensor-core kernels (SM clock cycles)
-  int stall_after = -1;               // fault injection in the 3xTF32 expansion's producer (-1: off)  // fixed line-pass choice (8, 16, 32 lines, -1 register two-step), 0 = tuned
+  int stall_after = -1;               // fault injection in the 3xTF32 expansion's producer (-1: off)
   void* tune_scratch = nullptr;
   size_t tune_scratch_bytes = 0;
   struct TuneRecord {
@@ -86,6 +87,14 @@ struct mpi_plan {
   int32_t* row_ptr = nullptr;
   uint8_t* row_has = nullptr;  // [n_rows]: 1 where the k-space row has samples; null when every row has some
   int n_rows = 0;
+  // 3D: per kz plane, its k-space rows with samples in order of ky:
+  // plane_rows [nz][max(plane_kmax, 1)] = {ky, first sample, end of samples, 0}
+  // (unused entries ky = -1), plane_nrows [nz] their number, plane_slot
+  // [nz][ny] each row's position in its plane's list (-1: no samples).
+  int4* plane_rows = nullptr;
+  int32_t* plane_nrows = nullptr;
+  int16_t* plane_slot = nullptr;
+  int plane_kmax = 0;
   // Radial (Kaiser-Bessel gridding)
   int W = 0, G = 0;
   float* traj = nullptr;      // [M][2]
@@ -363,6 +372,8 @@ mpi_status tune_line_passes(mpi_ctx* ctx, const mpi_plan* plan, int C);
 // transformed along z) -> samples y; inverse, samples -> data (to be
 // transformed along z).  Planes of 64 / 96 / 128 squared.
 bool plane_pass_supported(const mpi_plan* plan);
+// The passes along y and x of the (coil, kz) planes: the pipelined kernel where
+// ctx->plane_pipe is set and it applies, else one CTA per plane.
 mpi_status launch_plane_yx(mpi_ctx* ctx, const mpi_plan* plan, float2* data, int C, float2* y, bool inverse);
 // In-place FFT along z of [C][nz][ny][nx].
 mpi_status launch_fft_z(mpi_ctx* ctx, float2* data, int C, int nz, int ny, int nx, bool inverse);

@@ -392,20 +392,46 @@ def test_line_pass_kernels_match_oracle(mp, choice, dims, C, q, R):
     ctx.synchronize()
 
 
-@pytest.mark.parametrize("choice", [0, -2])
-def test_line_pass_kernels_3d_volume(mp, choice):
-    # the 3D path's passes along y and x: one kernel per (coil, kz) plane (0) or
-    # the separate, tuned passes (-2), on a 64 x 64 x 128 volume
+def _volume_mask(dims, kind, seed):
+    """3D sampling patterns for the plane passes: whole readouts on a
+    Poisson-disc (kz, ky) set; the same with a random 60 % of the samples kept
+    (rows partly sampled, some planes empty); or a dense centre (every row of
+    the central planes sampled, more rows per plane than the pipelined kernel
+    keeps in shared memory)."""
+    nz, ny, nx = dims
+    m = w.poisson_disc_mask_3d(nz, ny, nx, R=8, calib=(12, 12), seed=seed)
+    if kind == "partial":
+        rng = np.random.default_rng(seed + 1)
+        m = m & (rng.random(m.shape) < 0.6)
+        m[: nz // 4] = False  # a run of planes without samples
+    elif kind == "dense":
+        m[nz // 2 - 2: nz // 2 + 2] = True
+    return m
+
+
+@pytest.mark.parametrize("choice", [0, -2, -3])
+@pytest.mark.parametrize("dims,kind", [
+    ((64, 64, 128), "readouts"),
+    ((64, 128, 128), "readouts"),
+    ((96, 96, 96), "partial"),
+    ((64, 128, 64), "partial"),
+    ((64, 64, 96), "dense"),
+    ((64, 128, 128), "dense"),
+])
+def test_line_pass_kernels_3d_volume(mp, choice, dims, kind):
+    # the 3D path's passes along y and x: the pipelined plane kernel (0, where
+    # each plane's rows with samples fit), one CTA per plane (-3, and 0 where
+    # they do not) or the separate, tuned passes (-2)
     from oracle import tucker
 
     ctx = mp.Context(0)
     ctx.set_line_kernel(choice)
-    dims, ranks, q, C = (64, 64, 128), (16, 16, 16), 24, 3
+    ranks, q, C = (8, 12, 12), 16, 3
     core, fac = w.smooth_tucker_basis(dims, ranks, q, seed=27)
     core = core.astype(np.complex64).astype(np.complex128)
     fac = [f.astype(np.complex64).astype(np.complex128) for f in fac]
     tb = tucker.TuckerBasis(core, fac)
-    idx = w.mask_to_indices(w.poisson_disc_mask_3d(*dims, R=8, calib=(12, 12), seed=28))
+    idx = w.mask_to_indices(_volume_mask(dims, kind, seed=28))
     Fs = fourier.CartesianSampling(dims, idx)
     N = int(np.prod(dims))
     a = w.random_coefficients(C, q, seed=29).astype(np.complex64).astype(np.complex128)
@@ -413,6 +439,17 @@ def test_line_pass_kernels_3d_volume(mp, choice):
     r = w.random_coefficients(C, idx.size, seed=31, decay=False).astype(np.complex64).astype(np.complex128)
     plan = mp.Plan(ctx, dims, sample_idx=idx)
     B = mp.TuckerBasis(ctx, core, fac)
+    ctx.profile(True)
     assert rel(f64(mp.forward(ctx, plan, B, c64(a), c64(p))), op.forward(Fs, tb, a, p)) < TOL
     assert rel(f64(mp.adjoint(ctx, plan, B, c64(a), c64(r))), op.adjoint(Fs, tb, a, r)) < TOL
     ctx.synchronize()
+    _, kern = ctx.profile_read(kernels=True)
+    ctx.profile(False)
+    pipe = {k for k in kern if k.startswith("k_plane_pipe")}
+    single = {k for k in kern if k.startswith("k_plane_yx")}
+    if choice == -2:
+        assert not pipe and not single
+    elif choice == -3 or kind == "dense" and dims[1] == 128:
+        assert single == {"k_plane_yx<fwd>", "k_plane_yx<inv>"} and not pipe
+    else:
+        assert pipe == {"k_plane_pipe<fwd>", "k_plane_pipe<inv>"} and not single

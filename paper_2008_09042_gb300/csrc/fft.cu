@@ -983,7 +983,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   constexpr int NW = NT / 32;
   using L = PipeLayout<NY, NX>;
   extern __shared__ unsigned char smraw[];
-  unsigned char* base = (unsigned char*)align_up((size_t)smraw, 1024);
+  // offset from the shared array itself (not a cast integer), so that every
+  // access below compiles to shared-memory loads and stores
+  unsigned char* base = smraw + ((1024u - (mpi_ptx::smem_addr(smraw) & 1023u)) & 1023u);
   float2* bufs = (float2*)base;
   float2* R = (float2*)(base + L::R(kmax));
   float2* twy = (float2*)(base + L::tw(kmax));

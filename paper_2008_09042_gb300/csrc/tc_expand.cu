@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_expand_tc(const __grid_constant
     a.C = r.C;
   }
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array, so that accesses stay shared-memory ones
+  unsigned char* smem = smem_raw + ((1024u - (mpi_ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
   const int Kp = a.KC * kKChunk;
   const uint32_t b_bytes = (uint32_t)a.n_gemm * Kp * 2;
   unsigned char* sB = smem;

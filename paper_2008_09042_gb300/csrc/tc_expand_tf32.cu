@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     else a.out += a.tuck_B ? (size_t)c0 * a.tuck_B : (size_t)c0 * a.N;
   }
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array, so that accesses stay shared-memory ones
+  unsigned char* smem = smem_raw + ((1024u - (mpi_ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
   const int Kp = a.KC * kKChunk32;
   const uint32_t b_bytes = 2u * (uint32_t)a.n_gemm * Kp * 4;  // stacked [hi; lo] coefficient rows
   const uint32_t b_pad = (b_bytes + 1023) & ~1023u;

@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
   constexpr int R = N1 / 8;  // the DFT along z is 8 x R
   constexpr int STAGE = S::STAGE;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array, so that accesses stay shared-memory ones
+  unsigned char* smem = smem_raw + ((1024u - (mpi_ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
   const int stages = a.stages;
   unsigned char* sB = smem;
   float2* sX = reinterpret_cast<float2*>(smem + S::B_PAD);  // image block or coil-sum accumulator

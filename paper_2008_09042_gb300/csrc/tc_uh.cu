@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(kUhThreads, 1) k_uh_tc(const __grid_constant__
                                                          const __grid_constant__ CUtensorMap vmap, UhArgs a) {
   using Cfg = UhCfg<BF>;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array, so that accesses stay shared-memory ones
+  unsigned char* smem = smem_raw + ((1024u - (mpi_ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
   const int Cp = a.Cp, stages = a.stages;
   const uint32_t a_stage = kBoxes * kABox;
   const uint32_t b_box = (uint32_t)Cfg::kBRows * Cp * 128;

@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 2D/radial/batched/recon lines")
     ap.add_argument("--profile-workload", default=None,
                     help="only run --steps forward+adjoint pairs of this workload, untimed, for an external profiler")
+    ap.add_argument("--profile-op", default="pair", choices=["pair", "jacobian"],
+                    help="with --profile-workload: forward+adjoint pairs, or Jacobian + Jacobian-adjoint pairs")
     return ap.parse_args()
 
 
@@ -999,11 +1001,19 @@ def profile_workload(args):
     else:
         case = make_case(name)
         plan, B, a, pd = gpu_objects(mp, ctx, dev, case)
-    for _ in range(args.steps):
-        y = mp.forward(ctx, plan, B, a, pd, args.prec)
-        mp.adjoint(ctx, plan, B, a, y, args.prec)
+    if args.profile_op == "jacobian":
+        da = (0.5 * a).contiguous()
+        dp = (0.25 * pd).contiguous()
+        for _ in range(args.steps):
+            dy = mp.jacobian(ctx, plan, B, a, pd, dp, da, args.prec)
+            mp.jacobian_adjoint(ctx, plan, B, a, pd, dy, args.prec)
+    else:
+        for _ in range(args.steps):
+            y = mp.forward(ctx, plan, B, a, pd, args.prec)
+            mp.adjoint(ctx, plan, B, a, y, args.prec)
     ctx.synchronize()
-    print(f"{name}: {args.steps} forward+adjoint pairs ({args.prec})", flush=True)
+    what = "Jacobian + Jacobian-adjoint" if args.profile_op == "jacobian" else "forward+adjoint"
+    print(f"{name}: {args.steps} {what} pairs ({args.prec})", flush=True)
     return 0
 
 

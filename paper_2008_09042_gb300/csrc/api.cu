@@ -184,6 +184,10 @@ ExpandArgs base_args(const mpi_plan* plan, const mpi_basis* basis, int C) {
 mpi_status kspace_to_image(mpi_ctx* ctx, const mpi_plan* plan, const float2* y, int C, float2* w,
                            float2* grid) {
   if (plan->kind == MPI_TRAJ_RADIAL) return nufft_adjoint(ctx, plan, y, C, w, grid);
+  if (ctx->plane_pass && plane_pass_supported(plan)) {  // 3D: the passes along x and y per plane, then z
+    mpi_status st = launch_plane_yx(ctx, plan, w, C, (float2*)y, true);
+    return st ? st : launch_fft_z(ctx, w, C, plan->nz, plan->ny, plan->nx, true);
+  }
   mpi_status st = launch_rows_scatter_inv(ctx, plan, y, C, w);
   if (st) return st;
   st = launch_fft_cols(ctx, w, C, plan->nz, plan->ny, plan->nx, true, plan->row_has);
@@ -199,6 +203,7 @@ mpi_status image_to_kspace(mpi_ctx* ctx, const mpi_plan* plan, float2* v, int C,
   mpi_status st = MPI_OK;
   if (plan->ndim == 3) st = launch_fft_z(ctx, v, C, plan->nz, plan->ny, plan->nx, false);
   if (st) return st;
+  if (ctx->plane_pass && plane_pass_supported(plan)) return launch_plane_yx(ctx, plan, v, C, y, false);
   st = launch_fft_cols(ctx, v, C, plan->nz, plan->ny, plan->nx, false, plan->row_has);
   if (st) return st;
   return launch_rows_fwd_gather(ctx, plan, v, C, y);
@@ -738,6 +743,10 @@ extern "C" mpi_status mpi_basis_load_tucker(mpi_ctx* ctx, const mpi_c32* core, c
     mpi_basis_destroy(b);
     return st;
   }
+  if ((st = tucker_conj_factors(ctx, b))) {
+    mpi_basis_destroy(b);
+    return st;
+  }
   ctx_adopt(ctx, &b->ctx);  // only a fully made basis is tracked
   *out = b;
   return MPI_OK;
@@ -757,8 +766,10 @@ extern "C" mpi_status mpi_basis_destroy(mpi_basis* b) {
   if (b->Uf32) cudaFree(b->Uf32);
   tf32_basis_release(b);
   uh_tc_release(b);
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 3; ++k) {
     if (b->F[k]) cudaFree(b->F[k]);
+    if (b->Fh[k]) cudaFree(b->Fh[k]);
+  }
   if (b->core) mpi_basis_destroy(b->core);
   delete (CUtensorMap*)b->op_map;
   tucker_chain_release(b);
@@ -968,6 +979,21 @@ extern "C" mpi_status mpi_jacobian(mpi_ctx* ctx, const mpi_plan* plan, const mpi
   a.p = (const float2*)p;
   a.dp = (const float2*)dp;
   a.out = w.A;
+  if (tucker_x1_fused_supported(basis, plan, C, prec)) {
+    // J = F_s(S(dalpha) p + S(alpha) dp): the forward's fused x1 pass (maps,
+    // point-wise step, DFT along z) once per term, the second adding into the
+    // first, then the passes along y and x
+    void* op = nullptr;
+    void* map = nullptr;
+    if ((st = tucker_x1_operand(ctx, basis, a.dalpha, C, w.T, prec, &op, &map))) return st;
+    if ((st = tucker_x1_fused_launch(ctx, basis, plan, false, C, map, a.p, nullptr, w.A, a.scale, prec))) return st;
+    if ((st = tucker_x1_operand(ctx, basis, a.alpha, C, w.T, prec, &op, &map))) return st;
+    if ((st = tucker_x1_fused_launch(ctx, basis, plan, false, C, map, a.dp, nullptr, w.A, a.scale, prec, true)))
+      return st;
+    if (ctx->plane_pass && plane_pass_supported(plan)) return launch_plane_yx(ctx, plan, w.A, C, (float2*)dy, false);
+    if ((st = launch_fft_cols(ctx, w.A, C, plan->nz, plan->ny, plan->nx, false, plan->row_has))) return st;
+    return launch_rows_fwd_gather(ctx, plan, w.A, C, (float2*)dy);
+  }
   if ((st = run_expand(ctx, basis, EX_JFWD, a, prec, w))) return st;
   return image_to_kspace(ctx, plan, w.A, C, (float2*)dy, w.grid);
 }
@@ -982,6 +1008,25 @@ extern "C" mpi_status mpi_jacobian_adjoint(mpi_ctx* ctx, const mpi_plan* plan, c
   DeviceGuard g(ctx->device);
   Work w;
   if ((st = carve_work(ctx, plan, basis, C, &w))) return st;
+  if (tucker_jadj_tc_supported(basis, plan, C, prec)) {
+    // the inverse passes along x and y; dp = the adjoint's fused x1 pass (inverse
+    // DFT along z, maps, sum over coils); dalpha = the conjugate chain on the
+    // tensor cores from the same per-coil data
+    if (ctx->plane_pass && plane_pass_supported(plan)) {
+      if ((st = launch_plane_yx(ctx, plan, w.A, C, (float2*)r, true))) return st;
+    } else {
+      if ((st = launch_rows_scatter_inv(ctx, plan, (const float2*)r, C, w.A))) return st;
+      if ((st = launch_fft_cols(ctx, w.A, C, plan->nz, plan->ny, plan->nx, true, plan->row_has))) return st;
+    }
+    const float scale = base_args(plan, basis, C).scale;
+    void* op = nullptr;
+    void* map = nullptr;
+    if ((st = tucker_x1_operand(ctx, basis, (const float2*)alpha, C, w.T, prec, &op, &map))) return st;
+    if ((st = tucker_x1_fused_launch(ctx, basis, plan, true, C, map, nullptr, w.A, (float2*)dp, scale, prec)))
+      return st;
+    return tucker_jadj_alpha(ctx, basis, plan, w.A, (const float2*)p, scale, C, w.B, (float2*)dalpha, w.T,
+                             w.partials, w.partial_cap);
+  }
   if ((st = kspace_to_image(ctx, plan, (const float2*)r, C, w.A, w.grid))) return st;
   ExpandArgs a = base_args(plan, basis, C);
   a.alpha = (const float2*)alpha;

@@ -143,6 +143,7 @@ struct mpi_basis {
   bool tucker = false;
   int n[3] = {0, 0, 0}, r[3] = {0, 0, 0};
   float2* F[3] = {nullptr, nullptr, nullptr};
+  float2* Fh[3] = {nullptr, nullptr, nullptr};  // U_k^H [r_k][n_k] (the conjugate products' coefficient rows)
   mpi_basis* core = nullptr;
   // Tensor map of the flattened x1 operand in the workspace (tucker.cu), kept
   // while the workspace address, coil count and precision stay the same.
@@ -337,9 +338,17 @@ mpi_status tucker_x1_operand(mpi_ctx* ctx, const mpi_basis* b, const float2* alp
 // of `wk` [C][n1][n2 n3] and the adjoint's sum over coils of conj(s_c) w_c
 // (out = image [N]) (tc_tucker.cu).
 bool tucker_x1_fused_supported(const mpi_basis* b, const mpi_plan* plan, int C, mpi_precision prec);
+// Tucker: Fh[k] = U_k^H, made at basis load.
+mpi_status tucker_conj_factors(mpi_ctx* ctx, mpi_basis* b);
+// The Jacobian-adjoint's coefficient block on the tensor cores (FP32): from the
+// per-coil data after the inverse passes along x and y.
+bool tucker_jadj_tc_supported(const mpi_basis* b, const mpi_plan* plan, int C, mpi_precision prec);
+mpi_status tucker_jadj_alpha(mpi_ctx* ctx, const mpi_basis* b, const mpi_plan* plan, const float2* wk,
+                             const float2* p, float scale, int C, float2* opbuf, float2* dalpha, float2* tmp,
+                             float2* partials, size_t partial_cap);
 mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_plan* plan, bool adjoint, int C,
                                   const void* map, const float2* p, const float2* wk, float2* out, float scale,
-                                  mpi_precision prec);
+                                  mpi_precision prec, bool accumulate = false);
 
 // Loads the module holding the allocation-free forward's static scratch on the
 // current device (noalloc.cu); called once per context at creation.

@@ -159,6 +159,18 @@ static __host__ __device__ __forceinline__ uint32_t sw128_offset_e(int r, int k,
 
 static __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
+// lo(x) = x - hi(x), rounded to the nearest TF32 value (ties away from zero)
+// so that the tensor core reads it exactly.  An FP32 lo would be truncated by
+// the tensor core, and the truncation of every lo towards zero biases a long
+// sum of products; rounded, the error (at most 2^-11 of lo, 2^-22 of x) is
+// unbiased.
+static __device__ __forceinline__ float tf32_lo(float v) {
+  const float lo = v - tf32_hi(v);
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(lo));
+  return __uint_as_float(r);
+}
+
 // The coefficient operand, written straight into shared memory in the swizzled
 // K-major layout by the four epilogue warps (etid = 0..127) while the first
 // tiles of U are still in flight.  Per coil c, row 2c is [Re a_c, -Im a_c] and
@@ -203,8 +215,8 @@ static __device__ void build_coef_smem(const TcArgs& a, unsigned char* sB, int K
         float4 h0, h1, l0, l1;
         h0 = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
         h1 = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
-        l0 = make_float4(re[0] - h0.x, re[1] - h0.y, re[2] - h0.z, re[3] - h0.w);
-        l1 = make_float4(im[0] - h1.x, im[1] - h1.y, im[2] - h1.z, im[3] - h1.w);
+        l0 = make_float4(tf32_lo(re[0]), tf32_lo(re[1]), tf32_lo(re[2]), tf32_lo(re[3]));
+        l1 = make_float4(tf32_lo(im[0]), tf32_lo(im[1]), tf32_lo(im[2]), tf32_lo(im[3]));
         *reinterpret_cast<float4*>(sB + sw128_offset_e(r0, k0, rows, esize)) = h0;
         *reinterpret_cast<float4*>(sB + sw128_offset_e(r0 + 1, k0, rows, esize)) = h1;
         *reinterpret_cast<float4*>(sB + sw128_offset_e(r0 + a.n_gemm, k0, rows, esize)) = l0;

@@ -210,10 +210,10 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 v = x[j ^ (row & 7)];
-          lo[4 * j + 0] = v.x - tf32_hi(v.x);
-          lo[4 * j + 1] = v.y - tf32_hi(v.y);
-          lo[4 * j + 2] = v.z - tf32_hi(v.z);
-          lo[4 * j + 3] = v.w - tf32_hi(v.w);
+          lo[4 * j + 0] = tf32_lo(v.x);
+          lo[4 * j + 1] = tf32_lo(v.y);
+          lo[4 * j + 2] = tf32_lo(v.z);
+          lo[4 * j + 3] = tf32_lo(v.w);
         }
         tmem_st32(tmem_lo + lane_base + (uint32_t)(r.s * 32 * kBoxesPerStage + 32 * h), lo);
       }

@@ -65,6 +65,7 @@ struct TxArgs {
   const float2* p;   // image [N1][B]
   const float2* w;   // adjoint input [C][N1][B]
   float2* out;       // forward: vhat [C][N1][B]; adjoint: image [N1][B]
+  int accumulate;    // forward: add into out instead of storing
   const float2* wk;  // adjoint input: per-coil data along kz [C][N1][B]
   const float2* tw;  // exp(-2 pi i m / N1), m < N1
   int* err;
@@ -124,6 +125,11 @@ __device__ __forceinline__ bool epi_bar_any(int flag, int n) {
       : "r"(flag), "r"(n)
       : "memory");
   return out != 0;
+}
+
+// Bring 256 bytes at `p` (256-byte aligned) into L2, asynchronously.
+__device__ __forceinline__ void l2_prefetch_256(const void* p) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(p) : "memory");
 }
 
 __device__ __forceinline__ float pos_sign(int z, int b, int nx) {
@@ -248,10 +254,10 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 v = x[j ^ (row & 7)];
-          lo[4 * j + 0] = v.x - tf32_hi(v.x);
-          lo[4 * j + 1] = v.y - tf32_hi(v.y);
-          lo[4 * j + 2] = v.z - tf32_hi(v.z);
-          lo[4 * j + 3] = v.w - tf32_hi(v.w);
+          lo[4 * j + 0] = tf32_lo(v.x);
+          lo[4 * j + 1] = tf32_lo(v.y);
+          lo[4 * j + 2] = tf32_lo(v.z);
+          lo[4 * j + 3] = tf32_lo(v.w);
         }
         tmem_st32(tmem_lo + lane_base + (uint32_t)(r.s * 64 + 32 * h), lo);
       }
@@ -355,12 +361,27 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
         // the two warps of a lane quarter take alternate tiles (sub = buffer =
         // tile parity) and each runs the whole DFT of its 32 positions
         if ((tc & 1) != sub) continue;
+        if (a.accumulate) {
+          // the read-modify-write of the output: bring this warp's block of the
+          // tile after next (its next one) into L2 now, and of this one if first
+          for (int k = (tc == sub ? tc : tc + 2); k <= tc + 2 && k < my_tiles; k += 2) {
+            const int ck = (int)blockIdx.y + k * (int)gridDim.y;
+            const float2* blk = a.out + (size_t)ck * N1 * a.B + (size_t)blockIdx.x * kTileM + qd * 32;
+            for (int z = lane; z < N1; z += 32) l2_prefetch_256(blk + (size_t)z * a.B);
+          }
+        }
         const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err, a.wait_cycles);
         if (!__all_sync(0xffffffffu, got)) {
           failed = true;
           break;
         }
         fence_after();
+        float2* o = a.out + (size_t)c * N1 * a.B + b;
+        float2 pn[8];
+        if (a.accumulate) {
+#pragma unroll
+          for (int k1 = 0; k1 < 8; ++k1) pn[k1] = o[(size_t)(R * k1) * a.B];
+        }
         // stage 1: v = s p (sign and scale folded into the staged image) over
         // z = j1 + 8 j2, R-point DFT, twiddle, in place; two j1 per round
         for (int j1 = 0; j1 < 8; j1 += 2) {
@@ -385,9 +406,19 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
           }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        // stage 2: 8-point DFTs over j1 for each k2; output kz = k2 + R k1
-        float2* o = a.out + (size_t)c * N1 * a.B + b;
+        // stage 2: 8-point DFTs over j1 for each k2; output kz = k2 + R k1.
+        // Accumulating, the output values of k2 + 1 are loaded while k2 is
+        // transformed (those of k2 = 0 were loaded before stage 1).
         for (int k2 = 0; k2 < R; ++k2) {
+          float2 prev[8];
+          if (a.accumulate) {
+#pragma unroll
+            for (int k1 = 0; k1 < 8; ++k1) prev[k1] = pn[k1];
+            if (k2 + 1 < R) {
+#pragma unroll
+              for (int k1 = 0; k1 < 8; ++k1) pn[k1] = o[(size_t)(k2 + 1 + R * k1) * a.B];
+            }
+          }
           uint32_t raw[16];
           tmem_ld16_start(tacc + 16u * k2, raw);
           tmem_wait_ld();
@@ -397,8 +428,14 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
           for (int j1 = 0; j1 < 8; ++j1)
             u[j1] = make_float2(__uint_as_float(raw[2 * j1]), __uint_as_float(raw[2 * j1 + 1]));
           dft8(u);
+          if (a.accumulate) {
 #pragma unroll
-          for (int k1 = 0; k1 < 8; ++k1) o[(size_t)(k2 + R * k1) * a.B] = u[k1];
+            for (int k1 = 0; k1 < 8; ++k1)
+              o[(size_t)(k2 + R * k1) * a.B] = make_float2(prev[k1].x + u[k1].x, prev[k1].y + u[k1].y);
+          } else {
+#pragma unroll
+            for (int k1 = 0; k1 < 8; ++k1) o[(size_t)(k2 + R * k1) * a.B] = u[k1];
+          }
         }
         fence_before();
         __syncwarp();
@@ -538,10 +575,12 @@ bool tucker_x1_fused_supported(const mpi_basis* b, const mpi_plan* plan, int C, 
 // (forward: out = vhat [C][n1][n2 n3]), or with the inverse DFT along z of `wk`
 // and the adjoint's coil sum (adjoint: out = image [N]).  `map` is the tensor
 // map of the flattened operand [C B][64] (FP32 or BF16, from k_x1_operand).
+// `accumulate` (forward): add the result into out.
 mpi_status tucker_x1_fused_launch(mpi_ctx* ctx, const mpi_basis* b, const mpi_plan* plan, bool adjoint, int C,
                                   const void* map, const float2* p, const float2* wk, float2* out, float scale,
-                                  mpi_precision prec) {
+                                  mpi_precision prec, bool accumulate) {
   TxArgs a;
+  a.accumulate = !adjoint && accumulate;
   const long B = (long)b->n[1] * b->n[2];
   a.rows = (int)(C * B);
   a.B = (int)B;

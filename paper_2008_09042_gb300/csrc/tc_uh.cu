@@ -86,7 +86,7 @@ __device__ __forceinline__ void tmem_st32_uh(uint32_t taddr, const float (&v)[32
 }
 
 __device__ __forceinline__ float4 lo4(float4 x) {
-  return make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z), x.w - tf32_hi(x.w));
+  return make_float4(tf32_lo(x.x), tf32_lo(x.y), tf32_lo(x.z), tf32_lo(x.w));
 }
 // -i (a + i b) = b - i a on each of the two complex values of a 16-byte unit
 __device__ __forceinline__ float4 mul_mi4(float4 x) { return make_float4(x.y, -x.x, x.w, -x.z); }

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 
+#include "dft_reg.cuh"
 #include "mpi_internal.h"
 #include "ptx.cuh"
 
@@ -438,10 +439,11 @@ void operand_view(const mpi_basis* b, void* ptr, void* map, long rows, int q, mp
 
 // Tensor map cache of the chain's operands (re-encoded when the address or
 // the row count changes).
+// Slots 0-2: the forward chain's operands; 3-5: the conjugate chain's.
 struct ChainMaps {
-  CUtensorMap m[3];
-  const void* ptr[3] = {nullptr, nullptr, nullptr};
-  long rows[3] = {0, 0, 0};
+  CUtensorMap m[6];
+  const void* ptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  long rows[6] = {0, 0, 0, 0, 0, 0};
 };
 
 bool chain_map(mpi_basis* b, int i, void* ptr, long rows, int K, void** out) {
@@ -694,6 +696,241 @@ mpi_status tucker_adjoint(mpi_ctx* ctx, const mpi_basis* b, const float2* V, int
   if ((st = mode_b(ctx, true, t2, b->F[1], C * r1, n2, r2, n3, t1))) return st;
   if ((st = mode_last(ctx, true, t1, b->F[2], C * r1 * r2, n3, r3, g))) return st;
   return uh_v(ctx, b->core, g, C, dalpha, partials, partial_cap, prec);
+}
+
+// ------------------------------------------- Jacobian-adjoint on the tensor cores
+//
+// The coefficient block of the Jacobian-adjoint (the display after Eq. 7),
+// dalpha_c = U^H v_c with v_c = conj(p) (.) F^H r_c, through the Tucker factors
+// ("A Compression Scheme for Maxwell Basis", Eq. 19 read backwards): the
+// conjugate mode products x1^H, x2^H, x3^H on the 3xTF32 kernel, each
+// written by its scatter epilogue into the next one's K-major rows, then the
+// core's conjugate contraction.  v_c itself is formed from the per-coil data
+// after the passes along x and y: the inverse DFT along z and the point-wise
+// step, written straight as the x1^H operand.
+
+namespace {
+
+// Fh[k] = U_k^H [r_k][n_k]: the coefficient rows of the conjugate products.
+__global__ void k_conj_transpose(const float2* __restrict__ F, int n, int r, float2* __restrict__ Fh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * r) return;
+  const int row = i / n, col = i - row * n;  // Fh[row][col] = conj(F[col][row])
+  const float2 v = F[(size_t)col * r + row];
+  Fh[i] = make_float2(v.x, -v.y);
+}
+
+// The x1^H operand: per coil c and 32 consecutive positions b = y n3 + x of a
+// z-plane, the inverse DFT along z of wk_c[kz][b] (two steps, N1 = 8 R: DFT8
+// over kz = r + R m, twiddle, R-point DFT; output z = k1 + 8 k2, conjugation on
+// both sides), then v = conj(p) w sign(z, y, x) scale, stored as row (c, x, y)
+// of [Re v(z), z < N1 | Im v(z), z < N1] (FP32).
+template <int N1>
+__global__ void __launch_bounds__(256) k_jadj_operand(const float2* __restrict__ wk, const float2* __restrict__ p,
+                                                      const float2* __restrict__ tw_g, int B, int nx, int ny,
+                                                      float scale, float* __restrict__ out) {
+  constexpr int R = N1 / 8, P = 32, NT = 256, OS = 2 * N1 + 1;
+  constexpr int T_FLOATS = 2 * N1 * P, O_FLOATS = P * OS;
+  __shared__ float smf[T_FLOATS > O_FLOATS ? T_FLOATS : O_FLOATS];
+  __shared__ float2 tw[N1];
+  float2* T = reinterpret_cast<float2*>(smf);  // [N1][P]
+  float* O = smf;                              // [P][OS], after the transform
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  const int tid = threadIdx.x, c = blockIdx.y, b0 = blockIdx.x * P;
+  for (int i = tid; i < N1; i += NT) tw[i] = tw_g[i];
+  const float2* src = wk + (size_t)c * N1 * B + b0;
+  constexpr int LD = N1 * P / NT;  // loads per thread, all issued before the first is used
+  static_assert(N1 * P % NT == 0, "load split");
+  float2 ld[LD];
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int i = tid + u * NT, kz = i / P, pos = i - kz * P;
+    ld[u] = src[(size_t)kz * B + pos];
+  }
+#pragma unroll
+  for (int u = 0; u < LD; ++u) T[tid + u * NT] = make_float2(ld[u].x, -ld[u].y);
+  __syncthreads();
+  for (int it = tid; it < P * R; it += NT) {
+    const int pos = it % P, r = it / P;
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = T[(r + R * m) * P + pos];
+    mpi_dft::dft8(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) v[k1] = mpi_dft::cmulf(v[k1], tw[r * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) T[(r + R * k1) * P + pos] = v[k1];
+  }
+  __syncthreads();
+  // one item per thread: (pos, k1), P x 8 = NT
+  const int pos = tid % P, k1 = tid / P;
+  const int b = b0 + pos;
+  float2 u[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) u[r] = T[(R * k1 + r) * P + pos];
+  mpi_dft::dft_r<R>(u);
+  float2 pv[R];
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) pv[k2] = p[(size_t)(k1 + 8 * k2) * B + b];
+  __syncthreads();  // T is reused as O below
+  const int x = b % nx, y = b / nx;
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) {
+    const int z = k1 + 8 * k2;
+    const float2 w = make_float2(u[k2].x, -u[k2].y);
+    const float sg = ((x + y + z) & 1) ? -scale : scale;
+    // conj(p) w
+    const float re = pv[k2].x * w.x + pv[k2].y * w.y, im = pv[k2].x * w.y - pv[k2].y * w.x;
+    O[pos * OS + z] = re * sg;
+    O[pos * OS + N1 + z] = im * sg;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int q = warp; q < P; q += NT / 32) {
+    const int bq = b0 + q, xq = bq % nx, yq = bq / nx;
+    float* dst = out + ((size_t)c * B + (size_t)xq * ny + yq) * (2 * N1);
+    for (int i = lane; i < 2 * N1; i += 32) dst[i] = O[q * OS + i];
+  }
+}
+
+}  // namespace
+
+mpi_status tucker_conj_factors(mpi_ctx* ctx, mpi_basis* b) {
+  for (int k = 0; k < 3; ++k) {
+    const int n = b->n[k], r = b->r[k];
+    cudaError_t e = cudaMalloc(&b->Fh[k], (size_t)n * r * sizeof(float2));
+    if (e != cudaSuccess) return cuda_check(ctx, e, "Tucker conjugate factors");
+    MPI_PROF(ctx, KF_OTHER);
+    k_conj_transpose<<<(n * r + 255) / 256, 256, 0, ctx->stream>>>(b->F[k], n, r, b->Fh[k]);
+    MPI_LAUNCH_CHECK(ctx, "k_conj_transpose");
+  }
+  return MPI_OK;
+}
+
+namespace {
+
+mpi_basis conj_view(const mpi_basis* b, int i, void* ptr, long rows, int n, bool* ok) {
+  mpi_basis v;
+  void* m = nullptr;
+  *ok = chain_map(const_cast<mpi_basis*>(b), 3 + i, ptr, rows, 2 * n, &m);
+  operand_view(b, ptr, m, rows, n, &v);
+  return v;
+}
+
+bool conj_chain_shapes(const mpi_basis* b, int C) {
+  const int n1 = b->n[0], n2 = b->n[1], n3 = b->n[2], r1 = b->r[0], r2 = b->r[1];
+  const long rows1 = (long)C * n2 * n3, rows2 = (long)C * r1 * n3, rows3 = (long)C * r1 * r2;
+  if (rows1 > 0x7fffffffL - 128) return false;
+  for (int k = 0; k < 3; ++k)
+    if (b->n[k] % 2 || b->n[k] > 256) return false;
+  mpi_basis v1, v2, v3;  // shape-only views
+  operand_view(b, (void*)256, (void*)256, rows1, n1, &v1);
+  operand_view(b, (void*)256, (void*)256, rows2, n2, &v2);
+  operand_view(b, (void*)256, (void*)256, rows3, n3, &v3);
+  return tf32_group(&v1, EX_SCATTER, b->r[0]) > 0 && tf32_group(&v2, EX_SCATTER, b->r[1]) > 0 &&
+         tf32_group(&v3, EX_SCATTER, b->r[2]) > 0;
+}
+
+}  // namespace
+
+// FP32 and BF16 (the coefficient block then runs on the 3xTF32 kernels too,
+// more accurate than BF16 operands and faster than the CUDA-core products).
+bool tucker_jadj_tc_supported(const mpi_basis* b, const mpi_plan* plan, int C, mpi_precision prec) {
+  if ((prec != MPI_PREC_FP32 && prec != MPI_PREC_BF16) || !b->tucker || !b->Fh[0]) return false;
+  if (!tucker_x1_fused_supported(b, plan, C, prec) || !tucker_chain_on_tensor_cores(b, C)) return false;
+  if (b->n[0] != 64 && b->n[0] != 96 && b->n[0] != 128) return false;
+  const long B = (long)b->n[1] * b->n[2];
+  if (B % 32) return false;
+  return conj_chain_shapes(b, C);
+}
+
+// dalpha_c = U^H (conj(p) (.) w_c), w_c the inverse DFT along z of wk_c [C][n1][B]
+// (the per-coil data after the inverse passes along x and y).  `opbuf` holds
+// C n1 B complex elements (the x1^H operand); `tmp` the Tucker workspace.
+mpi_status tucker_jadj_alpha(mpi_ctx* ctx, const mpi_basis* b, const mpi_plan* plan, const float2* wk,
+                             const float2* p, float scale, int C, float2* opbuf, float2* dalpha, float2* tmp,
+                             float2* partials, size_t partial_cap) {
+  const int n1 = b->n[0], n2 = b->n[1], n3 = b->n[2];
+  const int r1 = b->r[0], r2 = b->r[1], r3 = b->r[2];
+  const long B = (long)n2 * n3, R = (long)r1 * r2 * r3;
+  const float2* tw = twiddle_table(ctx, n1);
+  if (!tw) return set_err(ctx, MPI_ERR_SHAPE, "Jacobian-adjoint: no twiddle table for n1");
+  float* op1 = (float*)opbuf;                                   // rows (c, x, y), K = 2 n1
+  float* op2 = align256<float>(tmp);                            // rows (c, a, x), K = 2 n2
+  float* op3 = align256<float>(op2 + (size_t)C * r1 * n3 * n2 * 2);  // rows (c, a, b), K = 2 n3
+  float* g = align256<float>(op3 + (size_t)C * r1 * r2 * n3 * 2);    // [C][R] complex
+  const dim3 grid((unsigned)(B / 32), (unsigned)C);
+  MPI_PROF(ctx, KF_EXPAND);
+  if (n1 == 64)
+    launch_pdl(ctx, k_jadj_operand<64>, grid, dim3(256), 0, wk, p, tw, (int)B, plan->nx, plan->ny, scale, op1);
+  else if (n1 == 96)
+    launch_pdl(ctx, k_jadj_operand<96>, grid, dim3(256), 0, wk, p, tw, (int)B, plan->nx, plan->ny, scale, op1);
+  else
+    launch_pdl(ctx, k_jadj_operand<128>, grid, dim3(256), 0, wk, p, tw, (int)B, plan->nx, plan->ny, scale, op1);
+  MPI_LAUNCH_CHECK(ctx, "k_jadj_operand");
+  bool ok1, ok2, ok3;
+  mpi_basis v1 = conj_view(b, 0, op1, (long)C * B, n1, &ok1);
+  mpi_basis v2 = conj_view(b, 1, op2, (long)C * r1 * n3, n2, &ok2);
+  mpi_basis v3 = conj_view(b, 2, op3, (long)C * r1 * r2, n3, &ok3);
+  mpi_status st = MPI_OK;
+  if (!ok1 || !ok2 || !ok3) st = set_err(ctx, MPI_ERR_UNSUPPORTED, "Jacobian-adjoint chain tensor maps");
+  // these kernels stream operands written by the kernel before: plain stream order
+  const bool pdl = ctx->pdl;
+  ctx->pdl = false;
+  if (!st) {  // x1^H: rows (c, x, y), K = z, column pairs a; out rows (c, a, x) with K = y
+    ExpandArgs a;
+    a.N = (int)(C * B);
+    a.q = n1;
+    a.C = r1;
+    a.alpha = b->Fh[0];
+    a.out = (float2*)op2;
+    a.sc.L0 = n2;
+    a.sc.L1 = n3;
+    a.sc.s_hi = (long)r1 * n3 * 2 * n2;
+    a.sc.s_mid = 2L * n2;
+    a.sc.s_col = (long)n3 * 2 * n2;
+    a.sc.im = n2;
+    a.kname = "k_expand_tf32x3<tucker x1h>";
+    st = expand(ctx, &v1, EX_SCATTER, a, MPI_PREC_FP32);
+  }
+  if (!st) {  // x2^H: rows (c, a, x), K = y, column pairs b; out rows (c, a, b) with K = x
+    ExpandArgs a;
+    a.N = (int)((long)C * r1 * n3);
+    a.q = n2;
+    a.C = r2;
+    a.alpha = b->Fh[1];
+    a.out = (float2*)op3;
+    a.sc.L0 = n3;
+    a.sc.L1 = r1;
+    a.sc.s_hi = (long)r1 * r2 * 2 * n3;
+    a.sc.s_mid = (long)r2 * 2 * n3;
+    a.sc.s_col = 2L * n3;
+    a.sc.im = n3;
+    a.kname = "k_expand_tf32x3<tucker x2h>";
+    st = expand(ctx, &v2, EX_SCATTER, a, MPI_PREC_FP32);
+  }
+  if (!st) {  // x3^H: rows (c, a, b), K = x, column pairs d; out g [C][R] complex
+    ExpandArgs a;
+    a.N = (int)((long)C * r1 * r2);
+    a.q = n3;
+    a.C = r3;
+    a.alpha = b->Fh[2];
+    a.out = (float2*)g;
+    a.sc.L0 = 1;
+    a.sc.L1 = 1 << 30;
+    a.sc.s_mid = 2L * r3;
+    a.sc.s_col = 2;
+    a.sc.im = 1;
+    a.kname = "k_expand_tf32x3<tucker x3h>";
+    st = expand(ctx, &v3, EX_SCATTER, a, MPI_PREC_FP32);
+  }
+  ctx->pdl = pdl;
+  v1.Uf32 = v2.Uf32 = v3.Uf32 = nullptr;  // views own nothing
+  v1.tmap32 = v2.tmap32 = v3.tmap32 = nullptr;
+  if (st) return st;
+  (void)R;
+  return uh_v(ctx, b->core, (const float2*)g, C, dalpha, partials, partial_cap, MPI_PREC_FP32);
 }
 
 mpi_status launch_pointwise(mpi_ctx* ctx, int mode, const ExpandArgs& a, const float2* S, const float2* dS) {

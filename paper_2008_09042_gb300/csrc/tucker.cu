@@ -10,14 +10,17 @@
 //      first (x3 U3, then x2 U2, then x1 U1), which keeps the intermediate
 //      tensors smallest;
 // and the adjoint U^H v runs the conjugate-transposed mode products in the
-// reverse order followed by the core's U^H V contraction.  The x3 and x2 mode
-// products are FP32 complex on CUDA cores.  The x1 product, which carries most
-// of the arithmetic, runs on the tensor-core expansion kernels (3xTF32 for FP32,
-// BF16): over all coils it is a dense expansion whose basis rows are the
-// positions (c, y, x) of T2 with K = r1 and whose coefficient rows are the rows
-// of U1.  Its maps are combined with the image in a point-wise kernel.  Where
-// the tensor-core kernels cannot take it, the forward's x1 product runs on the
-// CUDA cores fused with the point-wise step.
+// reverse order followed by the core's U^H V contraction.  FP32: the whole
+// chain, and the Jacobian-adjoint's conjugate chain, on the 3xTF32 tensor-core
+// kernel, each product written by its scatter epilogue in the K-major rows the
+// next one streams (tucker_chain_tc, tucker_jadj_alpha); the x1 product fused
+// with the operator steps around it (tc_tucker.cu).  BF16 and the shapes those
+// kernels do not take: the x3 and x2 products (and the conjugate ones) as FP32
+// complex on the CUDA cores (k_mode_last, k_mode_b), the x1 product on the
+// tensor-core expansion kernels (over all coils a dense expansion whose basis
+// rows are the positions (c, y, x) of T2 with K = r1 and whose coefficient rows
+// are the rows of U1) or, forward only, on the CUDA cores fused with the
+// point-wise step.
 #include <cuda.h>
 #include <cuda_bf16.h>
 

@@ -104,6 +104,29 @@ int64_t mpi_ctx_workspace_bytes(const mpi_ctx* ctx);
  * k < 0 switches it off.  Library machinery, no paper passage. */
 mpi_status mpi_ctx_set_wait_limit(mpi_ctx* ctx, int64_t cycles);
 mpi_status mpi_ctx_inject_stall(mpi_ctx* ctx, int stages);
+/* How the tensor core reads an FP32 shared-memory operand of a kind::tf32 MMA.
+ * The FP32 tensor-core kernels (the 3xTF32 split x = hi(x) + lo(x) behind the
+ * FP32 basis expansion of Eq. 5, its Jacobian forms of Eq. 7 and the
+ * Jacobian-adjoint display after it, the Tucker mode products of Eq. 19 and
+ * the coefficient block U^H v) feed each raw FP32 tile as hi(x) and add lo(x)
+ * separately, which is exact only if the tensor core reads the FP32 value as
+ * its upper 19 bits (truncation).  mpi_ctx_create measures the reading with
+ * one MMA on 128 test values (ties, values just above and below a TF32 step,
+ * both signs) and returns it here: MPI_TF32_READ_TRUNCATE (measured on GB300),
+ * _NEAREST_EVEN, _NEAREST_AWAY, _FULL (all 23 bits), _OTHER, or _FAILED (the
+ * probe did not run).  Only MPI_TF32_READ_TRUNCATE enables the 3xTF32 kernels;
+ * any other reading sends every FP32 call to the CUDA-core FP32 kernels (the
+ * paths MPI_PREC_FP32_SIMT takes, and for Tucker bases the CUDA-core mode
+ * products), so FP32 results keep their accuracy on any device.  -1 for a
+ * null context.  mpi_ctx_set_tf32x3(ctx, 0) switches the 3xTF32 kernels off
+ * for later calls (graphs already recorded by solvers or batches keep the
+ * kernels they were recorded with); (ctx, 1) switches them back on and is
+ * MPI_ERR_UNSUPPORTED unless the probe found truncation.  Library machinery,
+ * no paper passage. */
+enum { MPI_TF32_READ_FAILED = -2, MPI_TF32_READ_TRUNCATE = 0, MPI_TF32_READ_NEAREST_EVEN = 1,
+       MPI_TF32_READ_NEAREST_AWAY = 2, MPI_TF32_READ_FULL = 3, MPI_TF32_READ_OTHER = 4 };
+int mpi_ctx_tf32_reading(const mpi_ctx* ctx);
+mpi_status mpi_ctx_set_tf32x3(mpi_ctx* ctx, int enable);
 /* Launch-shape autotuning (on by default).  The first operator call that runs an
  * FFT line pass of a new shape (length, stride, line count, row mask) times each
  * candidate tile width of that pass with CUDA events on a free workspace buffer

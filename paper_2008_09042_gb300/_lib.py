@@ -28,7 +28,7 @@ EXPORTS = [
     "mpi_batch_destroy", "mpi_expand_path", "mpi_forward_host", "mpi_adjoint_host", "mpi_maxwell_basis_2d",
     "mpi_forward_maps", "mpi_adjoint_maps", "mpi_jacobian_maps", "mpi_jacobian_adjoint_maps", "mpi_sm_estimate_maps",
     "mpi_maxwell_basis_3d", "mpi_tucker_compress", "mpi_image_solve_dynamic",
-    "mpi_batch_group_count",
+    "mpi_batch_group_count", "mpi_ctx_tf32_reading", "mpi_ctx_set_tf32x3",
 ]
 
 
@@ -96,6 +96,7 @@ def load(path=LIB_PATH):
         "mpi_ctx_set_line_kernel": [vp, i],
         "mpi_ctx_set_wait_limit": [vp, i64],
         "mpi_ctx_inject_stall": [vp, i],
+        "mpi_ctx_set_tf32x3": [vp, i],
         "mpi_ctx_tuning_record": [vp, i, ctypes.POINTER(ctypes.c_char_p)],
         "mpi_ctx_profile": [vp, i],
         "mpi_ctx_profile_read": [vp, i, ctypes.POINTER(d), ctypes.POINTER(i64), i],
@@ -149,6 +150,8 @@ def load(path=LIB_PATH):
     lib.mpi_batch_kernel_count.restype = i64
     lib.mpi_batch_group_count.argtypes = [vp]
     lib.mpi_batch_group_count.restype = i
+    lib.mpi_ctx_tf32_reading.argtypes = [vp]
+    lib.mpi_ctx_tf32_reading.restype = i
     _lib = lib
     return lib
 

@@ -64,6 +64,18 @@ class Context:
         expansion's copy producer stops after `stages` ring stages (-1: off)."""
         check(self.h, self.lib.mpi_ctx_inject_stall(self.h, int(stages)))
 
+    TF32_READINGS = {-2: "failed", 0: "truncate", 1: "nearest_even", 2: "nearest_away", 3: "full", 4: "other"}
+
+    def tf32_reading(self):
+        """How the tensor core reads FP32 operands of kind::tf32, as measured when
+        the context was made ("truncate" enables the 3xTF32 kernels)."""
+        return self.TF32_READINGS.get(int(self.lib.mpi_ctx_tf32_reading(self.h)), "other")
+
+    def set_tf32x3(self, enable=True):
+        """Switch the 3xTF32 tensor-core kernels off (FP32 then runs on the CUDA
+        cores) or back on (only where the probe found the truncating reading)."""
+        check(self.h, self.lib.mpi_ctx_set_tf32x3(self.h, 1 if enable else 0))
+
     def set_line_kernel(self, choice=0):
         """Fix the FFT line passes' kernel: 8, 16, 32 (lines per CTA), -1 (register
         two-step pass along y) or 0 (tuned)."""

@@ -150,6 +150,11 @@ mpi_status expand(mpi_ctx* ctx, const mpi_basis* basis, int mode, const ExpandAr
     // and of the per-coil output
     if (g > 0) return launch_expand_tf32(ctx, basis, mode, a, g);
   }
+  if (a.kname && strncmp(a.kname, "k_expand_t", 10) == 0) {  // a tensor-core label: profile under the FFMA name
+    ExpandArgs f = a;
+    f.kname = "k_expand";
+    return launch_expand(ctx, mode, f);
+  }
   return launch_expand(ctx, mode, a);
 }
 
@@ -293,6 +298,11 @@ extern "C" mpi_status mpi_ctx_create(mpi_ctx** out, int device, void* cuda_strea
   // which the driver would otherwise load (and reserve 16 MiB for) at that
   // call's first use; load it now, while allocating is allowed.
   if (e == cudaSuccess) e = noalloc_preload();
+  if (e == cudaSuccess) {
+    ctx->tf32_read = tf32_reading_probe(ctx);
+    ctx->tf32x3 = ctx->tf32_read == MPI_TF32_READ_TRUNCATE;
+    if (ctx->tf32_read == MPI_TF32_READ_FAILED) e = cudaErrorLaunchFailure;  // no kernel of this library runs
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (ctx->twiddles) cudaFree(ctx->twiddles);
@@ -453,6 +463,16 @@ extern "C" mpi_status mpi_ctx_set_wait_limit(mpi_ctx* ctx, int64_t cycles) {
   if (!ctx) return MPI_ERR_ARG;
   if (cycles < 1000) return set_err(ctx, MPI_ERR_ARG, "wait limit below 1000 cycles");
   ctx->wait_cycles = cycles;
+  return MPI_OK;
+}
+
+extern "C" int mpi_ctx_tf32_reading(const mpi_ctx* ctx) { return ctx ? ctx->tf32_read : -1; }
+
+extern "C" mpi_status mpi_ctx_set_tf32x3(mpi_ctx* ctx, int enable) {
+  if (!ctx) return MPI_ERR_ARG;
+  if (enable && ctx->tf32_read != MPI_TF32_READ_TRUNCATE)
+    return set_err(ctx, MPI_ERR_UNSUPPORTED, "3xTF32 needs the truncating reading of FP32 kind::tf32 operands");
+  ctx->tf32x3 = enable != 0;
   return MPI_OK;
 }
 

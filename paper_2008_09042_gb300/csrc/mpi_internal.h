@@ -60,6 +60,8 @@ struct mpi_ctx {
   bool plane_pipe = true;  // ... as the pipelined persistent kernel (TMA tiles) where it applies
   long long wait_cycles = 4LL << 30;  // bounded-wait limit of the tensor-core kernels (SM clock cycles)
   int stall_after = -1;               // fault injection in the 3xTF32 expansion's producer (-1: off)
+  int tf32_read = MPI_TF32_READ_FAILED;  // the tensor core's reading of FP32 kind::tf32 operands (probed)
+  bool tf32x3 = false;                   // 3xTF32 kernels on (only with the truncating reading)
   void* tune_scratch = nullptr;
   size_t tune_scratch_bytes = 0;
   struct TuneRecord {
@@ -268,6 +270,9 @@ void tc_basis_release(mpi_basis* b);
 // (grid rows), each row streaming the same basis tiles in step.
 mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a, int group_coils = 0);
 bool tf32_supported(const mpi_basis* b, int mode, int C);
+// Measures how the tensor core reads an FP32 operand of kind::tf32 (one MMA on
+// the context's stream, synchronised); returns an MPI_TF32_READ_* value.
+int tf32_reading_probe(mpi_ctx* ctx);
 // Coils per launch of the 3xTF32 kernel: C when the whole call fits, else the
 // largest group that fits (forward-type modes only), or 0.
 int tf32_group(const mpi_basis* b, int mode, int C);

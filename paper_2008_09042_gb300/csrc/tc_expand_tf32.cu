@@ -28,6 +28,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "mpi_internal.h"
 #include "ptx.cuh"
@@ -296,6 +297,75 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
   }
 }
 
+// FP32 bit pattern of row r's test value in the operand-reading probe: the low
+// 13 mantissa bits (the part a TF32 reading drops or rounds away) take
+// half-way, just-above, just-below and scattered patterns, the sign alternates.
+__host__ __device__ inline uint32_t tf32_probe_bits(int r) {
+  constexpr uint32_t kLow[8] = {0x1000u, 0x1000u, 0x1FFFu, 0x0001u, 0x0FFFu, 0x1001u, 0x0800u, 0x17A5u};
+  uint32_t hi = ((uint32_t)r * 2654435761u) >> 9;  // 23 scattered bits
+  uint32_t low = r < 8 ? kLow[r] : (hi & 0x1FFFu);
+  if (r == 1) hi |= 0x2000u;  // a tie whose kept part is odd (nearest-even rounds up, nearest-away too)
+  if (r == 0) hi &= ~0x2000u; // a tie whose kept part is even (nearest-even keeps it)
+  return ((uint32_t)(r & 1) << 31) | (127u << 23) | (hi & 0x7FE000u) | low;
+}
+
+// One kind::tf32 MMA, D = A B^T with A = 128 rows of one test value each (first
+// K column; the other 31 zero) and B row 0 = e_0, so D[r][0] is exactly the
+// value the tensor core took for A[r][0].  One CTA of 128 threads; the wait on
+// the MMA's completion is bounded (on time-out the row reads NaN).
+__global__ void __launch_bounds__(128, 1) k_tf32_reading(float* __restrict__ out, int* err, long long wait_cycles) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (mpi_ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sA = smem;                  // 128 rows x 32 FP32, 128-byte swizzle
+  unsigned char* sB = smem + kTileM * 128;   // 16 rows x 32 FP32
+  uint64_t* done = reinterpret_cast<uint64_t*>(sB + 16 * 128);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int k = 0; k < kKChunk32; ++k) {
+    const float v = k == 0 ? __uint_as_float(tf32_probe_bits(tid)) : 0.f;
+    *reinterpret_cast<float*>(sA + sw128_offset_e(tid, k, kTileM, 4)) = v;
+  }
+  for (int e = tid; e < 16 * kKChunk32; e += 128) {
+    const int n = e / kKChunk32, k = e % kKChunk32;
+    *reinterpret_cast<float*>(sB + sw128_offset_e(n, k, 16, 4)) = (n == 0 && k == 0) ? 1.f : 0.f;
+  }
+  mpi_ptx::fence_proxy_async();  // the tensor core reads what the threads wrote
+  if (tid == 0) {
+    mpi_ptx::mbar_init(done, 1);
+    mpi_ptx::fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(mpi_ptx::smem_addr(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (tid == 0) {
+    mma_tf32(tmem, sdesc_sw128(mpi_ptx::smem_addr(sA)), sdesc_sw128(mpi_ptx::smem_addr(sB)), idesc_tf32(kTileM, 16), 0);
+    mma_commit(done);
+  }
+  const bool ok = mpi_ptx::mbar_wait(done, 0, err, wait_cycles);
+  fence_after();
+  float r = __uint_as_float(0x7FC00000u);
+  if (__all_sync(0xffffffffu, ok)) {
+    uint32_t v[16];
+    tmem_ld16_start(tmem + ((uint32_t)(warp * 32) << 16), v);
+    tmem_wait_ld();
+    reg_fence16(v);
+    r = __uint_as_float(v[0]);
+  }
+  out[tid] = r;
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+  }
+}
+
 __global__ void k_basis_to_f32(const float2* __restrict__ U, int N, int q, int Kp, float* __restrict__ out) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (size_t)N * Kp) return;
@@ -423,7 +493,46 @@ void tf32_basis_release(mpi_basis* b) {
 
 bool tf32_supported(const mpi_basis* b, int mode, int C) {
   TfPlan p;
+  // the 3xTF32 split is exact only where the probe found the truncating reading
+  if (!b->ctx || !b->ctx->tf32x3) return false;
   return b->Uf32 && b->tmap32 && plan_tf32(b, mode, C, &p);
+}
+
+int tf32_reading_probe(mpi_ctx* ctx) {
+  float* d = nullptr;
+  if (cudaMalloc(&d, 128 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return MPI_TF32_READ_FAILED;
+  }
+  const size_t smem = kTileM * 128 + 16 * 128 + 64 + 1024;
+  k_tf32_reading<<<1, 128, smem, ctx->stream>>>(d, ctx->dev_err, ctx->wait_cycles);
+  cudaError_t e = cudaGetLastError();
+  float h[128];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream);  // a timed-out wait
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MPI_TF32_READ_FAILED;
+  }
+  // compare each row with the candidate readings of its value (sign-magnitude
+  // bits: rounding the magnitude is rounding the value symmetrically)
+  bool trunc = true, even = true, away = true, full = true;
+  for (int r = 0; r < 128; ++r) {
+    const uint32_t x = tf32_probe_bits(r);
+    uint32_t g;
+    memcpy(&g, &h[r], 4);
+    trunc &= g == (x & ~0x1FFFu);
+    even &= g == ((x + 0x0FFFu + ((x >> 13) & 1u)) & ~0x1FFFu);
+    away &= g == ((x + 0x1000u) & ~0x1FFFu);
+    full &= g == x;
+  }
+  if (trunc) return MPI_TF32_READ_TRUNCATE;
+  if (even) return MPI_TF32_READ_NEAREST_EVEN;
+  if (away) return MPI_TF32_READ_NEAREST_AWAY;
+  if (full) return MPI_TF32_READ_FULL;
+  return MPI_TF32_READ_OTHER;
 }
 
 int tf32_group(const mpi_basis* b, int mode, int C) {

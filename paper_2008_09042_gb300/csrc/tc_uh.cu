@@ -470,7 +470,7 @@ void uh_tc_release(mpi_basis* b) {
 }
 
 bool uh_tc_supported(const mpi_basis* b, mpi_precision prec) {
-  if (prec == MPI_PREC_FP32) return b->umap32 != nullptr;
+  if (prec == MPI_PREC_FP32) return b->umap32 != nullptr && b->ctx && b->ctx->tf32x3;  // 3xTF32 split
   if (prec == MPI_PREC_BF16) return b->umap_bf != nullptr;
   return false;
 }

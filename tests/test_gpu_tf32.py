@@ -117,3 +117,66 @@ def test_fp32_operator_family_matches_oracle(ctx, mp, prec, shape, C, q):
     rp, ra = op.jacobian_adjoint(Fs, U, a, p, r)
     assert rel(f64(gp), rp) < TOL and rel(f64(ga), ra) < TOL
     ctx.synchronize()  # raises if a bounded wait ran out
+
+
+def test_tf32_reading_probe_and_cuda_core_route(mp):
+    # The 3xTF32 kernels pass each raw FP32 tile as hi(x) and add lo(x) = x - hi(x)
+    # separately, which is exact only if the tensor core reads an FP32 operand of
+    # kind::tf32 by truncation to 19 bits.  The context measures that reading when
+    # it is made; any other reading sends FP32 work to the CUDA-core kernels.  Here
+    # the reading is checked, then the route taken with the 3xTF32 kernels switched
+    # off is held to the same FP32 tolerance, dense and Tucker, every operator.
+    from oracle import tucker
+
+    ctx = mp.Context(0)
+    assert ctx.tf32_reading() == "truncate"
+    n, C, q = 64, 4, 24
+    U = _basis(n * n, q, 5)
+    idx = w.mask_to_indices(w.vd_lines_mask(n, n, 3, 16, seed=2))
+    Fs = fourier.CartesianSampling((n, n), idx)
+    plan = mp.Plan(ctx, (n, n), sample_idx=idx)
+    B = mp.Basis(ctx, U.T)
+    a2 = w.random_coefficients(C, q, seed=3).astype(np.complex64).astype(np.complex128)
+    p2 = w.random_image(n * n, seed=4).astype(np.complex64).astype(np.complex128)
+    y_ref = op.forward(Fs, U, a2, p2)
+    assert mp.expand_path(ctx, B, C) == "tf32x3"
+    ctx.set_tf32x3(False)
+    assert mp.expand_path(ctx, B, C) == "ffma"
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+
+    def four_operators(plan, B, Fs, basis_ref, a, p, N, M, Cn, qn):
+        dp = w.random_image(N, seed=5).astype(np.complex64).astype(np.complex128)
+        da = w.random_coefficients(Cn, qn, seed=6).astype(np.complex64).astype(np.complex128)
+        r = w.random_coefficients(Cn, M, seed=7, decay=False).astype(np.complex64).astype(np.complex128)
+        ag, pg = c64(a), c64(p)
+        assert rel(f64(mp.forward(ctx, plan, B, ag, pg)), op.forward(Fs, basis_ref, a, p)) < TOL
+        assert rel(f64(mp.adjoint(ctx, plan, B, ag, c64(r))), op.adjoint(Fs, basis_ref, a, r)) < TOL
+        assert rel(f64(mp.jacobian(ctx, plan, B, ag, pg, c64(dp), c64(da))),
+                   op.jacobian(Fs, basis_ref, a, p, dp, da)) < TOL
+        gp, ga = mp.jacobian_adjoint(ctx, plan, B, ag, pg, c64(r))
+        rp, ra = op.jacobian_adjoint(Fs, basis_ref, a, p, r)
+        assert rel(f64(gp), rp) < TOL and rel(f64(ga), ra) < TOL
+
+    four_operators(plan, B, Fs, U, a2, p2, n * n, idx.size, C, q)
+
+    dims, ranks, qt, Ct = (16, 32, 48), (4, 6, 8), 12, 3
+    core, fac = w.smooth_tucker_basis(dims, ranks, qt, seed=1)
+    core = core.astype(np.complex64).astype(np.complex128)
+    fac = [f.astype(np.complex64).astype(np.complex128) for f in fac]
+    idx3 = w.mask_to_indices(w.poisson_disc_mask_3d(*dims, R=3, calib=(6, 6), seed=2))
+    N3 = int(np.prod(dims))
+    a3 = w.random_coefficients(Ct, qt, seed=3).astype(np.complex64).astype(np.complex128)
+    p3 = w.random_image(N3, seed=4).astype(np.complex64).astype(np.complex128)
+    four_operators(mp.Plan(ctx, dims, sample_idx=idx3), mp.TuckerBasis(ctx, core, fac),
+                   fourier.CartesianSampling(dims, idx3), tucker.TuckerBasis(core, fac), a3, p3, N3, idx3.size,
+                   Ct, qt)
+    ctx.synchronize()
+    _, kernels = ctx.profile_read(kernels=True)
+    assert kernels and not any("tf32" in k or "k_uh_tc" in k for k in kernels), sorted(kernels)
+    ctx.profile(False)
+    # back on: the tensor-core route again, same result
+    ctx.set_tf32x3(True)
+    assert mp.expand_path(ctx, B, C) == "tf32x3"
+    assert rel(f64(mp.forward(ctx, plan, B, c64(a2), c64(p2))), y_ref) < TOL
+    ctx.synchronize()

@@ -173,7 +173,8 @@ def kernel_bytes_per_pair(case, prec):
         # the FP32 tensor-core chain (core -> x3 -> x2), each product written
         # in the next one's operand layout; twice per pair
         out["k_expand_tf32x3<tucker x3>"] = 2 * (8 * C * R + 8 * C * r1 * r2 * n3)
-        out["k_expand_tf32x3<tucker x2>"] = 2 * (8 * C * r1 * r2 * n3 + 8 * C * r1 * n2 * n3)
+        # (BF16: the x2 product writes the x1 operand as BF16 rows)
+        out["k_expand_tf32x3<tucker x2>"] = 2 * (8 * C * r1 * r2 * n3 + 2 * ob * C * r1 * n2 * n3)
         # the fused x1 kernels: operand in; forward: image in, DFT'd volume out;
         # adjoint: per-coil data in, image out
         pk = "bf16" if prec == "bf16" else "tf32x3"

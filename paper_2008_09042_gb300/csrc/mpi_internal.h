@@ -213,6 +213,7 @@ struct ScatterMap {
   int L0 = 1, L1 = 1;
   long s_hi = 0, s_mid = 0, s_col = 0;
   int im = 0;
+  bool bf16 = false;  // write BF16 values (the same element offsets) instead of FP32
 };
 
 // One row of a grouped expansion launch (grid row blockIdx.y): a slice that
@@ -281,6 +282,9 @@ void tf32_basis_release(mpi_basis* b);
 // Tensor maps of a K-major operand [rows][Kp] (BF16 or FP32) laid out as the
 // tensor-core kernels read their basis copies; `map` is a CUtensorMap.
 bool tc_encode_operand_map(void* map, void* ptr, long rows, int Kp);
+// BF16 operand rows of K values (K a multiple of 8) read as 64-element boxes;
+// columns past K read as zeros.
+bool tc_encode_operand_map_k(void* map, void* ptr, long rows, int K);
 bool tf32_encode_operand_map(void* map, void* ptr, long rows, int Kp);
 // FP32 operand of `rows` rows of K (a multiple of 4) values, read by the 3xTF32
 // kernel as Kp = round_up(K, 64) columns (the rest zero-filled by the copy engine).

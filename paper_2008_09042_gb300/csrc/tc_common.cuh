@@ -36,6 +36,7 @@ struct TcArgs {
   // EX_SCATTER output map (see ScatterMap); sc_col0 = the launch row's first column pair
   int sc_L0, sc_L1, sc_im, sc_col0;
   long sc_hi, sc_mid, sc_col;
+  int sc_bf16;            // EX_SCATTER: BF16 outputs (same element offsets)
   int accumulate;         // EX_FWD / EX_JFWD: add into out instead of storing
   const ExpandRow* rows;  // grouped launch: row blockIdx.y's pointers and coil count (nullptr: none)
   long long wait_cycles;  // bounded-wait limit (SM clock cycles)
@@ -271,7 +272,7 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
       const bool valid = n < a.N;
       const int nn = valid ? n : 0;
       const float sg = (a.centre ? centre_sign(nn, a.nx, a.ny) : 1.f) * a.scale;
-      const float2 pimg = (MODE != EX_MAPS) ? a.p[nn] : make_float2(0.f, 0.f);
+      const float2 pimg = (MODE != EX_MAPS && MODE != EX_SCATTER) ? a.p[nn] : make_float2(0.f, 0.f);
       // maps mode: where coil c of pixel n goes ([C][N], or the Tucker remap)
       size_t maps_base = (size_t)n, maps_cstride = (size_t)a.N;
       if (MODE == EX_MAPS && a.tuck_B) {
@@ -329,7 +330,11 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
           if (MODE == EX_MAPS) {
             if (cv) a.out[maps_base + (size_t)c * maps_cstride] = s;
           } else if (MODE == EX_SCATTER) {
-            if (cv) {
+            if (cv && a.sc_bf16) {
+              __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out) + sc_base + (size_t)c * a.sc_col;
+              o[0] = __float2bfloat16_rn(s.x);
+              o[a.sc_im] = __float2bfloat16_rn(s.y);
+            } else if (cv) {
               float* o = reinterpret_cast<float*>(a.out) + sc_base + (size_t)c * a.sc_col;
               o[0] = s.x;
               o[a.sc_im] = s.y;

@@ -248,6 +248,24 @@ bool tc_encode_operand_map(void* map, void* ptr, long rows, int Kp) {
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tc_encode_operand_map_k(void* map, void* ptr, long rows, int K) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+  if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn || K % 8) {
+    cudaGetLastError();
+    return false;
+  }
+  // K columns stored; boxes past K (up to the kernel's Kp) read as zeros
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {(cuuint32_t)kKChunk, (cuuint32_t)kTileM};
+  const cuuint32_t estr[2] = {1, 1};
+  return ((EncodeTiledFn)fn)((CUtensorMap*)map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void tc_basis_release(mpi_basis* b) {
   delete (CUtensorMap*)b->tmap;
   b->tmap = nullptr;
@@ -290,6 +308,14 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
   a.group_coils = 0;
   a.C_total = x.C;
   a.tuck_stride = x.tuck_stride;
+  a.sc_L0 = x.sc.L0;
+  a.sc_L1 = x.sc.L1;
+  a.sc_hi = x.sc.s_hi;
+  a.sc_mid = x.sc.s_mid;
+  a.sc_col = x.sc.s_col;
+  a.sc_im = x.sc.im;
+  a.sc_col0 = 0;
+  a.sc_bf16 = x.sc.bf16 ? 1 : 0;
   const size_t b_bytes = round_up(a.n_gemm * b->Kp * 2, 1024);
   // Two CTAs per SM (one's epilogue overlaps the other's loads) when each can
   // still keep four or more stages in flight within half of the SM's shared
@@ -324,6 +350,7 @@ mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const Ex
     MPI_TC_CASE(EX_JFWD)
     MPI_TC_CASE(EX_ADJ)
     MPI_TC_CASE(EX_JADJ)
+    MPI_TC_CASE(EX_SCATTER)
     default:
       return set_err(ctx, MPI_ERR_ARG, "unknown expansion mode");
   }

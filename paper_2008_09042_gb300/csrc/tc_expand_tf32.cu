@@ -586,6 +586,7 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.sc_mid = x.sc.s_mid;
   a.sc_col = x.sc.s_col;
   a.sc_im = x.sc.im;
+  a.sc_bf16 = x.sc.bf16 ? 1 : 0;
   a.sc_col0 = 0;
   a.group_coils = groups > 1 ? Cg : 0;
   a.C_total = x.C;

@@ -442,18 +442,23 @@ void operand_view(const mpi_basis* b, void* ptr, void* map, long rows, int q, mp
 
 // Tensor map cache of the chain's operands (re-encoded when the address or
 // the row count changes).
-// Slots 0-2: the forward chain's operands; 3-5: the conjugate chain's.
+// Slots 0-2: the forward chain's operands; 3-5: the conjugate chain's; 6: the
+// BF16 x1 operand the chain writes for the BF16 x1 kernel.
+constexpr int kChainSlots = 7;
+constexpr int kSlotX1Bf16 = 6;
 struct ChainMaps {
-  CUtensorMap m[6];
-  const void* ptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  long rows[6] = {0, 0, 0, 0, 0, 0};
+  CUtensorMap m[kChainSlots];
+  const void* ptr[kChainSlots] = {};
+  long rows[kChainSlots] = {};
 };
 
 bool chain_map(mpi_basis* b, int i, void* ptr, long rows, int K, void** out) {
   if (!b->chain_maps) b->chain_maps = new ChainMaps;
   ChainMaps* cm = (ChainMaps*)b->chain_maps;
   if (cm->ptr[i] != ptr || cm->rows[i] != rows) {
-    if (!tf32_encode_operand_map_k(&cm->m[i], ptr, rows, K)) {
+    const bool ok = i == kSlotX1Bf16 ? tc_encode_operand_map_k(&cm->m[i], ptr, rows, K)
+                                     : tf32_encode_operand_map_k(&cm->m[i], ptr, rows, K);
+    if (!ok) {
       cm->ptr[i] = nullptr;
       return false;
     }
@@ -489,18 +494,30 @@ bool tucker_chain_on_tensor_cores(const mpi_basis* b, int C) {
   return ok;
 }
 
+// BF16 form of the chain: the BF16 core contraction's coefficient rows fit one
+// MMA (2 C <= 256), the core has its BF16 copy, and the BF16 x1 operand rows
+// (2 r1 values) are whole 16-byte units.
+static bool tucker_chain_bf16_ok(const mpi_basis* b, int C) {
+  return C <= 128 && b->core && b->core->Ubf && b->core->tmap && (2 * b->r[0]) % 8 == 0;
+}
+
 namespace {
 
-// The FP32 chain on the tensor cores, every product written by the 3xTF32
-// kernel's scatter epilogue straight into the real-ified K-major rows the next
-// one streams:
+// The chain on the tensor cores, every product written by a scatter epilogue
+// straight into the real-ified K-major rows the next one streams.  FP32: all
+// three products on the 3xTF32 kernel.  BF16: the core contraction on the BF16
+// kernel (BF16 core and coefficients, FP32 output rows), x3 and x2 on the
+// 3xTF32 kernel, x2 writing the x1 operand as BF16 rows for the BF16 x1 kernel
+// (so the only BF16 roundings are those of the BF16 path's core, coefficients,
+// x1 operand and U1):
 //   g  = G alpha_c            rows (c, a, b) x [Re g(d) | Im g(d)]       (K = 2 r3)
 //   t1 = g x3 U3              rows (c, x, a) x [Re t1(b) | Im t1(b)]     (K = 2 r2)
 //   op = t1 x2 U2             rows (c, y, x) x [Re t2(a) | Im t2(a)]     (K = 2 r1)
 // (a, b, d index the ranks r1, r2, r3; z, y, x the grid n1, n2, n3).  Each
 // factor's rows are the coefficient rows of its product.
-mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp, void** op_out,
-                           void** map_out) {
+mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp,
+                           mpi_precision prec, void** op_out, void** map_out) {
+  const bool bf = prec == MPI_PREC_BF16;
   const int n2 = b->n[1], n3 = b->n[2];
   const int r1 = b->r[0], r2 = b->r[1], r3 = b->r[2];
   const long R = (long)r1 * r2 * r3;
@@ -511,7 +528,7 @@ mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha
   const long rows3 = (long)C * r1 * r2, rows2 = (long)C * n3 * r1, rows1 = (long)C * n2 * n3;
   void *m3 = nullptr, *m2 = nullptr, *m1 = nullptr;
   if (!chain_map(mb, 0, g, rows3, 2 * r3, &m3) || !chain_map(mb, 1, t1, rows2, 2 * r2, &m2) ||
-      !chain_map(mb, 2, op, rows1, 2 * r1, &m1))
+      !chain_map(mb, bf ? kSlotX1Bf16 : 2, op, rows1, 2 * r1, &m1))
     return set_err(ctx, MPI_ERR_UNSUPPORTED, "Tucker chain tensor maps");
   // the core contraction: rows (a, b, d) of the core, column pairs = coils
   ExpandArgs a;
@@ -526,8 +543,8 @@ mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha
   a.sc.s_mid = 2L * r3;
   a.sc.s_col = R / r3 * 2L * r3;
   a.sc.im = r3;
-  a.kname = "k_expand_tf32x3<tucker core>";
-  mpi_status st = expand(ctx, b->core, EX_SCATTER, a, MPI_PREC_FP32);
+  a.kname = bf ? "k_expand_tc<tucker core>" : "k_expand_tf32x3<tucker core>";
+  mpi_status st = expand(ctx, b->core, EX_SCATTER, a, bf ? MPI_PREC_BF16 : MPI_PREC_FP32);
   if (st) return st;
   // x3: rows (c, a, b) with K = d, column pairs = x; out rows (c, x, a)
   // (these kernels stream operands written by the kernel before: plain stream order)
@@ -564,6 +581,7 @@ mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha
     a2.sc.s_mid = 2L * r1;
     a2.sc.s_col = (long)n3 * 2 * r1;
     a2.sc.im = r1;
+    a2.sc.bf16 = bf;
     a2.kname = "k_expand_tf32x3<tucker x2>";
     st = expand(ctx, &v, EX_SCATTER, a2, MPI_PREC_FP32);
   }
@@ -583,11 +601,13 @@ mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha
 // [(c, b)][Kp] (FP32 or BF16) at a 256-byte aligned place in `tmp`; returns the
 // operand and its tensor map (re-encoded only when the workspace, C or the
 // precision change).  FP32 with even ranks: the whole chain on the tensor cores
-// (tucker_chain_tc), rows of 2 r1 values.
+// (tucker_chain_tc), rows of 2 r1 values; BF16 likewise where 2 r1 is a
+// multiple of 8 and the coils fit one BF16 core contraction (BF16 rows).
 mpi_status tucker_x1_operand(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha, int C, float2* tmp,
                              mpi_precision prec, void** op_out, void** map_out) {
-  if (prec == MPI_PREC_FP32 && tucker_chain_on_tensor_cores(b, C))
-    return tucker_chain_tc(ctx, b, alpha, C, tmp, op_out, map_out);
+  if ((prec == MPI_PREC_FP32 || (prec == MPI_PREC_BF16 && tucker_chain_bf16_ok(b, C))) &&
+      tucker_chain_on_tensor_cores(b, C))
+    return tucker_chain_tc(ctx, b, alpha, C, tmp, prec, op_out, map_out);
   float2* t2 = nullptr;
   mpi_status st = tucker_t2(ctx, b, alpha, C, tmp, prec, &t2);
   if (st) return st;

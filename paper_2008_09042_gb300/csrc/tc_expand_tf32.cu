@@ -160,9 +160,10 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
   const uint32_t tmem = *tmem_slot;
   const uint32_t tmem_lo = tmem + (uint32_t)(2 * a.half_cols);  // lo(U) slots, 32 columns per stage
   const int n_tiles = (a.N + kTileM - 1) / kTileM;
-  // ring stages this CTA processes (its tiles x KC / 2 boxes), numbered g = 0 .. G-1
+  // ring stages this CTA processes (its tiles x ceil(KC / 2)), numbered g = 0 .. G-1;
+  // with an odd box count KC the last stage of each tile holds one box
   const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int G = my_tiles * (a.KC / kBoxesPerStage);
+  const int G = my_tiles * ((a.KC + kBoxesPerStage - 1) / kBoxesPerStage);
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer: TMA tiles of U
@@ -174,12 +175,13 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
       if (a.stall_after >= 0 && g >= a.stall_after) break;
       if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err, a.wait_cycles)) break;
       unsigned char* dst = sA + (size_t)r.s * kStageBytes32;
-      mpi_ptx::mbar_arrive_expect_tx(&full[r.s], kStageBytes32);
+      const bool two = kc + 1 < a.KC;
+      mpi_ptx::mbar_arrive_expect_tx(&full[r.s], two ? kStageBytes32 : kBoxBytes32);
       tma_load_2d(dst, &tmap, kc * kKChunk32, t * kTileM, &full[r.s]);
-      tma_load_2d(dst + kBoxBytes32, &tmap, (kc + 1) * kKChunk32, t * kTileM, &full[r.s]);
+      if (two) tma_load_2d(dst + kBoxBytes32, &tmap, (kc + 1) * kKChunk32, t * kTileM, &full[r.s]);
       r.next(stages);
       kc += kBoxesPerStage;
-      if (kc == a.KC) {
+      if (kc >= a.KC) {
         kc = 0;
         t += (int)gridDim.x;
       }
@@ -196,14 +198,17 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     const int row = (warp & 3) * 32 + lane;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     RingPos r;
+    int kc = 0;  // first box of the stage (the last stage of a tile holds one box when KC is odd)
     for (int g = 0; g < G; ++g) {
       const bool got = mpi_ptx::mbar_wait(&full[r.s], r.ph, a.err, a.wait_cycles);
       if (!__all_sync(0xffffffffu, got)) {
         s_failed = 1;
         break;
       }
+      const int nb = kc + 1 < a.KC ? 2 : 1;
 #pragma unroll
       for (int h = 0; h < kBoxesPerStage; ++h) {
+        if (h >= nb) break;
         // the row's 32 FP32 values of box h: 16-byte unit j of a 128-byte row sits at unit j ^ (row % 8)
         const float4* x =
             reinterpret_cast<const float4*>(sA + (size_t)r.s * kStageBytes32 + h * kBoxBytes32 + row * 128);
@@ -223,6 +228,8 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
       __syncwarp();
       if (lane == 0) mpi_ptx::mbar_arrive(&conv[r.s]);
       r.next(stages);
+      kc += kBoxesPerStage;
+      if (kc >= a.KC) kc = 0;
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer: per 8-element K step, U_hi x [A_hi; A_lo] and U_lo x A_hi.
@@ -254,14 +261,17 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
         const uint64_t ad = a0 + (uint32_t)(s * (kStageBytes32 >> 4));
         const uint64_t bd = b0 + (uint32_t)kc * b_chunk;
         constexpr uint32_t kBoxDesc = kBoxBytes32 >> 4;
+        const bool two = kc + 1 < a.KC;  // else this stage holds one box (the last of a tile, KC odd)
         mma_tf32(tacc, ad, bd, idesc_hi, kc != 0);
         mma_tf32_acc(tacc, ad + 2, bd + 2, idesc_hi);
         mma_tf32_acc(tacc, ad + 4, bd + 4, idesc_hi);
         mma_tf32_acc(tacc, ad + 6, bd + 6, idesc_hi);
-        mma_tf32_acc(tacc, ad + kBoxDesc, bd + b_chunk, idesc_hi);
-        mma_tf32_acc(tacc, ad + kBoxDesc + 2, bd + b_chunk + 2, idesc_hi);
-        mma_tf32_acc(tacc, ad + kBoxDesc + 4, bd + b_chunk + 4, idesc_hi);
-        mma_tf32_acc(tacc, ad + kBoxDesc + 6, bd + b_chunk + 6, idesc_hi);
+        if (two) {
+          mma_tf32_acc(tacc, ad + kBoxDesc, bd + b_chunk, idesc_hi);
+          mma_tf32_acc(tacc, ad + kBoxDesc + 2, bd + b_chunk + 2, idesc_hi);
+          mma_tf32_acc(tacc, ad + kBoxDesc + 4, bd + b_chunk + 4, idesc_hi);
+          mma_tf32_acc(tacc, ad + kBoxDesc + 6, bd + b_chunk + 6, idesc_hi);
+        }
         if (!mpi_ptx::mbar_wait(&conv[s], r.ph, a.err, a.wait_cycles)) {
           ok = false;
           break;
@@ -272,10 +282,12 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
         mma_tf32_tmem_a(tacc, la + 8, bd + 2, idesc_lo);
         mma_tf32_tmem_a(tacc, la + 16, bd + 4, idesc_lo);
         mma_tf32_tmem_a(tacc, la + 24, bd + 6, idesc_lo);
-        mma_tf32_tmem_a(tacc, la + 32, bd + b_chunk, idesc_lo);
-        mma_tf32_tmem_a(tacc, la + 40, bd + b_chunk + 2, idesc_lo);
-        mma_tf32_tmem_a(tacc, la + 48, bd + b_chunk + 4, idesc_lo);
-        mma_tf32_tmem_a(tacc, la + 56, bd + b_chunk + 6, idesc_lo);
+        if (two) {
+          mma_tf32_tmem_a(tacc, la + 32, bd + b_chunk, idesc_lo);
+          mma_tf32_tmem_a(tacc, la + 40, bd + b_chunk + 2, idesc_lo);
+          mma_tf32_tmem_a(tacc, la + 48, bd + b_chunk + 4, idesc_lo);
+          mma_tf32_tmem_a(tacc, la + 56, bd + b_chunk + 6, idesc_lo);
+        }
         mma_commit(&empty[s]);  // frees the stage (tile and TMEM slot) once these MMAs have read it
         r.next(stages);
       }

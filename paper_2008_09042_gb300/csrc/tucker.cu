@@ -429,14 +429,15 @@ T* align256(void* p) {
 }
 
 // A 3xTF32 "basis" over an FP32 operand of `rows` rows of K = 2 q values
-// (real parts, then imaginary parts), read as round_up(K, 64) columns.
+// (real parts, then imaginary parts), read as round_up(K, 32) columns (whole
+// 32-value boxes; an odd box count ends each tile with a one-box stage).
 void operand_view(const mpi_basis* b, void* ptr, void* map, long rows, int q, mpi_basis* v) {
   v->ctx = b->ctx;
   v->device = b->device;
   v->N = (int)rows;
   v->q = q;
   v->Uf32 = (float*)ptr;
-  v->Kp32 = (2 * q + 63) / 64 * 64;
+  v->Kp32 = (2 * q + 31) / 32 * 32;
   v->tmap32 = map;
 }
 

@@ -428,7 +428,7 @@ bool plan_tf32(const mpi_basis* b, int mode, int C, TfPlan* p) {
 }  // namespace
 
 mpi_status tf32_basis_prepare(mpi_ctx* ctx, mpi_basis* b) {
-  const int Kp = round_up_i(2 * b->q, kKChunk32 * kBoxesPerStage);  // whole ring stages
+  const int Kp = round_up_i(2 * b->q, kKChunk32);  // whole 32-value boxes (an odd count ends a tile with a one-box stage)
   cudaError_t e = cudaMalloc(&b->Uf32, (size_t)b->N * Kp * sizeof(float));
   if (e != cudaSuccess) {
     cudaGetLastError();

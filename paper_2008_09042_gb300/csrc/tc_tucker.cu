@@ -352,6 +352,13 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
     constexpr int J1_PER = 8 / kNSub, K2_PER = (R + kNSub - 1) / kNSub;
     const int j1_lo = sub * J1_PER, k2_lo = sub * K2_PER, k2_hi = min(R, (sub + 1) * K2_PER);
     bool failed = false;
+    // adjoint: the per-coil data of the current j1, loaded one step ahead
+    float2 nxt[R];
+    if (MODE == kTxAdj && my_tiles > 0) {
+      const float2* wk0 = a.wk + (size_t)blockIdx.y * N1 * a.B + b;
+#pragma unroll
+      for (int j2 = 0; j2 < R; ++j2) nxt[j2] = wk0[(size_t)(j1_lo + 8 * j2) * a.B];
+    }
     for (int tc = 0; tc < my_tiles; ++tc) {
       const int c = (int)blockIdx.y + tc * (int)gridDim.y;
       const int buf = NACC == 2 ? (tc & 1) : 0;
@@ -445,10 +452,9 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
         // first half: conjugated inputs kz = j1 + 8 j2, R-point DFT, twiddle,
         // into the scratch columns j1 + 8 k2.  The next j1's loads are issued
         // before the current one is transformed.
+        // (The first j1's values were loaded before this tile: by the previous
+        // tile's last j1, or before the tile loop for the first tile.)
         const float2* wk = a.wk + (size_t)c * N1 * a.B + b;
-        float2 nxt[R];
-#pragma unroll
-        for (int j2 = 0; j2 < R; ++j2) nxt[j2] = wk[(size_t)(j1_lo + 8 * j2) * a.B];
         for (int j1 = j1_lo; j1 < j1_lo + J1_PER; ++j1) {
           float2 v[R];
 #pragma unroll
@@ -456,6 +462,11 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
           if (j1 + 1 < j1_lo + J1_PER) {
 #pragma unroll
             for (int j2 = 0; j2 < R; ++j2) nxt[j2] = wk[(size_t)(j1 + 1 + 8 * j2) * a.B];
+          } else if (tc + 1 < my_tiles) {
+            // the next tile's (coil's) first j1, in flight through this tile's stage 2
+            const float2* wn = wk + (size_t)gridDim.y * N1 * a.B;
+#pragma unroll
+            for (int j2 = 0; j2 < R; ++j2) nxt[j2] = wn[(size_t)(j1_lo + 8 * j2) * a.B];
           }
           dft_r<R>(v);
 #pragma unroll

@@ -127,6 +127,23 @@ __device__ __forceinline__ bool epi_bar_any(int flag, int n) {
   return out != 0;
 }
 
+// Barrier over the two epilogue warps of TMEM lane quarter `qd` (named barrier
+// 2 + qd, 64 threads), returning whether either passed `flag` != 0.  Those two
+// warps share the quarter's TMEM lanes (the DFT scratch columns) and nothing
+// else, so the adjoint synchronises them alone.
+__device__ __forceinline__ bool quarter_bar_any(int flag, int qd) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, 64, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"(flag), "r"(2 + qd)
+      : "memory");
+  return out != 0;
+}
+
 // Bring 256 bytes at `p` (256-byte aligned) into L2, asynchronously.
 __device__ __forceinline__ void l2_prefetch_256(const void* p) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(p) : "memory");
@@ -477,7 +494,7 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
         const bool got = mpi_ptx::mbar_wait(&acc_full[buf], par, a.err, a.wait_cycles);
-        if (epi_bar_any(!got, NT)) {
+        if (quarter_bar_any(!got, qd)) {  // the quarter's scratch is complete (or a wait ran out)
           failed = true;
           break;
         }
@@ -509,14 +526,15 @@ __global__ void __launch_bounds__(kTxThreads, 1) k_tucker_x1(const __grid_consta
         fence_before();
         __syncwarp();
         if (lane == 0) mpi_ptx::mbar_arrive(&acc_empty[buf]);
-        // the scratch columns are rewritten by the next tile's first stage
-        epi_bar_any(0, NT);
+        // the quarter's scratch columns are rewritten by the next tile's first stage
+        quarter_bar_any(0, qd);
         fence_after();
       }
     }
     if (failed) s_failed = 1;
-    if (MODE == kTxAdj && !failed && my_tiles > 0) {
-      epi_bar_any(0, NT);
+    // every epilogue thread arrives here, having finished its tiles or given up
+    // (the quarters decide separately), so the image is written only if none failed
+    if (MODE == kTxAdj && my_tiles > 0 && !epi_bar_any(failed, NT)) {
       // the coil sum of this position block: the image, with sign and scale
       for (int i = et; i < N1 * kTileM; i += NT) {
         const int z = i / kTileM, pos = i - z * kTileM;

@@ -202,7 +202,7 @@ inline cudaError_t launch_pdl(mpi_ctx* ctx, void (*kern)(KArgs...), dim3 grid, d
 
 // ------------------------------------------------------- expansion kernels
 
-enum ExpandMode { EX_MAPS = 0, EX_FWD = 1, EX_JFWD = 2, EX_ADJ = 3, EX_JADJ = 4, EX_SCATTER = 5 };
+enum ExpandMode { EX_MAPS = 0, EX_FWD = 1, EX_JFWD = 2, EX_ADJ = 3, EX_JADJ = 4, EX_SCATTER = 5, EX_SCATTER_ADD = 6 };
 
 // EX_SCATTER (3xTF32 kernel): the real and imaginary parts of output (row n,
 // column pair j) go to the FP32 array `out` at
@@ -254,6 +254,10 @@ struct ExpandArgs {
   const ExpandRow* rows = nullptr;
   int nrows = 0;
   int row_ctas = 0;
+  // 3xTF32 EX_SCATTER_ADD: split K into this many parts (grid rows, >= 2), each
+  // adding its partial products into `out` (scattered as EX_SCATTER), which the
+  // caller has zeroed
+  int ksplit = 0;
 };
 
 mpi_status launch_expand(mpi_ctx* ctx, int mode, const ExpandArgs& a);
@@ -271,6 +275,8 @@ void tc_basis_release(mpi_basis* b);
 // (grid rows), each row streaming the same basis tiles in step.
 mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& a, int group_coils = 0);
 bool tf32_supported(const mpi_basis* b, int mode, int C);
+// Whether the 3xTF32 scatter expansion of all C coils fits one launch with K split in `ksplit` parts.
+bool tf32_ksplit_supported(const mpi_basis* b, int mode, int C, int ksplit);
 // Measures how the tensor core reads an FP32 operand of kind::tf32 (one MMA on
 // the context's stream, synchronised); returns an MPI_TF32_READ_* value.
 int tf32_reading_probe(mpi_ctx* ctx);

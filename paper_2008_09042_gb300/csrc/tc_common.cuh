@@ -37,6 +37,11 @@ struct TcArgs {
   int sc_L0, sc_L1, sc_im, sc_col0;
   long sc_hi, sc_mid, sc_col;
   int sc_bf16;            // EX_SCATTER: BF16 outputs (same element offsets)
+  // K split (3xTF32 EX_SCATTER_ADD): grid row blockIdx.y takes K boxes
+  // [y KC, (y + 1) KC) of ksplit parts and adds its partial products into the
+  // (zeroed) output
+  int ksplit;
+  int k_off;              // global K index of the coefficient image's first column
   int accumulate;         // EX_FWD / EX_JFWD: add into out instead of storing
   const ExpandRow* rows;  // grouped launch: row blockIdx.y's pointers and coil count (nullptr: none)
   long long wait_cycles;  // bounded-wait limit (SM clock cycles)
@@ -206,7 +211,7 @@ static __device__ void build_coef_smem(const TcArgs& a, unsigned char* sB, int K
       float re[E], im[E];  // rows r0 and r0 + 1
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int k = k0 + e;
+        const int k = k0 + e + a.k_off;
         float2 al = make_float2(0.f, 0.f);
         if (k < 2 * a.q) al = src[k < a.q ? k : k - a.q];
         re[e] = k < a.q ? al.x : (k < 2 * a.q ? -al.y : 0.f);
@@ -272,7 +277,8 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
       const bool valid = n < a.N;
       const int nn = valid ? n : 0;
       const float sg = (a.centre ? centre_sign(nn, a.nx, a.ny) : 1.f) * a.scale;
-      const float2 pimg = (MODE != EX_MAPS && MODE != EX_SCATTER) ? a.p[nn] : make_float2(0.f, 0.f);
+      constexpr bool kScatter = MODE == EX_SCATTER || MODE == EX_SCATTER_ADD;
+      const float2 pimg = (MODE != EX_MAPS && !kScatter) ? a.p[nn] : make_float2(0.f, 0.f);
       // maps mode: where coil c of pixel n goes ([C][N], or the Tucker remap)
       size_t maps_base = (size_t)n, maps_cstride = (size_t)a.N;
       if (MODE == EX_MAPS && a.tuck_B) {
@@ -283,7 +289,7 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
       const float2 dpi = (MODE == EX_JFWD) ? a.dp[nn] : make_float2(0.f, 0.f);
       // scatter mode: this row's part of the output address
       size_t sc_base = 0;
-      if (MODE == EX_SCATTER) {
+      if (kScatter) {
         const int lo = nn % a.sc_L0, q1 = nn / a.sc_L0;
         sc_base = (size_t)(q1 / a.sc_L1) * a.sc_hi + (size_t)(q1 % a.sc_L1) * a.sc_mid + lo +
                   (size_t)a.sc_col0 * a.sc_col;
@@ -329,6 +335,15 @@ static __device__ __forceinline__ void tc_epilogue(const TcArgs& a, uint32_t tme
           const float2 s = make_float2(r[2 * i], r[2 * i + 1]);
           if (MODE == EX_MAPS) {
             if (cv) a.out[maps_base + (size_t)c * maps_cstride] = s;
+          } else if (MODE == EX_SCATTER_ADD) {
+            if (cv) {
+              // partial sums of the K parts: added into a zeroed output; with two
+              // parts (0 + a) + b = (0 + b) + a exactly, so the result does not
+              // depend on which part lands first
+              float* o = reinterpret_cast<float*>(a.out) + sc_base + (size_t)c * a.sc_col;
+              atomicAdd(o, s.x);
+              atomicAdd(o + a.sc_im, s.y);
+            }
           } else if (MODE == EX_SCATTER) {
             if (cv && a.sc_bf16) {
               __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(a.out) + sc_base + (size_t)c * a.sc_col;

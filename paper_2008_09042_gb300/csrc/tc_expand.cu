@@ -274,7 +274,7 @@ void tc_basis_release(mpi_basis* b) {
 mpi_status launch_expand_tc(mpi_ctx* ctx, const mpi_basis* b, int mode, const ExpandArgs& x) {
   if (!b->Ubf || !b->tmap) return set_err(ctx, MPI_ERR_UNSUPPORTED, "basis has no BF16 operand copy");
   if (x.N <= 0 || x.C <= 0) return MPI_OK;
-  TcArgs a;
+  TcArgs a{};  // every field not set below is zero (no K offset, no split)
   a.N = x.N;
   a.q = x.q;
   a.C = x.C;

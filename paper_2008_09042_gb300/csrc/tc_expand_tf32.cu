@@ -108,6 +108,12 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
     if (MODE == EX_SCATTER) a.sc_col0 = c0;
     else a.out += a.tuck_B ? (size_t)c0 * a.tuck_B : (size_t)c0 * a.N;
   }
+  // K split: this row's boxes start at box kc0 of the operand rows
+  int kc0 = 0;
+  if (MODE == EX_SCATTER_ADD) {
+    kc0 = (int)blockIdx.y * a.KC;
+    a.k_off = kc0 * kKChunk32;
+  }
   extern __shared__ unsigned char smem_raw[];
   // aligned by an offset from the shared array, so that accesses stay shared-memory ones
   unsigned char* smem = smem_raw + ((1024u - (mpi_ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -177,8 +183,8 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
       unsigned char* dst = sA + (size_t)r.s * kStageBytes32;
       const bool two = kc + 1 < a.KC;
       mpi_ptx::mbar_arrive_expect_tx(&full[r.s], two ? kStageBytes32 : kBoxBytes32);
-      tma_load_2d(dst, &tmap, kc * kKChunk32, t * kTileM, &full[r.s]);
-      if (two) tma_load_2d(dst + kBoxBytes32, &tmap, (kc + 1) * kKChunk32, t * kTileM, &full[r.s]);
+      tma_load_2d(dst, &tmap, (kc0 + kc) * kKChunk32, t * kTileM, &full[r.s]);
+      if (two) tma_load_2d(dst + kBoxBytes32, &tmap, (kc0 + kc + 1) * kKChunk32, t * kTileM, &full[r.s]);
       r.next(stages);
       kc += kBoxesPerStage;
       if (kc >= a.KC) {
@@ -401,7 +407,9 @@ struct TfPlan {
 
 constexpr int kMaxStages32 = 6;
 
-bool plan_tf32(const mpi_basis* b, int mode, int C, TfPlan* p) {
+// ksplit > 1: each CTA row takes 1/ksplit of the K boxes, so its coefficient
+// image covers that part of K only.
+bool plan_tf32(const mpi_basis* b, int mode, int C, TfPlan* p, int ksplit = 1) {
   const int cols = round_up_i(2 * C, 16);
   p->half = cols;
   p->n_gemm = mode == EX_JFWD ? 2 * cols : cols;
@@ -409,7 +417,7 @@ bool plan_tf32(const mpi_basis* b, int mode, int C, TfPlan* p) {
   int acc_cols = 32;
   while (acc_cols < 2 * p->n_gemm) acc_cols <<= 1;
   p->half_cols = acc_cols;
-  p->b_bytes = 2 * (size_t)p->n_gemm * b->Kp32 * 4;
+  p->b_bytes = 2 * (size_t)p->n_gemm * (b->Kp32 / ksplit) * 4;
   // alignment slack + the stacked coefficient image + 3 barriers per stage and 6 more + TMEM slot
   const size_t fixed = 1024 + ((p->b_bytes + 1023) & ~(size_t)1023) + 8 * (3 * kMaxStages32 + 6) + 16;
   if (fixed + 2 * (size_t)kStageBytes32 > kSmemMax) return false;
@@ -503,6 +511,13 @@ void tf32_basis_release(mpi_basis* b) {
   b->tmap32 = nullptr;
 }
 
+bool tf32_ksplit_supported(const mpi_basis* b, int mode, int C, int ksplit) {
+  TfPlan p;
+  if (!b->ctx || !b->ctx->tf32x3 || mode != EX_SCATTER_ADD || ksplit < 2 || (b->Kp32 / kKChunk32) % ksplit)
+    return false;
+  return b->Uf32 && b->tmap32 && plan_tf32(b, mode, C, &p, ksplit);
+}
+
 bool tf32_supported(const mpi_basis* b, int mode, int C) {
   TfPlan p;
   // the 3xTF32 split is exact only where the probe found the truncating reading
@@ -561,14 +576,18 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   TfPlan pl;
   const int Cg = group_coils > 0 ? std::min(group_coils, x.C) : x.C;  // coils per launch row
   const int groups = (x.C + Cg - 1) / Cg;
-  if (!b->Uf32 || !b->tmap32 || !plan_tf32(b, mode, Cg, &pl))
+  const int ks = mode == EX_SCATTER_ADD ? x.ksplit : 1;
+  if (mode == EX_SCATTER_ADD && (ks < 2 || groups > 1 || x.rows || (b->Kp32 / kKChunk32) % ks))
+    return set_err(ctx, MPI_ERR_ARG, "3xTF32 K split: two or more parts of whole boxes, one coil group");
+  if (!b->Uf32 || !b->tmap32 || !plan_tf32(b, mode, Cg, &pl, ks))
     return set_err(ctx, MPI_ERR_UNSUPPORTED, "3xTF32 expansion unavailable for this shape");
   if (x.N <= 0 || x.C <= 0) return MPI_OK;
-  TcArgs a;
+  TcArgs a{};  // every field not set below is zero (no K offset, no split)
   a.N = x.N;
   a.q = x.q;
   a.C = x.C;
-  a.KC = b->Kp32 / kKChunk32;
+  a.KC = b->Kp32 / kKChunk32 / ks;
+  a.ksplit = ks;
   a.half = pl.half;
   a.n_gemm = pl.n_gemm;
   a.half_cols = pl.half_cols;
@@ -604,8 +623,8 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   a.C_total = x.C;
   if (groups > 1) a.C = Cg;
   const int n_tiles = (x.N + kTileM - 1) / kTileM;
-  // one CTA per SM over all groups (or rows of a grouped launch)
-  const int nrows = x.rows ? x.nrows : groups;
+  // one CTA per SM over all groups (or rows of a grouped launch, or K parts)
+  const int nrows = x.rows ? x.nrows : (ks > 1 ? ks : groups);
   if (x.rows) a.group_coils = 0;
   const int per_row = x.rows && x.row_ctas > 0 ? x.row_ctas : std::max(std::max(ctx->num_sms, 1) / nrows, 1);
   const dim3 grid((unsigned)std::min(n_tiles, per_row), (unsigned)nrows);
@@ -625,6 +644,7 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
     MPI_TF_CASE(EX_ADJ)
     MPI_TF_CASE(EX_JADJ)
     MPI_TF_CASE(EX_SCATTER)
+    MPI_TF_CASE(EX_SCATTER_ADD)
     default:
       return set_err(ctx, MPI_ERR_ARG, "unknown expansion mode");
   }

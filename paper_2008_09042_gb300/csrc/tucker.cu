@@ -49,6 +49,19 @@ constexpr int kPB = 8;   // contracted elements loaded per batch
 constexpr int kMaxP = 256;  // longest contracted length of the CUDA-core mode products (factor length or rank)
 constexpr int kIB1 = 16; // outputs along i per thread of the CUDA-core x1 forward
 
+// Clears n floats at x (16-byte aligned), after the previous kernel in the
+// stream has completed (programmatic launch: the next kernel may start early
+// and waits for this one before its first dependent access).
+__global__ void k_zero_f32(float* __restrict__ x, size_t n) {
+  mpi_ptx::pdl_trigger();
+  mpi_ptx::pdl_wait();
+  const size_t n4 = n / 4, stride = (size_t)gridDim.x * blockDim.x;
+  float4* x4 = reinterpret_cast<float4*>(x);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
+    x4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (size_t i = 4 * n4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = 0.f;
+}
+
 // Y[r][i][b] = sum_p X[r][p][b] M(i, p), with M(i, p) = F[i][p] (forward, F is I x P)
 // or conj(F[p][i]) (adjoint, F is P x I).  Threads run along b (coalesced);
 // each thread keeps kIB outputs along i in registers; M is staged in shared
@@ -545,7 +558,22 @@ mpi_status tucker_chain_tc(mpi_ctx* ctx, const mpi_basis* b, const float2* alpha
   a.sc.s_col = R / r3 * 2L * r3;
   a.sc.im = r3;
   a.kname = bf ? "k_expand_tc<tucker core>" : "k_expand_tf32x3<tucker core>";
-  mpi_status st = expand(ctx, b->core, EX_SCATTER, a, bf ? MPI_PREC_BF16 : MPI_PREC_FP32);
+  mpi_status st;
+  if (!bf && tf32_ksplit_supported(b->core, EX_SCATTER_ADD, C, 2)) {
+    // all coils in one launch with K split in two (the real and the imaginary
+    // halves of the core rows), so the core streams through the SMs once: each
+    // half's CTAs add their partial products into g, cleared just before (both
+    // launches programmatic: the expansion streams the core while the clear
+    // runs, and its epilogue waits for the clear)
+    const size_t n = (size_t)C * R * 2;
+    MPI_PROF(ctx, KF_EXPAND);
+    launch_pdl(ctx, k_zero_f32, dim3((unsigned)std::max(1, 4 * ctx->num_sms)), dim3(256), 0, g, n);
+    MPI_LAUNCH_CHECK(ctx, "k_zero_f32");
+    a.ksplit = 2;
+    st = launch_expand_tf32(ctx, b->core, EX_SCATTER_ADD, a);
+  } else {
+    st = expand(ctx, b->core, EX_SCATTER, a, bf ? MPI_PREC_BF16 : MPI_PREC_FP32);
+  }
   if (st) return st;
   // x3: rows (c, a, b) with K = d, column pairs = x; out rows (c, x, a)
   // (these kernels stream operands written by the kernel before: plain stream order)

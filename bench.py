@@ -63,6 +63,9 @@ def parse():
                     help="only run --steps forward+adjoint pairs of this workload, untimed, for an external profiler")
     ap.add_argument("--profile-op", default="pair", choices=["pair", "jacobian"],
                     help="with --profile-workload: forward+adjoint pairs, or Jacobian + Jacobian-adjoint pairs")
+    ap.add_argument("--profile-coils", type=int, default=0,
+                    help="with --profile-workload: run only the first N coils (a smaller case of the same "
+                         "kernels for multi-pass profiler captures)")
     return ap.parse_args()
 
 
@@ -1002,6 +1005,8 @@ def profile_workload(args):
     else:
         case = make_case(name)
         plan, B, a, pd = gpu_objects(mp, ctx, dev, case)
+    if args.profile_coils > 0:
+        a = a[: args.profile_coils].contiguous()
     if args.profile_op == "jacobian":
         da = (0.5 * a).contiguous()
         dp = (0.25 * pd).contiguous()

@@ -132,7 +132,7 @@ struct mpi_basis {
   int Kp = 0;                    // padded K = round_up(2 q, 64)
   void* tmap = nullptr;          // CUtensorMap of Ubf (owned)
   float* Uf32 = nullptr;         // FP32 operand copy [N][Kp32] (3xTF32 tensor-core path)
-  int Kp32 = 0;                  // round_up(2 q, 32)
+  int Kp32 = 0;                  // padded K: round_up(2 q, 64) for a basis, round_up(2 q, 32) for a chain operand view
   void* tmap32 = nullptr;        // CUtensorMap of Uf32 (owned)
   // U^H V on the tensor cores (tc_uh.cu): tensor maps of the interleaved view
   // [q][2N] of U (FP32, in place) and of its BF16 copy Uview_bf

@@ -85,7 +85,9 @@ __device__ __forceinline__ void mma_tf32_tmem_a(uint32_t tmem_d, uint32_t tmem_a
 // double-buffered accumulator.  A stage holds two 32-element boxes (64 K
 // elements).  TMEM columns: [0, 2 half_cols) accumulators, then 64 columns of
 // lo(U) per stage.
-template <int MODE>
+// ODD: the K box count is odd, so the last ring stage of each tile holds one box
+// (a compile-time choice: with an even count the stage loop has no box test).
+template <int MODE, bool ODD = false>
 __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_constant__ CUtensorMap tmap, TcArgs a_in,
                                                                 int stages) {
   // Coil groups: the CTAs of row blockIdx.y expand their group's coils.  The
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
       if (a.stall_after >= 0 && g >= a.stall_after) break;
       if (!mpi_ptx::mbar_wait(&empty[r.s], r.ph ^ 1u, a.err, a.wait_cycles)) break;
       unsigned char* dst = sA + (size_t)r.s * kStageBytes32;
-      const bool two = kc + 1 < a.KC;
+      const bool two = !ODD || kc + 1 < a.KC;
       mpi_ptx::mbar_arrive_expect_tx(&full[r.s], two ? kStageBytes32 : kBoxBytes32);
       tma_load_2d(dst, &tmap, (kc0 + kc) * kKChunk32, t * kTileM, &full[r.s]);
       if (two) tma_load_2d(dst + kBoxBytes32, &tmap, (kc0 + kc + 1) * kKChunk32, t * kTileM, &full[r.s]);
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
         s_failed = 1;
         break;
       }
-      const int nb = kc + 1 < a.KC ? 2 : 1;
+      const int nb = (!ODD || kc + 1 < a.KC) ? 2 : 1;
 #pragma unroll
       for (int h = 0; h < kBoxesPerStage; ++h) {
         if (h >= nb) break;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kThreads32, 1) k_expand_tf32x3(const __grid_co
         const uint64_t ad = a0 + (uint32_t)(s * (kStageBytes32 >> 4));
         const uint64_t bd = b0 + (uint32_t)kc * b_chunk;
         constexpr uint32_t kBoxDesc = kBoxBytes32 >> 4;
-        const bool two = kc + 1 < a.KC;  // else this stage holds one box (the last of a tile, KC odd)
+        const bool two = !ODD || kc + 1 < a.KC;  // else this stage holds one box (the last of a tile, KC odd)
         mma_tf32(tacc, ad, bd, idesc_hi, kc != 0);
         mma_tf32_acc(tacc, ad + 2, bd + 2, idesc_hi);
         mma_tf32_acc(tacc, ad + 4, bd + 4, idesc_hi);
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(128, 1) k_tf32_reading(float* __restrict__ out
   unsigned char* sB = smem + kTileM * 128;   // 16 rows x 32 FP32
   uint64_t* done = reinterpret_cast<uint64_t*>(sB + 16 * 128);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   for (int k = 0; k < kKChunk32; ++k) {
     const float v = k == 0 ? __uint_as_float(tf32_probe_bits(tid)) : 0.f;
     *reinterpret_cast<float*>(sA + sw128_offset_e(tid, k, kTileM, 4)) = v;
@@ -436,7 +438,7 @@ bool plan_tf32(const mpi_basis* b, int mode, int C, TfPlan* p, int ksplit = 1) {
 }  // namespace
 
 mpi_status tf32_basis_prepare(mpi_ctx* ctx, mpi_basis* b) {
-  const int Kp = round_up_i(2 * b->q, kKChunk32);  // whole 32-value boxes (an odd count ends a tile with a one-box stage)
+  const int Kp = round_up_i(2 * b->q, kKChunk32 * kBoxesPerStage);  // whole ring stages (an even box count)
   cudaError_t e = cudaMalloc(&b->Uf32, (size_t)b->N * Kp * sizeof(float));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -630,25 +632,36 @@ mpi_status launch_expand_tf32(mpi_ctx* ctx, const mpi_basis* b, int mode, const 
   const dim3 grid((unsigned)std::min(n_tiles, per_row), (unsigned)nrows);
   const CUtensorMap& map = *(const CUtensorMap*)b->tmap32;
   cudaError_t e = cudaSuccess;
-#define MPI_TF_CASE(m)                                                                                        \
-  case m:                                                                                                     \
-    e = cudaFuncSetAttribute(k_expand_tf32x3<m>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);  \
+  // an odd K box count occurs only for the chain's operand views (whole-box
+  // padding); dense bases are padded to whole two-box stages
+  const bool odd = a.KC % 2 != 0;
+  if (odd && mode != EX_SCATTER && mode != EX_SCATTER_ADD)
+    return set_err(ctx, MPI_ERR_UNSUPPORTED, "3xTF32 expansion: odd K box count in this mode");
+#define MPI_TF_LAUNCH(m, o)                                                                                   \
+  do {                                                                                                        \
+    e = cudaFuncSetAttribute(k_expand_tf32x3<m, o>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem); \
     if (e != cudaSuccess) return cuda_check(ctx, e, "tf32 smem attribute");                                  \
     MPI_PROF(ctx, KF_EXPAND);                                                                                \
-    launch_pdl(ctx, k_expand_tf32x3<m>, grid, dim3(kThreads32), pl.smem, map, a, pl.stages);                          \
-    break;
+    launch_pdl(ctx, k_expand_tf32x3<m, o>, grid, dim3(kThreads32), pl.smem, map, a, pl.stages);            \
+  } while (0)
   switch (mode) {
-    MPI_TF_CASE(EX_MAPS)
-    MPI_TF_CASE(EX_FWD)
-    MPI_TF_CASE(EX_JFWD)
-    MPI_TF_CASE(EX_ADJ)
-    MPI_TF_CASE(EX_JADJ)
-    MPI_TF_CASE(EX_SCATTER)
-    MPI_TF_CASE(EX_SCATTER_ADD)
+    case EX_MAPS: MPI_TF_LAUNCH(EX_MAPS, false); break;
+    case EX_FWD: MPI_TF_LAUNCH(EX_FWD, false); break;
+    case EX_JFWD: MPI_TF_LAUNCH(EX_JFWD, false); break;
+    case EX_ADJ: MPI_TF_LAUNCH(EX_ADJ, false); break;
+    case EX_JADJ: MPI_TF_LAUNCH(EX_JADJ, false); break;
+    case EX_SCATTER:
+      if (odd) MPI_TF_LAUNCH(EX_SCATTER, true);
+      else MPI_TF_LAUNCH(EX_SCATTER, false);
+      break;
+    case EX_SCATTER_ADD:
+      if (odd) MPI_TF_LAUNCH(EX_SCATTER_ADD, true);
+      else MPI_TF_LAUNCH(EX_SCATTER_ADD, false);
+      break;
     default:
       return set_err(ctx, MPI_ERR_ARG, "unknown expansion mode");
   }
-#undef MPI_TF_CASE
+#undef MPI_TF_LAUNCH
   MPI_LAUNCH_CHECK(ctx, x.kname ? x.kname : "k_expand_tf32x3");
   return MPI_OK;
 }

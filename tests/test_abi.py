@@ -43,6 +43,11 @@ def test_null_context_is_rejected_without_gpu(lib):
     assert lib.mpi_ctx_create(None, 0, None) == 1  # MPI_ERR_ARG
     assert lib.mpi_forward(None, None, None, None, 1, None, None, 0) == 1
     assert lib.mpi_last_error(None) == b"null context"
+    # context settings and queries take a null context without touching a device
+    assert lib.mpi_ctx_tf32_reading(None) == -1
+    assert lib.mpi_ctx_set_tf32x3(None, 0) == 1
+    assert lib.mpi_ctx_set_wait_limit(None, 10**6) == 1
+    assert lib.mpi_ctx_workspace_bytes(None) == -1
     # no device here: creating a context reports a CUDA error instead of faulting
     h = ctypes.c_void_p()
     st = lib.mpi_ctx_create(ctypes.byref(h), 0, None)

@@ -16,8 +16,9 @@
 //  - U_hi against the stacked rows [A_hi; A_lo] (N = 2 n), which writes U_hi A_hi
 //    and U_hi A_lo into two column blocks that the epilogue adds.  U_hi is the
 //    raw FP32 tile: the tensor core reads an FP32 operand of kind::tf32 as its
-//    upper 19 bits, which is hi(x) exactly (measured on sm_103a; any other
-//    reading fails the FP32 parity tests).
+//    upper 19 bits, which is hi(x) exactly.  Each context measures that reading
+//    when it is made (k_tf32_reading below) and runs these kernels only where
+//    it holds.
 //  - U_lo against A_hi (N = n) into the first block, with U_lo taken from tensor
 //    memory: four converter warps read each landed tile from shared memory and
 //    store lo(x) with tcgen05.st into a TMEM slot of the stage, so the split
@@ -25,6 +26,10 @@
 // A tcgen05.mma costs about the same to issue for any N up to 64, so stacking
 // the coefficient rows saves a third of the instructions.  The stacked
 // coefficient image is built once per call.  Every mbarrier wait is bounded.
+// Operands whose K box count is odd end each tile with a one-box stage (a
+// compile-time variant).  EX_SCATTER_ADD splits K over the grid rows: each
+// row's coefficient image covers its part of K, and its partial products are
+// added into the output, which the caller has cleared.
 #include <cuda.h>
 
 #include <algorithm>

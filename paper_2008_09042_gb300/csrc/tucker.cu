@@ -13,10 +13,14 @@
 // reverse order followed by the core's U^H V contraction.  FP32: the whole
 // chain, and the Jacobian-adjoint's conjugate chain, on the 3xTF32 tensor-core
 // kernel, each product written by its scatter epilogue in the K-major rows the
-// next one streams (tucker_chain_tc, tucker_jadj_alpha); the x1 product fused
-// with the operator steps around it (tc_tucker.cu).  BF16 and the shapes those
-// kernels do not take: the x3 and x2 products (and the conjugate ones) as FP32
-// complex on the CUDA cores (k_mode_last, k_mode_b), the x1 product on the
+// next one streams (tucker_chain_tc, tucker_jadj_alpha); the core contraction
+// over all coils in one launch with K split in two, its halves adding their
+// partial products into the cleared g; the x1 product fused with the operator
+// steps around it (tc_tucker.cu).  BF16: the same chain with the core
+// contraction on the BF16 kernel and the x1 operand written as BF16 rows.  The
+// shapes those kernels do not take, and FP32 where the 3xTF32 kernels are off:
+// the x3 and x2 products (and the conjugate ones) as FP32 complex on the CUDA
+// cores (k_mode_last, k_mode_b), the x1 product on the
 // tensor-core expansion kernels (over all coils a dense expansion whose basis
 // rows are the positions (c, y, x) of T2 with K = r1 and whose coefficient rows
 // are the rows of U1) or, forward only, on the CUDA cores fused with the
